@@ -1,0 +1,199 @@
+/*
+ * ddgs.h -- C ABI of the GB300 (sm_103a) DDGS-CT DRR splatting library.
+ *
+ * Renders a digitally reconstructed radiograph (DRR) from a cloud of 3D
+ * Gaussians (DDGS-CT, Sec. 3.1-3.2 and Appendix A) and differentiates it with
+ * respect to every Gaussian parameter, the shared radiosity bases and the
+ * per-view source/detector pose (Sec. 3.1 "differentiable", Sec. 4.3 pose
+ * registration).
+ *
+ * Conventions
+ *   - All array pointers in the structs and calls are DEVICE pointers
+ *     (cudaMalloc / torch CUDA tensors) unless a comment says "host". They are
+ *     owned by the caller and must stay valid until the stream reaches the
+ *     end of the call's work. The library owns only a workspace.
+ *   - Every call is asynchronous on the given stream (a cudaStream_t passed as
+ *     void*; NULL = legacy default stream) unless stated otherwise.
+ *   - No call aborts, throws or prints. Each returns a ddgs_status. Errors
+ *     found while kernels run (capacity overflow in the no-sync mode) are
+ *     latched in the workspace and returned by ddgs_sync_status().
+ *   - Feature dimension k = 8 and harmonic degree L = 1 (k_L = L(L+2) = 3),
+ *     the paper's evaluation setting (Sec. 4.1).
+ *
+ * Geometry (the paper fixes cone-beam X-ray imaging but not its
+ * parameterisation; this is the library's reading). The X-ray source is the
+ * camera origin; the pose [R | t] maps world to camera coordinates; the
+ * detector is the plane z = sdd with pixel pitch (pitch_u, pitch_v); pixel
+ * (row i, col j) has centre (j + 1/2, i + 1/2) in pixel units; the principal
+ * point is (W/2 + off_u, H/2 + off_v).
+ */
+#ifndef DDGS_H
+#define DDGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DDGS_FEAT_DIM 8   /* k: features per Gaussian (Sec. 4.1) */
+#define DDGS_SH_DIM 3     /* k_L = L(L+2) at L = 1 (Sec. 3.2, after Eq. 3) */
+
+typedef enum {
+  DDGS_OK = 0,
+  DDGS_ERR_INVALID_ARG = 1,   /* a null pointer, negative size, bad tile ... */
+  DDGS_ERR_CAPACITY = 2,      /* no-sync mode: pairs exceeded the reserved capacity */
+  DDGS_ERR_NONFINITE = 3,     /* reserved */
+  DDGS_ERR_TIMEOUT = 4,       /* a bounded device wait gave up */
+  DDGS_ERR_CUDA = 5,          /* a CUDA runtime call failed (see ddgs_last_cuda_error) */
+  DDGS_ERR_UNSUPPORTED = 6,   /* e.g. no sm_103 device */
+  DDGS_ERR_OUT_OF_MEMORY = 7  /* workspace growth failed */
+} ddgs_status;
+
+/* A cloud of n Gaussians g_i = {mu_i, Sigma_i, alpha_i, f_i} (Sec. 3.1).
+ * Sigma_i = R(q_i) diag(exp(log_s_i))^2 R(q_i)^T; alpha_i = sigmoid(logit_i).
+ * Gaussians [0, n_iso) are isotropic, [n_iso, n) direction-dependent; the two
+ * sets are distinct Gaussians (Sec. 3.2, Eq. 3) rendered jointly (App. A.2). */
+typedef struct {
+  int64_t n;
+  int64_t n_iso;
+  const float *means;          /* [n][3] world coordinates */
+  const float *log_scales;     /* [n][3] */
+  const float *quats;          /* [n][4] (w, x, y, z), any non-zero norm */
+  const float *opacity_logits; /* [n] */
+  const float *feat_iso;       /* [n_iso][8] f_iso (Eq. 3); may be NULL if n_iso == 0 */
+  const void *feat_dir;        /* [n - n_iso][8] f_dir (Eq. 3); float32 or bfloat16 */
+  int32_t feat_dir_bf16;       /* 0: feat_dir is float32, 1: bfloat16 */
+  const float *b_iso;          /* [8] shared isotropic basis b_iso (Eq. 3) */
+  const float *B_dir;          /* [3][8] shared direction basis B_dir (Eq. 3), row-major */
+} ddgs_gaussians;
+
+/* n_views cone-beam views sharing one detector size. */
+typedef struct {
+  int32_t n_views;
+  int32_t height, width;       /* detector pixels (rows, columns); host values */
+  const float *world_to_cam;   /* [n_views][3][4] rigid pose (R | t), row-major */
+  const float *detector;       /* [n_views][5]: sdd, pitch_u, pitch_v, off_u, off_v */
+} ddgs_views;
+
+/* Cutoffs and tiling. The paper states none of them (Eq. 1 sums over all
+ * Gaussians); these are the usual 3D Gaussian splatting choices. */
+typedef struct {
+  int32_t tile;      /* tile edge in pixels: 8, 16 or 32 */
+  float dilation;    /* added to the 2D covariance diagonal, pixels^2 (e.g. 0.3) */
+  float near_plane;  /* Gaussians with camera z <= near_plane are culled; z >= sdd too */
+  float alpha_min;   /* sigma below this is skipped (e.g. 1/255) */
+  float alpha_max;   /* sigma = min(alpha_max, alpha G) (e.g. 0.99) */
+  float t_min;       /* the walk stops before T would drop below this (e.g. 1e-4) */
+  float q_max;       /* Mahalanobis cutoff q <= q_max (e.g. 9) */
+  int32_t no_sync;   /* 0: a render may synchronise the stream once to size the
+                        workspace; 1: never synchronise (CUDA-graph capture):
+                        capacities come from ddgs_workspace_reserve and an
+                        overflow is latched as DDGS_ERR_CAPACITY */
+} ddgs_config;
+
+/* Gradient outputs of ddgs_render_backward. Every pointer may be NULL (that
+ * gradient is skipped). Layouts equal the inputs', always float32; outputs
+ * are overwritten, not accumulated. */
+typedef struct {
+  float *means, *log_scales, *quats, *opacity_logits;
+  float *feat_iso, *feat_dir;
+  float *b_iso, *B_dir;
+  float *world_to_cam;         /* [n_views][3][4]: dL/d(pose entries) */
+} ddgs_grads;
+
+typedef struct ddgs_workspace ddgs_workspace;
+
+/* Workspace: per-(view, Gaussian) projections, sort buffers, tile ranges and
+ * the device status word, on the device that is current at creation. Owned by
+ * the library between create and destroy. One workspace serves one render at
+ * a time; ddgs_render_backward reads what the preceding ddgs_render left. */
+ddgs_status ddgs_workspace_create(ddgs_workspace **ws);
+ddgs_status ddgs_workspace_destroy(ddgs_workspace *ws);
+
+/* Grow the workspace so that renders of up to `records` (= views x
+ * Gaussians), `pairs` (Gaussian-tile overlaps) and `tiles` (= views x tiles
+ * per view) never reallocate. Synchronises the device. Required before
+ * no_sync renders. */
+ddgs_status ddgs_workspace_reserve(ddgs_workspace *ws, int64_t records,
+                                   int64_t pairs, int64_t tiles);
+
+/* Forward rendering, Eq. 1 of the paper with the radiosity of Eq. 3:
+ *   C(p) = sum_j c_j sigma_j prod_{l<j} (1 - sigma_l),
+ *   sigma_j = min(alpha_max, alpha_j exp(-q_j / 2)),
+ *   q_j = (p - mu-hat_j)^T Sigma-hat_j^-1 (p - mu-hat_j),
+ * over the Gaussians whose q <= q_max and sigma >= alpha_min, in ascending
+ * camera depth of their means (ties: ascending index), isotropic and
+ * direction-dependent Gaussians in one list (App. A.2), stopping before the
+ * transmittance would drop below t_min. mu-hat, Sigma-hat are the perspective
+ * projection of the mean and the Jacobian projection of Sigma (+ dilation).
+ * Radiosity (Eq. 3): c = sigmoid(b_iso . f) for isotropic Gaussians and
+ * c = sigmoid(Y_1(d) . B_dir f) for direction-dependent ones, with d the unit
+ * direction from the source to the mean in world coordinates and
+ * Y_1(d) = sqrt(3/(4 pi)) (-d_y, d_z, -d_x).
+ * Outputs (device, [n_views][height][width], overwritten):
+ *   image   C(p) (background 0, no log transform; App. A.1)
+ *   t_final transmittance after the last Gaussian added
+ *   n_last  1 + position, in the pixel's tile list, of the last Gaussian
+ *           added (0 if none); needed by the backward pass.
+ * Synchronises the stream once (to size the sort) unless cfg->no_sync. */
+ddgs_status ddgs_render(const ddgs_gaussians *g, const ddgs_views *v,
+                        const ddgs_config *cfg, ddgs_workspace *ws,
+                        float *image, float *t_final, uint32_t *n_last,
+                        void *stream);
+
+/* Backward pass of ddgs_render (Sec. 3.1: the rasterisation is
+ * differentiable; Sec. 4.3: back-propagation to the pose). Given dL/dC
+ * ([n_views][height][width]) and the t_final / n_last of the forward call,
+ * writes dL/d(every input) into the non-NULL fields of *out. The blending
+ * state is recomputed from the sorted lists, walking each pixel back to front
+ * (T_before = T_after / (1 - sigma)). Must follow the ddgs_render that filled
+ * ws, with the same g, v and cfg. */
+ddgs_status ddgs_render_backward(const ddgs_gaussians *g, const ddgs_views *v,
+                                 const ddgs_config *cfg, ddgs_workspace *ws,
+                                 const float *dL_dimage, const float *t_final,
+                                 const uint32_t *n_last, const ddgs_grads *out,
+                                 void *stream);
+
+/* Per-view mean L1 loss of the registration objective (Sec. 4.3 compares the
+ * rendering at a predicted pose with the target image; the l1 term of Eq. 2)
+ * and its gradient. image [n_views][hw]; target [hw] (shared by all views)
+ * or [n_views][hw] (target_per_view = 1). Writes loss [n_views] and
+ * dL_dimage [n_views][hw] = sign(image - target) / hw. */
+ddgs_status ddgs_l1_loss(const float *image, const float *target,
+                         int32_t target_per_view, int32_t n_views, int64_t hw,
+                         float *loss, float *dL_dimage, void *stream);
+
+/* Number of (Gaussian, tile) pairs of the last render, read from the host
+ * mirror written by that render (valid after the stream has synchronised). */
+ddgs_status ddgs_workspace_pairs(const ddgs_workspace *ws, int64_t *pairs);
+
+/* Copy the binning of the last render into caller buffers (device):
+ * tiles_touched [n_views][n], keys [pairs] ((global tile << 32) | depth bits,
+ * global tile = view * tiles_per_view + row * tiles_x + col), vals [pairs]
+ * (Gaussian index), ranges [n_views * tiles_per_view][2] ([start, end),
+ * (0, 0) when empty). Any pointer may be NULL. */
+ddgs_status ddgs_debug_binning(const ddgs_workspace *ws, uint32_t *tiles_touched,
+                               uint64_t *keys, uint32_t *vals, uint32_t *ranges,
+                               void *stream);
+
+/* Synchronise the stream, then return and clear the status latched by
+ * kernels since the last call (DDGS_OK, DDGS_ERR_CAPACITY, DDGS_ERR_TIMEOUT). */
+ddgs_status ddgs_sync_status(ddgs_workspace *ws, void *stream);
+
+/* Floats of a cloud: n * (3 + 4 + 3 + 1 + k) + k + k_L * k, i.e. 19 per
+ * Gaussian and a 32-float shared basis at k = 8, L = 1 (Sec. 4.2). Host only. */
+int64_t ddgs_parameter_count(int64_t n, int32_t k, int32_t L);
+
+/* Human-readable name of a status; the last CUDA error string. Host only. */
+const char *ddgs_status_string(ddgs_status s);
+const char *ddgs_last_cuda_error(void);
+
+/* 1 if a device of compute capability 10.3 is current and usable. Host only. */
+int32_t ddgs_device_supported(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DDGS_H */

@@ -1,0 +1,396 @@
+// api.cu -- the C ABI: argument checks, workspace management and the order of
+// the kernels of a render and of its backward pass.
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "ddgs_internal.cuh"
+
+namespace {
+
+thread_local char g_cuda_err[256] = "";
+
+ddgs_status cuda_fail(cudaError_t e, const char *what) {
+  std::snprintf(g_cuda_err, sizeof g_cuda_err, "%s: %s", what, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? DDGS_ERR_OUT_OF_MEMORY : DDGS_ERR_CUDA;
+}
+
+#define CK(call)                                         \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+  } while (0)
+
+template <class Tp>
+ddgs_status grow(Tp *&p, int64_t &cap_field, int64_t need, int64_t cur_cap, size_t elem) {
+  (void)cap_field;
+  if (need <= cur_cap && p) return DDGS_OK;
+  if (p) CK(cudaFree(p));
+  p = nullptr;
+  CK(cudaMalloc(reinterpret_cast<void **>(&p), (size_t)(need > 0 ? need : 1) * elem));
+  return DDGS_OK;
+}
+
+int bits_for(uint64_t x) {  // bits needed to represent values 0..x
+  int b = 0;
+  while (x) { ++b; x >>= 1; }
+  return b;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+ddgs_status check_inputs(const ddgs_gaussians *g, const ddgs_views *v, const ddgs_config *c) {
+  if (!g || !v || !c) return DDGS_ERR_INVALID_ARG;
+  if (g->n < 0 || g->n_iso < 0 || g->n_iso > g->n || g->n >= (int64_t(1) << 31))
+    return DDGS_ERR_INVALID_ARG;
+  if (v->n_views < 0 || v->height <= 0 || v->width <= 0 || v->height > 65535 * 8 ||
+      v->width > 65535 * 8)
+    return DDGS_ERR_INVALID_ARG;
+  if (c->tile != 8 && c->tile != 16 && c->tile != 32) return DDGS_ERR_INVALID_ARG;
+  if (!(c->q_max > 0) || !(c->alpha_max > 0) || !(c->t_min >= 0) || !(c->dilation >= 0))
+    return DDGS_ERR_INVALID_ARG;
+  if (g->n > 0) {
+    if (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->b_iso || !g->B_dir)
+      return DDGS_ERR_INVALID_ARG;
+    if (!aligned16(g->quats)) return DDGS_ERR_INVALID_ARG;
+    if (g->n_iso > 0 && (!g->feat_iso || !aligned16(g->feat_iso))) return DDGS_ERR_INVALID_ARG;
+    if (g->n > g->n_iso && (!g->feat_dir || !aligned16(g->feat_dir))) return DDGS_ERR_INVALID_ARG;
+  }
+  if (v->n_views > 0 && (!v->world_to_cam || !v->detector)) return DDGS_ERR_INVALID_ARG;
+  return DDGS_OK;
+}
+
+ddgs::RenderShape make_shape(const ddgs_gaussians *g, const ddgs_views *v, const ddgs_config *c) {
+  ddgs::RenderShape s{};
+  s.n = g->n;
+  s.n_iso = g->n_iso;
+  s.V = v->n_views;
+  s.H = v->height;
+  s.W = v->width;
+  s.tile = c->tile;
+  s.tiles_x = (v->width + c->tile - 1) / c->tile;
+  s.tiles_y = (v->height + c->tile - 1) / c->tile;
+  s.tiles_per_view = (int64_t)s.tiles_x * s.tiles_y;
+  s.total_tiles = s.tiles_per_view * s.V;
+  s.records = (int64_t)s.V * s.n;
+  s.key_bits = 32 + bits_for(s.total_tiles > 0 ? (uint64_t)(s.total_tiles - 1) : 0);
+  return s;
+}
+
+ddgs_status ensure_records(ddgs_workspace *ws, const ddgs::RenderShape &s) {
+  const int64_t blk = ddgs::preprocess_blocks(s);
+  if (s.records > ws->rec_cap || !ws->rec0) {
+    int64_t cap = s.records + s.records / 4 + 1024;
+    ddgs_status st;
+    if ((st = grow(ws->rec0, ws->rec_cap, cap, 0, sizeof(float4)))) return st;
+    if ((st = grow(ws->rec1, ws->rec_cap, cap, 0, sizeof(float4)))) return st;
+    if ((st = grow(ws->rect, ws->rec_cap, cap, 0, sizeof(uint4)))) return st;
+    if ((st = grow(ws->grad2d, ws->rec_cap, 2 * cap, 0, sizeof(float4)))) return st;
+    ws->rec_cap = cap;
+  }
+  if (blk > ws->blk_cap || !ws->blk_total) {
+    int64_t cap = blk + blk / 4 + 64;
+    ddgs_status st;
+    if ((st = grow(ws->blk_total, ws->blk_cap, cap, 0, sizeof(uint32_t)))) return st;
+    if ((st = grow(ws->blk_offset, ws->blk_cap, cap, 0, sizeof(uint64_t)))) return st;
+    ws->blk_cap = cap;
+  }
+  if (s.total_tiles > ws->tile_cap || !ws->ranges) {
+    int64_t cap = s.total_tiles + s.total_tiles / 4 + 64;
+    ddgs_status st;
+    if ((st = grow(ws->ranges, ws->tile_cap, cap, 0, sizeof(uint2)))) return st;
+    ws->tile_cap = cap;
+  }
+  return DDGS_OK;
+}
+
+ddgs_status ensure_pairs(ddgs_workspace *ws, int64_t pairs) {
+  if (pairs <= ws->pair_cap && ws->keys[0]) return DDGS_OK;
+  int64_t cap = pairs + pairs / 4 + 4096;
+  ddgs_status st;
+  for (int b = 0; b < 2; ++b) {
+    if ((st = grow(ws->keys[b], ws->pair_cap, cap, 0, sizeof(uint64_t)))) return st;
+    if ((st = grow(ws->vals[b], ws->pair_cap, cap, 0, sizeof(uint32_t)))) return st;
+  }
+  const int64_t sb = ddgs::sort_blocks((uint64_t)cap);
+  if ((st = grow(ws->hist, ws->sblk_cap, sb * ddgs::RADIX, 0, sizeof(uint32_t)))) return st;
+  ws->sblk_cap = sb;
+  ws->pair_cap = cap;
+  return DDGS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ddgs_status_string(ddgs_status s) {
+  switch (s) {
+    case DDGS_OK: return "ok";
+    case DDGS_ERR_INVALID_ARG: return "invalid argument";
+    case DDGS_ERR_CAPACITY: return "pair capacity exceeded";
+    case DDGS_ERR_NONFINITE: return "non-finite value";
+    case DDGS_ERR_TIMEOUT: return "device wait timed out";
+    case DDGS_ERR_CUDA: return "CUDA error";
+    case DDGS_ERR_UNSUPPORTED: return "unsupported device";
+    case DDGS_ERR_OUT_OF_MEMORY: return "out of device memory";
+  }
+  return "unknown status";
+}
+
+const char *ddgs_last_cuda_error(void) { return g_cuda_err; }
+
+int64_t ddgs_parameter_count(int64_t n, int32_t k, int32_t L) {
+  if (n < 0 || k < 0 || L < 0) return -1;
+  const int64_t kl = (int64_t)L * (L + 2);
+  return n * (3 + 4 + 3 + 1 + (int64_t)k) + k + kl * k;
+}
+
+int32_t ddgs_device_supported(void) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  cudaDeviceProp p;
+  if (cudaGetDeviceProperties(&p, dev) != cudaSuccess) return 0;
+  return (p.major == 10 && p.minor == 3) ? 1 : 0;
+}
+
+ddgs_status ddgs_workspace_create(ddgs_workspace **out) {
+  if (!out) return DDGS_ERR_INVALID_ARG;
+  *out = nullptr;
+  ddgs_workspace *ws = new (std::nothrow) ddgs_workspace();
+  if (!ws) return DDGS_ERR_OUT_OF_MEMORY;
+  cudaError_t e;
+  if ((e = cudaGetDevice(&ws->device)) != cudaSuccess ||
+      (e = cudaMalloc(&ws->d_pairs, sizeof(uint64_t))) != cudaSuccess ||
+      (e = cudaMalloc(&ws->d_status, sizeof(int32_t))) != cudaSuccess ||
+      (e = cudaMalloc(&ws->digit_total, ddgs::RADIX * sizeof(uint32_t))) != cudaSuccess ||
+      (e = cudaHostAlloc(&ws->h_pairs, sizeof(uint64_t), cudaHostAllocDefault)) != cudaSuccess ||
+      (e = cudaMemset(ws->d_status, 0, sizeof(int32_t))) != cudaSuccess ||
+      (e = cudaMemset(ws->d_pairs, 0, sizeof(uint64_t))) != cudaSuccess) {
+    ddgs_status st = cuda_fail(e, "workspace create");
+    ddgs_workspace_destroy(ws);
+    return st;
+  }
+  *ws->h_pairs = 0;
+  *out = ws;
+  return DDGS_OK;
+}
+
+ddgs_status ddgs_workspace_destroy(ddgs_workspace *ws) {
+  if (!ws) return DDGS_OK;
+  void *dev[] = {ws->rec0, ws->rec1, ws->rect, ws->tiles_touched, ws->grad2d, ws->blk_total,
+                 ws->blk_offset, ws->keys[0], ws->keys[1], ws->vals[0], ws->vals[1], ws->hist,
+                 ws->digit_total, ws->ranges, ws->d_pairs, ws->d_status};
+  for (void *p : dev)
+    if (p) cudaFree(p);
+  if (ws->h_pairs) cudaFreeHost(ws->h_pairs);
+  delete ws;
+  return DDGS_OK;
+}
+
+ddgs_status ddgs_workspace_reserve(ddgs_workspace *ws, int64_t records, int64_t pairs,
+                                   int64_t tiles) {
+  if (!ws || records < 0 || pairs < 0 || tiles < 0) return DDGS_ERR_INVALID_ARG;
+  CK(cudaDeviceSynchronize());
+  ddgs::RenderShape s{};
+  s.records = records;
+  s.n = records;  // bounds the preprocess block count for any split into views
+  s.total_tiles = tiles;
+  ddgs_status st = ensure_records(ws, s);
+  if (st) return st;
+  st = ensure_pairs(ws, pairs);
+  if (st) return st;
+  CK(cudaDeviceSynchronize());
+  return DDGS_OK;
+}
+
+ddgs_status ddgs_render(const ddgs_gaussians *g, const ddgs_views *v, const ddgs_config *c,
+                        ddgs_workspace *ws, float *image, float *t_final, uint32_t *n_last,
+                        void *stream) {
+  ddgs_status st = check_inputs(g, v, c);
+  if (st) return st;
+  if (!ws) return DDGS_ERR_INVALID_ARG;
+  if (v->n_views > 0 && (!image || !t_final || !n_last)) return DDGS_ERR_INVALID_ARG;
+  cudaStream_t s_ = static_cast<cudaStream_t>(stream);
+  const ddgs::RenderShape s = make_shape(g, v, c);
+  if (c->no_sync) {
+    if (s.records > ws->rec_cap || ddgs::preprocess_blocks(s) > ws->blk_cap ||
+        s.total_tiles > ws->tile_cap || !ws->keys[0])
+      return DDGS_ERR_CAPACITY;
+  } else if ((st = ensure_records(ws, s))) {
+    return st;
+  }
+  ws->have_render = false;
+  const int64_t nblk = ddgs::preprocess_blocks(s);
+  uint64_t bound = 0;
+  if (s.records > 0) {
+    ddgs::launch_preprocess_fwd(*g, *v, *c, s, *ws, s_);
+    CK(cudaGetLastError());
+    ddgs::launch_scan_blocks(nblk, *ws, s_);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(ws->h_pairs, ws->d_pairs, sizeof(uint64_t), cudaMemcpyDeviceToHost, s_));
+    if (!c->no_sync) {
+      CK(cudaStreamSynchronize(s_));
+      bound = *ws->h_pairs;
+      if (bound >= (uint64_t(1) << 32) - 1) return DDGS_ERR_CAPACITY;
+      if ((st = ensure_pairs(ws, (int64_t)bound))) return st;
+    } else {
+      bound = (uint64_t)ws->pair_cap;
+    }
+    if (bound > 0) {
+      ddgs::launch_emit_keys(s, *ws, s_);
+      CK(cudaGetLastError());
+      ddgs::launch_radix_sort(s, bound, *ws, s_);
+      CK(cudaGetLastError());
+    }
+  } else {
+    *ws->h_pairs = 0;
+    CK(cudaMemsetAsync(ws->d_pairs, 0, sizeof(uint64_t), s_));
+  }
+  if (s.total_tiles > 0) {
+    ddgs::launch_tile_ranges(s, bound, *ws, s_);
+    CK(cudaGetLastError());
+    ddgs::RasterParams P{c->alpha_min, c->alpha_max, c->t_min, c->q_max};
+    ddgs::launch_raster_fwd(s, P, *ws, image, t_final, n_last, s_);
+    CK(cudaGetLastError());
+  }
+  ws->shape = s;
+  ws->pair_bound = bound;
+  ws->have_render = true;
+  return DDGS_OK;
+}
+
+ddgs_status ddgs_render_backward(const ddgs_gaussians *g, const ddgs_views *v,
+                                 const ddgs_config *c, ddgs_workspace *ws,
+                                 const float *dL_dimage, const float *t_final,
+                                 const uint32_t *n_last, const ddgs_grads *out, void *stream) {
+  ddgs_status st = check_inputs(g, v, c);
+  if (st) return st;
+  if (!ws || !out || !ws->have_render) return DDGS_ERR_INVALID_ARG;
+  const ddgs::RenderShape s = make_shape(g, v, c);
+  if (s.n != ws->shape.n || s.V != ws->shape.V || s.H != ws->shape.H || s.W != ws->shape.W ||
+      s.tile != ws->shape.tile)
+    return DDGS_ERR_INVALID_ARG;
+  if (s.total_tiles > 0 && (!dL_dimage || !t_final || !n_last)) return DDGS_ERR_INVALID_ARG;
+  if ((out->quats && !aligned16(out->quats)) || (out->feat_iso && !aligned16(out->feat_iso)) ||
+      (out->feat_dir && !aligned16(out->feat_dir)))
+    return DDGS_ERR_INVALID_ARG;
+  cudaStream_t s_ = static_cast<cudaStream_t>(stream);
+  if (out->b_iso) CK(cudaMemsetAsync(out->b_iso, 0, ddgs::K * sizeof(float), s_));
+  if (out->B_dir) CK(cudaMemsetAsync(out->B_dir, 0, 3 * ddgs::K * sizeof(float), s_));
+  if (out->world_to_cam) CK(cudaMemsetAsync(out->world_to_cam, 0, (size_t)s.V * 12 * sizeof(float), s_));
+  if (s.records == 0) {
+    // no Gaussians: parameter gradients are empty, pose and basis gradients zero
+    return DDGS_OK;
+  }
+  CK(cudaMemsetAsync(ws->grad2d, 0, (size_t)s.records * 2 * sizeof(float4), s_));
+  ddgs::RasterParams P{c->alpha_min, c->alpha_max, c->t_min, c->q_max};
+  if (s.total_tiles > 0 && ws->pair_bound > 0) {
+    ddgs::launch_raster_bwd(s, P, *ws, dL_dimage, t_final, n_last, s_);
+    CK(cudaGetLastError());
+  }
+  ddgs::launch_preprocess_bwd(*g, *v, *c, s, *ws, *out, s_);
+  CK(cudaGetLastError());
+  return DDGS_OK;
+}
+
+ddgs_status ddgs_workspace_pairs(const ddgs_workspace *ws, int64_t *pairs) {
+  if (!ws || !pairs) return DDGS_ERR_INVALID_ARG;
+  *pairs = (int64_t)*ws->h_pairs;
+  return DDGS_OK;
+}
+
+}  // extern "C"
+
+namespace {
+__global__ void tiles_touched_kernel(const uint4 *info, int64_t n, uint32_t *out) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x)
+    out[j] = info[j].w;
+}
+
+__global__ void l1_loss_kernel(const float *image, const float *target, int per_view, int64_t hw,
+                               float *loss, float *grad) {
+  // one block row per view: blockIdx.y = view
+  const int v = blockIdx.y;
+  const float *img = image + (int64_t)v * hw;
+  const float *tgt = target + (per_view ? (int64_t)v * hw : 0);
+  float *gr = grad + (int64_t)v * hw;
+  const float inv = 1.0f / (float)hw;
+  float acc = 0.f;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < hw;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const float d = img[j] - tgt[j];
+    acc += fabsf(d);
+    gr[j] = d > 0.f ? inv : (d < 0.f ? -inv : 0.f);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  __shared__ float s_w[32];
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_w[w];
+    atomicAdd(loss + v, t * inv);
+  }
+}
+}  // namespace
+
+namespace ddgs {
+void launch_l1_loss(const float *image, const float *target, int per_view, int V, int64_t hw,
+                    float *loss, float *grad, cudaStream_t st) {
+  int64_t bx = (hw + 255) / 256;
+  if (bx > 64) bx = 64;
+  dim3 grid((unsigned)bx, (unsigned)V);
+  l1_loss_kernel<<<grid, 256, 0, st>>>(image, target, per_view, hw, loss, grad);
+}
+}  // namespace ddgs
+
+extern "C" {
+
+ddgs_status ddgs_debug_binning(const ddgs_workspace *ws, uint32_t *tiles_touched, uint64_t *keys,
+                               uint32_t *vals, uint32_t *ranges, void *stream) {
+  if (!ws || !ws->have_render) return DDGS_ERR_INVALID_ARG;
+  cudaStream_t s_ = static_cast<cudaStream_t>(stream);
+  const ddgs::RenderShape &s = ws->shape;
+  if (tiles_touched && s.records > 0) {
+    int64_t b = (s.records + 255) / 256;
+    if (b > 4096) b = 4096;
+    tiles_touched_kernel<<<(unsigned)b, 256, 0, s_>>>(reinterpret_cast<const uint4 *>(ws->rect),
+                                                      s.records, tiles_touched);
+    CK(cudaGetLastError());
+  }
+  uint64_t m = *ws->h_pairs;
+  if (m > (uint64_t)ws->pair_cap) m = (uint64_t)ws->pair_cap;  // after an overflow
+  if (keys && m) CK(cudaMemcpyAsync(keys, ws->keys[ws->sorted], m * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s_));
+  if (vals && m) CK(cudaMemcpyAsync(vals, ws->vals[ws->sorted], m * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s_));
+  if (ranges && s.total_tiles)
+    CK(cudaMemcpyAsync(ranges, ws->ranges, (size_t)s.total_tiles * sizeof(uint2), cudaMemcpyDeviceToDevice, s_));
+  return DDGS_OK;
+}
+
+ddgs_status ddgs_l1_loss(const float *image, const float *target, int32_t target_per_view,
+                         int32_t n_views, int64_t hw, float *loss, float *dL_dimage, void *stream) {
+  if (n_views < 0 || hw < 0) return DDGS_ERR_INVALID_ARG;
+  if (n_views == 0 || hw == 0) return DDGS_OK;
+  if (!image || !target || !loss || !dL_dimage || n_views > 65535) return DDGS_ERR_INVALID_ARG;
+  cudaStream_t s_ = static_cast<cudaStream_t>(stream);
+  CK(cudaMemsetAsync(loss, 0, (size_t)n_views * sizeof(float), s_));
+  ddgs::launch_l1_loss(image, target, target_per_view, n_views, hw, loss, dL_dimage, s_);
+  CK(cudaGetLastError());
+  return DDGS_OK;
+}
+
+ddgs_status ddgs_sync_status(ddgs_workspace *ws, void *stream) {
+  if (!ws) return DDGS_ERR_INVALID_ARG;
+  cudaStream_t s_ = static_cast<cudaStream_t>(stream);
+  int32_t h = 0;
+  CK(cudaStreamSynchronize(s_));
+  CK(cudaMemcpy(&h, ws->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  CK(cudaMemset(ws->d_status, 0, sizeof(int32_t)));
+  if (h & ddgs::ST_CAPACITY) return DDGS_ERR_CAPACITY;
+  if (h & ddgs::ST_TIMEOUT) return DDGS_ERR_TIMEOUT;
+  return DDGS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,140 @@
+// ddgs_internal.cuh -- shared declarations of the sm_103a DRR splatting kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/ddgs.h"
+
+namespace ddgs {
+
+constexpr int K = DDGS_FEAT_DIM;          // features per Gaussian
+constexpr int PRE_THREADS = 256;          // Gaussians per preprocess block
+constexpr int VIEW_CHUNK = 64;            // views staged in shared memory at once
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_ITEMS = 16;            // keys per thread per radix tile
+constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
+constexpr int RADIX_BITS = 8;
+constexpr int RADIX = 1 << RADIX_BITS;
+constexpr float SH_C1 = 0.48860251190291992f;  // sqrt(3 / (4 pi))
+
+// Device status bits (latched in the workspace).
+enum : int32_t { ST_CAPACITY = 1, ST_TIMEOUT = 2 };
+
+// Per-view constants derived once per block (IEEE-exact where the binning
+// depends on them).
+struct ViewConst {
+  float W[9];   // rotation rows
+  float t[3];
+  float wt[3];  // W^T t: the source sits at -wt in world coordinates
+  float fu, fv, cu, cv, sdd;
+};
+
+// Parameters shared by the rasterisers.
+struct RasterParams {
+  float alpha_min, alpha_max, t_min, q_max;
+};
+
+// Everything the kernels need about one render.
+struct RenderShape {
+  int64_t n, n_iso;
+  int32_t V, H, W, tile, tiles_x, tiles_y;
+  int64_t tiles_per_view, total_tiles, records;
+  int32_t key_bits;  // significant bits of the sort key
+};
+
+// IEEE-exact binary32 helpers: one correctly rounded operation each, never
+// contracted into an FMA, so that the binning matches its written definition.
+__device__ __forceinline__ float mulr(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float addr(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float subr(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float divr(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float sqrtr(float a) { return __fsqrt_rn(a); }
+__device__ __forceinline__ float dot3r(float a0, float a1, float a2, float b0, float b1, float b2) {
+  return addr(addr(mulr(a0, b0), mulr(a1, b1)), mulr(a2, b2));
+}
+
+// Per-pair evaluation shared by the forward and backward rasterisers, written
+// with explicit rounding so both kernels take bit-identical decisions.
+struct PairEval {
+  float dx, dy, G, aG, sigma;
+};
+
+__device__ __forceinline__ bool eval_pair(float u, float v, float ca, float cb, float cc,
+                                          float alpha, float px, float py,
+                                          const RasterParams &P, PairEval &e) {
+  e.dx = __fsub_rn(u, px);
+  e.dy = __fsub_rn(v, py);
+  float xx = __fmul_rn(e.dx, e.dx), yy = __fmul_rn(e.dy, e.dy), xy = __fmul_rn(e.dx, e.dy);
+  float q = __fmaf_rn(ca, xx, __fmaf_rn(cc, yy, __fmul_rn(__fadd_rn(cb, cb), xy)));
+  if (q > P.q_max || q < 0.f) return false;
+  e.G = __expf(__fmul_rn(-0.5f, q));
+  e.aG = __fmul_rn(alpha, e.G);
+  e.sigma = fminf(P.alpha_max, e.aG);
+  return e.sigma >= P.alpha_min;
+}
+
+}  // namespace ddgs
+
+// Workspace (device memory owned by the library).
+struct ddgs_workspace {
+  int device = -1;
+  int64_t rec_cap = 0, pair_cap = 0, tile_cap = 0, blk_cap = 0, sblk_cap = 0;
+  // per (view, Gaussian) records
+  float4 *rec0 = nullptr;        // (u, v, conic a, conic b)
+  float4 *rec1 = nullptr;        // (conic c, alpha, colour, depth)
+  uint2 *rect = nullptr;         // (tx0 | ty0 << 16, tx1 | ty1 << 16)
+  uint32_t *tiles_touched = nullptr;
+  float4 *grad2d = nullptr;      // [records][2]: (u, v, ca, cb), (cc, alpha, colour, 0)
+  // scan
+  uint32_t *blk_total = nullptr;
+  uint64_t *blk_offset = nullptr;
+  // pairs
+  uint64_t *keys[2] = {nullptr, nullptr};
+  uint32_t *vals[2] = {nullptr, nullptr};
+  int sorted = 0;                // which buffer holds the sorted pairs
+  uint32_t *hist = nullptr;      // [RADIX][sort blocks]
+  uint32_t *digit_total = nullptr;  // [RADIX]
+  uint2 *ranges = nullptr;       // [tiles]
+  // scalars
+  uint64_t *d_pairs = nullptr;   // device pair count M
+  uint64_t *h_pairs = nullptr;   // pinned host mirror
+  int32_t *d_status = nullptr;
+  // the last render
+  ddgs::RenderShape shape{};
+  bool have_render = false;
+  uint64_t pair_bound = 0;       // grid bound used for the pair kernels
+};
+
+namespace ddgs {
+
+// preprocess.cu
+void launch_preprocess_fwd(const ddgs_gaussians &g, const ddgs_views &v, const ddgs_config &c,
+                           const RenderShape &s, ddgs_workspace &ws, cudaStream_t st);
+void launch_emit_keys(const RenderShape &s, ddgs_workspace &ws, cudaStream_t st);
+void launch_preprocess_bwd(const ddgs_gaussians &g, const ddgs_views &v, const ddgs_config &c,
+                           const RenderShape &s, ddgs_workspace &ws, const ddgs_grads &out,
+                           cudaStream_t st);
+int64_t preprocess_blocks(const RenderShape &s);
+
+// sort.cu
+void launch_scan_blocks(int64_t nblk, ddgs_workspace &ws, cudaStream_t st);
+void launch_radix_sort(const RenderShape &s, uint64_t pair_bound, ddgs_workspace &ws,
+                       cudaStream_t st);
+void launch_tile_ranges(const RenderShape &s, uint64_t pair_bound, ddgs_workspace &ws,
+                        cudaStream_t st);
+int64_t sort_blocks(uint64_t pair_bound);
+
+// raster.cu
+void launch_raster_fwd(const RenderShape &s, const RasterParams &p, ddgs_workspace &ws,
+                       float *image, float *t_final, uint32_t *n_last, cudaStream_t st);
+void launch_raster_bwd(const RenderShape &s, const RasterParams &p, ddgs_workspace &ws,
+                       const float *dL_dimage, const float *t_final, const uint32_t *n_last,
+                       cudaStream_t st);
+
+// api.cu
+void launch_l1_loss(const float *image, const float *target, int per_view, int V, int64_t hw,
+                    float *loss, float *grad, cudaStream_t st);
+
+}  // namespace ddgs

@@ -1,0 +1,323 @@
+// raster.cu -- per-tile front-to-back blending (Eq. 1) and its backward pass.
+//
+// One thread block renders one (view, tile) list; one thread owns one pixel.
+// Warps own 8 x 4 pixel blocks, so a Gaussian whose q <= q_max ellipse misses
+// a warp's block is skipped by the whole warp with one uniform test. Gaussians
+// of the list are staged in shared memory one batch (one per thread) at a
+// time: the batch is a gather by Gaussian index from the per-view records,
+// which is why it uses plain vector loads rather than a bulk tensor copy.
+//
+// Forward per pixel p, over the list in ascending depth (Eq. 1):
+//   q = (p - mu-hat)^T conic (p - mu-hat); skip if q > q_max;
+//   sigma = min(alpha_max, alpha exp(-q/2)); skip if sigma < alpha_min;
+//   T' = T (1 - sigma); stop (without adding) if T' < t_min;
+//   C += c sigma T; T = T'.
+// Backward per pixel, over the same list from the last added Gaussian to the
+// first, recovering T before each Gaussian as T' / (1 - sigma) and carrying
+// the suffix sum S = sum over later Gaussians of c sigma T:
+//   dC/dc = sigma T,  dC/dsigma = c T - S / (1 - sigma),
+//   dsigma/dalpha = G and dsigma/dq = -alpha G / 2 unless sigma was clamped.
+// The per-pixel 2D gradients of one Gaussian are summed over the warp with
+// shuffles, over the block in shared memory, and reach global memory with one
+// vector atomic per (tile, Gaussian).
+#include "ddgs_internal.cuh"
+
+namespace ddgs {
+namespace {
+
+struct RasterArgs {
+  RenderShape s;
+  RasterParams P;
+  const float4 *rec0, *rec1;
+  const uint32_t *vals;
+  const uint2 *ranges;
+  float4 *grad2d;
+  float *image, *t_final;
+  uint32_t *n_last;
+  const float *dL_dimage, *t_final_in;
+  const uint32_t *n_last_in;
+};
+
+// Conservative pixel-space box of the q <= q_max ellipse of a conic.
+__device__ __forceinline__ float4 ellipse_box(float4 r0, float4 r1, float q_max) {
+  const float det = r0.z * r1.x - r0.w * r0.w;
+  const float cxx = r1.x / det, cyy = r0.z / det;
+  const float ex = sqrtf(q_max * cxx) * 1.001f + 1e-3f;
+  const float ey = sqrtf(q_max * cyy) * 1.001f + 1e-3f;
+  return make_float4(r0.x - ex, r0.x + ex, r0.y - ey, r0.y + ey);
+}
+
+__device__ __forceinline__ float4 empty_box() {
+  return make_float4(__int_as_float(0x7f800000), -__int_as_float(0x7f800000),
+                     __int_as_float(0x7f800000), -__int_as_float(0x7f800000));
+}
+
+template <int T>
+struct TileGeom {
+  int v, txi, tyi, px, py, wx0, wy0;
+  bool inside;
+  int64_t gtile;
+  __device__ __forceinline__ TileGeom(const RenderShape &s, int64_t gt) {
+    gtile = gt;
+    v = (int)(gt / s.tiles_per_view);
+    const int64_t local = gt - (int64_t)v * s.tiles_per_view;
+    tyi = (int)(local / s.tiles_x);
+    txi = (int)(local - (int64_t)tyi * s.tiles_x);
+    constexpr int WX = T / 8;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wx = w % WX, wy = w / WX;
+    wx0 = txi * T + wx * 8;
+    wy0 = tyi * T + wy * 4;
+    px = wx0 + (lane & 7);
+    py = wy0 + (lane >> 3);
+    inside = px < s.W && py < s.H;
+  }
+  // does the box miss this warp's 8 x 4 pixel centres?
+  __device__ __forceinline__ bool misses(float4 b) const {
+    return b.x > wx0 + 7.5f || b.y < wx0 + 0.5f || b.z > wy0 + 3.5f || b.w < wy0 + 0.5f;
+  }
+};
+
+constexpr int BATCH = 256;  // list entries staged per round
+
+template <int T>
+__global__ void __launch_bounds__(T *T) raster_fwd_kernel(RasterArgs a) {
+  constexpr int NT = T * T;
+  __shared__ float4 s_a[BATCH], s_b[BATCH], s_box[BATCH];
+  const int tid = threadIdx.x;
+  const TileGeom<T> tg(a.s, blockIdx.x);
+  const uint2 range = a.ranges[tg.gtile];
+  const int64_t rec_base = (int64_t)tg.v * a.s.n;
+  const float px = tg.px + 0.5f, py = tg.py + 0.5f;
+  float Tr = 1.f, C = 0.f;
+  uint32_t last = 0;
+  bool done = !tg.inside;
+  for (uint32_t b0 = range.x; b0 < range.y; b0 += BATCH) {
+    if (__syncthreads_count(done) == NT) break;
+    for (int e = tid; e < BATCH; e += NT) {
+      const uint32_t j = b0 + e;
+      if (j < range.y) {
+        const uint32_t id = a.vals[j];
+        if (id < a.s.n) {
+          const int64_t r = rec_base + id;
+          const float4 r0 = a.rec0[r], r1 = a.rec1[r];
+          s_a[e] = r0;
+          s_b[e] = r1;
+          s_box[e] = ellipse_box(r0, r1, a.P.q_max);
+        } else {
+          s_box[e] = empty_box();  // only after a capacity overflow
+        }
+      }
+    }
+    __syncthreads();
+    const int cnt = (int)min((uint32_t)BATCH, range.y - b0);
+    for (int k = 0; k < cnt; ++k) {
+      if (tg.misses(s_box[k])) continue;
+      if (__all_sync(0xffffffffu, done)) break;
+      if (done) continue;
+      const float4 A = s_a[k], B = s_b[k];
+      PairEval e;
+      if (!eval_pair(A.x, A.y, A.z, A.w, B.x, B.y, px, py, a.P, e)) continue;
+      const float Tn = __fmul_rn(Tr, __fsub_rn(1.f, e.sigma));
+      if (Tn < a.P.t_min) {
+        done = true;
+        continue;
+      }
+      C = fmaf(B.z * e.sigma, Tr, C);
+      Tr = Tn;
+      last = b0 + (uint32_t)k - range.x + 1u;
+    }
+  }
+  if (tg.inside) {
+    const int64_t pix = ((int64_t)tg.v * a.s.H + tg.py) * a.s.W + tg.px;
+    a.image[pix] = C;
+    a.t_final[pix] = Tr;
+    a.n_last[pix] = last;
+  }
+}
+
+// Sum 8 per-lane values over the warp with 9 shuffles. Afterwards lanes whose
+// two low bits are 0 hold component ((l >> 4) & 1) * 4 + ((l >> 3) & 1) * 2 +
+// ((l >> 2) & 1) in v[0]; the function returns that index.
+__device__ __forceinline__ int warp_reduce8(float v[8]) {
+  const int lane = threadIdx.x & 31;
+  bool hi = lane & 16;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    float send = hi ? v[k] : v[k + 4];
+    float keep = hi ? v[k + 4] : v[k];
+    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  hi = lane & 8;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    float send = hi ? v[k] : v[k + 2];
+    float keep = hi ? v[k + 2] : v[k];
+    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  hi = lane & 4;
+  {
+    float send = hi ? v[0] : v[1];
+    float keep = hi ? v[1] : v[0];
+    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+  return ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+}
+
+template <int T>
+__global__ void __launch_bounds__(T *T) raster_bwd_kernel(RasterArgs a) {
+  __shared__ float4 s_a[BATCH], s_b[BATCH], s_box[BATCH];
+  __shared__ uint32_t s_id[BATCH];
+  __shared__ float s_acc[BATCH][8];
+  constexpr int NT = T * T;
+  __shared__ uint32_t s_max;
+  const int tid = threadIdx.x;
+  const TileGeom<T> tg(a.s, blockIdx.x);
+  const uint2 range = a.ranges[tg.gtile];
+  const int64_t rec_base = (int64_t)tg.v * a.s.n;
+  const float px = tg.px + 0.5f, py = tg.py + 0.5f;
+  float Tr = 1.f, g = 0.f;
+  uint32_t last = 0;
+  if (tg.inside) {
+    const int64_t pix = ((int64_t)tg.v * a.s.H + tg.py) * a.s.W + tg.px;
+    Tr = a.t_final_in[pix];
+    last = a.n_last_in[pix];
+    g = a.dL_dimage[pix];
+  }
+  if (g == 0.f) last = 0;  // nothing to propagate from this pixel
+  if (last > range.y - range.x) last = range.y - range.x;  // never read past the list
+  if (tid == 0) s_max = 0;
+  __syncthreads();
+  if (last) atomicMax(&s_max, last);
+  __syncthreads();
+  const uint32_t max_last = s_max;
+  float S = 0.f;
+  for (int64_t hi = max_last; hi > 0; hi -= BATCH) {
+    const int64_t lo = hi > BATCH ? hi - BATCH : 0;
+    for (int e = tid; e < BATCH; e += NT) {
+      const int64_t pos_t = hi - 1 - e;  // batches run back to front
+      if (pos_t >= lo) {
+        const uint32_t id = a.vals[range.x + (uint32_t)pos_t];
+        if (id < a.s.n) {
+          const int64_t r = rec_base + id;
+          const float4 r0 = a.rec0[r], r1 = a.rec1[r];
+          s_a[e] = r0;
+          s_b[e] = r1;
+          s_box[e] = ellipse_box(r0, r1, a.P.q_max);
+        } else {
+          s_box[e] = empty_box();  // only after a capacity overflow
+        }
+        s_id[e] = id;
+      }
+#pragma unroll
+      for (int c = 0; c < 8; ++c) s_acc[e][c] = 0.f;
+    }
+    __syncthreads();
+    const int cnt = (int)(hi - lo);
+    for (int k = 0; k < cnt; ++k) {
+      if (tg.misses(s_box[k])) continue;
+      const uint32_t pos = (uint32_t)(hi - 1 - k);
+      float gv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      bool act = pos < last;
+      if (act) {
+        const float4 A = s_a[k], B = s_b[k];
+        PairEval e;
+        act = eval_pair(A.x, A.y, A.z, A.w, B.x, B.y, px, py, a.P, e);
+        if (act) {
+          const float om = __fsub_rn(1.f, e.sigma);
+          Tr = __fdiv_rn(Tr, om);  // transmittance before this Gaussian
+          const float c = B.z;
+          const float dC_dsigma = c * Tr - S / om;
+          S = fmaf(c * e.sigma, Tr, S);
+          const float gs = g * dC_dsigma;
+          float gq = 0.f;
+          if (!(e.aG > a.P.alpha_max)) {
+            gv[5] = gs * e.G;
+            gq = -0.5f * gs * B.y * e.G;
+          }
+          const float tdx = 2.f * e.dx, tdy = 2.f * e.dy;
+          gv[0] = gq * (A.z * tdx + A.w * tdy);
+          gv[1] = gq * (A.w * tdx + B.x * tdy);
+          gv[2] = gq * e.dx * e.dx;
+          gv[3] = gq * tdx * e.dy;
+          gv[4] = gq * e.dy * e.dy;
+          gv[6] = g * e.sigma * Tr;
+        }
+      }
+      if (__any_sync(0xffffffffu, act)) {
+        const int comp = warp_reduce8(gv);
+        if ((threadIdx.x & 3) == 0) atomicAdd(&s_acc[k][comp], gv[0]);
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < cnt; e += NT) {
+      const float *acc = s_acc[e];
+      const bool nz = (acc[0] != 0.f) | (acc[1] != 0.f) | (acc[2] != 0.f) | (acc[3] != 0.f) |
+                      (acc[4] != 0.f) | (acc[5] != 0.f) | (acc[6] != 0.f);
+      if (nz) {
+        float4 *dst = a.grad2d + 2 * (rec_base + s_id[e]);
+        atomicAdd(dst, make_float4(acc[0], acc[1], acc[2], acc[3]));
+        atomicAdd(dst + 1, make_float4(acc[4], acc[5], acc[6], 0.f));
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int T>
+void launch_fwd_t(const RasterArgs &a, cudaStream_t st) {
+  if (a.s.total_tiles > 0)
+    raster_fwd_kernel<T><<<(unsigned)a.s.total_tiles, T * T, 0, st>>>(a);
+}
+
+template <int T>
+void launch_bwd_t(const RasterArgs &a, cudaStream_t st) {
+  if (a.s.total_tiles > 0)
+    raster_bwd_kernel<T><<<(unsigned)a.s.total_tiles, T * T, 0, st>>>(a);
+}
+
+}  // namespace
+
+void launch_raster_fwd(const RenderShape &s, const RasterParams &p, ddgs_workspace &ws,
+                       float *image, float *t_final, uint32_t *n_last, cudaStream_t st) {
+  RasterArgs a{};
+  a.s = s;
+  a.P = p;
+  a.rec0 = ws.rec0;
+  a.rec1 = ws.rec1;
+  a.vals = ws.vals[ws.sorted];
+  a.ranges = ws.ranges;
+  a.image = image;
+  a.t_final = t_final;
+  a.n_last = n_last;
+  switch (s.tile) {
+    case 8: launch_fwd_t<8>(a, st); break;
+    case 16: launch_fwd_t<16>(a, st); break;
+    default: launch_fwd_t<32>(a, st); break;
+  }
+}
+
+void launch_raster_bwd(const RenderShape &s, const RasterParams &p, ddgs_workspace &ws,
+                       const float *dL_dimage, const float *t_final, const uint32_t *n_last,
+                       cudaStream_t st) {
+  RasterArgs a{};
+  a.s = s;
+  a.P = p;
+  a.rec0 = ws.rec0;
+  a.rec1 = ws.rec1;
+  a.vals = ws.vals[ws.sorted];
+  a.ranges = ws.ranges;
+  a.grad2d = ws.grad2d;
+  a.dL_dimage = dL_dimage;
+  a.t_final_in = t_final;
+  a.n_last_in = n_last;
+  switch (s.tile) {
+    case 8: launch_bwd_t<8>(a, st); break;
+    case 16: launch_bwd_t<16>(a, st); break;
+    default: launch_bwd_t<32>(a, st); break;
+  }
+}
+
+}  // namespace ddgs

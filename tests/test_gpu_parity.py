@@ -1,0 +1,312 @@
+"""GPU parity: the CUDA library against the CPU oracle, through the C ABI.
+
+Sizes are chosen so the oracle finishes in seconds while spanning several
+tiles and ragged tile edges; the full-size workloads are checked on sampled
+pixels. Tolerances are in tests/_parity.py.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2406_02518_gb300 import binding as B
+from paper_2406_02518_gb300 import synthetic as syn
+from _parity import check_image, compare_binning, compare_grads, last_ids
+
+pytestmark = pytest.mark.gpu
+
+GRAD_NAMES = ["means", "log_scales", "quats", "opacity_logits", "feat", "b_iso", "B_dir", "pose"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_2406_02518_gb300 import build
+    build.build()
+    B.load()
+    assert B.device_supported(), "needs an sm_103 (GB300) device"
+
+
+@pytest.fixture(scope="module")
+def ws():
+    w = B.Workspace()
+    yield w
+    w.close()
+
+
+def _views(poses, sdd, pitch, H, W):
+    poses = np.ascontiguousarray(np.asarray(poses, np.float32).reshape(-1, 3, 4))
+    return syn.Views(poses, syn.detector(poses.shape[0], sdd, pitch), H, W)
+
+
+def _two_views(H, W, pitch=8.0 / 96):
+    return _views([syn.pose_matrix(np.eye(3), np.array([0.0, 0.0, 2.0])),
+                   syn.pose_matrix(syn.rot_y(0.5) @ syn.rot_x(-0.2), np.array([0.05, -0.1, 2.3]))],
+                  4.0, pitch, H, W)
+
+
+def _run(scene, views, st, ws, bf16=None):
+    cloud = B.cloud_from_arrays(scene, feat_dir_bf16=bf16)
+    gv = B.views_from_arrays(views)
+    cfg = B.config_from_settings(st)
+    img, tf, nl = B.render(cloud, gv, cfg, ws)
+    torch.cuda.synchronize()
+    return cloud, gv, cfg, img, tf, nl
+
+
+def _bins(ws, scene, views, st):
+    t = st.tile
+    tiles = views.n_views * (-(-views.width // t)) * (-(-views.height // t))
+    return B.debug_binning(ws, views.n_views, scene.n, tiles)
+
+
+CASES = {
+    "plain_4096_128px": lambda: syn.plain_forward_workload(),
+    "ragged_100x75_2views": lambda: (syn.uniform_cloud(2000, seed=5), _two_views(75, 100),
+                                     syn.Settings(near_plane=0.2)),
+    "tile8": lambda: (syn.uniform_cloud(1500, seed=6), _two_views(41, 57, 8.0 / 50),
+                      syn.Settings(near_plane=0.2, tile=8)),
+    "tile32": lambda: (syn.uniform_cloud(1500, seed=7), _two_views(70, 90, 8.0 / 80),
+                       syn.Settings(near_plane=0.2, tile=32)),
+    "strong_dir": lambda: (syn.uniform_cloud(1200, seed=8, dir_frac=0.5, dir_std=1.0),
+                           _two_views(48, 64, 8.0 / 60), syn.Settings(near_plane=0.2)),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_binning_is_bit_exact(case, ws):
+    scene, views, st = CASES[case]()
+    _run(scene, views, st, ws)
+    gpu = _bins(ws, scene, views, st)
+    ref = oracle.bin32(scene, views, st)
+    compare_binning(gpu, ref)
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_image_matches_oracle(case, ws):
+    scene, views, st = CASES[case]()
+    _, _, _, img, tf, nl = _run(scene, views, st, ws)
+    bins = _bins(ws, scene, views, st)
+    ids = last_ids(nl.cpu().numpy().view(np.uint32), bins, views, st.tile)
+    rep = check_image(scene, views, st, img.cpu().numpy(), tf.cpu().numpy(), ids,
+                      depth32=bins_depth(scene, views, st))
+    assert rep["range"] > 0.1
+    assert rep["unresolved_frac"] <= 1e-3
+
+
+def bins_depth(scene, views, st):
+    return oracle.project32(scene, views, st)["depth"]
+
+
+def _masked_weights(ref, seed=0):
+    rng = np.random.default_rng(seed)
+    w = rng.uniform(-1, 1, ref["image"].shape)
+    return np.where((ref["flags"] == 0), w, 0.0)
+
+
+@pytest.mark.parametrize("case", ["plain_4096_128px", "ragged_100x75_2views", "strong_dir",
+                                  "tile8", "tile32"])
+def test_gradients_match_oracle(case, ws):
+    scene, views, st = CASES[case]()
+    cloud, gv, cfg, img, tf, nl = _run(scene, views, st, ws)
+    ref = oracle.render(scene, views, st)
+    w = _masked_weights(ref)
+    dL = torch.as_tensor(w, dtype=torch.float32, device="cuda")
+    g = B.render_backward(cloud, gv, cfg, ws, dL, tf, nl)
+    torch.cuda.synchronize()
+    gr = oracle.render_backward(scene, views, st, w)
+    gpu = {k: v.cpu().numpy() for k, v in g.items()}
+    gpu["feat"] = np.concatenate([gpu.pop("feat_iso"), gpu.pop("feat_dir")])
+    gpu["pose"] = gpu.pop("world_to_cam")
+    compare_grads(gpu, gr, GRAD_NAMES)
+
+
+def test_bf16_direction_features(ws):
+    ph = syn.make_phantom(48, seed=2, fov=96.0)
+    scene = syn.gaussians_from_phantom(ph, 3000, seed=2, bf16_dir=True)
+    views = syn.Views(syn.orbit_poses(2, 300.0), syn.detector(2, 375.0, 96.0 / 64), 64, 64)
+    st = syn.Settings(near_plane=30.0)
+    cloud, gv, cfg, img, tf, nl = _run(scene, views, st, ws, bf16=True)
+    assert cloud.feat_dir.dtype == torch.bfloat16
+    bins = _bins(ws, scene, views, st)
+    compare_binning(bins, oracle.bin32(scene, views, st))
+    ids = last_ids(nl.cpu().numpy().view(np.uint32), bins, views, st.tile)
+    check_image(scene, views, st, img.cpu().numpy(), tf.cpu().numpy(), ids)
+    ref = oracle.render(scene, views, st)
+    w = _masked_weights(ref, 1)
+    g = B.render_backward(cloud, gv, cfg, ws, torch.as_tensor(w, dtype=torch.float32, device="cuda"),
+                          tf, nl)
+    gr = oracle.render_backward(scene, views, st, w)
+    gpu = {k: v.float().cpu().numpy() for k, v in g.items()}
+    gpu["feat"] = np.concatenate([gpu.pop("feat_iso"), gpu.pop("feat_dir")])
+    gpu["pose"] = gpu.pop("world_to_cam")
+    compare_grads(gpu, gr, GRAD_NAMES)
+
+
+def test_empty_and_degenerate_inputs(ws):
+    # no Gaussians
+    scene = syn.uniform_cloud(0, seed=0)
+    views = _two_views(20, 30)
+    st = syn.Settings(near_plane=0.2)
+    cloud, gv, cfg, img, tf, nl = _run(scene, views, st, ws)
+    assert float(img.abs().max()) == 0.0 and float(tf.min()) == 1.0 and int(nl.max()) == 0
+    g = B.render_backward(cloud, gv, cfg, ws, torch.ones_like(img), tf, nl,
+                          want=["world_to_cam", "b_iso", "B_dir"])
+    assert float(g["world_to_cam"].abs().max()) == 0.0
+    # every Gaussian behind the near plane or beyond the detector
+    scene = syn.uniform_cloud(300, seed=1)
+    scene.means[:, 2] = np.where(np.arange(300) % 2 == 0, -1.95, 2.5).astype(np.float32)
+    view1 = _views(syn.pose_matrix(np.eye(3), np.array([0.0, 0.0, 2.0])), 4.0, 8.0 / 30, 20, 30)
+    cloud, gv, cfg, img, tf, nl = _run(scene, view1, st, ws)
+    assert float(img.abs().max()) == 0.0 and ws.pairs() == 0
+    # all isotropic / all direction-dependent
+    for frac in (0.0, 1.0):
+        scene = syn.uniform_cloud(400, seed=2, dir_frac=frac)
+        views1 = _two_views(33, 47, 8.0 / 40)
+        _, _, _, img, tf, nl = _run(scene, views1, st, ws)
+        bins = _bins(ws, scene, views1, st)
+        compare_binning(bins, oracle.bin32(scene, views1, st))
+        ids = last_ids(nl.cpu().numpy().view(np.uint32), bins, views1, st.tile)
+        check_image(scene, views1, st, img.cpu().numpy(), tf.cpu().numpy(), ids)
+    # a single pixel detector, a single Gaussian
+    scene = syn.uniform_cloud(1, seed=3, log_scale_range=(-1.0, -0.9))
+    scene.means[:] = 0
+    views1 = _views(syn.pose_matrix(np.eye(3), np.array([0.0, 0.0, 2.0])), 4.0, 0.5, 1, 1)
+    _, _, _, img, tf, nl = _run(scene, views1, st, ws)
+    ref = oracle.render(scene, views1, st)
+    assert abs(float(img[0, 0, 0]) - ref["image"][0, 0, 0]) < 1e-6
+    assert int(nl[0, 0, 0]) == 1
+
+
+def test_autograd_function_matches_direct_backward(ws):
+    scene, views, st = CASES["ragged_100x75_2views"]()
+    cloud = B.cloud_from_arrays(scene)
+    gv = B.views_from_arrays(views)
+    cfg = B.config_from_settings(st)
+    params = [cloud.means, cloud.log_scales, cloud.quats, cloud.opacity_logits, cloud.feat_iso,
+              cloud.feat_dir, cloud.b_iso, cloud.B_dir, gv.world_to_cam]
+    for p in params:
+        p.requires_grad_(True)
+    img, tf, nl = B.render_differentiable(cloud, gv, cfg, ws)
+    w = torch.linspace(-1, 1, img.numel(), device="cuda").reshape(img.shape)
+    (img * w).sum().backward()
+    grads_auto = [p.grad.clone() for p in params]
+    cloud2 = B.Cloud(*[p.detach() for p in params[:8]])
+    gv2 = B.Views(gv.world_to_cam.detach(), gv.detector, gv.height, gv.width)
+    img2, tf2, nl2 = B.render(cloud2, gv2, cfg, ws)
+    g = B.render_backward(cloud2, gv2, cfg, ws, w, tf2, nl2)
+    torch.cuda.synchronize()
+    assert torch.equal(img.detach(), img2)
+    names = ["means", "log_scales", "quats", "opacity_logits", "feat_iso", "feat_dir", "b_iso",
+             "B_dir", "world_to_cam"]
+    for ga, n in zip(grads_auto, names):
+        scale = float(g[n].abs().max()) + 1e-30
+        assert float((ga - g[n]).abs().max()) <= 1e-5 * scale, n
+
+
+def test_gpu_fp32_gradient_agrees_with_finite_differences(ws):
+    # sanity only: FP32 renders, steps large enough to be resolved in FP32,
+    # cutoffs pushed out so that a step cannot flip a visible decision
+    scene = syn.uniform_cloud(6, seed=21, extent=0.5, log_scale_range=(-2.2, -1.4),
+                              alpha_range=(0.2, 0.7), dir_frac=0.5, dir_std=1.0)
+    views = _two_views(20, 24, 0.2)
+    st = syn.Settings(near_plane=0.2, t_min=1e-7, alpha_min=1e-7, q_max=30.0)
+    cloud, gv, cfg, img, tf, nl = _run(scene, views, st, ws)
+    w = torch.as_tensor(np.random.default_rng(3).uniform(-1, 1, img.shape), dtype=torch.float32,
+                        device="cuda")
+    g = B.render_backward(cloud, gv, cfg, ws, w, tf, nl, want=["means", "world_to_cam"])
+    for name, tensor in (("means", cloud.means), ("world_to_cam", gv.world_to_cam)):
+        G = g[name].reshape(-1).cpu().numpy()
+        base = tensor.clone()
+        fd = np.zeros_like(G)
+        for idx in range(G.size):
+            vals = []
+            for sgn in (1, -1):
+                t = base.clone().reshape(-1)
+                t[idx] += sgn * 1e-3
+                tensor.copy_(t.reshape(base.shape))
+                im, _, _ = B.render(cloud, gv, cfg, ws)
+                vals.append(float((im * w).double().sum()))
+            fd[idx] = (vals[0] - vals[1]) / 2e-3
+        tensor.copy_(base)
+        err = np.abs(fd - G).max() / np.abs(G).max()
+        assert err < 2e-2, (name, err)
+
+
+def test_l1_loss_kernel(ws):
+    rng = np.random.default_rng(0)
+    img = torch.as_tensor(rng.uniform(0, 1, (3, 17, 23)), dtype=torch.float32, device="cuda")
+    tgt = torch.as_tensor(rng.uniform(0, 1, (17, 23)), dtype=torch.float32, device="cuda")
+    loss, grad = B.l1_loss(img, tgt)
+    torch.cuda.synchronize()
+    d = img.cpu().numpy().astype(np.float64) - tgt.cpu().numpy()[None]
+    assert np.allclose(loss.cpu().numpy(), np.abs(d).mean(axis=(1, 2)), rtol=1e-5)
+    assert np.array_equal(grad.cpu().numpy(), (np.sign(d) / (17 * 23)).astype(np.float32))
+
+
+def test_capacity_overflow_is_reported_not_faulted(ws):
+    scene = syn.uniform_cloud(20000, seed=5)
+    views = _two_views(75, 100)
+    st = syn.Settings(near_plane=0.2)
+    m_needed = oracle.bin32(scene, views, st)["m"]
+    w2 = B.Workspace()
+    recs = views.n_views * scene.n
+    w2.reserve(recs, 64, views.n_views * 42)  # far fewer pairs than needed
+    assert m_needed > 64 + 64 // 4 + 4096
+    cloud = B.cloud_from_arrays(scene)
+    gv = B.views_from_arrays(views)
+    cfg = B.config_from_settings(st, no_sync=True)
+    B.render(cloud, gv, cfg, w2)
+    assert w2.sync_status() == 2  # DDGS_ERR_CAPACITY
+    assert w2.sync_status() == 0  # cleared
+    # the same workspace renders correctly once it is large enough
+    w2.reserve(recs, m_needed, views.n_views * 42)
+    img, tf, nl = B.render(cloud, gv, cfg, w2)
+    assert w2.sync_status() == 0
+    img_ref, _, _ = B.render(cloud, gv, B.config_from_settings(st), ws)
+    torch.cuda.synchronize()
+    assert torch.equal(img, img_ref)
+    w2.close()
+
+
+@pytest.mark.slow
+def test_registration_workload_sampled_pixels(ws):
+    """500k Gaussians, 64 poses, 256^2: the batched launch the benchmark times,
+    checked on sampled pixels of a few views (oracle one pixel at a time)."""
+    scene, views, st = syn.registration_workload()
+    cloud, gv, cfg, img, tf, nl = _run(scene, views, st, ws)
+    bins = _bins(ws, scene, views, st)
+    # bit-exact binning on two views' worth of keys
+    ref_proj = oracle.project32(scene, views, st)
+    assert np.array_equal(bins["tiles_touched"].reshape(ref_proj["tiles_touched"].shape),
+                          ref_proj["tiles_touched"])
+    assert bins["m"] == int(ref_proj["tiles_touched"].sum())
+    keys = bins["keys"]
+    assert np.all(keys[1:] >= keys[:-1])
+    check_views = [0, 37]
+    sub = dataclasses.replace(views, world_to_cam=views.world_to_cam[check_views].copy(),
+                              detector=views.detector[check_views].copy())
+    pix = syn.sample_pixels(sub, n_random=768, n_rows=1, seed=4)
+    sel_v = np.array(check_views)[pix[:, 0]]
+    ids_all = last_ids(nl.cpu().numpy().view(np.uint32), bins, views, st.tile)
+    gi = img.cpu().numpy()[sel_v, pix[:, 1], pix[:, 2]]
+    gt = tf.cpu().numpy()[sel_v, pix[:, 1], pix[:, 2]]
+    gid = ids_all[sel_v, pix[:, 1], pix[:, 2]]
+    rep = check_image(scene, sub, st, gi, gt, gid, depth32=ref_proj["depth"][check_views], pix=pix)
+    assert rep["range"] > 0.1
+    # pose gradients of a loss on the sampled pixels only (same mask both sides)
+    w = np.zeros(img.shape, np.float64)
+    flags = rep["ref"]["flags"]
+    rng = np.random.default_rng(9)
+    wv = np.where(flags == 0, rng.uniform(-1, 1, pix.shape[0]), 0.0)
+    w[sel_v, pix[:, 1], pix[:, 2]] = wv
+    g = B.render_backward(cloud, gv, cfg, ws, torch.as_tensor(w, dtype=torch.float32, device="cuda"),
+                          tf, nl, want=["world_to_cam"])
+    gr = oracle.render_backward(scene, sub, st, wv, pix=pix, depth32=ref_proj["depth"][check_views])
+    gp = g["world_to_cam"].cpu().numpy()
+    compare_grads({"pose": gp[check_views]}, {"pose": gr["pose"]}, ["pose"])
+    others = np.setdiff1d(np.arange(views.n_views), check_views)
+    assert np.abs(gp[others]).max() == 0.0

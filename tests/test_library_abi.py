@@ -1,0 +1,61 @@
+"""The C-ABI library builds, loads and exports every symbol include/ddgs.h
+declares (no GPU needed; no compute call is made)."""
+import ctypes
+import json
+import os
+import re
+
+import pytest
+
+from paper_2406_02518_gb300 import binding as B
+from paper_2406_02518_gb300 import build as bld
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    bld.build()
+    return B.load()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "ddgs.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(ddgs_[a-z0-9_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_header_declares_the_documented_entry_points():
+    d = _declared()
+    for n in ("ddgs_render", "ddgs_render_backward", "ddgs_workspace_create",
+              "ddgs_workspace_destroy", "ddgs_debug_binning"):
+        assert n in d
+
+
+def test_library_exports_every_declared_symbol(lib):
+    raw = ctypes.CDLL(bld.LIB)
+    for name in _declared():
+        assert hasattr(raw, name), name
+    assert sorted(B.EXPORTS) == _declared()
+
+
+def test_parameter_count_matches_paper(lib):
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "parameter_count.json")))
+    assert B.parameter_count(g["n_gaussians"], g["k"], g["L"]) == g["total_floats"]
+    assert B.parameter_count(1, 8, 1) - B.parameter_count(0, 8, 1) == g["floats_per_gaussian"]
+    assert B.parameter_count(0, 8, 1) == g["basis_floats"]
+    assert B.parameter_count(-1, 8, 1) == -1
+
+
+def test_status_strings(lib):
+    lib.ddgs_status_string.restype = ctypes.c_char_p
+    assert lib.ddgs_status_string(0) == b"ok"
+    assert lib.ddgs_status_string(2) == b"pair capacity exceeded"
+
+
+def test_null_arguments_are_rejected_without_a_gpu(lib):
+    # argument validation happens on the host before any CUDA call
+    assert lib.ddgs_render(None, None, None, None, None, None, None, None) == 1
+    assert lib.ddgs_workspace_create(None) == 1
+    assert lib.ddgs_l1_loss(None, None, 0, -1, 0, None, None, None) == 1
