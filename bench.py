@@ -1,0 +1,485 @@
+#!/usr/bin/env python
+"""Benchmark: DRR forward+backward renders/s, 500k Gaussians, 256^2 detector,
+64 candidate poses per step (one pose-registration step), batched vs plain.
+
+One step = render the 64 poses, per-view L1 loss against the target image,
+backward to the per-pose gradients dL/d(pose) (Sec. 4.3's registration step).
+  batched: one ddgs_render / ddgs_l1_loss / ddgs_render_backward sequence over
+           all 64 views, captured once in a CUDA graph and replayed;
+  plain:   64 x (ddgs_render + loss + ddgs_render_backward) with one view each.
+The headline value is the batched throughput. Inputs are seeded synthetic
+data (a 256^3 ellipsoid CT phantom stands in for the paper's CT datasets).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun, one rank per GPU) every rank renders its own 64 poses
+(weak scaling, no data-path collective); value = all ranks' renders / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DRR fwd+bwd renders/s at 500k Gaussians, 256² det, 64 poses batched vs plain"
+UNIT = "renders/s"
+N_GAUSS, N_VIEWS, SIZE, GRID = 500_000, 64, 256, 256
+
+
+def _dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def shard_seed(rank: int) -> int:
+    """Each rank's candidate poses come from their own seed (independent units)."""
+    return 1000 + rank
+
+
+def workload(rank: int = 0, n_gauss=N_GAUSS, n_views=N_VIEWS, size=SIZE, grid=GRID):
+    from paper_2406_02518_gb300 import synthetic as syn
+    scene, views, st = syn.registration_workload(n_gauss, n_views, size, grid, seed=0)
+    rng = np.random.default_rng(shard_seed(rank))
+    views.world_to_cam = syn.registration_poses(rng, n_views, syn.SID_MM)
+    return scene, views, st
+
+
+class Clocks:
+    """nvidia-smi clock sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, path):
+        self.path = path
+        self.proc = None
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self, device_index=0):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9 or not p[0].isdigit() or int(p[0]) != device_index:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, p[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def cpu_baseline(scene, views, st, target, n_pix=4096, n_small=16):
+    """The oracle, as it stands, on a bounded sample: view 0, n_pix random
+    pixels, forward + L1 backward; per-view setup separated from the per-pixel
+    cost by a two-point fit, then scaled to a full 256^2 render."""
+    import dataclasses
+
+    import oracle
+    from paper_2406_02518_gb300 import synthetic as syn
+    v1 = dataclasses.replace(views, world_to_cam=views.world_to_cam[:1].copy(),
+                             detector=views.detector[:1].copy())
+    d32 = oracle.project32(scene, v1, st)["depth"]
+    hw = views.height * views.width
+
+    def run(npx, seed):
+        pix = syn.sample_pixels(v1, n_random=npx, n_rows=0, seed=seed)
+        t0 = time.perf_counter()
+        r = oracle.render(scene, v1, st, pix=pix, depth32=d32)
+        tgt = target[pix[:, 1], pix[:, 2]]
+        w = np.sign(r["image"] - tgt) / hw
+        oracle.render_backward(scene, v1, st, w, pix=pix, depth32=d32)
+        return time.perf_counter() - t0, pix.shape[0], float(r["n_contrib"].mean())
+
+    t_small, p_small, _ = run(n_small, 1)
+    t_big, p_big, contrib = run(n_pix, 2)
+    per_px = max(t_big - t_small, 1e-9) / (p_big - p_small)
+    per_render = t_small + per_px * (hw - p_small)
+    cores = os.cpu_count() or 1
+    return {"value": 1.0 / per_render, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"view 0 of 64: {p_big} random pixels (+{p_small}) fwd+L1 bwd through the FP64 "
+                       f"oracle (all Gaussians per pixel, no tiles); per-render time = setup + "
+                       f"per-pixel x 65536 px ({t_small + t_big:.1f} s measured)"),
+            "contrib_per_pixel": contrib}
+
+
+def target_image(scene, views, st, oracle_render=False):
+    """Target X-ray: the rendering at the unperturbed AP pose."""
+    from paper_2406_02518_gb300 import synthetic as syn
+    ap = syn.Views(syn.ap_pose(syn.SID_MM), views.detector[:1].copy(), views.height, views.width)
+    if oracle_render:
+        import oracle
+        return oracle.render(scene, ap, st)["image"][0]
+    import torch
+
+    from paper_2406_02518_gb300 import binding as B
+    ws = B.Workspace()
+    img, _, _ = B.render(B.cloud_from_arrays(scene), B.views_from_arrays(ap),
+                         B.config_from_settings(st), ws)
+    out = img[0].clone()
+    torch.cuda.synchronize()
+    ws.close()
+    return out
+
+
+def run_reference(args):
+    rank, world, _ = _dist_env()
+    if rank != 0:
+        return 0
+    scene, views, st = workload(0)
+    # The L1 target (the AP view) is rendered by the oracle at each step's
+    # sampled pixels, outside the timed part of the step.
+    import dataclasses
+
+    import oracle
+    from paper_2406_02518_gb300 import synthetic as syn
+    v1 = dataclasses.replace(views, world_to_cam=views.world_to_cam[:1].copy(),
+                             detector=views.detector[:1].copy())
+    ap = syn.Views(syn.ap_pose(syn.SID_MM), views.detector[:1].copy(), views.height, views.width)
+    d32 = oracle.project32(scene, v1, st)["depth"]
+    d32_ap = oracle.project32(scene, ap, st)["depth"]
+    hw = views.height * views.width
+    n_pix = 1024
+
+    def step(seed, npx=n_pix):
+        pix = syn.sample_pixels(v1, n_random=npx, n_rows=0, seed=seed)
+        tgt = oracle.render(scene, ap, st, pix=pix, depth32=d32_ap)["image"]
+        t0 = time.perf_counter()
+        r = oracle.render(scene, v1, st, pix=pix, depth32=d32)
+        w = np.sign(r["image"] - tgt) / hw
+        oracle.render_backward(scene, v1, st, w, pix=pix, depth32=d32)
+        return time.perf_counter() - t0, pix.shape[0]
+
+    # per-view setup (projection + depth order of every Gaussian, both passes)
+    t_setup, p_setup = step(99, npx=16)
+    for k in range(args.warmup):
+        step(100 + k)
+    ts, renders = [], []
+    for k in range(args.steps):
+        t, p = step(200 + k)
+        ts.append(t)
+        per_px = max(t - t_setup, 1e-9) / (p - p_setup)
+        renders.append(t_setup + per_px * (hw - p_setup))
+    per_render = sum(renders) / len(renders)
+    value = 1.0 / per_render
+    cores = os.cpu_count() or 1
+    sample = (f"each step: view 0, {n_pix} random pixels of 256^2, FP64 oracle fwd + L1 bwd over all "
+              f"500k Gaussians; per render = setup + per-pixel time x 65536 (setup from a 16-pixel call)")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sum(ts) / len(ts), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "pose registration step: 500k Gaussians (256^3 phantom), 64 poses, "
+                                   "256x256 detector, fwd+bwd to pose gradients",
+                       "global_batch": N_VIEWS, "seq_len": None, "parallelism": "oracle (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def algorithmic_bytes(kernel, s):
+    """Algorithmic DRAM bytes per launch of an HBM-bound kernel."""
+    M, N, V = s["pairs"], s["n"], s["views"]
+    return {
+        "radix_downsweep": 24 * M,          # read + write 8 B key + 4 B value
+        "radix_upsweep": 8 * M,             # read keys
+        "emit_keys": 16 * N * V + 12 * M,   # read binning record, write key + value
+        "preprocess_fwd": 76 * N + 48 * N * V,  # read params once, write 48 B records
+        "preprocess_bwd": 76 * N + 32 * N * V,  # read params once, read 2D gradients
+        "tile_ranges": 8 * M,
+    }.get(kernel)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2406_02518_gb300 import binding as B
+    from paper_2406_02518_gb300 import build as bld
+
+    rank, world, local = _dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    bld.build()
+    B.load()
+    if not B.device_supported():
+        raise RuntimeError("needs an sm_103 (GB300) device")
+
+    scene, views, st = workload(rank, size=args.size, n_gauss=args.n_gauss)
+    H, W, V = views.height, views.width, views.n_views
+    cloud = B.cloud_from_arrays(scene)
+    gv = B.views_from_arrays(views)
+    cfg = B.config_from_settings(st)
+    target = target_image(scene, views, st)
+    dev = torch.device("cuda", local)
+
+    # size the workspace once with a synchronising render, then go graph-only
+    ws = B.Workspace()
+    B.render(cloud, gv, cfg, ws)
+    torch.cuda.synchronize()
+    pairs = ws.pairs()
+    tiles = V * (-(-W // st.tile)) * (-(-H // st.tile))
+    ws.reserve(V * scene.n, int(pairs * 1.10) + 4096, tiles)
+    cfg_ns = B.config_from_settings(st, no_sync=True)
+    img = torch.empty((V, H, W), dtype=torch.float32, device=dev)
+    tf = torch.empty_like(img)
+    nl = torch.empty((V, H, W), dtype=torch.int32, device=dev)
+    loss = torch.empty(V, dtype=torch.float32, device=dev)
+    dL = torch.empty_like(img)
+    gpose = torch.empty((V, 3, 4), dtype=torch.float32, device=dev)
+
+    def step():
+        B.render(cloud, gv, cfg_ns, ws, out=(img, tf, nl))
+        B.l1_loss(img, target, loss=loss, grad=dL)
+        B.render_backward(cloud, gv, cfg_ns, ws, dL, tf, nl, want=["world_to_cam"],
+                          out={"world_to_cam": gpose})
+
+    # capture the batched step in a CUDA graph
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        step()
+    torch.cuda.current_stream().wait_stream(s)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    torch.cuda.synchronize()
+    assert ws.sync_status() == 0, "pair capacity exceeded"
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- batched, graph replay (headline) ----
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    launches0 = B.kernel_launches()
+    clocks = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
+                    if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/ddgs_clocks_{rank}.csv")
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        graph.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    ms_batched = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+    clk = clocks.stop(local)
+    status = ws.sync_status()
+    assert status == 0, f"device status {status}"
+    # kernels per step: count one eager step (a graph replay launches the same kernels)
+    l0 = B.kernel_launches()
+    step()
+    torch.cuda.synchronize()
+    kernels_per_step = B.kernel_launches() - l0
+
+    # ---- per-kernel times (same kernels, eager, CUDA events on the launch stream) ----
+    B.profiler_enable(True)
+    prof_steps = max(2, min(args.steps, 5))
+    for _ in range(prof_steps):
+        step()
+    torch.cuda.synchronize()
+    prof = B.profiler_collect()
+    B.profiler_enable(False)
+
+    # ---- plain: one pose per launch sequence, host loop ----
+    ws_p = B.Workspace()
+    views1 = [B.Views(gv.world_to_cam[v:v + 1], gv.detector[v:v + 1], H, W) for v in range(V)]
+    img1 = torch.empty((1, H, W), dtype=torch.float32, device=dev)
+    tf1, nl1 = torch.empty_like(img1), torch.empty((1, H, W), dtype=torch.int32, device=dev)
+    loss1, dL1 = torch.empty(1, dtype=torch.float32, device=dev), torch.empty_like(img1)
+    gp1 = torch.empty((1, 3, 4), dtype=torch.float32, device=dev)
+
+    def plain_step():
+        for v1 in views1:
+            B.render(cloud, v1, cfg, ws_p, out=(img1, tf1, nl1))
+            B.l1_loss(img1, target, loss=loss1, grad=dL1)
+            B.render_backward(cloud, v1, cfg, ws_p, dL1, tf1, nl1, want=["world_to_cam"],
+                              out={"world_to_cam": gp1})
+
+    plain_step()
+    torch.cuda.synchronize()
+    plain_steps = max(1, args.steps // 4)
+    barrier()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record()
+    for _ in range(plain_steps):
+        plain_step()
+    p1.record()
+    torch.cuda.synchronize()
+    ms_plain = max_over_ranks(p0.elapsed_time(p1) / plain_steps)
+
+    # ---- end to end through the API with host buffers ----
+    poses_h = torch.empty((V, 3, 4), dtype=torch.float32).pin_memory()
+    poses_h.copy_(torch.from_numpy(views.world_to_cam))
+    target_h = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    target_h.copy_(target.cpu())
+    gpose_h = torch.empty((V, 3, 4), dtype=torch.float32).pin_memory()
+    loss_h = torch.empty(V, dtype=torch.float32).pin_memory()
+    e2e_steps = args.steps
+    for it in range(e2e_steps + 1):
+        if it == 1:
+            torch.cuda.synchronize()
+            barrier()
+            t0 = time.perf_counter()
+        gv.world_to_cam.copy_(poses_h, non_blocking=True)
+        target.copy_(target_h, non_blocking=True)
+        graph.replay()
+        gpose_h.copy_(gpose, non_blocking=True)
+        loss_h.copy_(loss, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    t_e2e = max_over_ranks((time.perf_counter() - t0) / e2e_steps)
+
+    renders_step = V * world
+    value = renders_step / (ms_batched / 1e3)
+    plain_value = renders_step / (ms_plain / 1e3)
+    h2d = poses_h.numel() * 4 + target_h.numel() * 4
+    d2h = gpose_h.numel() * 4 + loss_h.numel() * 4
+
+    # ---- roofline of the dominant kernel ----
+    peaks = measured_peaks()
+    per_launch = {k: (ms / max(n, 1), n / prof_steps) for k, (ms, n) in prof.items()}
+    total_ms = sum(ms for ms, _ in prof.values())
+    dom = max(prof.items(), key=lambda kv: kv[1][0])[0]
+    shape = {"pairs": pairs, "n": scene.n, "views": V}
+    roof = None
+    algb = algorithmic_bytes(dom, shape)
+    ms_launch = per_launch[dom][0]
+    if algb is not None:
+        peak = peaks.get("hbm_gbs", 6800.0)
+        ach = algb / (ms_launch / 1e3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "traffic": None,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    else:
+        roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s",
+                "frac": None, "traffic": None, "note": "see rasteriser ALU roofline in kernels"}
+    kernels = {k: {"ms_per_launch": round(v[0], 4), "launches_per_step": v[1],
+                   "share": round(prof[k][0] / total_ms, 4)} for k, v in per_launch.items()}
+    for k in kernels:
+        b = algorithmic_bytes(k, shape)
+        if b is not None:
+            kernels[k]["algorithmic_GBps"] = round(b / (per_launch[k][0] / 1e3) / 1e9, 1)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(scene, views, st, target.cpu().numpy())
+        rcp = cpu.pop("contrib_per_pixel")
+        # ALU roofline of the rasterisers from the blended-pair count
+        blended = rcp * H * W * V
+        sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1447.0)
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
+        for k, ops in (("raster_fwd", 15 + 1), ("raster_bwd", 45 + 1)):
+            if k in per_launch:
+                tf_s = blended * ops / (per_launch[k][0] / 1e3) / 1e12
+                kernels[k]["algorithmic_TFLOPs"] = round(tf_s, 3)
+                kernels[k]["fp32_peak_TFLOPs"] = round(fp32_peak, 1)
+                kernels[k]["alu_frac"] = round(tf_s / fp32_peak, 4)
+                if k == dom:
+                    roof = {"kernel": dom, "bound": "alu", "achieved": tf_s, "peak": fp32_peak,
+                            "unit": "TFLOP/s", "frac": tf_s / fp32_peak, "traffic": None,
+                            "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_batched, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"pose registration step: {scene.n} Gaussians (256^3 ellipsoid phantom), "
+                                   f"{V} poses, {H}x{W} detector, fwd + L1 + bwd to pose gradients",
+                       "global_batch": V * world, "seq_len": None,
+                       "parallelism": f"dp{world} (independent pose batches)",
+                       "l2": "working set larger than L2 (records 1.5 GB, pairs 0.6 GB per step)",
+                       "graph": "batched step replayed from one CUDA graph"},
+            "plain": {"value": plain_value, "ms_per_step": ms_plain,
+                      "how": "64 x (ddgs_render + ddgs_l1_loss + ddgs_render_backward), 1 view each"},
+            "batched_over_plain": value / plain_value,
+            "pairs_per_step": pairs,
+            "e2e": {"value": renders_step / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": kernels_per_step * args.steps,
+            "kernels_per_step": kernels_per_step,
+            "clocks": clk, "roofline": roof, "kernels": kernels, "cpu_baseline": cpu}
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--size", type=int, default=SIZE)
+    ap.add_argument("--n-gauss", type=int, default=N_GAUSS)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -193,6 +193,23 @@ const char *ddgs_last_cuda_error(void);
 /* 1 if a device of compute capability 10.3 is current and usable. Host only. */
 int32_t ddgs_device_supported(void);
 
+/* ---- tracing (no counterpart in the paper; measurement support) ----
+ * Number of kernels this library has launched in this process. Host only. */
+int64_t ddgs_kernel_launches(void);
+
+/* When enabled, every kernel launch is bracketed by two CUDA events recorded
+ * on the launch's own stream (not inside CUDA-graph capture). Host only. */
+ddgs_status ddgs_profiler_enable(int32_t on);
+
+/* Wait for the recorded events, then write per kernel id the summed device
+ * time in milliseconds and the launch count (arrays of max_kernels entries,
+ * host memory), set *n_kernels to the number of kernel ids, and reset. */
+ddgs_status ddgs_profiler_collect(int32_t max_kernels, double *total_ms,
+                                  int64_t *launches, int32_t *n_kernels);
+
+/* Name of a kernel id reported by ddgs_profiler_collect ("" if out of range). */
+const char *ddgs_profiler_kernel_name(int32_t id);
+
 #ifdef __cplusplus
 }
 #endif

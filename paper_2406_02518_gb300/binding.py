@@ -28,7 +28,9 @@ _STATUS = {0: "ok", 1: "invalid argument", 2: "pair capacity exceeded", 3: "non-
 EXPORTS = ["ddgs_workspace_create", "ddgs_workspace_destroy", "ddgs_workspace_reserve",
            "ddgs_render", "ddgs_render_backward", "ddgs_l1_loss", "ddgs_workspace_pairs",
            "ddgs_debug_binning", "ddgs_sync_status", "ddgs_parameter_count",
-           "ddgs_status_string", "ddgs_last_cuda_error", "ddgs_device_supported"]
+           "ddgs_status_string", "ddgs_last_cuda_error", "ddgs_device_supported",
+           "ddgs_kernel_launches", "ddgs_profiler_enable", "ddgs_profiler_collect",
+           "ddgs_profiler_kernel_name"]
 
 
 class DDGSError(RuntimeError):
@@ -93,9 +95,15 @@ def load(path: Optional[str] = None):
     lib.ddgs_status_string.restype = C.c_char_p
     lib.ddgs_last_cuda_error.restype = C.c_char_p
     lib.ddgs_device_supported.restype = i32
+    lib.ddgs_kernel_launches.restype = i64
+    lib.ddgs_profiler_enable.argtypes = [i32]
+    lib.ddgs_profiler_collect.argtypes = [i32, vp, vp, vp]
+    lib.ddgs_profiler_kernel_name.argtypes = [i32]
+    lib.ddgs_profiler_kernel_name.restype = C.c_char_p
     for name in EXPORTS:
         if name not in ("ddgs_parameter_count", "ddgs_status_string", "ddgs_last_cuda_error",
-                        "ddgs_device_supported"):
+                        "ddgs_device_supported", "ddgs_kernel_launches",
+                        "ddgs_profiler_kernel_name"):
             getattr(lib, name).restype = i32
     _lib = lib
     return lib
@@ -310,6 +318,28 @@ def debug_binning(ws: Workspace, n_views: int, n: int, n_tiles: int):
     torch.cuda.current_stream().synchronize()
     return dict(tiles_touched=tt.cpu().numpy().view(np.uint32), keys=keys[:m].cpu().numpy().view(np.uint64),
                 vals=vals[:m].cpu().numpy().view(np.uint32), ranges=rng.cpu().numpy().view(np.uint32), m=m)
+
+
+def kernel_launches() -> int:
+    """Kernels this library has launched in this process."""
+    return int(load().ddgs_kernel_launches())
+
+
+def profiler_enable(on: bool = True):
+    _check(load().ddgs_profiler_enable(int(on)), "ddgs_profiler_enable")
+
+
+def profiler_collect() -> dict:
+    """{kernel name: (total ms, launches)} since the last collect; resets."""
+    lib = load()
+    n = 64
+    ms = (C.c_double * n)()
+    cnt = (C.c_int64 * n)()
+    nk = C.c_int32()
+    _check(lib.ddgs_profiler_collect(n, C.addressof(ms), C.addressof(cnt), C.addressof(nk)),
+           "ddgs_profiler_collect")
+    return {lib.ddgs_profiler_kernel_name(i).decode(): (ms[i], cnt[i]) for i in range(nk.value)
+            if cnt[i] > 0}
 
 
 def parameter_count(n: int, k: int = 8, L: int = 1) -> int:

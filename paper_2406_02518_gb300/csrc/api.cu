@@ -1,8 +1,11 @@
 // api.cu -- the C ABI: argument checks, workspace management and the order of
 // the kernels of a render and of its backward pass.
+#include <atomic>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <vector>
 
 #include "ddgs_internal.cuh"
 
@@ -119,9 +122,102 @@ ddgs_status ensure_pairs(ddgs_workspace *ws, int64_t pairs) {
   return DDGS_OK;
 }
 
+// ---- launch counter and event profiler ----
+std::atomic<int64_t> g_launches{0};
+std::atomic<int> g_prof_on{0};
+std::mutex g_prof_mu;
+struct ProfRec {
+  int id;
+  cudaEvent_t a, b;
+};
+std::vector<ProfRec> g_pending;
+std::vector<cudaEvent_t> g_pool;
+const char *const KERNEL_NAMES[ddgs::KID_COUNT] = {
+    "preprocess_fwd", "scan_blocks", "emit_keys", "radix_upsweep", "radix_scan",
+    "radix_downsweep", "tile_ranges", "raster_fwd", "l1_loss", "raster_bwd",
+    "preprocess_bwd", "debug_copy"};
+
+cudaEvent_t pool_event() {  // caller holds g_prof_mu
+  if (!g_pool.empty()) {
+    cudaEvent_t e = g_pool.back();
+    g_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+bool capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return true;
+  return cs != cudaStreamCaptureStatusNone;
+}
+
 }  // namespace
 
+ddgs::LaunchScope::LaunchScope(int kid, cudaStream_t s) : id(kid), st(s) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  if (!g_prof_on.load(std::memory_order_relaxed) || capturing(s)) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  ev0 = pool_event();
+  if (ev0 && cudaEventRecord(ev0, s) != cudaSuccess) {
+    g_pool.push_back(ev0);
+    ev0 = nullptr;
+  }
+}
+
+ddgs::LaunchScope::~LaunchScope() {
+  if (!ev0) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  cudaEvent_t e1 = pool_event();
+  if (e1 && cudaEventRecord(e1, st) == cudaSuccess) {
+    g_pending.push_back({id, ev0, e1});
+  } else {
+    g_pool.push_back(ev0);
+    if (e1) g_pool.push_back(e1);
+  }
+}
+
 extern "C" {
+
+int64_t ddgs_kernel_launches(void) { return g_launches.load(); }
+
+ddgs_status ddgs_profiler_enable(int32_t on) {
+  g_prof_on.store(on ? 1 : 0);
+  return DDGS_OK;
+}
+
+ddgs_status ddgs_profiler_collect(int32_t max_kernels, double *total_ms, int64_t *launches,
+                                  int32_t *n_kernels) {
+  if (max_kernels < 0 || (max_kernels > 0 && (!total_ms || !launches))) return DDGS_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (int k = 0; k < max_kernels; ++k) {
+    total_ms[k] = 0.0;
+    launches[k] = 0;
+  }
+  ddgs_status st = DDGS_OK;
+  for (const ProfRec &r : g_pending) {
+    float ms = 0.f;
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+    if (e != cudaSuccess) {
+      st = cuda_fail(e, "profiler event");
+    } else if (r.id < max_kernels) {
+      total_ms[r.id] += ms;
+      launches[r.id] += 1;
+    }
+    g_pool.push_back(r.a);
+    g_pool.push_back(r.b);
+  }
+  g_pending.clear();
+  if (n_kernels) *n_kernels = ddgs::KID_COUNT;
+  return st;
+}
+
+const char *ddgs_profiler_kernel_name(int32_t id) {
+  return (id >= 0 && id < ddgs::KID_COUNT) ? KERNEL_NAMES[id] : "";
+}
 
 const char *ddgs_status_string(ddgs_status s) {
   switch (s) {
@@ -342,6 +438,7 @@ void launch_l1_loss(const float *image, const float *target, int per_view, int V
   int64_t bx = (hw + 255) / 256;
   if (bx > 64) bx = 64;
   dim3 grid((unsigned)bx, (unsigned)V);
+  LaunchScope ls(KID_L1_LOSS, st);
   l1_loss_kernel<<<grid, 256, 0, st>>>(image, target, per_view, hw, loss, grad);
 }
 }  // namespace ddgs
@@ -356,6 +453,7 @@ ddgs_status ddgs_debug_binning(const ddgs_workspace *ws, uint32_t *tiles_touched
   if (tiles_touched && s.records > 0) {
     int64_t b = (s.records + 255) / 256;
     if (b > 4096) b = 4096;
+    ddgs::LaunchScope ls(ddgs::KID_DEBUG, s_);
     tiles_touched_kernel<<<(unsigned)b, 256, 0, s_>>>(reinterpret_cast<const uint4 *>(ws->rect),
                                                       s.records, tiles_touched);
     CK(cudaGetLastError());

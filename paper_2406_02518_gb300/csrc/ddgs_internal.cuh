@@ -109,6 +109,22 @@ struct ddgs_workspace {
 
 namespace ddgs {
 
+// Kernel ids of the launch counter and profiler (api.cu).
+enum KernelId : int {
+  KID_PREPROCESS_FWD = 0, KID_SCAN_BLOCKS, KID_EMIT_KEYS, KID_RADIX_UPSWEEP, KID_RADIX_SCAN,
+  KID_RADIX_DOWNSWEEP, KID_TILE_RANGES, KID_RASTER_FWD, KID_L1_LOSS, KID_RASTER_BWD,
+  KID_PREPROCESS_BWD, KID_DEBUG, KID_COUNT
+};
+
+// Brackets one kernel launch: counts it and, when profiling, records events.
+struct LaunchScope {
+  int id;
+  cudaStream_t st;
+  cudaEvent_t ev0 = nullptr;
+  LaunchScope(int kid, cudaStream_t s);
+  ~LaunchScope();
+};
+
 // preprocess.cu
 void launch_preprocess_fwd(const ddgs_gaussians &g, const ddgs_views &v, const ddgs_config &c,
                            const RenderShape &s, ddgs_workspace &ws, cudaStream_t st);

@@ -702,7 +702,10 @@ void launch_preprocess_fwd(const ddgs_gaussians &g, const ddgs_views &v, const d
   a.rec0 = ws.rec0; a.rec1 = ws.rec1; a.bin_info = reinterpret_cast<uint4 *>(ws.rect);
   a.blk_total = ws.blk_total;
   const int64_t nb = preprocess_blocks(s);
-  if (nb > 0) preprocess_fwd_kernel<<<(unsigned)nb, PRE_THREADS, 0, st>>>(a);
+  if (nb > 0) {
+    LaunchScope ls(KID_PREPROCESS_FWD, st);
+    preprocess_fwd_kernel<<<(unsigned)nb, PRE_THREADS, 0, st>>>(a);
+  }
 }
 
 void launch_emit_keys(const RenderShape &s, ddgs_workspace &ws, cudaStream_t st) {
@@ -715,7 +718,10 @@ void launch_emit_keys(const RenderShape &s, ddgs_workspace &ws, cudaStream_t st)
   a.cap = (uint64_t)ws.pair_cap;
   a.status = ws.d_status;
   const int64_t nb = preprocess_blocks(s);
-  if (nb > 0) emit_keys_kernel<<<(unsigned)nb, PRE_THREADS, 0, st>>>(a);
+  if (nb > 0) {
+    LaunchScope ls(KID_EMIT_KEYS, st);
+    emit_keys_kernel<<<(unsigned)nb, PRE_THREADS, 0, st>>>(a);
+  }
 }
 
 void launch_preprocess_bwd(const ddgs_gaussians &g, const ddgs_views &v, const ddgs_config &c,
@@ -734,7 +740,10 @@ void launch_preprocess_bwd(const ddgs_gaussians &g, const ddgs_views &v, const d
   a.want_basis = (out.b_iso || out.B_dir) ? 1 : 0;
   a.want_pose = out.world_to_cam ? 1 : 0;
   const int64_t nb = preprocess_blocks(s);
-  if (nb > 0) preprocess_bwd_kernel<<<(unsigned)nb, PRE_THREADS, 0, st>>>(a);
+  if (nb > 0) {
+    LaunchScope ls(KID_PREPROCESS_BWD, st);
+    preprocess_bwd_kernel<<<(unsigned)nb, PRE_THREADS, 0, st>>>(a);
+  }
 }
 
 }  // namespace ddgs

@@ -268,14 +268,18 @@ __global__ void __launch_bounds__(T *T) raster_bwd_kernel(RasterArgs a) {
 
 template <int T>
 void launch_fwd_t(const RasterArgs &a, cudaStream_t st) {
-  if (a.s.total_tiles > 0)
+  if (a.s.total_tiles > 0) {
+    LaunchScope ls(KID_RASTER_FWD, st);
     raster_fwd_kernel<T><<<(unsigned)a.s.total_tiles, T * T, 0, st>>>(a);
+  }
 }
 
 template <int T>
 void launch_bwd_t(const RasterArgs &a, cudaStream_t st) {
-  if (a.s.total_tiles > 0)
+  if (a.s.total_tiles > 0) {
+    LaunchScope ls(KID_RASTER_BWD, st);
     raster_bwd_kernel<T><<<(unsigned)a.s.total_tiles, T * T, 0, st>>>(a);
+  }
 }
 
 }  // namespace

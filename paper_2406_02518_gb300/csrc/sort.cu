@@ -216,6 +216,7 @@ __global__ void tile_ranges_kernel(const uint64_t *keys, const uint64_t *d_pairs
 }  // namespace
 
 void launch_scan_blocks(int64_t nblk, ddgs_workspace &ws, cudaStream_t st) {
+  LaunchScope ls(KID_SCAN_BLOCKS, st);
   scan_blocks_kernel<<<1, 1024, 0, st>>>(ws.blk_total, ws.blk_offset, nblk, ws.d_pairs, nullptr);
 }
 
@@ -232,12 +233,21 @@ void launch_radix_sort(const RenderShape &s, uint64_t pair_bound, ddgs_workspace
     for (int p = 0; p < passes; ++p) {
       const int shift = p * RADIX_BITS;
       cudaMemsetAsync(ws.digit_total, 0, RADIX * sizeof(uint32_t), st);
-      radix_upsweep_kernel<<<(unsigned)nblk, SORT_THREADS, 0, st>>>(
-          ws.keys[cur], ws.d_pairs, (uint64_t)ws.pair_cap, shift, ws.hist, ws.digit_total, nblk);
-      radix_scan_kernel<<<RADIX, 1024, 0, st>>>(ws.hist, ws.digit_total, nblk);
-      radix_downsweep_kernel<<<(unsigned)nblk, SORT_THREADS, 0, st>>>(
-          ws.keys[cur], ws.vals[cur], ws.keys[cur ^ 1], ws.vals[cur ^ 1], ws.d_pairs,
-          (uint64_t)ws.pair_cap, shift, ws.hist, nblk);
+      {
+        LaunchScope ls(KID_RADIX_UPSWEEP, st);
+        radix_upsweep_kernel<<<(unsigned)nblk, SORT_THREADS, 0, st>>>(
+            ws.keys[cur], ws.d_pairs, (uint64_t)ws.pair_cap, shift, ws.hist, ws.digit_total, nblk);
+      }
+      {
+        LaunchScope ls(KID_RADIX_SCAN, st);
+        radix_scan_kernel<<<RADIX, 1024, 0, st>>>(ws.hist, ws.digit_total, nblk);
+      }
+      {
+        LaunchScope ls(KID_RADIX_DOWNSWEEP, st);
+        radix_downsweep_kernel<<<(unsigned)nblk, SORT_THREADS, 0, st>>>(
+            ws.keys[cur], ws.vals[cur], ws.keys[cur ^ 1], ws.vals[cur ^ 1], ws.d_pairs,
+            (uint64_t)ws.pair_cap, shift, ws.hist, nblk);
+      }
       cur ^= 1;
     }
   }
@@ -250,6 +260,7 @@ void launch_tile_ranges(const RenderShape &s, uint64_t pair_bound, ddgs_workspac
   if (pair_bound == 0) return;
   int64_t blocks = (int64_t)((pair_bound + 255) / 256);
   if (blocks > 152 * 32) blocks = 152 * 32;
+  LaunchScope ls(KID_TILE_RANGES, st);
   tile_ranges_kernel<<<(unsigned)blocks, 256, 0, st>>>(ws.keys[ws.sorted], ws.d_pairs,
                                                        (uint64_t)ws.pair_cap, ws.ranges,
                                                        (uint64_t)s.total_tiles);
