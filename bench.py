@@ -249,7 +249,7 @@ def run_ours(args):
     if not B.device_supported():
         raise RuntimeError("needs an sm_103 (GB300) device")
 
-    scene, views, st = workload(rank, size=args.size, n_gauss=args.n_gauss)
+    scene, views, st = workload(rank, size=args.size, n_gauss=args.n_gauss, n_views=args.views)
     H, W, V = views.height, views.width, views.n_views
     cloud = B.cloud_from_arrays(scene)
     gv = B.views_from_arrays(views)
@@ -277,6 +277,20 @@ def run_ours(args):
         B.l1_loss(img, target, loss=loss, grad=dL)
         B.render_backward(cloud, gv, cfg_ns, ws, dL, tf, nl, want=["world_to_cam"],
                           out={"world_to_cam": gpose})
+
+    if args.profile_step:
+        # ncu target: warm-up steps, then one eager step inside the NVTX range
+        # "ddgs_step" (capture with --nvtx --nvtx-include "ddgs_step/")
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("ddgs_step")
+        step()
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+        assert ws.sync_status() == 0
+        print(json.dumps({"profile_step": True, "views": V, "gaussians": scene.n, "pairs": pairs}))
+        return 0
 
     # capture the batched step in a CUDA graph
     s = torch.cuda.Stream()
@@ -473,6 +487,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--size", type=int, default=SIZE)
     ap.add_argument("--n-gauss", type=int, default=N_GAUSS)
+    ap.add_argument("--views", type=int, default=N_VIEWS)
+    ap.add_argument("--profile-step", action="store_true",
+                    help="run warm-up steps and one eager step in an NVTX range, then exit")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
