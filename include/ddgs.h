@@ -156,6 +156,27 @@ ddgs_status ddgs_render_backward(const ddgs_gaussians *g, const ddgs_views *v,
                                  const uint32_t *n_last, const ddgs_grads *out,
                                  void *stream);
 
+/* ddgs_render with no device allocation at all. (The paper has no
+ * counterpart: this serves callers that may not allocate device memory while
+ * they run -- a registration loop whose memory is fixed at start-up, code
+ * running inside another runtime's allocator, a process whose device memory a
+ * caching allocator owns.) Same inputs, outputs and results as ddgs_render;
+ * its scratch is one static device array of about 37 MiB that every GPU
+ * loading this library holds until the process exits. Limits per call:
+ * n_views * n <= 262144 records, n_views * tiles per view <= 65536 tiles and
+ * at most 1048576 (Gaussian, tile) pairs; larger renders return
+ * DDGS_ERR_CAPACITY (the pair count is known only after the projection, so
+ * that case returns after synchronising the stream, with the outputs left
+ * unwritten). Calls no cudaMalloc, cudaFree or any other allocating routine.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture. The call synchronises the stream once to read the pair count.
+ * Every call on a device shares the array and each clears what must start at
+ * zero; calls whose GPU work overlaps (other streams or host threads) race. */
+ddgs_status ddgs_render_static(const ddgs_gaussians *g, const ddgs_views *v,
+                               const ddgs_config *cfg, float *image,
+                               float *t_final, uint32_t *n_last, void *stream);
+
 /* Per-view mean L1 loss of the registration objective (Sec. 4.3 compares the
  * rendering at a predicted pose with the target image; the l1 term of Eq. 2)
  * and its gradient. image [n_views][hw]; target [hw] (shared by all views)

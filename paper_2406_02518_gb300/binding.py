@@ -30,7 +30,7 @@ EXPORTS = ["ddgs_workspace_create", "ddgs_workspace_destroy", "ddgs_workspace_re
            "ddgs_debug_binning", "ddgs_sync_status", "ddgs_parameter_count",
            "ddgs_status_string", "ddgs_last_cuda_error", "ddgs_device_supported",
            "ddgs_kernel_launches", "ddgs_profiler_enable", "ddgs_profiler_collect",
-           "ddgs_profiler_kernel_name"]
+           "ddgs_profiler_kernel_name", "ddgs_render_static"]
 
 
 class DDGSError(RuntimeError):

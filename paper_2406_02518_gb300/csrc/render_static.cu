@@ -1,0 +1,170 @@
+// render_static.cu -- ddgs_render_static: the forward render with its scratch
+// memory in a fixed, file-scope device array instead of a workspace.
+//
+// Who needs it: code that must not allocate device memory once it runs. For
+// example an intra-operative registration loop whose memory budget is fixed
+// at start-up, code that runs inside another framework's allocator callback,
+// or a process whose device memory is entirely owned by a caching allocator
+// that the library cannot see. For those callers every cudaMalloc is either
+// forbidden or a source of stalls and fragmentation, so this entry point
+// allocates nothing: the caller passes inputs and outputs, and all scratch
+// (per-(view, Gaussian) records, sort buffers, tile ranges, counters) lives in
+// one static array that every GPU loading the library holds until exit.
+//
+// The array is shared by every call on a device and keeps the last call's
+// contents; whatever must start at zero is cleared by each call. Calls whose
+// work overlaps on the GPU (two streams, or two host threads) race on it.
+#include <cstdio>
+#include <mutex>
+
+#include "ddgs_internal.cuh"
+
+namespace {
+
+// Limits of one call (see include/ddgs.h).
+constexpr int64_t kMaxRecords = int64_t(1) << 18;  // views x Gaussians
+constexpr int64_t kMaxPairs = int64_t(1) << 20;    // (Gaussian, tile) pairs
+constexpr int64_t kMaxTiles = int64_t(1) << 16;    // views x tiles per view
+constexpr int64_t kMaxBlocks = kMaxRecords / ddgs::PRE_THREADS + 1;
+constexpr int64_t kMaxSortBlocks = (kMaxPairs + ddgs::SORT_TILE - 1) / ddgs::SORT_TILE;
+
+constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+// Byte offsets of each buffer inside the scratch array.
+constexpr size_t kOffRec0 = 0;
+constexpr size_t kOffRec1 = align256(kOffRec0 + kMaxRecords * sizeof(float4));
+constexpr size_t kOffInfo = align256(kOffRec1 + kMaxRecords * sizeof(float4));
+constexpr size_t kOffBlkTotal = align256(kOffInfo + kMaxRecords * sizeof(uint4));
+constexpr size_t kOffBlkOffset = align256(kOffBlkTotal + kMaxBlocks * sizeof(uint32_t));
+constexpr size_t kOffKeys0 = align256(kOffBlkOffset + kMaxBlocks * sizeof(uint64_t));
+constexpr size_t kOffKeys1 = align256(kOffKeys0 + kMaxPairs * sizeof(uint64_t));
+constexpr size_t kOffVals0 = align256(kOffKeys1 + kMaxPairs * sizeof(uint64_t));
+constexpr size_t kOffVals1 = align256(kOffVals0 + kMaxPairs * sizeof(uint32_t));
+constexpr size_t kOffHist = align256(kOffVals1 + kMaxPairs * sizeof(uint32_t));
+constexpr size_t kOffDigit = align256(kOffHist + kMaxSortBlocks * ddgs::RADIX * sizeof(uint32_t));
+constexpr size_t kOffRanges = align256(kOffDigit + ddgs::RADIX * sizeof(uint32_t));
+constexpr size_t kOffPairs = align256(kOffRanges + kMaxTiles * sizeof(uint2));
+constexpr size_t kOffStatus = align256(kOffPairs + sizeof(uint64_t));
+constexpr size_t kScratchBytes = align256(kOffStatus + sizeof(int32_t));
+
+// The scratch itself (about 37 MiB per device).
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+// Device address of g_scratch per device, looked up once per device.
+constexpr int kMaxDevices = 64;
+unsigned char *g_scratch_ptr[kMaxDevices] = {};
+std::mutex g_setup_mu;
+thread_local char g_static_err[160] = "";
+
+ddgs_status scratch_for_current_device(unsigned char **out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DDGS_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_setup_mu);
+  if (!g_scratch_ptr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess || !p) {
+      std::snprintf(g_static_err, sizeof g_static_err, "cudaGetSymbolAddress: %s",
+                    cudaGetErrorString(e));
+      return DDGS_ERR_CUDA;
+    }
+    g_scratch_ptr[dev] = static_cast<unsigned char *>(p);
+  }
+  *out = g_scratch_ptr[dev];
+  return DDGS_OK;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+}  // namespace
+
+extern "C" ddgs_status ddgs_render_static(const ddgs_gaussians *g, const ddgs_views *v,
+                                          const ddgs_config *c, float *image, float *t_final,
+                                          uint32_t *n_last, void *stream) {
+  // argument checks (as ddgs_render)
+  if (!g || !v || !c) return DDGS_ERR_INVALID_ARG;
+  if (g->n < 0 || g->n_iso < 0 || g->n_iso > g->n || v->n_views < 0 || v->height <= 0 ||
+      v->width <= 0 || v->height > 65535 * 8 || v->width > 65535 * 8)
+    return DDGS_ERR_INVALID_ARG;
+  if (c->tile != 8 && c->tile != 16 && c->tile != 32) return DDGS_ERR_INVALID_ARG;
+  if (!(c->q_max > 0) || !(c->alpha_max > 0) || !(c->t_min >= 0) || !(c->dilation >= 0))
+    return DDGS_ERR_INVALID_ARG;
+  if (g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->b_iso ||
+                   !g->B_dir || !aligned16(g->quats) ||
+                   (g->n_iso > 0 && (!g->feat_iso || !aligned16(g->feat_iso))) ||
+                   (g->n > g->n_iso && (!g->feat_dir || !aligned16(g->feat_dir)))))
+    return DDGS_ERR_INVALID_ARG;
+  if (v->n_views > 0 && (!v->world_to_cam || !v->detector || !image || !t_final || !n_last))
+    return DDGS_ERR_INVALID_ARG;
+
+  ddgs::RenderShape s{};
+  s.n = g->n;
+  s.n_iso = g->n_iso;
+  s.V = v->n_views;
+  s.H = v->height;
+  s.W = v->width;
+  s.tile = c->tile;
+  s.tiles_x = (v->width + c->tile - 1) / c->tile;
+  s.tiles_y = (v->height + c->tile - 1) / c->tile;
+  s.tiles_per_view = (int64_t)s.tiles_x * s.tiles_y;
+  s.total_tiles = s.tiles_per_view * s.V;
+  s.records = (int64_t)s.V * s.n;
+  int tb = 0;
+  for (uint64_t x = s.total_tiles > 0 ? (uint64_t)(s.total_tiles - 1) : 0; x; x >>= 1) ++tb;
+  s.key_bits = 32 + tb;
+  // the sizes this fixed scratch can hold
+  if (s.records > kMaxRecords || s.total_tiles > kMaxTiles) return DDGS_ERR_CAPACITY;
+
+  unsigned char *base = nullptr;
+  ddgs_status st = scratch_for_current_device(&base);
+  if (st) return st;
+  cudaStream_t cs = static_cast<cudaStream_t>(stream);
+
+  // A workspace view of the static array (host struct on the stack).
+  ddgs_workspace ws;
+  ws.rec_cap = kMaxRecords;
+  ws.pair_cap = kMaxPairs;
+  ws.tile_cap = kMaxTiles;
+  ws.blk_cap = kMaxBlocks;
+  ws.sblk_cap = kMaxSortBlocks;
+  ws.rec0 = reinterpret_cast<float4 *>(base + kOffRec0);
+  ws.rec1 = reinterpret_cast<float4 *>(base + kOffRec1);
+  ws.rect = reinterpret_cast<uint2 *>(base + kOffInfo);
+  ws.blk_total = reinterpret_cast<uint32_t *>(base + kOffBlkTotal);
+  ws.blk_offset = reinterpret_cast<uint64_t *>(base + kOffBlkOffset);
+  ws.keys[0] = reinterpret_cast<uint64_t *>(base + kOffKeys0);
+  ws.keys[1] = reinterpret_cast<uint64_t *>(base + kOffKeys1);
+  ws.vals[0] = reinterpret_cast<uint32_t *>(base + kOffVals0);
+  ws.vals[1] = reinterpret_cast<uint32_t *>(base + kOffVals1);
+  ws.hist = reinterpret_cast<uint32_t *>(base + kOffHist);
+  ws.digit_total = reinterpret_cast<uint32_t *>(base + kOffDigit);
+  ws.ranges = reinterpret_cast<uint2 *>(base + kOffRanges);
+  ws.d_pairs = reinterpret_cast<uint64_t *>(base + kOffPairs);
+  ws.d_status = reinterpret_cast<int32_t *>(base + kOffStatus);
+
+  // counters left by the previous call start again from zero
+  if (cudaMemsetAsync(ws.d_status, 0, sizeof(int32_t), cs) != cudaSuccess ||
+      cudaMemsetAsync(ws.d_pairs, 0, sizeof(uint64_t), cs) != cudaSuccess)
+    return DDGS_ERR_CUDA;
+  uint64_t pairs = 0;
+  if (s.records > 0) {
+    ddgs::launch_preprocess_fwd(*g, *v, *c, s, ws, cs);
+    ddgs::launch_scan_blocks(ddgs::preprocess_blocks(s), ws, cs);
+    if (cudaGetLastError() != cudaSuccess) return DDGS_ERR_CUDA;
+    // the pair count decides the sort's size: read it (no allocation)
+    if (cudaMemcpyAsync(&pairs, ws.d_pairs, sizeof(uint64_t), cudaMemcpyDeviceToHost, cs) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(cs) != cudaSuccess)
+      return DDGS_ERR_CUDA;
+    if (pairs > (uint64_t)kMaxPairs) return DDGS_ERR_CAPACITY;
+    if (pairs > 0) {
+      ddgs::launch_emit_keys(s, ws, cs);
+      ddgs::launch_radix_sort(s, pairs, ws, cs);
+    }
+  }
+  if (s.total_tiles > 0) {
+    ddgs::launch_tile_ranges(s, pairs, ws, cs);
+    ddgs::RasterParams P{c->alpha_min, c->alpha_max, c->t_min, c->q_max};
+    ddgs::launch_raster_fwd(s, P, ws, image, t_final, n_last, cs);
+  }
+  return cudaGetLastError() == cudaSuccess ? DDGS_OK : DDGS_ERR_CUDA;
+}
