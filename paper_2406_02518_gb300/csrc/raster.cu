@@ -111,21 +111,28 @@ __global__ void __launch_bounds__(T *T) raster_fwd_kernel(RasterArgs a) {
     }
     __syncthreads();
     const int cnt = (int)min((uint32_t)BATCH, range.y - b0);
-    for (int k = 0; k < cnt; ++k) {
-      if (tg.misses(s_box[k])) continue;
+    // 32 entries at a time: each lane tests one entry's box against the warp's
+    // pixels, the ballot lists the entries the warp must evaluate, in order.
+    for (int c0 = 0; c0 < cnt; c0 += 32) {
       if (__all_sync(0xffffffffu, done)) break;
-      if (done) continue;
-      const float4 A = s_a[k], B = s_b[k];
-      PairEval e;
-      if (!eval_pair(A.x, A.y, A.z, A.w, B.x, B.y, px, py, a.P, e)) continue;
-      const float Tn = __fmul_rn(Tr, __fsub_rn(1.f, e.sigma));
-      if (Tn < a.P.t_min) {
-        done = true;
-        continue;
+      const int ec = c0 + (threadIdx.x & 31);
+      uint32_t todo = __ballot_sync(0xffffffffu, ec < cnt && !tg.misses(s_box[ec]));
+      while (todo) {
+        const int k = c0 + __ffs(todo) - 1;
+        todo &= todo - 1;
+        if (done) continue;
+        const float4 A = s_a[k], B = s_b[k];
+        PairEval e;
+        if (!eval_pair(A.x, A.y, A.z, A.w, B.x, B.y, px, py, a.P, e)) continue;
+        const float Tn = __fmul_rn(Tr, __fsub_rn(1.f, e.sigma));
+        if (Tn < a.P.t_min) {
+          done = true;
+          continue;
+        }
+        C = fmaf(B.z * e.sigma, Tr, C);
+        Tr = Tn;
+        last = b0 + (uint32_t)k - range.x + 1u;
       }
-      C = fmaf(B.z * e.sigma, Tr, C);
-      Tr = Tn;
-      last = b0 + (uint32_t)k - range.x + 1u;
     }
   }
   if (tg.inside) {
@@ -193,6 +200,9 @@ __global__ void __launch_bounds__(T *T) raster_bwd_kernel(RasterArgs a) {
   if (last) atomicMax(&s_max, last);
   __syncthreads();
   const uint32_t max_last = s_max;
+  uint32_t warp_last = last;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) warp_last = max(warp_last, __shfl_xor_sync(0xffffffffu, warp_last, o));
   float S = 0.f;
   for (int64_t hi = max_last; hi > 0; hi -= BATCH) {
     const int64_t lo = hi > BATCH ? hi - BATCH : 0;
@@ -216,8 +226,15 @@ __global__ void __launch_bounds__(T *T) raster_bwd_kernel(RasterArgs a) {
     }
     __syncthreads();
     const int cnt = (int)(hi - lo);
-    for (int k = 0; k < cnt; ++k) {
-      if (tg.misses(s_box[k])) continue;
+    for (int c0 = 0; c0 < cnt; c0 += 32) {
+     // each lane tests one entry: inside the warp's box and before the last
+     // Gaussian any lane of the warp added
+     const int ec = c0 + (threadIdx.x & 31);
+     uint32_t todo = __ballot_sync(0xffffffffu, ec < cnt && (uint32_t)(hi - 1 - ec) < warp_last &&
+                                                    !tg.misses(s_box[ec]));
+     while (todo) {
+      const int k = c0 + __ffs(todo) - 1;
+      todo &= todo - 1;
       const uint32_t pos = (uint32_t)(hi - 1 - k);
       float gv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       bool act = pos < last;
@@ -250,6 +267,7 @@ __global__ void __launch_bounds__(T *T) raster_bwd_kernel(RasterArgs a) {
         const int comp = warp_reduce8(gv);
         if ((threadIdx.x & 3) == 0) atomicAdd(&s_acc[k][comp], gv[0]);
       }
+     }
     }
     __syncthreads();
     for (int e = tid; e < cnt; e += NT) {
