@@ -267,6 +267,11 @@ ddgs_status ddgs_workspace_create(ddgs_workspace **out) {
     return st;
   }
   *ws->h_pairs = 0;
+  if ((e = ddgs::prepare_sort_kernels()) != cudaSuccess) {
+    ddgs_status st = cuda_fail(e, "sort kernel set-up");
+    ddgs_workspace_destroy(ws);
+    return st;
+  }
   *out = ws;
   return DDGS_OK;
 }

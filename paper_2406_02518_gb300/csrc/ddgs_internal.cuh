@@ -141,6 +141,7 @@ void launch_radix_sort(const RenderShape &s, uint64_t pair_bound, ddgs_workspace
 void launch_tile_ranges(const RenderShape &s, uint64_t pair_bound, ddgs_workspace &ws,
                         cudaStream_t st);
 int64_t sort_blocks(uint64_t pair_bound);
+cudaError_t prepare_sort_kernels();  // once per device, before any capture
 
 // raster.cu
 void launch_raster_fwd(const RenderShape &s, const RasterParams &p, ddgs_workspace &ws,

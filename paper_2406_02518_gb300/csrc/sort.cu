@@ -14,6 +14,8 @@
 // (3) downsweep -- every block ranks its keys stably within the tile (warp
 // match + per-warp digit counters) and scatters keys and values. No block
 // waits on another, so no spin-waits are needed.
+#include <mutex>
+
 #include "ddgs_internal.cuh"
 
 namespace ddgs {
@@ -90,13 +92,33 @@ __global__ void __launch_bounds__(SORT_THREADS) radix_upsweep_kernel(
   __shared__ uint32_t s_hist[SORT_THREADS / 32][RADIX];
   const int tid = threadIdx.x, wid = tid >> 5;
   for (int d = tid; d < (SORT_THREADS / 32) * RADIX; d += SORT_THREADS) (&s_hist[0][0])[d] = 0;
-  __syncthreads();
   const uint64_t m = pair_count(d_pairs, cap);
   const uint64_t start = (uint64_t)blockIdx.x * SORT_TILE;
-#pragma unroll 4
-  for (int k = 0; k < SORT_ITEMS; ++k) {
-    const uint64_t j = start + (uint64_t)k * SORT_THREADS + tid;
-    if (j < m) atomicAdd(&s_hist[wid][(keys[j] >> shift) & (RADIX - 1)], 1u);
+  // all of the thread's loads first (two keys per 16-byte load), then count
+  uint64_t k[SORT_ITEMS];
+  const bool full = start + SORT_TILE <= m;
+  if (full) {
+    const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(keys + start);
+#pragma unroll
+    for (int r = 0; r < SORT_ITEMS / 2; ++r) {
+      const ulonglong2 v = p[r * SORT_THREADS + tid];
+      k[2 * r] = v.x;
+      k[2 * r + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < SORT_ITEMS / 2; ++r)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const uint64_t j = start + 2 * ((uint64_t)r * SORT_THREADS + tid) + h;
+        k[2 * r + h] = j < m ? keys[j] : ~0ull;
+      }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < SORT_ITEMS; ++r) {
+    const uint64_t j = start + 2 * ((uint64_t)(r >> 1) * SORT_THREADS + tid) + (r & 1);
+    if (j < m) atomicAdd(&s_hist[wid][(k[r] >> shift) & (RADIX - 1)], 1u);
   }
   __syncthreads();
   for (int d = tid; d < RADIX; d += SORT_THREADS) {
@@ -151,54 +173,108 @@ __global__ void __launch_bounds__(1024) radix_scan_kernel(uint32_t *hist, const 
   }
 }
 
+// Downsweep. Warp w of the block owns the contiguous segment
+// [w * 512, (w + 1) * 512) of the block's tile of 4096 keys and ranks its keys
+// stably with a warp-private counter per digit (warp match + leader update),
+// so the tile needs only a few block barriers. The tile is then staged in
+// shared memory in digit order and each digit's run is written out with
+// consecutive threads writing consecutive addresses.
+constexpr int DS_WARPS = SORT_THREADS / 32;
+constexpr int DS_SEG = SORT_TILE / DS_WARPS;  // 512 keys per warp
+constexpr size_t DS_DYN_SMEM = SORT_TILE * (sizeof(uint64_t) + sizeof(uint32_t));
+
 __global__ void __launch_bounds__(SORT_THREADS) radix_downsweep_kernel(
     const uint64_t *keys_in, const uint32_t *vals_in, uint64_t *keys_out, uint32_t *vals_out,
     const uint64_t *d_pairs, uint64_t cap, int shift, const uint32_t *offsets, int64_t nblk) {
-  constexpr int NW = SORT_THREADS / 32;
-  __shared__ uint32_t s_base[RADIX];     // running output position per digit
-  __shared__ uint32_t s_cnt[NW][RADIX];  // per-warp counts of the current round
+  extern __shared__ __align__(16) unsigned char ds_smem[];
+  uint64_t *s_keys = reinterpret_cast<uint64_t *>(ds_smem);
+  uint32_t *s_vals = reinterpret_cast<uint32_t *>(ds_smem + SORT_TILE * sizeof(uint64_t));
+  __shared__ uint32_t s_cnt[DS_WARPS][RADIX];  // per-warp digit counts, then bases
+  __shared__ uint32_t s_glob[RADIX];           // global position of the tile's digit run - local start
+  __shared__ uint32_t s_wsum[DS_WARPS];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint64_t m = pair_count(d_pairs, cap);
   const uint64_t start = (uint64_t)blockIdx.x * SORT_TILE;
   if (start >= m) return;
-  for (int d = tid; d < RADIX; d += SORT_THREADS) s_base[d] = offsets[(int64_t)d * nblk + blockIdx.x];
+  const int count = (int)min((uint64_t)SORT_TILE, m - start);
+  for (int d = lane; d < RADIX; d += 32) s_cnt[wid][d] = 0;
+  __syncwarp();
   const uint32_t lt_mask = (1u << lane) - 1u;
-  for (int k = 0; k < SORT_ITEMS; ++k) {
-    const uint64_t j = start + (uint64_t)k * SORT_THREADS + tid;
-    const bool ok = j < m;
-    uint64_t key = 0;
-    uint32_t val = 0;
-    if (ok) { key = keys_in[j]; val = vals_in[j]; }
-    const uint32_t digit = ok ? (uint32_t)((key >> shift) & (RADIX - 1)) : RADIX;  // RADIX: none
-    for (int d = lane; d < RADIX; d += 32) s_cnt[wid][d] = 0;
-    __syncthreads();  // s_base ready (first round), s_cnt cleared
-    const uint32_t peers = __match_any_sync(0xffffffffu, digit);
-    const uint32_t rank_in_warp = __popc(peers & lt_mask);
-    const bool leader = (peers & lt_mask) == 0;
-    if (ok && leader) s_cnt[wid][digit] = __popc(peers);
-    __syncthreads();
-    // per digit: exclusive prefix over warps, starting at the running base
-    for (int d = tid; d < RADIX; d += SORT_THREADS) {
-      uint32_t run = s_base[d];
+  uint64_t key[SORT_ITEMS];
+  uint32_t val[SORT_ITEMS], rank[SORT_ITEMS];
+  // issue every load of the thread before ranking
 #pragma unroll
-      for (int w = 0; w < NW; ++w) {
-        uint32_t c = s_cnt[w][d];
-        s_cnt[w][d] = run;
-        run += c;
-      }
-      s_base[d] = run;
+  for (int r = 0; r < SORT_ITEMS; ++r) {
+    const int li = wid * DS_SEG + r * 32 + lane;  // position in the tile
+    const bool ok = li < count;
+    key[r] = ok ? keys_in[start + li] : 0;
+    val[r] = ok ? vals_in[start + li] : 0;
+  }
+#pragma unroll
+  for (int r = 0; r < SORT_ITEMS; ++r) {
+    const int li = wid * DS_SEG + r * 32 + lane;
+    const bool ok = li < count;
+    const uint32_t digit = ok ? (uint32_t)((key[r] >> shift) & (RADIX - 1)) : RADIX;
+    const uint32_t peers = __match_any_sync(0xffffffffu, digit);
+    const int leader = __ffs(peers) - 1;
+    uint32_t before = 0;
+    if (ok && lane == leader) {
+      before = s_cnt[wid][digit];
+      s_cnt[wid][digit] = before + __popc(peers);
     }
-    __syncthreads();
-    if (ok) {
-      const uint32_t pos = s_cnt[wid][digit] + rank_in_warp;
-      keys_out[pos] = key;
-      vals_out[pos] = val;
+    before = __shfl_sync(0xffffffffu, before, leader);
+    rank[r] = before + __popc(peers & lt_mask);
+    __syncwarp();
+  }
+  __syncthreads();
+  // per digit d (thread d): bases of each warp's run, digit total, and the
+  // exclusive prefix of the totals over digits
+  {
+    const int d = tid;  // SORT_THREADS == RADIX
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < DS_WARPS; ++w) {
+      const uint32_t c = s_cnt[w][d];
+      s_cnt[w][d] = run;
+      run += c;
     }
+    uint32_t inc = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_wsum[wid] = inc;
     __syncthreads();
+    uint32_t wbase = 0;
+#pragma unroll
+    for (int w = 0; w < DS_WARPS; ++w) wbase += (w < wid) ? s_wsum[w] : 0u;
+    const uint32_t pref = wbase + inc - run;  // first local position of digit d
+#pragma unroll
+    for (int w = 0; w < DS_WARPS; ++w) s_cnt[w][d] += pref;
+    s_glob[d] = offsets[(int64_t)d * nblk + blockIdx.x] - pref;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < SORT_ITEMS; ++r) {
+    const int li = wid * DS_SEG + r * 32 + lane;
+    if (li < count) {
+      const uint32_t digit = (uint32_t)((key[r] >> shift) & (RADIX - 1));
+      const uint32_t pos = s_cnt[wid][digit] + rank[r];
+      s_keys[pos] = key[r];
+      s_vals[pos] = val[r];
+    }
+  }
+  __syncthreads();
+  for (int p = tid; p < count; p += SORT_THREADS) {
+    const uint64_t k = s_keys[p];
+    const uint32_t digit = (uint32_t)((k >> shift) & (RADIX - 1));
+    const uint32_t o = s_glob[digit] + (uint32_t)p;
+    keys_out[o] = k;
+    vals_out[o] = s_vals[p];
   }
 }
 
-// K5: [start, end) of every global tile's list.
 // Tiles outside [0, n_tiles) can only come from a capacity overflow (stale
 // keys); they are ignored so that the render stays memory-safe.
 __global__ void tile_ranges_kernel(const uint64_t *keys, const uint64_t *d_pairs, uint64_t cap,
@@ -224,9 +300,26 @@ int64_t sort_blocks(uint64_t pair_bound) {
   return (int64_t)((pair_bound + SORT_TILE - 1) / SORT_TILE);
 }
 
+cudaError_t prepare_sort_kernels() {
+  // the downsweep stages a 4096-key tile (48 KiB) in dynamic shared memory;
+  // the attribute is set once per device, outside any stream capture
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+  e = cudaFuncSetAttribute(radix_downsweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)DS_DYN_SMEM);
+  if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
+  return e;
+}
+
 void launch_radix_sort(const RenderShape &s, uint64_t pair_bound, ddgs_workspace &ws,
                        cudaStream_t st) {
   const int64_t nblk = sort_blocks(pair_bound);
+  if (nblk > 0 && prepare_sort_kernels() != cudaSuccess) return;  // surfaces via cudaGetLastError
   int cur = 0;
   if (nblk > 0) {
     const int passes = (s.key_bits + RADIX_BITS - 1) / RADIX_BITS;
@@ -244,7 +337,7 @@ void launch_radix_sort(const RenderShape &s, uint64_t pair_bound, ddgs_workspace
       }
       {
         LaunchScope ls(KID_RADIX_DOWNSWEEP, st);
-        radix_downsweep_kernel<<<(unsigned)nblk, SORT_THREADS, 0, st>>>(
+        radix_downsweep_kernel<<<(unsigned)nblk, SORT_THREADS, DS_DYN_SMEM, st>>>(
             ws.keys[cur], ws.vals[cur], ws.keys[cur ^ 1], ws.vals[cur ^ 1], ws.d_pairs,
             (uint64_t)ws.pair_cap, shift, ws.hist, nblk);
       }
