@@ -134,6 +134,10 @@ def cpu_baseline(scene, views, st, target, n_pix=4096, n_small=16):
 
     t_small, p_small, _ = run(n_small, 1)
     t_big, p_big, contrib = run(n_pix, 2)
+    # roofline units of the rasterisers (not timed): pixel-Gaussian pairs
+    # inside the q <= q_max ellipse, before early termination
+    pix = syn.sample_pixels(v1, n_random=n_pix, n_rows=0, seed=2)
+    inside = float(oracle.count_inside(scene, v1, st, pix=pix, depth32=d32).mean())
     per_px = max(t_big - t_small, 1e-9) / (p_big - p_small)
     per_render = t_small + per_px * (hw - p_small)
     cores = os.cpu_count() or 1
@@ -141,7 +145,7 @@ def cpu_baseline(scene, views, st, target, n_pix=4096, n_small=16):
             "sample": (f"view 0 of 64: {p_big} random pixels (+{p_small}) fwd+L1 bwd through the FP64 "
                        f"oracle (all Gaussians per pixel, no tiles); per-render time = setup + "
                        f"per-pixel x 65536 px ({t_small + t_big:.1f} s measured)"),
-            "contrib_per_pixel": contrib}
+            "contrib_per_pixel": contrib, "inside_per_pixel": inside}
 
 
 def target_image(scene, views, st, oracle_render=False):
@@ -437,9 +441,10 @@ def run_ours(args):
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(scene, views, st, target.cpu().numpy())
-        rcp = cpu.pop("contrib_per_pixel")
-        # ALU roofline of the rasterisers from the blended-pair count
-        blended = rcp * H * W * V
+        cpu.pop("contrib_per_pixel")
+        inside = cpu.pop("inside_per_pixel")
+        # ALU roofline of the rasterisers: pairs inside the q <= q_max ellipse
+        blended = inside * H * W * V
         sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1447.0)
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
         fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12

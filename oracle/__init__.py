@@ -79,6 +79,7 @@ def lib():
         _lib.or_project.argtypes = [vp, vp, vp, vp]
         _lib.or32_project.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         _lib.or32_bin.argtypes = [vp, vp, C.c_int32, vp, vp, vp, C.c_int64, vp, vp, vp]
+        _lib.or_count_inside.argtypes = [vp, vp, vp, vp, C.c_int64, vp, vp, C.c_int]
         _lib.or_exp32.argtypes = [C.c_float]
         _lib.or_exp32.restype = C.c_float
     return _lib
@@ -240,3 +241,18 @@ def render_backward(scene, views, settings, dL_dC, pix=None, depth32=None, threa
     if want_2d:
         out["grad2d"] = g2
     return out
+
+
+def count_inside(scene, views, settings, pix=None, depth32=None, threads=0):
+    """Per pixel: Gaussians with q <= q_max at the pixel centre (whole list)."""
+    pk = _Pack(scene, views, settings)
+    if depth32 is None:
+        depth32 = project32(scene, views, settings)["depth"]
+    depth32 = np.ascontiguousarray(depth32, dtype=np.float32)
+    pix, m = _pix(views, pix)
+    out = np.zeros(m, np.int32)
+    rc = lib().or_count_inside(C.byref(pk.scene), C.byref(pk.views), C.byref(pk.cfg),
+                               _p(depth32), m, _p(pix), _p(out), threads)
+    if rc:
+        raise RuntimeError(f"or_count_inside failed ({rc})")
+    return out if pix is not None else out.reshape(views.n_views, views.height, views.width)

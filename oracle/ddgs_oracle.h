@@ -101,6 +101,13 @@ int or_render_backward(const or_scene *s, const or_views *vw,
                        double *g_2d /* [V][n][7]: u, v, conic a, b, c, alpha, color */,
                        int n_threads);
 
+/* Per requested pixel: the number of projected Gaussians with q <= q_max at
+ * the pixel centre, over the whole list (no early termination, no alpha_min):
+ * the pixel-Gaussian pairs inside the cutoff ellipse. */
+int or_count_inside(const or_scene *s, const or_views *vw, const or_config *cfg,
+                    const float *depth32, int64_t n_pix, const int32_t *pix,
+                    int32_t *n_inside, int n_threads);
+
 /* Per (view, Gaussian) projected quantities, FP64, for tests:
  * out [V][n][9] = u, v, conic a, b, c, alpha, color, depth, valid. */
 int or_project(const or_scene *s, const or_views *vw, const or_config *cfg,

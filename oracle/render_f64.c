@@ -611,3 +611,31 @@ int or_render_backward(const or_scene *sc, const or_views *vw,
   free(g2);
   return 0;
 }
+
+int or_count_inside(const or_scene *sc, const or_views *vw, const or_config *cfg,
+                    const float *depth32, int64_t n_pix, const int32_t *pix,
+                    int32_t *n_inside, int n_threads) {
+  if (check_args(sc, vw, n_pix, pix) || !n_inside) return 1;
+  SET_THREADS(n_threads);
+  for (int64_t v = 0; v < vw->n_views; ++v) {
+    view_cache vc;
+    if (build_view(sc, vw, cfg, depth32, v, &vc)) return 2;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t p = 0; p < n_pix; ++p) {
+      int64_t pv, row, col;
+      pixel_at(vw, pix, p, &pv, &row, &col);
+      if (pv != v) continue;
+      double px = col + 0.5, py = row + 0.5;
+      int32_t cnt = 0;
+      for (int64_t j = 0; j < vc.n_order; ++j) {
+        const g64 *g = &vc.g[vc.order[j]];
+        double dx = g->u - px, dy = g->v - py;
+        double q = g->conic[0] * dx * dx + 2 * g->conic[1] * dx * dy + g->conic[2] * dy * dy;
+        cnt += (q <= cfg->q_max && q >= 0);
+      }
+      n_inside[p] = cnt;
+    }
+    free_view(&vc);
+  }
+  return 0;
+}

@@ -453,3 +453,18 @@ def test_analytic_gradient_matches_central_differences():
             assert abs(fd - G[idx]) <= 1e-6 * scale + 1e-9, (name, idx, fd, G[idx])
             checked += 1
     assert checked > 150
+
+
+def test_count_inside_matches_brute_force():
+    sc = syn.uniform_cloud(60, seed=9)
+    views = _views(_pose(np.eye(3), [0.0, 0.0, 2.0]), 4.0, 0.25, 16, 20)
+    st = syn.Settings(near_plane=0.2)
+    n_in = oracle.count_inside(sc, views, st)
+    P = oracle.project64(sc, views, st)[0]
+    jj, ii = np.meshgrid(np.arange(20) + 0.5, np.arange(16) + 0.5)
+    ref = np.zeros((16, 20), np.int64)
+    for u, v, a, b, c, _, _, _, valid in P:
+        if valid:
+            dx, dy = u - jj, v - ii
+            ref += (a * dx * dx + 2 * b * dx * dy + c * dy * dy) <= st.q_max
+    assert np.array_equal(n_in[0], ref) and ref.sum() > 50
