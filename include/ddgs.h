@@ -105,10 +105,13 @@ typedef struct {
 
 typedef struct ddgs_workspace ddgs_workspace;
 
-/* Workspace: per-(view, Gaussian) projections, sort buffers, tile ranges and
- * the device status word, on the device that is current at creation. Owned by
- * the library between create and destroy. One workspace serves one render at
- * a time; ddgs_render_backward reads what the preceding ddgs_render left. */
+/* Workspace: per-(view, Gaussian) projections, sort buffers, tile ranges,
+ * request/view tables and the device status word, on the device that is
+ * current at creation. Owned by the library between create and destroy. One
+ * workspace serves one render at a time; ddgs_render_backward reads what the
+ * preceding ddgs_render left. A CUDA graph that captured calls on a workspace
+ * stays valid while no call with another batch layout (counts, view sizes,
+ * tile) or a larger size runs on that workspace. */
 ddgs_status ddgs_workspace_create(ddgs_workspace **ws);
 ddgs_status ddgs_workspace_destroy(ddgs_workspace *ws);
 
@@ -163,8 +166,8 @@ ddgs_status ddgs_render_backward(const ddgs_gaussians *g, const ddgs_views *v,
  * caching allocator owns.) Same inputs, outputs and results as ddgs_render;
  * its scratch is one static device array of about 37 MiB that every GPU
  * loading this library holds until the process exits. Limits per call:
- * n_views * n <= 262144 records, n_views * tiles per view <= 65536 tiles and
- * at most 1048576 (Gaussian, tile) pairs; larger renders return
+ * n_views * n <= 262144 records, n_views <= 1024, n_views * tiles per view
+ * <= 65536 tiles and at most 1048576 (Gaussian, tile) pairs; larger renders return
  * DDGS_ERR_CAPACITY (the pair count is known only after the projection, so
  * that case returns after synchronising the stream, with the outputs left
  * unwritten). Calls no cudaMalloc, cudaFree or any other allocating routine.
@@ -176,6 +179,48 @@ ddgs_status ddgs_render_backward(const ddgs_gaussians *g, const ddgs_views *v,
 ddgs_status ddgs_render_static(const ddgs_gaussians *g, const ddgs_views *v,
                                const ddgs_config *cfg, float *image,
                                float *t_final, uint32_t *n_last, void *stream);
+
+/* A batch of independent requests rendered by one sequence of launches: many
+ * candidate poses of one patient, or many patients at once (Sec. 4.3's
+ * registration renders many poses; a serving system renders many clouds).
+ * Request r has its own cloud, its own bases and its own views; every view has
+ * its own detector size. Device arrays are concatenated over the requests in
+ * order; the counts and sizes are host arrays. */
+typedef struct {
+  int32_t n_requests;              /* R */
+  const int64_t *gaussian_counts;  /* host [R]: N_r */
+  const int64_t *iso_counts;       /* host [R]: the first iso_counts[r] of request r are isotropic */
+  const int32_t *view_counts;      /* host [R]: V_r */
+  const int32_t *heights, *widths; /* host [V], V = sum V_r: detector pixels of each view */
+  const float *means;              /* [N][3], N = sum N_r, request order */
+  const float *log_scales;         /* [N][3] */
+  const float *quats;              /* [N][4] (w, x, y, z), 16-byte aligned */
+  const float *opacity_logits;     /* [N] */
+  const float *feat_iso;           /* [sum iso_counts][8], request order, 16-byte aligned */
+  const void *feat_dir;            /* [N - sum iso_counts][8], float32 or bfloat16 */
+  int32_t feat_dir_bf16;
+  const float *b_iso;              /* [R][8] */
+  const float *B_dir;              /* [R][3][8] */
+  const float *world_to_cam;       /* [V][3][4], views in request order */
+  const float *detector;           /* [V][5] */
+} ddgs_batch;
+
+/* ddgs_render over a batch (same rule, Eq. 1 and Eq. 3, per view). Outputs are
+ * concatenated per view: view v occupies H_v * W_v floats, row-major, after
+ * the views before it. Each request's Gaussians are sorted and blended only
+ * in its own views. */
+ddgs_status ddgs_render_batched(const ddgs_batch *b, const ddgs_config *cfg,
+                                ddgs_workspace *ws, float *image, float *t_final,
+                                uint32_t *n_last, void *stream);
+
+/* ddgs_render_backward over a batch. Gradient layouts follow the batch's
+ * arrays: per-Gaussian fields [N][...], b_iso [R][8], B_dir [R][3][8],
+ * world_to_cam [V][3][4]. Must follow the ddgs_render_batched that filled ws
+ * with the same batch. */
+ddgs_status ddgs_render_batched_backward(const ddgs_batch *b, const ddgs_config *cfg,
+                                         ddgs_workspace *ws, const float *dL_dimage,
+                                         const float *t_final, const uint32_t *n_last,
+                                         const ddgs_grads *out, void *stream);
 
 /* Per-view mean L1 loss of the registration objective (Sec. 4.3 compares the
  * rendering at a predicted pose with the target image; the l1 term of Eq. 2)

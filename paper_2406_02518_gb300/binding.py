@@ -30,7 +30,8 @@ EXPORTS = ["ddgs_workspace_create", "ddgs_workspace_destroy", "ddgs_workspace_re
            "ddgs_debug_binning", "ddgs_sync_status", "ddgs_parameter_count",
            "ddgs_status_string", "ddgs_last_cuda_error", "ddgs_device_supported",
            "ddgs_kernel_launches", "ddgs_profiler_enable", "ddgs_profiler_collect",
-           "ddgs_profiler_kernel_name", "ddgs_render_static"]
+           "ddgs_profiler_kernel_name", "ddgs_render_static", "ddgs_render_batched",
+           "ddgs_render_batched_backward"]
 
 
 class DDGSError(RuntimeError):
@@ -58,6 +59,15 @@ class _Config(C.Structure):
     _fields_ = [("tile", C.c_int32), ("dilation", C.c_float), ("near_plane", C.c_float),
                 ("alpha_min", C.c_float), ("alpha_max", C.c_float), ("t_min", C.c_float),
                 ("q_max", C.c_float), ("no_sync", C.c_int32)]
+
+
+class _Batch(C.Structure):
+    _fields_ = [("n_requests", C.c_int32), ("gaussian_counts", C.c_void_p),
+                ("iso_counts", C.c_void_p), ("view_counts", C.c_void_p), ("heights", C.c_void_p),
+                ("widths", C.c_void_p), ("means", C.c_void_p), ("log_scales", C.c_void_p),
+                ("quats", C.c_void_p), ("opacity_logits", C.c_void_p), ("feat_iso", C.c_void_p),
+                ("feat_dir", C.c_void_p), ("feat_dir_bf16", C.c_int32), ("b_iso", C.c_void_p),
+                ("B_dir", C.c_void_p), ("world_to_cam", C.c_void_p), ("detector", C.c_void_p)]
 
 
 class _Grads(C.Structure):
@@ -95,6 +105,8 @@ def load(path: Optional[str] = None):
     lib.ddgs_status_string.restype = C.c_char_p
     lib.ddgs_last_cuda_error.restype = C.c_char_p
     lib.ddgs_device_supported.restype = i32
+    lib.ddgs_render_batched.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    lib.ddgs_render_batched_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
     lib.ddgs_kernel_launches.restype = i64
     lib.ddgs_profiler_enable.argtypes = [i32]
     lib.ddgs_profiler_collect.argtypes = [i32, vp, vp, vp]
@@ -391,3 +403,115 @@ def render_differentiable(cloud: Cloud, views: Views, cfg: Config, ws: Workspace
                                 cloud.feat_iso, cloud.feat_dir, cloud.b_iso, cloud.B_dir,
                                 views.world_to_cam, views.detector, views.height, views.width,
                                 cfg, ws)
+
+
+@dataclasses.dataclass
+class ViewGroup:
+    """The views of one request of a batch; each view has its own detector size."""
+    world_to_cam: torch.Tensor  # [Vr,3,4] float32, device
+    detector: torch.Tensor      # [Vr,5] float32, device
+    sizes: list                 # [(H, W)] per view
+
+    @property
+    def n_views(self):
+        return len(self.sizes)
+
+    @staticmethod
+    def of(views_list, device="cuda"):
+        """From a list of single-size Views (device tensors)."""
+        if not views_list:
+            return ViewGroup(torch.empty((0, 3, 4), device=device), torch.empty((0, 5), device=device), [])
+        return ViewGroup(torch.cat([v.world_to_cam for v in views_list]).contiguous(),
+                         torch.cat([v.detector for v in views_list]).contiguous(),
+                         [(v.height, v.width) for v in views_list for _ in range(v.n_views)])
+
+
+def _sizes(v):
+    return list(v.sizes) if isinstance(v, ViewGroup) else [(v.height, v.width)] * v.n_views
+
+
+class Batch:
+    """Device tensors of a batch of requests (ddgs_batch): concatenated clouds,
+    per-request bases, per-view poses and detectors, host count arrays.
+    `views[r]` is a Views (one size) or a ViewGroup (per-view sizes)."""
+
+    def __init__(self, clouds, views):
+        assert len(clouds) == len(views)
+        self.clouds, self.views = clouds, views
+        self.means = torch.cat([c.means for c in clouds]).contiguous()
+        self.log_scales = torch.cat([c.log_scales for c in clouds]).contiguous()
+        self.quats = torch.cat([c.quats for c in clouds]).contiguous()
+        self.opacity_logits = torch.cat([c.opacity_logits for c in clouds]).contiguous()
+        self.feat_iso = torch.cat([c.feat_iso for c in clouds]).contiguous()
+        self.feat_dir = torch.cat([c.feat_dir for c in clouds]).contiguous()
+        self.b_iso = torch.stack([c.b_iso for c in clouds]).contiguous()
+        self.B_dir = torch.stack([c.B_dir for c in clouds]).contiguous()
+        self.world_to_cam = torch.cat([v.world_to_cam for v in views]).contiguous()
+        self.detector = torch.cat([v.detector for v in views]).contiguous()
+        self.n = np.array([c.n for c in clouds], np.int64)
+        self.n_iso = np.array([c.n_iso for c in clouds], np.int64)
+        self.nv = np.array([v.n_views for v in views], np.int32)
+        sizes = [hw for v in views for hw in _sizes(v)]
+        self.H = np.array([h for h, _ in sizes] or [0], np.int32)[:len(sizes)]
+        self.W = np.array([w for _, w in sizes] or [0], np.int32)[:len(sizes)]
+        self.pixel_offsets = np.concatenate([[0], np.cumsum(self.H.astype(np.int64) * self.W)])
+
+    @property
+    def n_requests(self):
+        return len(self.clouds)
+
+    @property
+    def pixels(self):
+        return int(self.pixel_offsets[-1])
+
+    def struct(self) -> _Batch:
+        bf16 = self.feat_dir.dtype == torch.bfloat16
+        R = self.n_requests
+        p = lambda t: _ptr(t) if t.numel() else None
+        return _Batch(R, self.n.ctypes.data, self.n_iso.ctypes.data, self.nv.ctypes.data,
+                      self.H.ctypes.data, self.W.ctypes.data, p(self.means), p(self.log_scales),
+                      p(self.quats), p(self.opacity_logits), p(self.feat_iso), p(self.feat_dir),
+                      int(bf16), p(self.b_iso), p(self.B_dir), p(self.world_to_cam), p(self.detector))
+
+    def view_slice(self, flat: torch.Tensor, v: int) -> torch.Tensor:
+        a, b = int(self.pixel_offsets[v]), int(self.pixel_offsets[v + 1])
+        return flat[a:b].view(int(self.H[v]), int(self.W[v]))
+
+
+def render_batched(batch: Batch, cfg: Config, ws: Workspace, out=None):
+    """ddgs_render_batched: flat (image, t_final, n_last) over all views."""
+    lib = load()
+    P = batch.pixels
+    dev = batch.means.device
+    if out is None:
+        out = (torch.empty(P, dtype=torch.float32, device=dev),
+               torch.empty(P, dtype=torch.float32, device=dev),
+               torch.empty(P, dtype=torch.int32, device=dev))
+    img, tf, nl = out
+    b, c = batch.struct(), cfg.struct()
+    _check(lib.ddgs_render_batched(C.byref(b), C.byref(c), ws.handle, _ptr(img), _ptr(tf),
+                                   _ptr(nl), _stream()), "ddgs_render_batched")
+    return img, tf, nl
+
+
+def render_batched_backward(batch: Batch, cfg: Config, ws: Workspace, dL_dimage, t_final, n_last,
+                            want=GRAD_FIELDS, out=None):
+    lib = load()
+    dev = batch.means.device
+    shapes = dict(means=batch.means.shape, log_scales=batch.log_scales.shape,
+                  quats=batch.quats.shape, opacity_logits=batch.opacity_logits.shape,
+                  feat_iso=batch.feat_iso.shape, feat_dir=batch.feat_dir.shape,
+                  b_iso=batch.b_iso.shape, B_dir=batch.B_dir.shape,
+                  world_to_cam=batch.world_to_cam.shape)
+    grads = dict(out or {})
+    for k in want:
+        if k not in grads:
+            grads[k] = torch.empty(shapes[k], dtype=torch.float32, device=dev)
+    gs = _Grads(*[(_ptr(grads[k]) if grads[k].numel() else None) if k in grads else None
+                  for k in GRAD_FIELDS])
+    b, c = batch.struct(), cfg.struct()
+    _check(lib.ddgs_render_batched_backward(C.byref(b), C.byref(c), ws.handle,
+                                            _ptr(dL_dimage.contiguous()), _ptr(t_final),
+                                            _ptr(n_last), C.byref(gs), _stream()),
+           "ddgs_render_batched_backward")
+    return grads

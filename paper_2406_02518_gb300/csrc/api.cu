@@ -1,5 +1,6 @@
 // api.cu -- the C ABI: argument checks, workspace management and the order of
 // the kernels of a render and of its backward pass.
+#include <algorithm>
 #include <atomic>
 #include <cstdio>
 #include <cstring>
@@ -63,25 +64,122 @@ ddgs_status check_inputs(const ddgs_gaussians *g, const ddgs_views *v, const ddg
   return DDGS_OK;
 }
 
-ddgs::RenderShape make_shape(const ddgs_gaussians *g, const ddgs_views *v, const ddgs_config *c) {
-  ddgs::RenderShape s{};
-  s.n = g->n;
-  s.n_iso = g->n_iso;
-  s.V = v->n_views;
-  s.H = v->height;
-  s.W = v->width;
-  s.tile = c->tile;
-  s.tiles_x = (v->width + c->tile - 1) / c->tile;
-  s.tiles_y = (v->height + c->tile - 1) / c->tile;
-  s.tiles_per_view = (int64_t)s.tiles_x * s.tiles_y;
-  s.total_tiles = s.tiles_per_view * s.V;
-  s.records = (int64_t)s.V * s.n;
-  s.key_bits = 32 + bits_for(s.total_tiles > 0 ? (uint64_t)(s.total_tiles - 1) : 0);
-  return s;
+// Host description of one render: the request and view tables plus totals.
+struct Layout {
+  int32_t R = 0, V = 0, tile = 16;
+  std::vector<ddgs::ReqTab> req;   // R + 1 (sentinel)
+  std::vector<ddgs::ViewTab> view; // V + 1 (sentinel)
+  ddgs::RenderShape shape{};       // totals; device pointers filled by upload
+  uint64_t hash = 0;
+};
+
+uint64_t mix(uint64_t h, uint64_t x) {
+  h ^= x + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+  return h;
+}
+
+// counts per request, views per request, sizes per view
+ddgs_status make_layout(int32_t R, const int64_t *n, const int64_t *n_iso, const int32_t *nv,
+                        const int32_t *H, const int32_t *W, int32_t heights_uniform,
+                        int32_t tile, Layout &L) {
+  if (R < 0 || (R > 0 && (!n || !n_iso || !nv))) return DDGS_ERR_INVALID_ARG;
+  L.R = R;
+  L.tile = tile;
+  L.req.assign((size_t)R + 1, ddgs::ReqTab{});
+  int64_t g = 0, iso = 0, dir = 0, blk = 0;
+  int32_t v = 0;
+  uint64_t h = mix(0, (uint64_t)R);
+  h = mix(h, (uint64_t)tile);
+  for (int32_t r = 0; r < R; ++r) {
+    if (n[r] < 0 || n_iso[r] < 0 || n_iso[r] > n[r] || nv[r] < 0) return DDGS_ERR_INVALID_ARG;
+    ddgs::ReqTab &q = L.req[r];
+    q.g_off = g; q.n = n[r]; q.n_iso = n_iso[r]; q.iso_row = iso; q.dir_row = dir;
+    q.blk_base = blk; q.v_off = v; q.n_views = nv[r];
+    g += n[r]; iso += n_iso[r]; dir += n[r] - n_iso[r];
+    blk += (n[r] + ddgs::PRE_THREADS - 1) / ddgs::PRE_THREADS;
+    v += nv[r];
+    h = mix(mix(mix(h, (uint64_t)n[r]), (uint64_t)n_iso[r]), (uint64_t)nv[r]);
+  }
+  if (g >= (int64_t(1) << 31)) return DDGS_ERR_INVALID_ARG;
+  L.req[R].g_off = g; L.req[R].iso_row = iso; L.req[R].dir_row = dir; L.req[R].blk_base = blk;
+  L.req[R].v_off = v;
+  L.V = v;
+  L.view.assign((size_t)v + 1, ddgs::ViewTab{});
+  int64_t tiles = 0, recs = 0, pix = 0;
+  for (int32_t r = 0, vi = 0; r < R; ++r)
+    for (int32_t k = 0; k < nv[r]; ++k, ++vi) {
+      const int32_t hv = heights_uniform ? H[0] : H[vi], wv = heights_uniform ? W[0] : W[vi];
+      if (hv <= 0 || wv <= 0 || hv > 65535 * 8 || wv > 65535 * 8) return DDGS_ERR_INVALID_ARG;
+      ddgs::ViewTab &t = L.view[vi];
+      t.req = r; t.H = hv; t.W = wv; t.tiles_x = (wv + tile - 1) / tile;
+      t.tile_base = tiles; t.rec_off = recs; t.img_off = pix;
+      tiles += (int64_t)t.tiles_x * ((hv + tile - 1) / tile);
+      recs += n[r];
+      pix += (int64_t)hv * wv;
+      h = mix(mix(h, (uint64_t)hv), (uint64_t)wv);
+    }
+  L.view[v].tile_base = tiles; L.view[v].rec_off = recs; L.view[v].img_off = pix;
+  L.view[v].req = R;
+  ddgs::RenderShape &s = L.shape;
+  s.R = R; s.V = v; s.tile = tile;
+  s.n_total = g; s.total_tiles = tiles; s.records = recs; s.pixels = pix; s.n_blocks = blk;
+  s.key_bits = 32 + bits_for(tiles > 0 ? (uint64_t)(tiles - 1) : 0);
+  L.hash = h ? h : 1;
+  return DDGS_OK;
+}
+
+constexpr int64_t kTabReq0 = 4096, kTabView0 = 16384;  // initial table capacity
+
+ddgs_status ensure_tables(ddgs_workspace *ws, int64_t R, int64_t V) {
+  if (R + 1 <= ws->req_cap && V + 1 <= ws->view_cap && ws->h_tab) return DDGS_OK;
+  const int64_t rc = std::max<int64_t>(R + 1, std::max<int64_t>(ws->req_cap, kTabReq0));
+  const int64_t vc = std::max<int64_t>(V + 1, std::max<int64_t>(ws->view_cap, kTabView0));
+  if (ws->h_tab) {
+    CK(cudaDeviceSynchronize());  // the staging area may still feed a copy
+    CK(cudaFreeHost(ws->h_tab));
+    ws->h_tab = nullptr;
+  }
+  if (ws->d_req) CK(cudaFree(ws->d_req));
+  if (ws->d_view) CK(cudaFree(ws->d_view));
+  ws->d_req = nullptr;
+  ws->d_view = nullptr;
+  ws->req_cap = ws->view_cap = 0;
+  CK(cudaHostAlloc(&ws->h_tab, rc * sizeof(ddgs::ReqTab) + vc * sizeof(ddgs::ViewTab),
+                   cudaHostAllocDefault));
+  CK(cudaMalloc(&ws->d_req, rc * sizeof(ddgs::ReqTab)));
+  CK(cudaMalloc(&ws->d_view, vc * sizeof(ddgs::ViewTab)));
+  ws->req_cap = rc;
+  ws->view_cap = vc;
+  ws->last_hash = 0;
+  return DDGS_OK;
+}
+
+// Copy the tables to the device when the layout differs from the last one;
+// repeated renders of one layout (and CUDA-graph replays) reuse them.
+ddgs_status upload_layout(ddgs_workspace *ws, Layout &L, bool no_sync, cudaStream_t st) {
+  if (L.R + 1 > ws->req_cap || L.V + 1 > ws->view_cap) {
+    if (no_sync) return DDGS_ERR_CAPACITY;
+    ddgs_status e = ensure_tables(ws, L.R, L.V);
+    if (e) return e;
+  }
+  if (ws->last_hash != L.hash) {
+    // the previous upload must have left the staging area before it is reused
+    if (ws->last_hash != 0) CK(cudaStreamSynchronize(st));
+    ddgs::ReqTab *hr = reinterpret_cast<ddgs::ReqTab *>(ws->h_tab);
+    ddgs::ViewTab *hv = reinterpret_cast<ddgs::ViewTab *>(ws->h_tab + ws->req_cap * sizeof(ddgs::ReqTab));
+    std::memcpy(hr, L.req.data(), L.req.size() * sizeof(ddgs::ReqTab));
+    std::memcpy(hv, L.view.data(), L.view.size() * sizeof(ddgs::ViewTab));
+    CK(cudaMemcpyAsync(ws->d_req, hr, L.req.size() * sizeof(ddgs::ReqTab), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ws->d_view, hv, L.view.size() * sizeof(ddgs::ViewTab), cudaMemcpyHostToDevice, st));
+    ws->last_hash = L.hash;
+  }
+  L.shape.req = ws->d_req;
+  L.shape.view = ws->d_view;
+  return DDGS_OK;
 }
 
 ddgs_status ensure_records(ddgs_workspace *ws, const ddgs::RenderShape &s) {
-  const int64_t blk = ddgs::preprocess_blocks(s);
+  const int64_t blk = s.n_blocks;
   if (s.records > ws->rec_cap || !ws->rec0) {
     int64_t cap = s.records + s.records / 4 + 1024;
     ddgs_status st;
@@ -267,6 +365,10 @@ ddgs_status ddgs_workspace_create(ddgs_workspace **out) {
     return st;
   }
   *ws->h_pairs = 0;
+  if (ensure_tables(ws, 0, 0) != DDGS_OK) {
+    ddgs_workspace_destroy(ws);
+    return DDGS_ERR_OUT_OF_MEMORY;
+  }
   if ((e = ddgs::prepare_sort_kernels()) != cudaSuccess) {
     ddgs_status st = cuda_fail(e, "sort kernel set-up");
     ddgs_workspace_destroy(ws);
@@ -280,10 +382,11 @@ ddgs_status ddgs_workspace_destroy(ddgs_workspace *ws) {
   if (!ws) return DDGS_OK;
   void *dev[] = {ws->rec0, ws->rec1, ws->rect, ws->tiles_touched, ws->grad2d, ws->blk_total,
                  ws->blk_offset, ws->keys[0], ws->keys[1], ws->vals[0], ws->vals[1], ws->hist,
-                 ws->digit_total, ws->ranges, ws->d_pairs, ws->d_status};
+                 ws->digit_total, ws->ranges, ws->d_pairs, ws->d_status, ws->d_req, ws->d_view};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (ws->h_pairs) cudaFreeHost(ws->h_pairs);
+  if (ws->h_tab) cudaFreeHost(ws->h_tab);
   delete ws;
   return DDGS_OK;
 }
@@ -294,39 +397,45 @@ ddgs_status ddgs_workspace_reserve(ddgs_workspace *ws, int64_t records, int64_t 
   CK(cudaDeviceSynchronize());
   ddgs::RenderShape s{};
   s.records = records;
-  s.n = records;  // bounds the preprocess block count for any split into views
+  // any split of the records into requests and views needs at most this many
+  // preprocess blocks (one partial block per request, up to 4096 requests)
+  s.n_blocks = records / ddgs::PRE_THREADS + 4096;
   s.total_tiles = tiles;
   ddgs_status st = ensure_records(ws, s);
   if (st) return st;
   st = ensure_pairs(ws, pairs);
   if (st) return st;
+  st = ensure_tables(ws, 0, 0);
+  if (st) return st;
   CK(cudaDeviceSynchronize());
   return DDGS_OK;
 }
 
-ddgs_status ddgs_render(const ddgs_gaussians *g, const ddgs_views *v, const ddgs_config *c,
-                        ddgs_workspace *ws, float *image, float *t_final, uint32_t *n_last,
-                        void *stream) {
-  ddgs_status st = check_inputs(g, v, c);
-  if (st) return st;
-  if (!ws) return DDGS_ERR_INVALID_ARG;
-  if (v->n_views > 0 && (!image || !t_final || !n_last)) return DDGS_ERR_INVALID_ARG;
-  cudaStream_t s_ = static_cast<cudaStream_t>(stream);
-  const ddgs::RenderShape s = make_shape(g, v, c);
+}  // extern "C"
+
+namespace {
+
+// The kernels read the parameter arrays through ddgs_gaussians / ddgs_views
+// (pointers only); sizes come from the layout.
+ddgs_status render_common(const ddgs_gaussians &g, const ddgs_views &v, const ddgs_config *c,
+                          Layout &L, ddgs_workspace *ws, float *image, float *t_final,
+                          uint32_t *n_last, cudaStream_t s_) {
+  ddgs_status st;
+  ddgs::RenderShape &s = L.shape;
   if (c->no_sync) {
-    if (s.records > ws->rec_cap || ddgs::preprocess_blocks(s) > ws->blk_cap ||
-        s.total_tiles > ws->tile_cap || !ws->keys[0])
+    if (s.records > ws->rec_cap || s.n_blocks > ws->blk_cap || s.total_tiles > ws->tile_cap ||
+        !ws->keys[0])
       return DDGS_ERR_CAPACITY;
   } else if ((st = ensure_records(ws, s))) {
     return st;
   }
+  if ((st = upload_layout(ws, L, c->no_sync != 0, s_))) return st;
   ws->have_render = false;
-  const int64_t nblk = ddgs::preprocess_blocks(s);
   uint64_t bound = 0;
   if (s.records > 0) {
-    ddgs::launch_preprocess_fwd(*g, *v, *c, s, *ws, s_);
+    ddgs::launch_preprocess_fwd(g, v, *c, s, *ws, s_);
     CK(cudaGetLastError());
-    ddgs::launch_scan_blocks(nblk, *ws, s_);
+    ddgs::launch_scan_blocks(s.n_blocks, *ws, s_);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(ws->h_pairs, ws->d_pairs, sizeof(uint64_t), cudaMemcpyDeviceToHost, s_));
     if (!c->no_sync) {
@@ -360,38 +469,136 @@ ddgs_status ddgs_render(const ddgs_gaussians *g, const ddgs_views *v, const ddgs
   return DDGS_OK;
 }
 
-ddgs_status ddgs_render_backward(const ddgs_gaussians *g, const ddgs_views *v,
-                                 const ddgs_config *c, ddgs_workspace *ws,
-                                 const float *dL_dimage, const float *t_final,
-                                 const uint32_t *n_last, const ddgs_grads *out, void *stream) {
-  ddgs_status st = check_inputs(g, v, c);
-  if (st) return st;
-  if (!ws || !out || !ws->have_render) return DDGS_ERR_INVALID_ARG;
-  const ddgs::RenderShape s = make_shape(g, v, c);
-  if (s.n != ws->shape.n || s.V != ws->shape.V || s.H != ws->shape.H || s.W != ws->shape.W ||
-      s.tile != ws->shape.tile)
-    return DDGS_ERR_INVALID_ARG;
+ddgs_status backward_common(const ddgs_gaussians &g, const ddgs_views &v, const ddgs_config *c,
+                            Layout &L, ddgs_workspace *ws, const float *dL_dimage,
+                            const float *t_final, const uint32_t *n_last, const ddgs_grads *out,
+                            cudaStream_t s_) {
+  if (!ws || !out || !ws->have_render || L.hash != ws->last_hash) return DDGS_ERR_INVALID_ARG;
+  ddgs::RenderShape &s = L.shape;
+  s.req = ws->d_req;
+  s.view = ws->d_view;
   if (s.total_tiles > 0 && (!dL_dimage || !t_final || !n_last)) return DDGS_ERR_INVALID_ARG;
   if ((out->quats && !aligned16(out->quats)) || (out->feat_iso && !aligned16(out->feat_iso)) ||
       (out->feat_dir && !aligned16(out->feat_dir)))
     return DDGS_ERR_INVALID_ARG;
-  cudaStream_t s_ = static_cast<cudaStream_t>(stream);
-  if (out->b_iso) CK(cudaMemsetAsync(out->b_iso, 0, ddgs::K * sizeof(float), s_));
-  if (out->B_dir) CK(cudaMemsetAsync(out->B_dir, 0, 3 * ddgs::K * sizeof(float), s_));
-  if (out->world_to_cam) CK(cudaMemsetAsync(out->world_to_cam, 0, (size_t)s.V * 12 * sizeof(float), s_));
-  if (s.records == 0) {
-    // no Gaussians: parameter gradients are empty, pose and basis gradients zero
-    return DDGS_OK;
-  }
-  CK(cudaMemsetAsync(ws->grad2d, 0, (size_t)s.records * 2 * sizeof(float4), s_));
+  if (out->b_iso) CK(cudaMemsetAsync(out->b_iso, 0, (size_t)s.R * ddgs::K * sizeof(float), s_));
+  if (out->B_dir) CK(cudaMemsetAsync(out->B_dir, 0, (size_t)s.R * 3 * ddgs::K * sizeof(float), s_));
+  if (out->world_to_cam)
+    CK(cudaMemsetAsync(out->world_to_cam, 0, (size_t)s.V * 12 * sizeof(float), s_));
+  if (s.n_total == 0) return DDGS_OK;  // parameter gradients empty, pose/basis zero
+  // with no views the backward preprocess still writes the (zero) gradients
+  if (s.records > 0) CK(cudaMemsetAsync(ws->grad2d, 0, (size_t)s.records * 2 * sizeof(float4), s_));
   ddgs::RasterParams P{c->alpha_min, c->alpha_max, c->t_min, c->q_max};
-  if (s.total_tiles > 0 && ws->pair_bound > 0) {
+  if (s.records > 0 && s.total_tiles > 0 && ws->pair_bound > 0) {
     ddgs::launch_raster_bwd(s, P, *ws, dL_dimage, t_final, n_last, s_);
     CK(cudaGetLastError());
   }
-  ddgs::launch_preprocess_bwd(*g, *v, *c, s, *ws, *out, s_);
+  ddgs::launch_preprocess_bwd(g, v, *c, s, *ws, *out, s_);
   CK(cudaGetLastError());
   return DDGS_OK;
+}
+
+ddgs_status single_layout(const ddgs_gaussians *g, const ddgs_views *v, const ddgs_config *c,
+                          Layout &L) {
+  ddgs_status st = check_inputs(g, v, c);
+  if (st) return st;
+  const int64_t n = g->n, ni = g->n_iso;
+  const int32_t nv = v->n_views;
+  return make_layout(1, &n, &ni, &nv, &v->height, &v->width, 1, c->tile, L);
+}
+
+ddgs_status check_batch(const ddgs_batch *b, const ddgs_config *c) {
+  if (!b || !c || b->n_requests < 0) return DDGS_ERR_INVALID_ARG;
+  if (c->tile != 8 && c->tile != 16 && c->tile != 32) return DDGS_ERR_INVALID_ARG;
+  if (!(c->q_max > 0) || !(c->alpha_max > 0) || !(c->t_min >= 0) || !(c->dilation >= 0))
+    return DDGS_ERR_INVALID_ARG;
+  if (b->n_requests > 0 && (!b->gaussian_counts || !b->iso_counts || !b->view_counts))
+    return DDGS_ERR_INVALID_ARG;
+  int64_t n = 0, ni = 0, nv = 0;
+  for (int32_t r = 0; r < b->n_requests; ++r) {
+    n += b->gaussian_counts[r];
+    ni += b->iso_counts[r];
+    nv += b->view_counts[r];
+  }
+  if (nv > 0 && (!b->heights || !b->widths || !b->world_to_cam || !b->detector))
+    return DDGS_ERR_INVALID_ARG;
+  if (n > 0) {
+    if (!b->means || !b->log_scales || !b->quats || !b->opacity_logits || !b->b_iso || !b->B_dir ||
+        !aligned16(b->quats))
+      return DDGS_ERR_INVALID_ARG;
+    if (ni > 0 && (!b->feat_iso || !aligned16(b->feat_iso))) return DDGS_ERR_INVALID_ARG;
+    if (n > ni && (!b->feat_dir || !aligned16(b->feat_dir))) return DDGS_ERR_INVALID_ARG;
+  }
+  return DDGS_OK;
+}
+
+void batch_structs(const ddgs_batch *b, ddgs_gaussians &g, ddgs_views &v) {
+  g = ddgs_gaussians{};
+  g.means = b->means; g.log_scales = b->log_scales; g.quats = b->quats;
+  g.opacity_logits = b->opacity_logits; g.feat_iso = b->feat_iso; g.feat_dir = b->feat_dir;
+  g.feat_dir_bf16 = b->feat_dir_bf16; g.b_iso = b->b_iso; g.B_dir = b->B_dir;
+  v = ddgs_views{};
+  v.world_to_cam = b->world_to_cam;
+  v.detector = b->detector;
+}
+
+}  // namespace
+
+extern "C" {
+
+ddgs_status ddgs_render(const ddgs_gaussians *g, const ddgs_views *v, const ddgs_config *c,
+                        ddgs_workspace *ws, float *image, float *t_final, uint32_t *n_last,
+                        void *stream) {
+  Layout L;
+  ddgs_status st = single_layout(g, v, c, L);
+  if (st) return st;
+  if (!ws) return DDGS_ERR_INVALID_ARG;
+  if (v->n_views > 0 && (!image || !t_final || !n_last)) return DDGS_ERR_INVALID_ARG;
+  return render_common(*g, *v, c, L, ws, image, t_final, n_last, static_cast<cudaStream_t>(stream));
+}
+
+ddgs_status ddgs_render_backward(const ddgs_gaussians *g, const ddgs_views *v,
+                                 const ddgs_config *c, ddgs_workspace *ws,
+                                 const float *dL_dimage, const float *t_final,
+                                 const uint32_t *n_last, const ddgs_grads *out, void *stream) {
+  Layout L;
+  ddgs_status st = single_layout(g, v, c, L);
+  if (st) return st;
+  return backward_common(*g, *v, c, L, ws, dL_dimage, t_final, n_last, out,
+                         static_cast<cudaStream_t>(stream));
+}
+
+ddgs_status ddgs_render_batched(const ddgs_batch *b, const ddgs_config *c, ddgs_workspace *ws,
+                                float *image, float *t_final, uint32_t *n_last, void *stream) {
+  ddgs_status st = check_batch(b, c);
+  if (st) return st;
+  if (!ws) return DDGS_ERR_INVALID_ARG;
+  Layout L;
+  if ((st = make_layout(b->n_requests, b->gaussian_counts, b->iso_counts, b->view_counts,
+                        b->heights, b->widths, 0, c->tile, L)))
+    return st;
+  if (L.shape.pixels > 0 && (!image || !t_final || !n_last)) return DDGS_ERR_INVALID_ARG;
+  ddgs_gaussians g;
+  ddgs_views v;
+  batch_structs(b, g, v);
+  return render_common(g, v, c, L, ws, image, t_final, n_last, static_cast<cudaStream_t>(stream));
+}
+
+ddgs_status ddgs_render_batched_backward(const ddgs_batch *b, const ddgs_config *c,
+                                         ddgs_workspace *ws, const float *dL_dimage,
+                                         const float *t_final, const uint32_t *n_last,
+                                         const ddgs_grads *out, void *stream) {
+  ddgs_status st = check_batch(b, c);
+  if (st) return st;
+  Layout L;
+  if ((st = make_layout(b->n_requests, b->gaussian_counts, b->iso_counts, b->view_counts,
+                        b->heights, b->widths, 0, c->tile, L)))
+    return st;
+  ddgs_gaussians g;
+  ddgs_views v;
+  batch_structs(b, g, v);
+  return backward_common(g, v, c, L, ws, dL_dimage, t_final, n_last, out,
+                         static_cast<cudaStream_t>(stream));
 }
 
 ddgs_status ddgs_workspace_pairs(const ddgs_workspace *ws, int64_t *pairs) {

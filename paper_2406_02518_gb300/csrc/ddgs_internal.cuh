@@ -22,13 +22,37 @@ constexpr float SH_C1 = 0.48860251190291992f;  // sqrt(3 / (4 pi))
 // Device status bits (latched in the workspace).
 enum : int32_t { ST_CAPACITY = 1, ST_TIMEOUT = 2 };
 
-// Per-view constants derived once per block (IEEE-exact where the binning
-// depends on them).
+// A batch is R requests; request r owns a contiguous range of Gaussians (its
+// own cloud and bases) and a contiguous range of views; every view has its
+// own detector size. The single-cloud calls are the case R = 1. The tables
+// live in device memory (entry R / V is a sentinel holding the totals).
+struct ReqTab {
+  int64_t g_off;     // first Gaussian of the request in the parameter arrays
+  int64_t n;         // Gaussians of the request
+  int64_t n_iso;     // its first n_iso Gaussians are isotropic
+  int64_t iso_row;   // first row of the request in feat_iso
+  int64_t dir_row;   // first row of the request in feat_dir
+  int64_t blk_base;  // first preprocess block of the request
+  int32_t v_off;     // first view of the request
+  int32_t n_views;
+};
+
+struct ViewTab {
+  int64_t tile_base;  // first global tile of the view
+  int64_t rec_off;    // first (view, Gaussian) record of the view
+  int64_t img_off;    // first pixel of the view in the concatenated images
+  int32_t req, H, W, tiles_x;
+};
+
+// Per-view constants staged in shared memory by the preprocess kernels
+// (IEEE-exact where the binning depends on them).
 struct ViewConst {
   float W[9];   // rotation rows
   float t[3];
   float wt[3];  // W^T t: the source sits at -wt in world coordinates
   float fu, fv, cu, cv, sdd;
+  int32_t H, Wd, tiles_x;
+  int64_t tile_base, rec_off;
 };
 
 // Parameters shared by the rasterisers.
@@ -36,13 +60,33 @@ struct RasterParams {
   float alpha_min, alpha_max, t_min, q_max;
 };
 
-// Everything the kernels need about one render.
+// Everything the kernels need about one render (passed by value).
 struct RenderShape {
-  int64_t n, n_iso;
-  int32_t V, H, W, tile, tiles_x, tiles_y;
-  int64_t tiles_per_view, total_tiles, records;
-  int32_t key_bits;  // significant bits of the sort key
+  int32_t R, V, tile, key_bits;
+  int64_t n_total, total_tiles, records, pixels, n_blocks;
+  const ReqTab *req;    // device [R + 1]
+  const ViewTab *view;  // device [V + 1]
 };
+
+// Largest r with tab[r].blk_base <= b (the sentinel tab[R] holds the total).
+__device__ __forceinline__ int find_request(const ReqTab *tab, int R, int64_t b) {
+  int lo = 0, hi = R;  // invariant: tab[lo].blk_base <= b < tab[hi].blk_base
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (tab[mid].blk_base <= b) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Largest v with tab[v].tile_base <= t.
+__device__ __forceinline__ int find_view(const ViewTab *tab, int V, int64_t t) {
+  int lo = 0, hi = V;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (tab[mid].tile_base <= t) lo = mid; else hi = mid;
+  }
+  return lo;
+}
 
 // IEEE-exact binary32 helpers: one correctly rounded operation each, never
 // contracted into an FMA, so that the binning matches its written definition.
@@ -101,10 +145,16 @@ struct ddgs_workspace {
   uint64_t *d_pairs = nullptr;   // device pair count M
   uint64_t *h_pairs = nullptr;   // pinned host mirror
   int32_t *d_status = nullptr;
+  // request / view tables: device copies and a pinned host staging area
+  ddgs::ReqTab *d_req = nullptr;
+  ddgs::ViewTab *d_view = nullptr;
+  unsigned char *h_tab = nullptr;
+  int64_t req_cap = 0, view_cap = 0;
   // the last render
   ddgs::RenderShape shape{};
   bool have_render = false;
   uint64_t pair_bound = 0;       // grid bound used for the pair kernels
+  int64_t last_hash = 0;         // identifies the batch layout of the last render
 };
 
 namespace ddgs {
@@ -132,7 +182,6 @@ void launch_emit_keys(const RenderShape &s, ddgs_workspace &ws, cudaStream_t st)
 void launch_preprocess_bwd(const ddgs_gaussians &g, const ddgs_views &v, const ddgs_config &c,
                            const RenderShape &s, ddgs_workspace &ws, const ddgs_grads &out,
                            cudaStream_t st);
-int64_t preprocess_blocks(const RenderShape &s);
 
 // sort.cu
 void launch_scan_blocks(int64_t nblk, ddgs_workspace &ws, cudaStream_t st);

@@ -161,7 +161,7 @@ __device__ __forceinline__ uint32_t tile_rect(const ViewProj &p, float q_max, in
   return (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
 }
 
-__device__ __forceinline__ void load_view(const float *pose, const float *det, int H, int W,
+__device__ __forceinline__ void load_view(const float *pose, const float *det, const ViewTab &vt,
                                           ViewConst &vc) {
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
@@ -175,18 +175,24 @@ __device__ __forceinline__ void load_view(const float *pose, const float *det, i
   vc.sdd = det[0];
   vc.fu = divr(det[0], det[1]);
   vc.fv = divr(det[0], det[2]);
-  vc.cu = addr(mulr(0.5f, (float)W), det[3]);
-  vc.cv = addr(mulr(0.5f, (float)H), det[4]);
+  vc.cu = addr(mulr(0.5f, (float)vt.W), det[3]);
+  vc.cv = addr(mulr(0.5f, (float)vt.H), det[4]);
+  vc.H = vt.H;
+  vc.Wd = vt.W;
+  vc.tiles_x = vt.tiles_x;
+  vc.tile_base = vt.tile_base;
+  vc.rec_off = vt.rec_off;
 }
 
+// Feature row of the request's local Gaussian l.
 __device__ __forceinline__ void load_feat(const float *feat_iso, const void *feat_dir, int bf16,
-                                          int64_t i, int64_t n_iso, float f[K]) {
-  if (i < n_iso) {
-    const float4 *p = reinterpret_cast<const float4 *>(feat_iso + i * K);
+                                          const ReqTab &rq, int64_t l, float f[K]) {
+  if (l < rq.n_iso) {
+    const float4 *p = reinterpret_cast<const float4 *>(feat_iso + (rq.iso_row + l) * K);
     float4 a = p[0], b = p[1];
     f[0] = a.x; f[1] = a.y; f[2] = a.z; f[3] = a.w; f[4] = b.x; f[5] = b.y; f[6] = b.z; f[7] = b.w;
   } else if (bf16) {
-    const uint4 raw = *(reinterpret_cast<const uint4 *>(feat_dir) + (i - n_iso));
+    const uint4 raw = *(reinterpret_cast<const uint4 *>(feat_dir) + (rq.dir_row + l - rq.n_iso));
     const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -194,7 +200,8 @@ __device__ __forceinline__ void load_feat(const float *feat_iso, const void *fea
       f[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
     }
   } else {
-    const float4 *p = reinterpret_cast<const float4 *>(static_cast<const float *>(feat_dir) + (i - n_iso) * K);
+    const float4 *p = reinterpret_cast<const float4 *>(static_cast<const float *>(feat_dir) +
+                                                       (rq.dir_row + l - rq.n_iso) * K);
     float4 a = p[0], b = p[1];
     f[0] = a.x; f[1] = a.y; f[2] = a.z; f[3] = a.w; f[4] = b.x; f[5] = b.y; f[6] = b.z; f[7] = b.w;
   }
@@ -224,16 +231,32 @@ __device__ __forceinline__ uint32_t block_sum_u32(uint32_t x, uint32_t *s_red) {
   return t;
 }
 
+// The request of this block and the thread's local Gaussian index.
+struct BlockReq {
+  ReqTab rq;
+  int r;
+  int64_t l;
+  bool live;
+  __device__ __forceinline__ BlockReq(const RenderShape &s) {
+    r = find_request(s.req, s.R, blockIdx.x);
+    rq = s.req[r];
+    l = ((int64_t)blockIdx.x - rq.blk_base) * PRE_THREADS + threadIdx.x;
+    live = l < rq.n;
+  }
+};
+
 __global__ void __launch_bounds__(PRE_THREADS) preprocess_fwd_kernel(PreArgs a) {
   __shared__ ViewConst sv[VIEW_CHUNK];
   __shared__ float s_b[K], s_B[3 * K];
   __shared__ uint32_t s_red[PRE_THREADS / 32];
   const int tid = threadIdx.x;
   const RenderShape &s = a.s;
-  const int64_t i = (int64_t)blockIdx.x * PRE_THREADS + tid;
-  const bool live = i < s.n;
-  if (tid < K) s_b[tid] = a.b_iso[tid];
-  if (tid < 3 * K) s_B[tid] = a.B_dir[tid];
+  const BlockReq br(s);
+  const ReqTab &rq = br.rq;
+  const bool live = br.live;
+  const int64_t i = rq.g_off + br.l;  // index into the parameter arrays
+  if (tid < K) s_b[tid] = a.b_iso[br.r * K + tid];
+  if (tid < 3 * K) s_B[tid] = a.B_dir[br.r * 3 * K + tid];
   __syncthreads();
 
   GaussGeom gg;
@@ -247,8 +270,8 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_fwd_kernel(PreArgs a) 
     gauss_geom(ls, q, gg);
     alpha = sigmoidf_(a.logits[i]);
     float f[K];
-    load_feat(a.feat_iso, a.feat_dir, a.feat_dir_bf16, i, s.n_iso, f);
-    is_dir = i >= s.n_iso;
+    load_feat(a.feat_iso, a.feat_dir, a.feat_dir_bf16, rq, br.l, f);
+    is_dir = br.l >= rq.n_iso;
     if (!is_dir) {
       float zl = 0.f;
 #pragma unroll
@@ -266,20 +289,23 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_fwd_kernel(PreArgs a) 
   }
 
   uint32_t total = 0;
-  for (int v0 = 0; v0 < s.V; v0 += VIEW_CHUNK) {
-    const int nv = min(VIEW_CHUNK, s.V - v0);
+  for (int v0 = 0; v0 < rq.n_views; v0 += VIEW_CHUNK) {
+    const int nv = min(VIEW_CHUNK, rq.n_views - v0);
     __syncthreads();
-    if (tid < nv) load_view(a.world_to_cam + 12 * (v0 + tid), a.detector + 5 * (v0 + tid), s.H, s.W, sv[tid]);
+    if (tid < nv) {
+      const int v = rq.v_off + v0 + tid;
+      load_view(a.world_to_cam + 12 * v, a.detector + 5 * v, s.view[v], sv[tid]);
+    }
     __syncthreads();
     if (!live) continue;
     for (int vv = 0; vv < nv; ++vv) {
       const ViewConst &vc = sv[vv];
-      const int64_t rec = (int64_t)(v0 + vv) * s.n + i;
+      const int64_t rec = vc.rec_off + br.l;
       ViewProj p;
       view_proj(mu, gg.S, vc, a.dilation, a.near_plane, p);
       uint32_t tt = 0;
       int tx0 = 0, ty0 = 0, tx1 = -1, ty1 = -1;
-      if (p.valid) tt = tile_rect(p, a.q_max, s.H, s.W, s.tile, tx0, ty0, tx1, ty1);
+      if (p.valid) tt = tile_rect(p, a.q_max, vc.H, vc.Wd, s.tile, tx0, ty0, tx1, ty1);
       const float depth = p.xc[2];
       a.bin_info[rec] = make_uint4((uint32_t)tx0 | ((uint32_t)ty0 << 16),
                                    (uint32_t)tx1 | ((uint32_t)ty1 << 16), __float_as_uint(depth), tt);
@@ -335,16 +361,18 @@ struct EmitArgs {
 };
 
 // K3: pairs in (block, view, Gaussian, tile row, tile column) order, so that
-// pairs of one view with equal keys appear in ascending Gaussian index.
+// pairs of one view with equal keys appear in ascending Gaussian index. The
+// value is the Gaussian's index within its request.
 __global__ void __launch_bounds__(PRE_THREADS) emit_keys_kernel(EmitArgs a) {
   __shared__ uint32_t s_warp[PRE_THREADS / 32];
   const RenderShape &s = a.s;
-  const int64_t i = (int64_t)blockIdx.x * PRE_THREADS + threadIdx.x;
-  const bool live = i < s.n;
+  const BlockReq br(s);
+  const ReqTab &rq = br.rq;
   uint64_t base = a.blk_offset[blockIdx.x];
   bool overflow = false;
-  for (int v = 0; v < s.V; ++v) {
-    uint4 info = live ? a.bin_info[(int64_t)v * s.n + i] : make_uint4(0, 0, 0, 0);
+  for (int v = rq.v_off; v < rq.v_off + rq.n_views; ++v) {
+    const ViewTab vt = s.view[v];
+    uint4 info = br.live ? a.bin_info[vt.rec_off + br.l] : make_uint4(0, 0, 0, 0);
     uint32_t total;
     const uint32_t excl = block_excl_scan(info.w, s_warp, &total);
     if (info.w) {
@@ -353,12 +381,11 @@ __global__ void __launch_bounds__(PRE_THREADS) emit_keys_kernel(EmitArgs a) {
         overflow = true;
       } else {
         const int tx0 = info.x & 0xffff, ty0 = info.x >> 16, tx1 = info.y & 0xffff, ty1 = info.y >> 16;
-        const uint64_t tbase = (uint64_t)v * s.tiles_per_view;
         for (int ty = ty0; ty <= ty1; ++ty)
           for (int tx = tx0; tx <= tx1; ++tx) {
-            const uint64_t gt = tbase + (uint64_t)ty * s.tiles_x + tx;
+            const uint64_t gt = (uint64_t)vt.tile_base + (uint64_t)ty * vt.tiles_x + tx;
             a.keys[off] = (gt << 32) | info.z;
-            a.vals[off] = (uint32_t)i;
+            a.vals[off] = (uint32_t)br.l;
             ++off;
           }
       }
@@ -384,9 +411,8 @@ struct PreBwdArgs {
   int want_param, want_basis, want_pose;
 };
 
-// Sum 16 per-lane values over the warp with 15 shuffles; afterwards lane l
-// holds the total of component ((l >> 1) & 15) with bits reversed as below.
-// Returns the component index held by this lane.
+// Sum 16 per-lane values over the warp with 15 shuffles; returns the
+// component held by this lane (lanes with bit 0 clear and set both hold it).
 __device__ __forceinline__ int warp_reduce16(float v[16]) {
   const int lane = threadIdx.x & 31;
   bool hi = lane & 16;
@@ -426,10 +452,12 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_bwd_kernel(PreBwdArgs 
   __shared__ float s_b[K], s_B[3 * K], s_basis[4 * K];
   const int tid = threadIdx.x, lane = tid & 31;
   const RenderShape &s = a.s;
-  const int64_t i = (int64_t)blockIdx.x * PRE_THREADS + tid;
-  const bool live = i < s.n;
-  if (tid < K) s_b[tid] = a.b_iso[tid];
-  if (tid < 3 * K) s_B[tid] = a.B_dir[tid];
+  const BlockReq br(s);
+  const ReqTab &rq = br.rq;
+  const bool live = br.live;
+  const int64_t i = rq.g_off + br.l;
+  if (tid < K) s_b[tid] = a.b_iso[br.r * K + tid];
+  if (tid < 3 * K) s_B[tid] = a.B_dir[br.r * 3 * K + tid];
   if (tid < 4 * K) s_basis[tid] = 0.f;
   __syncthreads();
 
@@ -445,8 +473,8 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_bwd_kernel(PreBwdArgs 
     float q[4] = {q4.x, q4.y, q4.z, q4.w};
     gauss_geom(ls, q, gg);
     alpha = sigmoidf_(a.logits[i]);
-    load_feat(a.feat_iso, a.feat_dir, a.feat_dir_bf16, i, s.n_iso, f);
-    is_dir = i >= s.n_iso;
+    load_feat(a.feat_iso, a.feat_dir, a.feat_dir_bf16, rq, br.l, f);
+    is_dir = br.l >= rq.n_iso;
     if (!is_dir) {
       float zl = 0.f;
 #pragma unroll
@@ -466,10 +494,13 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_bwd_kernel(PreBwdArgs 
   float dSig[6] = {0, 0, 0, 0, 0, 0}, dmu[3] = {0, 0, 0};
   float dz_iso = 0.f, dh[3] = {0, 0, 0}, galpha = 0.f;
 
-  for (int v0 = 0; v0 < s.V; v0 += VIEW_CHUNK) {
-    const int nv = min(VIEW_CHUNK, s.V - v0);
+  for (int v0 = 0; v0 < rq.n_views; v0 += VIEW_CHUNK) {
+    const int nv = min(VIEW_CHUNK, rq.n_views - v0);
     __syncthreads();
-    if (tid < nv) load_view(a.world_to_cam + 12 * (v0 + tid), a.detector + 5 * (v0 + tid), s.H, s.W, sv[tid]);
+    if (tid < nv) {
+      const int v = rq.v_off + v0 + tid;
+      load_view(a.world_to_cam + 12 * v, a.detector + 5 * v, s.view[v], sv[tid]);
+    }
     for (int e = tid; e < nv * 12; e += blockDim.x) (&s_pose[0][0])[e] = 0.f;
     __syncthreads();
     for (int vv = 0; vv < nv; ++vv) {
@@ -477,7 +508,7 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_bwd_kernel(PreBwdArgs 
       float dW[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, dt[3] = {0, 0, 0};
       bool any = false;
       if (live) {
-        const int64_t rec = (int64_t)(v0 + vv) * s.n + i;
+        const int64_t rec = vc.rec_off + br.l;
         const float4 g0 = a.grad2d[2 * rec], g1 = a.grad2d[2 * rec + 1];
         any = (g0.x != 0.f) | (g0.y != 0.f) | (g0.z != 0.f) | (g0.w != 0.f) | (g1.x != 0.f) |
               (g1.y != 0.f) | (g1.z != 0.f);
@@ -590,14 +621,11 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_bwd_kernel(PreBwdArgs 
       __syncthreads();
       for (int e = tid; e < nv * 12; e += blockDim.x) {
         float x = (&s_pose[0][0])[e];
-        if (x != 0.f) atomicAdd(a.out.world_to_cam + 12 * v0 + e, x);
+        if (x != 0.f) atomicAdd(a.out.world_to_cam + 12 * (int64_t)(rq.v_off + v0) + e, x);
       }
     }
   }
 
-  if (!live) {
-    // still take part in the block-wide basis reduction below
-  }
   // per-Gaussian outputs
   if (live && a.want_param) {
     if (a.out.opacity_logits) a.out.opacity_logits[i] = galpha * alpha * (1.f - alpha);
@@ -609,7 +637,7 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_bwd_kernel(PreBwdArgs 
 #pragma unroll
       for (int k = 0; k < K; ++k) gf[k] = dz_iso * s_b[k];
       if (a.out.feat_iso) {
-        float4 *o = reinterpret_cast<float4 *>(a.out.feat_iso + i * K);
+        float4 *o = reinterpret_cast<float4 *>(a.out.feat_iso + (rq.iso_row + br.l) * K);
         o[0] = make_float4(gf[0], gf[1], gf[2], gf[3]);
         o[1] = make_float4(gf[4], gf[5], gf[6], gf[7]);
       }
@@ -617,7 +645,7 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_bwd_kernel(PreBwdArgs 
 #pragma unroll
       for (int k = 0; k < K; ++k) gf[k] = s_B[k] * dh[0] + s_B[K + k] * dh[1] + s_B[2 * K + k] * dh[2];
       if (a.out.feat_dir) {
-        float4 *o = reinterpret_cast<float4 *>(a.out.feat_dir + (i - s.n_iso) * K);
+        float4 *o = reinterpret_cast<float4 *>(a.out.feat_dir + (rq.dir_row + br.l - rq.n_iso) * K);
         o[0] = make_float4(gf[0], gf[1], gf[2], gf[3]);
         o[1] = make_float4(gf[4], gf[5], gf[6], gf[7]);
       }
@@ -671,7 +699,6 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_bwd_kernel(PreBwdArgs 
     for (int m = 0; m < 3; ++m)
 #pragma unroll
       for (int k = 0; k < K; ++k) v32[K + m * K + k] = (live && is_dir) ? dh[m] * f[k] : 0.f;
-    // reduce 32 values over the warp: two 16-value reductions
     float lo[16], hi2[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) { lo[k] = v32[k]; hi2[k] = v32[16 + k]; }
@@ -682,14 +709,13 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_bwd_kernel(PreBwdArgs 
       atomicAdd(&s_basis[16 + c_lo], hi2[0]);
     }
     __syncthreads();
-    if (tid < K && a.out.b_iso) atomicAdd(a.out.b_iso + tid, s_basis[tid]);
-    if (tid >= K && tid < 4 * K && a.out.B_dir) atomicAdd(a.out.B_dir + (tid - K), s_basis[tid]);
+    if (tid < K && a.out.b_iso) atomicAdd(a.out.b_iso + br.r * K + tid, s_basis[tid]);
+    if (tid >= K && tid < 4 * K && a.out.B_dir)
+      atomicAdd(a.out.B_dir + br.r * 3 * K + (tid - K), s_basis[tid]);
   }
 }
 
 }  // namespace
-
-int64_t preprocess_blocks(const RenderShape &s) { return (s.n + PRE_THREADS - 1) / PRE_THREADS; }
 
 void launch_preprocess_fwd(const ddgs_gaussians &g, const ddgs_views &v, const ddgs_config &c,
                            const RenderShape &s, ddgs_workspace &ws, cudaStream_t st) {
@@ -701,10 +727,9 @@ void launch_preprocess_fwd(const ddgs_gaussians &g, const ddgs_views &v, const d
   a.s = s;
   a.rec0 = ws.rec0; a.rec1 = ws.rec1; a.bin_info = reinterpret_cast<uint4 *>(ws.rect);
   a.blk_total = ws.blk_total;
-  const int64_t nb = preprocess_blocks(s);
-  if (nb > 0) {
+  if (s.n_blocks > 0) {
     LaunchScope ls(KID_PREPROCESS_FWD, st);
-    preprocess_fwd_kernel<<<(unsigned)nb, PRE_THREADS, 0, st>>>(a);
+    preprocess_fwd_kernel<<<(unsigned)s.n_blocks, PRE_THREADS, 0, st>>>(a);
   }
 }
 
@@ -717,10 +742,9 @@ void launch_emit_keys(const RenderShape &s, ddgs_workspace &ws, cudaStream_t st)
   a.vals = ws.vals[0];
   a.cap = (uint64_t)ws.pair_cap;
   a.status = ws.d_status;
-  const int64_t nb = preprocess_blocks(s);
-  if (nb > 0) {
+  if (s.n_blocks > 0) {
     LaunchScope ls(KID_EMIT_KEYS, st);
-    emit_keys_kernel<<<(unsigned)nb, PRE_THREADS, 0, st>>>(a);
+    emit_keys_kernel<<<(unsigned)s.n_blocks, PRE_THREADS, 0, st>>>(a);
   }
 }
 
@@ -739,10 +763,9 @@ void launch_preprocess_bwd(const ddgs_gaussians &g, const ddgs_views &v, const d
                   out.feat_dir) ? 1 : 0;
   a.want_basis = (out.b_iso || out.B_dir) ? 1 : 0;
   a.want_pose = out.world_to_cam ? 1 : 0;
-  const int64_t nb = preprocess_blocks(s);
-  if (nb > 0) {
+  if (s.n_blocks > 0) {
     LaunchScope ls(KID_PREPROCESS_BWD, st);
-    preprocess_bwd_kernel<<<(unsigned)nb, PRE_THREADS, 0, st>>>(a);
+    preprocess_bwd_kernel<<<(unsigned)s.n_blocks, PRE_THREADS, 0, st>>>(a);
   }
 }
 

@@ -54,15 +54,21 @@ __device__ __forceinline__ float4 empty_box() {
 
 template <int T>
 struct TileGeom {
-  int v, txi, tyi, px, py, wx0, wy0;
+  int v, txi, tyi, px, py, wx0, wy0, H, W;
   bool inside;
-  int64_t gtile;
+  int64_t gtile, rec_base, img_off, n_req;
   __device__ __forceinline__ TileGeom(const RenderShape &s, int64_t gt) {
     gtile = gt;
-    v = (int)(gt / s.tiles_per_view);
-    const int64_t local = gt - (int64_t)v * s.tiles_per_view;
-    tyi = (int)(local / s.tiles_x);
-    txi = (int)(local - (int64_t)tyi * s.tiles_x);
+    v = find_view(s.view, s.V, gt);
+    const ViewTab vt = s.view[v];
+    H = vt.H;
+    W = vt.W;
+    rec_base = vt.rec_off;
+    img_off = vt.img_off;
+    n_req = s.req[vt.req].n;
+    const int64_t local = gt - vt.tile_base;
+    tyi = (int)(local / vt.tiles_x);
+    txi = (int)(local - (int64_t)tyi * vt.tiles_x);
     constexpr int WX = T / 8;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wx = w % WX, wy = w / WX;
@@ -70,8 +76,9 @@ struct TileGeom {
     wy0 = tyi * T + wy * 4;
     px = wx0 + (lane & 7);
     py = wy0 + (lane >> 3);
-    inside = px < s.W && py < s.H;
+    inside = px < W && py < H;
   }
+  __device__ __forceinline__ int64_t pixel() const { return img_off + (int64_t)py * W + px; }
   // does the box miss this warp's 8 x 4 pixel centres?
   __device__ __forceinline__ bool misses(float4 b) const {
     return b.x > wx0 + 7.5f || b.y < wx0 + 0.5f || b.z > wy0 + 3.5f || b.w < wy0 + 0.5f;
@@ -87,7 +94,7 @@ __global__ void __launch_bounds__(T *T) raster_fwd_kernel(RasterArgs a) {
   const int tid = threadIdx.x;
   const TileGeom<T> tg(a.s, blockIdx.x);
   const uint2 range = a.ranges[tg.gtile];
-  const int64_t rec_base = (int64_t)tg.v * a.s.n;
+  const int64_t rec_base = tg.rec_base;
   const float px = tg.px + 0.5f, py = tg.py + 0.5f;
   float Tr = 1.f, C = 0.f;
   uint32_t last = 0;
@@ -98,7 +105,7 @@ __global__ void __launch_bounds__(T *T) raster_fwd_kernel(RasterArgs a) {
       const uint32_t j = b0 + e;
       if (j < range.y) {
         const uint32_t id = a.vals[j];
-        if (id < a.s.n) {
+        if (id < tg.n_req) {
           const int64_t r = rec_base + id;
           const float4 r0 = a.rec0[r], r1 = a.rec1[r];
           s_a[e] = r0;
@@ -136,7 +143,7 @@ __global__ void __launch_bounds__(T *T) raster_fwd_kernel(RasterArgs a) {
     }
   }
   if (tg.inside) {
-    const int64_t pix = ((int64_t)tg.v * a.s.H + tg.py) * a.s.W + tg.px;
+    const int64_t pix = tg.pixel();
     a.image[pix] = C;
     a.t_final[pix] = Tr;
     a.n_last[pix] = last;
@@ -183,12 +190,12 @@ __global__ void __launch_bounds__(T *T) raster_bwd_kernel(RasterArgs a) {
   const int tid = threadIdx.x;
   const TileGeom<T> tg(a.s, blockIdx.x);
   const uint2 range = a.ranges[tg.gtile];
-  const int64_t rec_base = (int64_t)tg.v * a.s.n;
+  const int64_t rec_base = tg.rec_base;
   const float px = tg.px + 0.5f, py = tg.py + 0.5f;
   float Tr = 1.f, g = 0.f;
   uint32_t last = 0;
   if (tg.inside) {
-    const int64_t pix = ((int64_t)tg.v * a.s.H + tg.py) * a.s.W + tg.px;
+    const int64_t pix = tg.pixel();
     Tr = a.t_final_in[pix];
     last = a.n_last_in[pix];
     g = a.dL_dimage[pix];
@@ -210,7 +217,7 @@ __global__ void __launch_bounds__(T *T) raster_bwd_kernel(RasterArgs a) {
       const int64_t pos_t = hi - 1 - e;  // batches run back to front
       if (pos_t >= lo) {
         const uint32_t id = a.vals[range.x + (uint32_t)pos_t];
-        if (id < a.s.n) {
+        if (id < tg.n_req) {
           const int64_t r = rec_base + id;
           const float4 r0 = a.rec0[r], r1 = a.rec1[r];
           s_a[e] = r0;

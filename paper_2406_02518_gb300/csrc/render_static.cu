@@ -25,6 +25,7 @@ namespace {
 constexpr int64_t kMaxRecords = int64_t(1) << 18;  // views x Gaussians
 constexpr int64_t kMaxPairs = int64_t(1) << 20;    // (Gaussian, tile) pairs
 constexpr int64_t kMaxTiles = int64_t(1) << 16;    // views x tiles per view
+constexpr int64_t kMaxViews = 1024;                // views per call
 constexpr int64_t kMaxBlocks = kMaxRecords / ddgs::PRE_THREADS + 1;
 constexpr int64_t kMaxSortBlocks = (kMaxPairs + ddgs::SORT_TILE - 1) / ddgs::SORT_TILE;
 
@@ -44,7 +45,13 @@ constexpr size_t kOffDigit = align256(kOffHist + kMaxSortBlocks * ddgs::RADIX * 
 constexpr size_t kOffRanges = align256(kOffDigit + ddgs::RADIX * sizeof(uint32_t));
 constexpr size_t kOffPairs = align256(kOffRanges + kMaxTiles * sizeof(uint2));
 constexpr size_t kOffStatus = align256(kOffPairs + sizeof(uint64_t));
-constexpr size_t kScratchBytes = align256(kOffStatus + sizeof(int32_t));
+constexpr size_t kOffReq = align256(kOffStatus + sizeof(int32_t));
+constexpr size_t kOffView = align256(kOffReq + 2 * sizeof(ddgs::ReqTab));
+constexpr size_t kScratchBytes = align256(kOffView + (kMaxViews + 1) * sizeof(ddgs::ViewTab));
+
+// Host-side tables of one call (thread-local storage, not heap).
+thread_local ddgs::ReqTab t_req[2];
+thread_local ddgs::ViewTab t_view[kMaxViews + 1];
 
 // The scratch itself (about 37 MiB per device).
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
@@ -96,23 +103,36 @@ extern "C" ddgs_status ddgs_render_static(const ddgs_gaussians *g, const ddgs_vi
   if (v->n_views > 0 && (!v->world_to_cam || !v->detector || !image || !t_final || !n_last))
     return DDGS_ERR_INVALID_ARG;
 
+  // one request, n_views equal views
+  if (v->n_views > kMaxViews) return DDGS_ERR_CAPACITY;
+  const int32_t tile = c->tile;
+  const int32_t tx = (v->width + tile - 1) / tile, ty = (v->height + tile - 1) / tile;
   ddgs::RenderShape s{};
-  s.n = g->n;
-  s.n_iso = g->n_iso;
+  s.R = 1;
   s.V = v->n_views;
-  s.H = v->height;
-  s.W = v->width;
-  s.tile = c->tile;
-  s.tiles_x = (v->width + c->tile - 1) / c->tile;
-  s.tiles_y = (v->height + c->tile - 1) / c->tile;
-  s.tiles_per_view = (int64_t)s.tiles_x * s.tiles_y;
-  s.total_tiles = s.tiles_per_view * s.V;
-  s.records = (int64_t)s.V * s.n;
+  s.tile = tile;
+  s.n_total = g->n;
+  s.total_tiles = (int64_t)tx * ty * v->n_views;
+  s.records = (int64_t)v->n_views * g->n;
+  s.pixels = (int64_t)v->n_views * v->height * v->width;
+  s.n_blocks = (g->n + ddgs::PRE_THREADS - 1) / ddgs::PRE_THREADS;
   int tb = 0;
   for (uint64_t x = s.total_tiles > 0 ? (uint64_t)(s.total_tiles - 1) : 0; x; x >>= 1) ++tb;
   s.key_bits = 32 + tb;
   // the sizes this fixed scratch can hold
   if (s.records > kMaxRecords || s.total_tiles > kMaxTiles) return DDGS_ERR_CAPACITY;
+  t_req[0] = ddgs::ReqTab{0, g->n, g->n_iso, 0, 0, 0, 0, v->n_views};
+  t_req[1] = ddgs::ReqTab{g->n, 0, 0, g->n_iso, g->n - g->n_iso, s.n_blocks, v->n_views, 0};
+  for (int32_t k = 0; k <= v->n_views; ++k) {
+    ddgs::ViewTab &t = t_view[k];
+    t.tile_base = (int64_t)k * tx * ty;
+    t.rec_off = (int64_t)k * g->n;
+    t.img_off = (int64_t)k * v->height * v->width;
+    t.req = k < v->n_views ? 0 : 1;
+    t.H = v->height;
+    t.W = v->width;
+    t.tiles_x = tx;
+  }
 
   unsigned char *base = nullptr;
   ddgs_status st = scratch_for_current_device(&base);
@@ -140,6 +160,15 @@ extern "C" ddgs_status ddgs_render_static(const ddgs_gaussians *g, const ddgs_vi
   ws.ranges = reinterpret_cast<uint2 *>(base + kOffRanges);
   ws.d_pairs = reinterpret_cast<uint64_t *>(base + kOffPairs);
   ws.d_status = reinterpret_cast<int32_t *>(base + kOffStatus);
+  ddgs::ReqTab *d_req = reinterpret_cast<ddgs::ReqTab *>(base + kOffReq);
+  ddgs::ViewTab *d_view = reinterpret_cast<ddgs::ViewTab *>(base + kOffView);
+  s.req = d_req;
+  s.view = d_view;
+  // tables from pageable host memory: each copy returns once its source is staged
+  if (cudaMemcpyAsync(d_req, t_req, sizeof(t_req), cudaMemcpyHostToDevice, cs) != cudaSuccess ||
+      cudaMemcpyAsync(d_view, t_view, (size_t)(v->n_views + 1) * sizeof(ddgs::ViewTab),
+                      cudaMemcpyHostToDevice, cs) != cudaSuccess)
+    return DDGS_ERR_CUDA;
 
   // counters left by the previous call start again from zero
   if (cudaMemsetAsync(ws.d_status, 0, sizeof(int32_t), cs) != cudaSuccess ||
@@ -148,7 +177,7 @@ extern "C" ddgs_status ddgs_render_static(const ddgs_gaussians *g, const ddgs_vi
   uint64_t pairs = 0;
   if (s.records > 0) {
     ddgs::launch_preprocess_fwd(*g, *v, *c, s, ws, cs);
-    ddgs::launch_scan_blocks(ddgs::preprocess_blocks(s), ws, cs);
+    ddgs::launch_scan_blocks(s.n_blocks, ws, cs);
     if (cudaGetLastError() != cudaSuccess) return DDGS_ERR_CUDA;
     // the pair count decides the sort's size: read it (no allocation)
     if (cudaMemcpyAsync(&pairs, ws.d_pairs, sizeof(uint64_t), cudaMemcpyDeviceToHost, cs) !=
