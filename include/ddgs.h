@@ -91,6 +91,8 @@ typedef struct {
                         workspace; 1: never synchronise (CUDA-graph capture):
                         capacities come from ddgs_workspace_reserve and an
                         overflow is latched as DDGS_ERR_CAPACITY */
+  int32_t batch_depth; /* list entries a rasteriser block stages per round:
+                          128 or 256 (0 = 256) */
 } ddgs_config;
 
 /* Gradient outputs of ddgs_render_backward. Every pointer may be NULL (that
@@ -234,6 +236,15 @@ ddgs_status ddgs_l1_loss(const float *image, const float *target,
 /* Number of (Gaussian, tile) pairs of the last render, read from the host
  * mirror written by that render (valid after the stream has synchronised). */
 ddgs_status ddgs_workspace_pairs(const ddgs_workspace *ws, int64_t *pairs);
+
+/* Per-request timing of the last batched render + backward on this workspace
+ * (measurement support, no counterpart in the paper). Synchronises the stream;
+ * writes to host arrays of n_requests entries the nanoseconds (%globaltimer)
+ * from the start of the render's first kernel to the end of the request's
+ * last forward-raster tile (fwd_ns) and last backward-raster tile (bwd_ns);
+ * 0 where that pass did not run. Either pointer may be NULL. */
+ddgs_status ddgs_request_times(const ddgs_workspace *ws, uint64_t *fwd_ns, uint64_t *bwd_ns,
+                               void *stream);
 
 /* Copy the binning of the last render into caller buffers (device):
  * tiles_touched [n_views][n], keys [pairs] ((global tile << 32) | depth bits,

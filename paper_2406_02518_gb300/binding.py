@@ -31,7 +31,7 @@ EXPORTS = ["ddgs_workspace_create", "ddgs_workspace_destroy", "ddgs_workspace_re
            "ddgs_status_string", "ddgs_last_cuda_error", "ddgs_device_supported",
            "ddgs_kernel_launches", "ddgs_profiler_enable", "ddgs_profiler_collect",
            "ddgs_profiler_kernel_name", "ddgs_render_static", "ddgs_render_batched",
-           "ddgs_render_batched_backward"]
+           "ddgs_render_batched_backward", "ddgs_request_times"]
 
 
 class DDGSError(RuntimeError):
@@ -58,7 +58,7 @@ class _Views(C.Structure):
 class _Config(C.Structure):
     _fields_ = [("tile", C.c_int32), ("dilation", C.c_float), ("near_plane", C.c_float),
                 ("alpha_min", C.c_float), ("alpha_max", C.c_float), ("t_min", C.c_float),
-                ("q_max", C.c_float), ("no_sync", C.c_int32)]
+                ("q_max", C.c_float), ("no_sync", C.c_int32), ("batch_depth", C.c_int32)]
 
 
 class _Batch(C.Structure):
@@ -107,6 +107,7 @@ def load(path: Optional[str] = None):
     lib.ddgs_device_supported.restype = i32
     lib.ddgs_render_batched.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     lib.ddgs_render_batched_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.ddgs_request_times.argtypes = [vp, vp, vp, vp]
     lib.ddgs_kernel_launches.restype = i64
     lib.ddgs_profiler_enable.argtypes = [i32]
     lib.ddgs_profiler_collect.argtypes = [i32, vp, vp, vp]
@@ -195,10 +196,12 @@ class Config:
     t_min: float = 1e-4
     q_max: float = 9.0
     no_sync: bool = False
+    batch_depth: int = 256
 
     def struct(self) -> _Config:
         return _Config(self.tile, self.dilation, self.near_plane, self.alpha_min,
-                       self.alpha_max, self.t_min, self.q_max, int(self.no_sync))
+                       self.alpha_max, self.t_min, self.q_max, int(self.no_sync),
+                       int(self.batch_depth))
 
 
 def cloud_from_arrays(scene, device="cuda", feat_dir_bf16: Optional[bool] = None) -> Cloud:
@@ -217,10 +220,10 @@ def views_from_arrays(views, device="cuda") -> Views:
     return Views(t(views.world_to_cam), t(views.detector), views.height, views.width)
 
 
-def config_from_settings(st, no_sync=False) -> Config:
+def config_from_settings(st, no_sync=False, batch_depth=256) -> Config:
     return Config(near_plane=st.near_plane, tile=st.tile, dilation=st.dilation,
                   alpha_min=st.alpha_min, alpha_max=st.alpha_max, t_min=st.t_min,
-                  q_max=st.q_max, no_sync=no_sync)
+                  q_max=st.q_max, no_sync=no_sync, batch_depth=batch_depth)
 
 
 class Workspace:
@@ -244,6 +247,14 @@ class Workspace:
         m = C.c_int64()
         _check(load().ddgs_workspace_pairs(self._h, C.byref(m)), "ddgs_workspace_pairs")
         return m.value
+
+    def request_times(self, n_requests: int):
+        """(fwd_ns, bwd_ns) per request of the last batched render + backward."""
+        f = np.zeros(n_requests, np.uint64)
+        b = np.zeros(n_requests, np.uint64)
+        _check(load().ddgs_request_times(self._h, f.ctypes.data, b.ctypes.data, _stream()),
+               "ddgs_request_times")
+        return f, b
 
     def sync_status(self) -> int:
         return load().ddgs_sync_status(self._h, _stream())

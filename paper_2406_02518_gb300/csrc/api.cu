@@ -141,13 +141,16 @@ ddgs_status ensure_tables(ddgs_workspace *ws, int64_t R, int64_t V) {
   }
   if (ws->d_req) CK(cudaFree(ws->d_req));
   if (ws->d_view) CK(cudaFree(ws->d_view));
+  if (ws->req_time) CK(cudaFree(ws->req_time));
   ws->d_req = nullptr;
   ws->d_view = nullptr;
+  ws->req_time = nullptr;
   ws->req_cap = ws->view_cap = 0;
   CK(cudaHostAlloc(&ws->h_tab, rc * sizeof(ddgs::ReqTab) + vc * sizeof(ddgs::ViewTab),
                    cudaHostAllocDefault));
   CK(cudaMalloc(&ws->d_req, rc * sizeof(ddgs::ReqTab)));
   CK(cudaMalloc(&ws->d_view, vc * sizeof(ddgs::ViewTab)));
+  CK(cudaMalloc(&ws->req_time, (1 + 2 * rc) * sizeof(unsigned long long)));
   ws->req_cap = rc;
   ws->view_cap = vc;
   ws->last_hash = 0;
@@ -200,6 +203,7 @@ ddgs_status ensure_records(ddgs_workspace *ws, const ddgs::RenderShape &s) {
     int64_t cap = s.total_tiles + s.total_tiles / 4 + 64;
     ddgs_status st;
     if ((st = grow(ws->ranges, ws->tile_cap, cap, 0, sizeof(uint2)))) return st;
+    if ((st = grow(ws->order, ws->tile_cap, cap, 0, sizeof(uint32_t)))) return st;
     ws->tile_cap = cap;
   }
   return DDGS_OK;
@@ -233,7 +237,7 @@ std::vector<cudaEvent_t> g_pool;
 const char *const KERNEL_NAMES[ddgs::KID_COUNT] = {
     "preprocess_fwd", "scan_blocks", "emit_keys", "radix_upsweep", "radix_scan",
     "radix_downsweep", "tile_ranges", "raster_fwd", "l1_loss", "raster_bwd",
-    "preprocess_bwd", "debug_copy"};
+    "preprocess_bwd", "debug_copy", "tile_order"};
 
 cudaEvent_t pool_event() {  // caller holds g_prof_mu
   if (!g_pool.empty()) {
@@ -357,6 +361,8 @@ ddgs_status ddgs_workspace_create(ddgs_workspace **out) {
       (e = cudaMalloc(&ws->d_pairs, sizeof(uint64_t))) != cudaSuccess ||
       (e = cudaMalloc(&ws->d_status, sizeof(int32_t))) != cudaSuccess ||
       (e = cudaMalloc(&ws->digit_total, ddgs::RADIX * sizeof(uint32_t))) != cudaSuccess ||
+      (e = cudaMalloc(&ws->lpt_counts, 128 * sizeof(uint32_t))) != cudaSuccess ||
+      (e = cudaMalloc(&ws->queue, 2 * sizeof(uint32_t))) != cudaSuccess ||
       (e = cudaHostAlloc(&ws->h_pairs, sizeof(uint64_t), cudaHostAllocDefault)) != cudaSuccess ||
       (e = cudaMemset(ws->d_status, 0, sizeof(int32_t))) != cudaSuccess ||
       (e = cudaMemset(ws->d_pairs, 0, sizeof(uint64_t))) != cudaSuccess) {
@@ -382,7 +388,8 @@ ddgs_status ddgs_workspace_destroy(ddgs_workspace *ws) {
   if (!ws) return DDGS_OK;
   void *dev[] = {ws->rec0, ws->rec1, ws->rect, ws->tiles_touched, ws->grad2d, ws->blk_total,
                  ws->blk_offset, ws->keys[0], ws->keys[1], ws->vals[0], ws->vals[1], ws->hist,
-                 ws->digit_total, ws->ranges, ws->d_pairs, ws->d_status, ws->d_req, ws->d_view};
+                 ws->digit_total, ws->ranges, ws->d_pairs, ws->d_status, ws->d_req, ws->d_view,
+                 ws->order, ws->lpt_counts, ws->queue, ws->req_time};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (ws->h_pairs) cudaFreeHost(ws->h_pairs);
@@ -431,6 +438,10 @@ ddgs_status render_common(const ddgs_gaussians &g, const ddgs_views &v, const dd
   }
   if ((st = upload_layout(ws, L, c->no_sync != 0, s_))) return st;
   ws->have_render = false;
+  ws->batch_depth = c->batch_depth == 128 ? 128 : 256;
+  // timing slots: batch start (min) and per-request ends (max)
+  CK(cudaMemsetAsync(ws->req_time, 0xff, sizeof(unsigned long long), s_));
+  CK(cudaMemsetAsync(ws->req_time + 1, 0, 2 * (size_t)s.R * sizeof(unsigned long long), s_));
   uint64_t bound = 0;
   if (s.records > 0) {
     ddgs::launch_preprocess_fwd(g, v, *c, s, *ws, s_);
@@ -458,6 +469,8 @@ ddgs_status render_common(const ddgs_gaussians &g, const ddgs_views &v, const dd
   }
   if (s.total_tiles > 0) {
     ddgs::launch_tile_ranges(s, bound, *ws, s_);
+    CK(cudaGetLastError());
+    ddgs::launch_tile_order(s, *ws, s_);
     CK(cudaGetLastError());
     ddgs::RasterParams P{c->alpha_min, c->alpha_max, c->t_min, c->q_max};
     ddgs::launch_raster_fwd(s, P, *ws, image, t_final, n_last, s_);
@@ -599,6 +612,21 @@ ddgs_status ddgs_render_batched_backward(const ddgs_batch *b, const ddgs_config 
   batch_structs(b, g, v);
   return backward_common(g, v, c, L, ws, dL_dimage, t_final, n_last, out,
                          static_cast<cudaStream_t>(stream));
+}
+
+ddgs_status ddgs_request_times(const ddgs_workspace *ws, uint64_t *fwd_ns, uint64_t *bwd_ns,
+                               void *stream) {
+  if (!ws || !ws->have_render) return DDGS_ERR_INVALID_ARG;
+  const int R = ws->shape.R;
+  std::vector<unsigned long long> t((size_t)(1 + 2 * R));
+  CK(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  CK(cudaMemcpy(t.data(), ws->req_time, t.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+  const unsigned long long t0 = t[0];
+  for (int r = 0; r < R; ++r) {
+    if (fwd_ns) fwd_ns[r] = (t[1 + r] && t[1 + r] >= t0) ? t[1 + r] - t0 : 0;
+    if (bwd_ns) bwd_ns[r] = (t[1 + R + r] && t[1 + R + r] >= t0) ? t[1 + R + r] - t0 : 0;
+  }
+  return DDGS_OK;
 }
 
 ddgs_status ddgs_workspace_pairs(const ddgs_workspace *ws, int64_t *pairs) {

@@ -141,6 +141,11 @@ struct ddgs_workspace {
   uint32_t *hist = nullptr;      // [RADIX][sort blocks]
   uint32_t *digit_total = nullptr;  // [RADIX]
   uint2 *ranges = nullptr;       // [tiles]
+  uint32_t *order = nullptr;     // [tiles] work order of the persistent rasterisers
+  uint32_t *lpt_counts = nullptr;  // bucket counts and cursors of that order
+  uint32_t *queue = nullptr;     // work-queue heads of the forward / backward rasterisers
+  unsigned long long *req_time = nullptr;  // [1 + 2 R]: batch start, per-request fwd / bwd ends
+  int batch_depth = 256;         // list entries staged per round in the rasterisers
   // scalars
   uint64_t *d_pairs = nullptr;   // device pair count M
   uint64_t *h_pairs = nullptr;   // pinned host mirror
@@ -163,7 +168,7 @@ namespace ddgs {
 enum KernelId : int {
   KID_PREPROCESS_FWD = 0, KID_SCAN_BLOCKS, KID_EMIT_KEYS, KID_RADIX_UPSWEEP, KID_RADIX_SCAN,
   KID_RADIX_DOWNSWEEP, KID_TILE_RANGES, KID_RASTER_FWD, KID_L1_LOSS, KID_RASTER_BWD,
-  KID_PREPROCESS_BWD, KID_DEBUG, KID_COUNT
+  KID_PREPROCESS_BWD, KID_DEBUG, KID_TILE_ORDER, KID_COUNT
 };
 
 // Brackets one kernel launch: counts it and, when profiling, records events.
@@ -193,6 +198,7 @@ int64_t sort_blocks(uint64_t pair_bound);
 cudaError_t prepare_sort_kernels();  // once per device, before any capture
 
 // raster.cu
+void launch_tile_order(const RenderShape &s, ddgs_workspace &ws, cudaStream_t st);
 void launch_raster_fwd(const RenderShape &s, const RasterParams &p, ddgs_workspace &ws,
                        float *image, float *t_final, uint32_t *n_last, cudaStream_t st);
 void launch_raster_bwd(const RenderShape &s, const RasterParams &p, ddgs_workspace &ws,

@@ -217,6 +217,7 @@ struct PreArgs {
   float4 *rec0, *rec1;
   uint4 *bin_info;  // (rect lo, rect hi, depth bits, tiles touched)
   uint32_t *blk_total;
+  unsigned long long *t0;  // batch start (min over blocks of %globaltimer), or null
 };
 
 __device__ __forceinline__ uint32_t block_sum_u32(uint32_t x, uint32_t *s_red) {
@@ -255,6 +256,11 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_fwd_kernel(PreArgs a) 
   const ReqTab &rq = br.rq;
   const bool live = br.live;
   const int64_t i = rq.g_off + br.l;  // index into the parameter arrays
+  if (tid == 0 && a.t0) {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    atomicMin(a.t0, t);
+  }
   if (tid < K) s_b[tid] = a.b_iso[br.r * K + tid];
   if (tid < 3 * K) s_B[tid] = a.B_dir[br.r * 3 * K + tid];
   __syncthreads();
@@ -727,6 +733,7 @@ void launch_preprocess_fwd(const ddgs_gaussians &g, const ddgs_views &v, const d
   a.s = s;
   a.rec0 = ws.rec0; a.rec1 = ws.rec1; a.bin_info = reinterpret_cast<uint4 *>(ws.rect);
   a.blk_total = ws.blk_total;
+  a.t0 = ws.req_time;
   if (s.n_blocks > 0) {
     LaunchScope ls(KID_PREPROCESS_FWD, st);
     preprocess_fwd_kernel<<<(unsigned)s.n_blocks, PRE_THREADS, 0, st>>>(a);

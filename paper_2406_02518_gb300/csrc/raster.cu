@@ -20,6 +20,8 @@
 // The per-pixel 2D gradients of one Gaussian are summed over the warp with
 // shuffles, over the block in shared memory, and reach global memory with one
 // vector atomic per (tile, Gaussian).
+#include <mutex>
+
 #include "ddgs_internal.cuh"
 
 namespace ddgs {
@@ -36,7 +38,16 @@ struct RasterArgs {
   uint32_t *n_last;
   const float *dL_dimage, *t_final_in;
   const uint32_t *n_last_in;
+  const uint32_t *order;     // global tiles, longest list first
+  uint32_t *counter;         // work-queue head (zero at launch)
+  unsigned long long *req_end;  // [R]: latest %globaltimer of a finished tile, or null
 };
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 // Conservative pixel-space box of the q <= q_max ellipse of a conic.
 __device__ __forceinline__ float4 ellipse_box(float4 r0, float4 r1, float q_max) {
@@ -85,14 +96,14 @@ struct TileGeom {
   }
 };
 
-constexpr int BATCH = 256;  // list entries staged per round
-
-template <int T>
-__global__ void __launch_bounds__(T *T) raster_fwd_kernel(RasterArgs a) {
+// One (view, tile) work item of the forward pass; BATCH list entries are
+// staged in shared memory per round.
+template <int T, int BATCH>
+__device__ __forceinline__ void fwd_tile(const RasterArgs &a, int64_t gt, float4 *s_a, float4 *s_b,
+                                         float4 *s_box) {
   constexpr int NT = T * T;
-  __shared__ float4 s_a[BATCH], s_b[BATCH], s_box[BATCH];
   const int tid = threadIdx.x;
-  const TileGeom<T> tg(a.s, blockIdx.x);
+  const TileGeom<T> tg(a.s, gt);
   const uint2 range = a.ranges[tg.gtile];
   const int64_t rec_base = tg.rec_base;
   const float px = tg.px + 0.5f, py = tg.py + 0.5f;
@@ -150,6 +161,25 @@ __global__ void __launch_bounds__(T *T) raster_fwd_kernel(RasterArgs a) {
   }
 }
 
+// Persistent forward rasteriser: each block takes work items from the queue
+// (longest tile lists first) until it is empty.
+template <int T, int BATCH>
+__global__ void __launch_bounds__(T *T) raster_fwd_kernel(RasterArgs a) {
+  __shared__ float4 s_a[BATCH], s_b[BATCH], s_box[BATCH];
+  __shared__ uint32_t s_item;
+  for (;;) {
+    __syncthreads();  // the previous item is finished by every thread
+    if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1u);
+    __syncthreads();
+    const uint32_t item = s_item;
+    if (item >= (uint32_t)a.s.total_tiles) break;
+    const int64_t gt = a.order[item];
+    fwd_tile<T, BATCH>(a, gt, s_a, s_b, s_box);
+    if (a.req_end && threadIdx.x == 0)
+      atomicMax(a.req_end + a.s.view[find_view(a.s.view, a.s.V, gt)].req, global_ns());
+  }
+}
+
 // Sum 8 per-lane values over the warp with 9 shuffles. Afterwards lanes whose
 // two low bits are 0 hold component ((l >> 4) & 1) * 4 + ((l >> 3) & 1) * 2 +
 // ((l >> 2) & 1) in v[0]; the function returns that index.
@@ -180,15 +210,24 @@ __device__ __forceinline__ int warp_reduce8(float v[8]) {
   return ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
 }
 
-template <int T>
-__global__ void __launch_bounds__(T *T) raster_bwd_kernel(RasterArgs a) {
-  __shared__ float4 s_a[BATCH], s_b[BATCH], s_box[BATCH];
-  __shared__ uint32_t s_id[BATCH];
-  __shared__ float s_acc[BATCH][8];
+template <int BATCH>
+struct BwdSmem {
+  float4 a[BATCH], b[BATCH], box[BATCH];
+  uint32_t id[BATCH];
+  float acc[BATCH][8];
+  uint32_t max_last;
+};
+
+// One (view, tile) work item of the backward pass.
+template <int T, int BATCH>
+__device__ __forceinline__ void bwd_tile(const RasterArgs &a, int64_t gt, BwdSmem<BATCH> &sm) {
+  float4 *s_a = sm.a, *s_b = sm.b, *s_box = sm.box;
+  uint32_t *s_id = sm.id;
+  float (*s_acc)[8] = sm.acc;
+  uint32_t &s_max = sm.max_last;
   constexpr int NT = T * T;
-  __shared__ uint32_t s_max;
   const int tid = threadIdx.x;
-  const TileGeom<T> tg(a.s, blockIdx.x);
+  const TileGeom<T> tg(a.s, gt);
   const uint2 range = a.ranges[tg.gtile];
   const int64_t rec_base = tg.rec_base;
   const float px = tg.px + 0.5f, py = tg.py + 0.5f;
@@ -291,23 +330,149 @@ __global__ void __launch_bounds__(T *T) raster_bwd_kernel(RasterArgs a) {
   }
 }
 
-template <int T>
-void launch_fwd_t(const RasterArgs &a, cudaStream_t st) {
-  if (a.s.total_tiles > 0) {
-    LaunchScope ls(KID_RASTER_FWD, st);
-    raster_fwd_kernel<T><<<(unsigned)a.s.total_tiles, T * T, 0, st>>>(a);
+template <int T, int BATCH>
+__global__ void __launch_bounds__(T *T) raster_bwd_kernel(RasterArgs a) {
+  __shared__ BwdSmem<BATCH> sm;
+  __shared__ uint32_t s_item;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1u);
+    __syncthreads();
+    const uint32_t item = s_item;
+    if (item >= (uint32_t)a.s.total_tiles) break;
+    const int64_t gt = a.order[item];
+    bwd_tile<T, BATCH>(a, gt, sm);
+    if (a.req_end && threadIdx.x == 0)
+      atomicMax(a.req_end + a.s.view[find_view(a.s.view, a.s.V, gt)].req, global_ns());
   }
 }
 
-template <int T>
+// ---- work order: tiles by descending list length (bucketed by log2) ----
+
+constexpr int LPT_BUCKETS = 34;  // 0 = empty list, b = 1 + floor(log2(len))
+
+__device__ __forceinline__ int lpt_bucket(uint2 r) {
+  const uint32_t len = r.y - r.x;
+  return len ? 33 - __clz(len) : 0;  // 1..33
+}
+
+__global__ void tile_bucket_count_kernel(const uint2 *ranges, int64_t n_tiles, uint32_t *counts) {
+  __shared__ uint32_t h[LPT_BUCKETS];
+  for (int b = threadIdx.x; b < LPT_BUCKETS; b += blockDim.x) h[b] = 0;
+  __syncthreads();
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles;
+       t += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&h[lpt_bucket(ranges[t])], 1u);
+  __syncthreads();
+  for (int b = threadIdx.x; b < LPT_BUCKETS; b += blockDim.x)
+    if (h[b]) atomicAdd(&counts[b], h[b]);
+}
+
+// counts[0..B) then cursors[0..B): every block derives the bucket starts
+// (longest bucket first) and claims slots with one atomic per tile.
+__global__ void tile_bucket_scatter_kernel(const uint2 *ranges, int64_t n_tiles,
+                                           const uint32_t *counts, uint32_t *cursors,
+                                           uint32_t *order) {
+  __shared__ uint32_t start[LPT_BUCKETS];
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int b = LPT_BUCKETS - 1; b >= 0; --b) {
+      start[b] = run;
+      run += counts[b];
+    }
+  }
+  __syncthreads();
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int b = lpt_bucket(ranges[t]);
+    order[start[b] + atomicAdd(&cursors[b], 1u)] = (uint32_t)t;
+  }
+}
+
+int device_sms() {
+  static int sms[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return 152;
+  if (!sms[dev]) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    sms[dev] = n > 0 ? n : 152;
+  }
+  return sms[dev];
+}
+
+// Resident blocks per SM of a kernel (cached; the query is not a stream
+// operation, so it is also legal while a stream is being captured).
+template <class Kern>
+int blocks_per_sm(Kern k, int threads) {
+  static std::mutex mu;
+  static int cache[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  if (dev >= 0 && dev < 64 && cache[dev]) return cache[dev];
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, 0) != cudaSuccess || n < 1) n = 1;
+  if (dev >= 0 && dev < 64) cache[dev] = n;
+  return n;
+}
+
+template <int T, int BATCH>
+void launch_fwd_t(const RasterArgs &a, cudaStream_t st) {
+  if (a.s.total_tiles <= 0) return;
+  auto k = raster_fwd_kernel<T, BATCH>;
+  int64_t grid = (int64_t)blocks_per_sm(k, T * T) * device_sms();
+  if (grid > a.s.total_tiles) grid = a.s.total_tiles;
+  LaunchScope ls(KID_RASTER_FWD, st);
+  k<<<(unsigned)grid, T * T, 0, st>>>(a);
+}
+
+template <int T, int BATCH>
 void launch_bwd_t(const RasterArgs &a, cudaStream_t st) {
-  if (a.s.total_tiles > 0) {
-    LaunchScope ls(KID_RASTER_BWD, st);
-    raster_bwd_kernel<T><<<(unsigned)a.s.total_tiles, T * T, 0, st>>>(a);
+  if (a.s.total_tiles <= 0) return;
+  auto k = raster_bwd_kernel<T, BATCH>;
+  int64_t grid = (int64_t)blocks_per_sm(k, T * T) * device_sms();
+  if (grid > a.s.total_tiles) grid = a.s.total_tiles;
+  LaunchScope ls(KID_RASTER_BWD, st);
+  k<<<(unsigned)grid, T * T, 0, st>>>(a);
+}
+
+template <int BATCH>
+void fwd_dispatch(const RasterArgs &a, int tile, cudaStream_t st) {
+  switch (tile) {
+    case 8: launch_fwd_t<8, BATCH>(a, st); break;
+    case 16: launch_fwd_t<16, BATCH>(a, st); break;
+    default: launch_fwd_t<32, BATCH>(a, st); break;
+  }
+}
+
+template <int BATCH>
+void bwd_dispatch(const RasterArgs &a, int tile, cudaStream_t st) {
+  switch (tile) {
+    case 8: launch_bwd_t<8, BATCH>(a, st); break;
+    case 16: launch_bwd_t<16, BATCH>(a, st); break;
+    default: launch_bwd_t<32, BATCH>(a, st); break;
   }
 }
 
 }  // namespace
+
+void launch_tile_order(const RenderShape &s, ddgs_workspace &ws, cudaStream_t st) {
+  if (s.total_tiles <= 0) return;
+  cudaMemsetAsync(ws.lpt_counts, 0, 2 * LPT_BUCKETS * sizeof(uint32_t), st);
+  int64_t blocks = (s.total_tiles + 255) / 256;
+  if (blocks > 1024) blocks = 1024;
+  {
+    LaunchScope ls(KID_TILE_ORDER, st);
+    tile_bucket_count_kernel<<<(unsigned)blocks, 256, 0, st>>>(ws.ranges, s.total_tiles, ws.lpt_counts);
+  }
+  {
+    LaunchScope ls(KID_TILE_ORDER, st);
+    tile_bucket_scatter_kernel<<<(unsigned)blocks, 256, 0, st>>>(
+        ws.ranges, s.total_tiles, ws.lpt_counts, ws.lpt_counts + LPT_BUCKETS, ws.order);
+  }
+}
 
 void launch_raster_fwd(const RenderShape &s, const RasterParams &p, ddgs_workspace &ws,
                        float *image, float *t_final, uint32_t *n_last, cudaStream_t st) {
@@ -321,11 +486,12 @@ void launch_raster_fwd(const RenderShape &s, const RasterParams &p, ddgs_workspa
   a.image = image;
   a.t_final = t_final;
   a.n_last = n_last;
-  switch (s.tile) {
-    case 8: launch_fwd_t<8>(a, st); break;
-    case 16: launch_fwd_t<16>(a, st); break;
-    default: launch_fwd_t<32>(a, st); break;
-  }
+  a.order = ws.order;
+  a.counter = ws.queue;
+  a.req_end = ws.req_time ? ws.req_time + 1 : nullptr;
+  cudaMemsetAsync(ws.queue, 0, sizeof(uint32_t), st);
+  if (ws.batch_depth == 128) fwd_dispatch<128>(a, s.tile, st);
+  else fwd_dispatch<256>(a, s.tile, st);
 }
 
 void launch_raster_bwd(const RenderShape &s, const RasterParams &p, ddgs_workspace &ws,
@@ -342,11 +508,12 @@ void launch_raster_bwd(const RenderShape &s, const RasterParams &p, ddgs_workspa
   a.dL_dimage = dL_dimage;
   a.t_final_in = t_final;
   a.n_last_in = n_last;
-  switch (s.tile) {
-    case 8: launch_bwd_t<8>(a, st); break;
-    case 16: launch_bwd_t<16>(a, st); break;
-    default: launch_bwd_t<32>(a, st); break;
-  }
+  a.order = ws.order;
+  a.counter = ws.queue + 1;
+  a.req_end = ws.req_time ? ws.req_time + 1 + s.R : nullptr;
+  cudaMemsetAsync(ws.queue + 1, 0, sizeof(uint32_t), st);
+  if (ws.batch_depth == 128) bwd_dispatch<128>(a, s.tile, st);
+  else bwd_dispatch<256>(a, s.tile, st);
 }
 
 }  // namespace ddgs

@@ -45,7 +45,10 @@ constexpr size_t kOffDigit = align256(kOffHist + kMaxSortBlocks * ddgs::RADIX * 
 constexpr size_t kOffRanges = align256(kOffDigit + ddgs::RADIX * sizeof(uint32_t));
 constexpr size_t kOffPairs = align256(kOffRanges + kMaxTiles * sizeof(uint2));
 constexpr size_t kOffStatus = align256(kOffPairs + sizeof(uint64_t));
-constexpr size_t kOffReq = align256(kOffStatus + sizeof(int32_t));
+constexpr size_t kOffOrder = align256(kOffStatus + sizeof(int32_t));
+constexpr size_t kOffLpt = align256(kOffOrder + kMaxTiles * sizeof(uint32_t));
+constexpr size_t kOffQueue = align256(kOffLpt + 128 * sizeof(uint32_t));
+constexpr size_t kOffReq = align256(kOffQueue + 2 * sizeof(uint32_t));
 constexpr size_t kOffView = align256(kOffReq + 2 * sizeof(ddgs::ReqTab));
 constexpr size_t kScratchBytes = align256(kOffView + (kMaxViews + 1) * sizeof(ddgs::ViewTab));
 
@@ -160,6 +163,11 @@ extern "C" ddgs_status ddgs_render_static(const ddgs_gaussians *g, const ddgs_vi
   ws.ranges = reinterpret_cast<uint2 *>(base + kOffRanges);
   ws.d_pairs = reinterpret_cast<uint64_t *>(base + kOffPairs);
   ws.d_status = reinterpret_cast<int32_t *>(base + kOffStatus);
+  ws.order = reinterpret_cast<uint32_t *>(base + kOffOrder);
+  ws.lpt_counts = reinterpret_cast<uint32_t *>(base + kOffLpt);
+  ws.queue = reinterpret_cast<uint32_t *>(base + kOffQueue);
+  ws.req_time = nullptr;
+  ws.batch_depth = c->batch_depth == 128 ? 128 : 256;
   ddgs::ReqTab *d_req = reinterpret_cast<ddgs::ReqTab *>(base + kOffReq);
   ddgs::ViewTab *d_view = reinterpret_cast<ddgs::ViewTab *>(base + kOffView);
   s.req = d_req;
@@ -192,6 +200,7 @@ extern "C" ddgs_status ddgs_render_static(const ddgs_gaussians *g, const ddgs_vi
   }
   if (s.total_tiles > 0) {
     ddgs::launch_tile_ranges(s, pairs, ws, cs);
+    ddgs::launch_tile_order(s, ws, cs);
     ddgs::RasterParams P{c->alpha_min, c->alpha_max, c->t_min, c->q_max};
     ddgs::launch_raster_fwd(s, P, ws, image, t_final, n_last, cs);
   }

@@ -125,3 +125,41 @@ def test_empty_batch_and_batch_without_views():
     torch.cuda.synchronize()
     assert img.numel() == 0 and float(g["means"].abs().max()) == 0.0
     ws.close()
+
+
+def test_batch_depth_and_tile_variants_agree():
+    """The staging depth changes only how many list entries a block loads per
+    round, never the per-pixel order: images are bit-identical."""
+    sc = syn.uniform_cloud(3000, seed=41)
+    views = syn.Views(np.ascontiguousarray(np.stack([
+        syn.pose_matrix(np.eye(3), np.array([0.0, 0.0, 2.0])),
+        syn.pose_matrix(syn.rot_x(0.3), np.array([0.0, 0.0, 2.1]))]).astype(np.float32)),
+        syn.detector(2, 4.0, 8.0 / 90), 77, 90)
+    cloud, gv = B.cloud_from_arrays(sc), B.views_from_arrays(views)
+    ws = B.Workspace()
+    for tile in (8, 16, 32):
+        st = syn.Settings(near_plane=0.2, tile=tile)
+        outs = []
+        for depth in (128, 256):
+            img, tf, nl = B.render(cloud, gv, B.config_from_settings(st, batch_depth=depth), ws)
+            outs.append((img.clone(), tf.clone(), nl.clone()))
+        torch.cuda.synchronize()
+        for a, b in zip(outs[0], outs[1]):
+            assert torch.equal(a, b), tile
+    ws.close()
+
+
+def test_request_times_are_reported():
+    reqs = _requests()
+    cfg = B.config_from_settings(syn.Settings(near_plane=0.2))
+    batch = _batch(reqs)
+    ws = B.Workspace()
+    img, tf, nl = B.render_batched(batch, cfg, ws)
+    B.render_batched_backward(batch, cfg, ws, torch.ones_like(img), tf, nl, want=["world_to_cam"])
+    f, b = ws.request_times(batch.n_requests)
+    for r, (sc, vs) in enumerate(reqs):
+        if vs:
+            assert 0 < f[r] < b[r] < 10**10, (r, f[r], b[r])
+        else:
+            assert f[r] == 0 and b[r] == 0
+    ws.close()
