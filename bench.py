@@ -18,6 +18,7 @@ With N > 1 (torchrun, one rank per GPU) every rank renders its own 64 poses
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -257,9 +258,38 @@ def run_ours(args):
     H, W, V = views.height, views.width, views.n_views
     cloud = B.cloud_from_arrays(scene)
     gv = B.views_from_arrays(views)
-    cfg = B.config_from_settings(st)
     target = target_image(scene, views, st)
     dev = torch.device("cuda", local)
+
+    # autotune the rasteriser launch shape (tile edge, staging depth) on this workload
+    def tune_step(tile, depth):
+        c = B.config_from_settings(dataclasses.replace(st, tile=tile), batch_depth=depth)
+        w = B.Workspace()
+        try:
+            for _ in range(2):
+                im, t_, n_ = B.render(cloud, gv, c, w)
+                lo, d_ = B.l1_loss(im, target)
+                B.render_backward(cloud, gv, c, w, d_, t_, n_, want=["world_to_cam"])
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record()
+            for _ in range(3):
+                im, t_, n_ = B.render(cloud, gv, c, w)
+                lo, d_ = B.l1_loss(im, target)
+                B.render_backward(cloud, gv, c, w, d_, t_, n_, want=["world_to_cam"])
+            a1.record()
+            torch.cuda.synchronize()
+            return a0.elapsed_time(a1) / 3
+        finally:
+            w.close()
+
+    tuned = None
+    if args.autotune:
+        from paper_2406_02518_gb300 import autotune as at
+        props = torch.cuda.get_device_properties(dev)
+        key = at.workload_key(props.name, props.multi_processor_count, H * W, scene.n, V)
+        tuned = at.tune(tune_step, key, force=args.autotune == "force")
+        st = dataclasses.replace(st, tile=tuned["tile"])
+    cfg = B.config_from_settings(st, batch_depth=tuned["batch_depth"] if tuned else 256)
 
     # size the workspace once with a synchronising render, then go graph-only
     ws = B.Workspace()
@@ -268,7 +298,7 @@ def run_ours(args):
     pairs = ws.pairs()
     tiles = V * (-(-W // st.tile)) * (-(-H // st.tile))
     ws.reserve(V * scene.n, int(pairs * 1.10) + 4096, tiles)
-    cfg_ns = B.config_from_settings(st, no_sync=True)
+    cfg_ns = B.config_from_settings(st, no_sync=True, batch_depth=cfg.batch_depth)
     img = torch.empty((V, H, W), dtype=torch.float32, device=dev)
     tf = torch.empty_like(img)
     nl = torch.empty((V, H, W), dtype=torch.int32, device=dev)
@@ -466,8 +496,10 @@ def run_ours(args):
                                    f"{V} poses, {H}x{W} detector, fwd + L1 + bwd to pose gradients",
                        "global_batch": V * world, "seq_len": None,
                        "parallelism": f"dp{world} (independent pose batches)",
-                       "l2": "working set larger than L2 (records 1.5 GB, pairs 0.6 GB per step)",
-                       "graph": "batched step replayed from one CUDA graph"},
+                       "l2": "working set larger than L2 (records 2.6 GB, pairs 1.1 GB per step)",
+                       "graph": "batched step replayed from one CUDA graph",
+                       "tile": st.tile, "batch_depth": cfg.batch_depth,
+                       "autotune": tuned},
             "plain": {"value": plain_value, "ms_per_step": ms_plain,
                       "how": "64 x (ddgs_render + ddgs_l1_loss + ddgs_render_backward), 1 view each"},
             "batched_over_plain": value / plain_value,
@@ -483,6 +515,119 @@ def run_ours(args):
     return 0
 
 
+def run_uneven(args):
+    """Uneven batch: 256 render + backward requests (own cloud of 10^4-10^6
+    Gaussians, own detector 128^2-1024^2, one view each) in one batched call
+    sequence replayed from a CUDA graph; requests/s and per-request latency."""
+    import torch
+
+    from paper_2406_02518_gb300 import autotune as at
+    from paper_2406_02518_gb300 import binding as B
+    from paper_2406_02518_gb300 import build as bld
+    from paper_2406_02518_gb300 import synthetic as syn
+
+    rank, world, local = _dist_env()
+    torch.cuda.set_device(local)
+    bld.build()
+    B.load()
+    t0 = time.time()
+    scenes, views, st = syn.uneven_workload(args.requests, seed=rank)
+    gen_s = time.time() - t0
+    dev = torch.device("cuda", local)
+    clouds = [B.cloud_from_arrays(sc) for sc in scenes]
+    gviews = [B.views_from_arrays(v) for v in views]
+    batch = B.Batch(clouds, gviews)
+    R = batch.n_requests
+    # dL/dC = 1 / (pixels of the view) everywhere: every rendered pixel back-propagates
+    hw = (batch.H.astype(np.int64) * batch.W)
+    dL = torch.cat([torch.full((int(n),), 1.0 / float(n), device=dev) for n in hw])
+
+    def run(c, w):
+        im, t_, n_ = B.render_batched(batch, c, w)
+        B.render_batched_backward(batch, c, w, dL, t_, n_, want=["world_to_cam"])
+
+    def tune_step(tile, depth):
+        c = B.config_from_settings(dataclasses.replace(st, tile=tile), batch_depth=depth)
+        w = B.Workspace()
+        try:
+            run(c, w)
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record()
+            for _ in range(2):
+                run(c, w)
+            a1.record()
+            torch.cuda.synchronize()
+            return a0.elapsed_time(a1) / 2
+        finally:
+            w.close()
+
+    props = torch.cuda.get_device_properties(dev)
+    key = at.workload_key(props.name, props.multi_processor_count, int(hw.max()),
+                          int(batch.n.sum()), int(len(hw)))
+    tuned = at.tune(tune_step, key, force=args.autotune == "force") if args.autotune else None
+    if tuned:
+        st = dataclasses.replace(st, tile=tuned["tile"])
+    depth = tuned["batch_depth"] if tuned else 256
+    cfg = B.config_from_settings(st, batch_depth=depth)
+    ws = B.Workspace()
+    img, tf, nl = B.render_batched(batch, cfg, ws)
+    torch.cuda.synchronize()
+    pairs = ws.pairs()
+    tiles = sum(int(-(-int(h) // st.tile) * -(-int(w_) // st.tile)) for h, w_ in zip(batch.H, batch.W))
+    ws.reserve(int(batch.n.sum()), int(pairs * 1.10) + 4096, tiles)
+    cfg_ns = B.config_from_settings(st, no_sync=True, batch_depth=depth)
+    gpose = torch.empty((len(hw), 3, 4), dtype=torch.float32, device=dev)
+
+    def step():
+        B.render_batched(batch, cfg_ns, ws, out=(img, tf, nl))
+        B.render_batched_backward(batch, cfg_ns, ws, dL, tf, nl, want=["world_to_cam"],
+                                  out={"world_to_cam": gpose})
+
+    s_ = torch.cuda.Stream()
+    s_.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s_):
+        step()
+    torch.cuda.current_stream().wait_stream(s_)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    clocks = Clocks(f"/tmp/ddgs_clocks_uneven_{rank}.csv")
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        graph.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    clk = clocks.stop(local)
+    assert ws.sync_status() == 0
+    # per-request latency of one step (eager, same kernels)
+    step()
+    f_ns, b_ns = ws.request_times(R)
+    lat = b_ns[b_ns > 0].astype(np.float64) / 1e6
+    line = {"metric": "uneven batch render+backward requests/s (256 requests, 1e4-1e6 Gaussians, "
+                      "128^2-1024^2 detectors)",
+            "value": R / (ms / 1e3), "unit": "requests/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{R} requests, {int(batch.n.sum())} Gaussians total, "
+                                   f"{int(hw.sum())} pixels, {pairs} pairs",
+                       "tile": st.tile, "batch_depth": depth, "autotune": tuned,
+                       "generation_s": round(gen_s, 1)},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(lat.max()),
+                           "definition": "start of the render's first kernel to the request's last "
+                                         "backward-raster tile (%globaltimer)"},
+            "clocks": clk}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -495,11 +640,19 @@ def main():
     ap.add_argument("--views", type=int, default=N_VIEWS)
     ap.add_argument("--profile-step", action="store_true",
                     help="run warm-up steps and one eager step in an NVTX range, then exit")
+    ap.add_argument("--autotune", nargs="?", const="on", default="on", choices=["on", "off", "force"],
+                    help="tune (tile, staging depth) before timing (cached per workload class)")
+    ap.add_argument("--workload", choices=["registration", "uneven"], default="registration")
+    ap.add_argument("--requests", type=int, default=256)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.autotune == "off":
+        args.autotune = None
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "uneven":
+        return run_uneven(args)
     return run_ours(args)
 
 

@@ -300,14 +300,15 @@ def body_voxels(ph: Phantom) -> np.ndarray:
 
 def gaussians_from_phantom(ph: Phantom, n_gauss: int, seed: int = 0,
                            k: int = K_FEAT, dir_frac: float = 0.2,
-                           bf16_dir: bool = False) -> Scene:
+                           bf16_dir: bool = False, candidates=None) -> Scene:
     """One candidate per voxel above -800 HU, subsampled without replacement to
     n_gauss. mu = voxel centre; log_s = log(voxel/2) + U(-1/4, 1/4);
     uniform unit quaternions; alpha = clip(0.05 + 0.9 (HU + 800) / 2300, 0.05,
     0.95) as a logit; the last floor(dir_frac n) Gaussians (a seeded random
-    subset) are direction-dependent."""
+    subset) are direction-dependent. `candidates` (body_voxels(ph)) may be
+    passed in when many clouds come from one phantom."""
     rng = np.random.default_rng(seed)
-    cand = body_voxels(ph)
+    cand = body_voxels(ph) if candidates is None else candidates
     if n_gauss > cand.size:
         raise ValueError(f"phantom has only {cand.size} voxels above -800 HU")
     pick = np.sort(rng.choice(cand.size, n_gauss, replace=False))
@@ -362,6 +363,25 @@ def large_fit_workload(n_gauss: int = 2_000_000, size: int = 1024, grid: int = 5
     views = Views(orbit_poses(n_views, SID_MM), detector(n_views, SDD_MM, 256.0 / size),
                   size, size)
     return scene, views, Settings(near_plane=0.1 * SID_MM)
+
+
+def uneven_workload(n_requests: int = 256, grid: int = 512, seed: int = 0,
+                    log10_range=(4.0, 6.0), sizes=(128, 256, 512, 1024)):
+    """Uneven batch: n_requests clouds of floor(10^U(4, 6)) Gaussians, each
+    subsampled from one 512^3 phantom (0.5 mm voxels, with lesions), each with
+    one view: a detector side drawn from `sizes` (pitch 256/side mm) and a
+    registration pose (+-15 deg, +-20 mm) about the isocenter."""
+    ph = make_phantom(grid, seed, lesions=20)
+    cand = body_voxels(ph)
+    rng = np.random.default_rng(seed + 7)
+    scenes, views = [], []
+    for r in range(n_requests):
+        n = int(10 ** rng.uniform(*log10_range))
+        scenes.append(gaussians_from_phantom(ph, n, seed=seed + 100 + r, candidates=cand))
+        side = int(rng.choice(sizes))
+        views.append(Views(registration_poses(rng, 1, SID_MM), detector(1, SDD_MM, 256.0 / side),
+                           side, side))
+    return scenes, views, Settings(near_plane=0.1 * SID_MM)
 
 
 def perturb_scene(scene: Scene, seed: int = 1, mu_mm: float = 1.0,

@@ -137,6 +137,7 @@ def test_batch_depth_and_tile_variants_agree():
         syn.detector(2, 4.0, 8.0 / 90), 77, 90)
     cloud, gv = B.cloud_from_arrays(sc), B.views_from_arrays(views)
     ws = B.Workspace()
+    images = []
     for tile in (8, 16, 32):
         st = syn.Settings(near_plane=0.2, tile=tile)
         outs = []
@@ -146,6 +147,11 @@ def test_batch_depth_and_tile_variants_agree():
         torch.cuda.synchronize()
         for a, b in zip(outs[0], outs[1]):
             assert torch.equal(a, b), tile
+        images.append(outs[0][:2])
+    # the tiling changes which lists hold a Gaussian, not which Gaussians
+    # contribute to a pixel nor their order: image and T agree across tiles
+    for other in images[1:]:
+        assert torch.equal(other[0], images[0][0]) and torch.equal(other[1], images[0][1])
     ws.close()
 
 
