@@ -225,6 +225,17 @@ def run_reference(args):
     return 0
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest of every rank's x (the step time of the slowest rank)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def algorithmic_bytes(kernel, s):
     """Algorithmic DRAM bytes per launch of an HBM-bound kernel."""
     M, N, V = s["pairs"], s["n"], s["views"]
@@ -342,12 +353,6 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
 
     # ---- batched, graph replay (headline) ----
     for _ in range(args.warmup):
@@ -366,7 +371,7 @@ def run_ours(args):
     e1.record()
     torch.cuda.synchronize()
     barrier()
-    ms_batched = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+    ms_batched = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
     clk = clocks.stop(local)
     status = ws.sync_status()
     assert status == 0, f"device status {status}"
@@ -410,7 +415,7 @@ def run_ours(args):
         plain_step()
     p1.record()
     torch.cuda.synchronize()
-    ms_plain = max_over_ranks(p0.elapsed_time(p1) / plain_steps)
+    ms_plain = max_over_ranks(p0.elapsed_time(p1) / plain_steps, world, dev)
 
     # ---- end to end through the API with host buffers ----
     poses_h = torch.empty((V, 3, 4), dtype=torch.float32).pin_memory()
@@ -431,7 +436,7 @@ def run_ours(args):
         gpose_h.copy_(gpose, non_blocking=True)
         loss_h.copy_(loss, non_blocking=True)
         torch.cuda.current_stream().synchronize()
-    t_e2e = max_over_ranks((time.perf_counter() - t0) / e2e_steps)
+    t_e2e = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world, dev)
 
     renders_step = V * world
     value = renders_step / (ms_batched / 1e3)

@@ -310,3 +310,64 @@ def test_registration_workload_sampled_pixels(ws):
     compare_grads({"pose": gp[check_views]}, {"pose": gr["pose"]}, ["pose"])
     others = np.setdiff1d(np.arange(views.n_views), check_views)
     assert np.abs(gp[others]).max() == 0.0
+
+
+def _sampled_check(scene, views, st, ws, check_views, n_random, seed, grads=("pose",), bf16=None):
+    """Full-size render and backward on the GPU; the oracle evaluates sampled
+    pixels of a few views one by one; gradients of a loss on those pixels only."""
+    cloud, gv, cfg, img, tf, nl = _run(scene, views, st, ws, bf16=bf16)
+    bins = _bins(ws, scene, views, st)
+    ref_proj = oracle.project32(scene, views, st)
+    assert np.array_equal(bins["tiles_touched"].reshape(ref_proj["tiles_touched"].shape),
+                          ref_proj["tiles_touched"])
+    assert bins["m"] == int(ref_proj["tiles_touched"].sum())
+    assert np.all(bins["keys"][1:] >= bins["keys"][:-1])
+    sub = dataclasses.replace(views, world_to_cam=views.world_to_cam[check_views].copy(),
+                              detector=views.detector[check_views].copy())
+    pix = syn.sample_pixels(sub, n_random=n_random, n_rows=1, seed=seed)
+    sel_v = np.array(check_views)[pix[:, 0]]
+    ids_all = last_ids(nl.cpu().numpy().view(np.uint32), bins, views, st.tile)
+    gi = img.cpu().numpy()[sel_v, pix[:, 1], pix[:, 2]]
+    gt = tf.cpu().numpy()[sel_v, pix[:, 1], pix[:, 2]]
+    gid = ids_all[sel_v, pix[:, 1], pix[:, 2]]
+    d32 = ref_proj["depth"][check_views]
+    rep = check_image(scene, sub, st, gi, gt, gid, depth32=d32, pix=pix)
+    assert rep["range"] > 0.05
+    w = np.zeros(img.shape, np.float64)
+    rng = np.random.default_rng(seed + 1)
+    wv = np.where(rep["ref"]["flags"] == 0, rng.uniform(-1, 1, pix.shape[0]), 0.0)
+    w[sel_v, pix[:, 1], pix[:, 2]] = wv
+    want = ["world_to_cam"] + [n for n in ("means", "log_scales", "quats", "opacity_logits",
+                                           "feat_iso", "feat_dir", "b_iso", "B_dir") if n in grads]
+    g = B.render_backward(cloud, gv, cfg, ws, torch.as_tensor(w, dtype=torch.float32, device="cuda"),
+                          tf, nl, want=want)
+    gr = oracle.render_backward(scene, sub, st, wv, pix=pix, depth32=d32)
+    gpu = {k: v.float().cpu().numpy() for k, v in g.items()}
+    gpu["pose"] = gpu.pop("world_to_cam")[check_views]
+    if "feat_iso" in gpu:
+        gpu["feat"] = np.concatenate([gpu.pop("feat_iso"), gpu.pop("feat_dir")])
+    names = [n for n in ("means", "log_scales", "quats", "opacity_logits", "feat", "b_iso", "B_dir",
+                         "pose") if n in gpu]
+    compare_grads(gpu, gr, names)
+    return rep
+
+
+@pytest.mark.slow
+def test_fit_workload_sampled_pixels(ws):
+    """100k Gaussians from a 128^3 phantom, 512^2 at 0.5 mm: forward + backward
+    with respect to every Gaussian parameter, the bases and the pose."""
+    scene, views, st = syn.fit_workload()
+    _sampled_check(scene, views, st, ws, [0], 2048, 5,
+                   grads=("means", "log_scales", "quats", "opacity_logits", "feat_iso", "feat_dir",
+                          "b_iso", "B_dir", "pose"))
+
+
+@pytest.mark.slow
+def test_large_fit_workload_sampled_pixels(ws):
+    """2M Gaussians from a 512^3 phantom with lesions, 8 orbit views at 1024^2,
+    bf16 direction features: sampled pixels of two views, all gradients."""
+    scene, views, st = syn.large_fit_workload()
+    assert scene.feat_dir_bf16
+    _sampled_check(scene, views, st, ws, [0, 5], 640, 6, bf16=True,
+                   grads=("means", "log_scales", "quats", "opacity_logits", "feat_iso", "feat_dir",
+                          "b_iso", "B_dir", "pose"))
