@@ -92,7 +92,7 @@ typedef struct {
                         capacities come from ddgs_workspace_reserve and an
                         overflow is latched as DDGS_ERR_CAPACITY */
   int32_t batch_depth; /* list entries a rasteriser block stages per round:
-                          128 or 256 (0 = 256) */
+                          128, 256 or 512 (other values = 256) */
 } ddgs_config;
 
 /* Gradient outputs of ddgs_render_backward. Every pointer may be NULL (that

@@ -16,7 +16,7 @@ import time
 from typing import Callable, Dict, Iterable, Optional, Tuple
 
 TILES = (8, 16, 32)
-DEPTHS = (128, 256)
+DEPTHS = (128, 256, 512)
 CANDIDATES = tuple((t, d) for t in TILES for d in DEPTHS)
 
 

@@ -102,16 +102,18 @@ __device__ __forceinline__ float dot3r(float a0, float a1, float a2, float b0, f
 // Per-pair evaluation shared by the forward and backward rasterisers, written
 // with explicit rounding so both kernels take bit-identical decisions.
 struct PairEval {
-  float dx, dy, G, aG, sigma;
+  float dx, dy, tx, ty, G, aG, sigma;
 };
 
+// q = d^T K d computed as d . t with t = K d (t is reused by the gradients).
 __device__ __forceinline__ bool eval_pair(float u, float v, float ca, float cb, float cc,
                                           float alpha, float px, float py,
                                           const RasterParams &P, PairEval &e) {
   e.dx = __fsub_rn(u, px);
   e.dy = __fsub_rn(v, py);
-  float xx = __fmul_rn(e.dx, e.dx), yy = __fmul_rn(e.dy, e.dy), xy = __fmul_rn(e.dx, e.dy);
-  float q = __fmaf_rn(ca, xx, __fmaf_rn(cc, yy, __fmul_rn(__fadd_rn(cb, cb), xy)));
+  e.tx = __fmaf_rn(ca, e.dx, __fmul_rn(cb, e.dy));
+  e.ty = __fmaf_rn(cb, e.dx, __fmul_rn(cc, e.dy));
+  const float q = __fmaf_rn(e.dx, e.tx, __fmul_rn(e.dy, e.ty));
   if (q > P.q_max || q < 0.f) return false;
   e.G = __expf(__fmul_rn(-0.5f, q));
   e.aG = __fmul_rn(alpha, e.G);

@@ -289,10 +289,12 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs &a, int64_t gt, BwdSme
         PairEval e;
         act = eval_pair(A.x, A.y, A.z, A.w, B.x, B.y, px, py, a.P, e);
         if (act) {
-          const float om = __fsub_rn(1.f, e.sigma);
-          Tr = __fdiv_rn(Tr, om);  // transmittance before this Gaussian
+          // 1 / (1 - sigma) with sigma <= alpha_max < 1: the fast reciprocal's
+          // relative error (~1 ulp) is far inside the gradient tolerance
+          const float inv_om = __frcp_rn(__fsub_rn(1.f, e.sigma));
+          Tr = Tr * inv_om;  // transmittance before this Gaussian
           const float c = B.z;
-          const float dC_dsigma = c * Tr - S / om;
+          const float dC_dsigma = fmaf(c, Tr, -S * inv_om);
           S = fmaf(c * e.sigma, Tr, S);
           const float gs = g * dC_dsigma;
           float gq = 0.f;
@@ -300,11 +302,11 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs &a, int64_t gt, BwdSme
             gv[5] = gs * e.G;
             gq = -0.5f * gs * B.y * e.G;
           }
-          const float tdx = 2.f * e.dx, tdy = 2.f * e.dy;
-          gv[0] = gq * (A.z * tdx + A.w * tdy);
-          gv[1] = gq * (A.w * tdx + B.x * tdy);
+          const float gq2 = gq + gq;
+          gv[0] = gq2 * e.tx;
+          gv[1] = gq2 * e.ty;
           gv[2] = gq * e.dx * e.dx;
-          gv[3] = gq * tdx * e.dy;
+          gv[3] = gq2 * e.dx * e.dy;
           gv[4] = gq * e.dy * e.dy;
           gv[6] = g * e.sigma * Tr;
         }
@@ -491,6 +493,7 @@ void launch_raster_fwd(const RenderShape &s, const RasterParams &p, ddgs_workspa
   a.req_end = ws.req_time ? ws.req_time + 1 : nullptr;
   cudaMemsetAsync(ws.queue, 0, sizeof(uint32_t), st);
   if (ws.batch_depth == 128) fwd_dispatch<128>(a, s.tile, st);
+  else if (ws.batch_depth == 512) fwd_dispatch<512>(a, s.tile, st);
   else fwd_dispatch<256>(a, s.tile, st);
 }
 
@@ -513,6 +516,7 @@ void launch_raster_bwd(const RenderShape &s, const RasterParams &p, ddgs_workspa
   a.req_end = ws.req_time ? ws.req_time + 1 + s.R : nullptr;
   cudaMemsetAsync(ws.queue + 1, 0, sizeof(uint32_t), st);
   if (ws.batch_depth == 128) bwd_dispatch<128>(a, s.tile, st);
+  else if (ws.batch_depth == 512) bwd_dispatch<512>(a, s.tile, st);
   else bwd_dispatch<256>(a, s.tile, st);
 }
 

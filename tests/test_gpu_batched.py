@@ -141,12 +141,13 @@ def test_batch_depth_and_tile_variants_agree():
     for tile in (8, 16, 32):
         st = syn.Settings(near_plane=0.2, tile=tile)
         outs = []
-        for depth in (128, 256):
+        for depth in (128, 256, 512):
             img, tf, nl = B.render(cloud, gv, B.config_from_settings(st, batch_depth=depth), ws)
             outs.append((img.clone(), tf.clone(), nl.clone()))
         torch.cuda.synchronize()
-        for a, b in zip(outs[0], outs[1]):
-            assert torch.equal(a, b), tile
+        for o in outs[1:]:
+            for a, b in zip(outs[0], o):
+                assert torch.equal(a, b), tile
         images.append(outs[0][:2])
     # the tiling changes which lists hold a Gaussian, not which Gaussians
     # contribute to a pixel nor their order: image and T agree across tiles
