@@ -85,16 +85,32 @@ struct TileGeom {
     const int wx = w % WX, wy = w / WX;
     wx0 = txi * T + wx * 8;
     wy0 = tyi * T + wy * 4;
-    px = wx0 + (lane & 7);
-    py = wy0 + (lane >> 3);
+    // the warp's 8 x 4 pixels are four 4 x 2 quarters of 8 lanes each
+    const int q = lane >> 3;
+    px = wx0 + ((q & 1) << 2) + (lane & 3);
+    py = wy0 + ((q >> 1) << 1) + ((lane >> 2) & 1);
     inside = px < W && py < H;
   }
   __device__ __forceinline__ int64_t pixel() const { return img_off + (int64_t)py * W + px; }
-  // does the box miss this warp's 8 x 4 pixel centres?
-  __device__ __forceinline__ bool misses(float4 b) const {
-    return b.x > wx0 + 7.5f || b.y < wx0 + 0.5f || b.z > wy0 + 3.5f || b.w < wy0 + 0.5f;
+  // does the box miss the 4 x 2 pixel centres of quarter q of this warp?
+  __device__ __forceinline__ bool misses_q(float4 b, int q) const {
+    const float x0 = (float)(wx0 + ((q & 1) << 2)), y0 = (float)(wy0 + ((q >> 1) << 1));
+    return b.x > x0 + 3.5f || b.y < x0 + 0.5f || b.z > y0 + 1.5f || b.w < y0 + 0.5f;
   }
 };
+
+// Each lane tests list entry c0 + lane of the staged batch against the four
+// quarters of its warp (ok: the entry exists and passes the caller's test);
+// returns the entries this lane's quarter must evaluate, in list order.
+template <int T>
+__device__ __forceinline__ uint32_t quarter_todo(const TileGeom<T> &tg, float4 box, bool ok) {
+  const int q = (threadIdx.x & 31) >> 3;
+  const uint32_t m0 = __ballot_sync(0xffffffffu, ok && !tg.misses_q(box, 0));
+  const uint32_t m1 = __ballot_sync(0xffffffffu, ok && !tg.misses_q(box, 1));
+  const uint32_t m2 = __ballot_sync(0xffffffffu, ok && !tg.misses_q(box, 2));
+  const uint32_t m3 = __ballot_sync(0xffffffffu, ok && !tg.misses_q(box, 3));
+  return q == 0 ? m0 : (q == 1 ? m1 : (q == 2 ? m2 : m3));
+}
 
 // One (view, tile) work item of the forward pass; BATCH list entries are
 // staged in shared memory per round.
@@ -129,15 +145,21 @@ __device__ __forceinline__ void fwd_tile(const RasterArgs &a, int64_t gt, float4
     }
     __syncthreads();
     const int cnt = (int)min((uint32_t)BATCH, range.y - b0);
-    // 32 entries at a time: each lane tests one entry's box against the warp's
-    // pixels, the ballot lists the entries the warp must evaluate, in order.
+    // 32 entries at a time: each lane tests one entry's box against the four
+    // quarters of its warp; each quarter then walks its own entries, so one
+    // instruction serves up to four (quarter, entry) pairs.
+    const int lane = threadIdx.x & 31;
     for (int c0 = 0; c0 < cnt; c0 += 32) {
-      if (__all_sync(0xffffffffu, done)) break;
-      const int ec = c0 + (threadIdx.x & 31);
-      uint32_t todo = __ballot_sync(0xffffffffu, ec < cnt && !tg.misses(s_box[ec]));
-      while (todo) {
-        const int k = c0 + __ffs(todo) - 1;
-        todo &= todo - 1;
+      const uint32_t dmask = __ballot_sync(0xffffffffu, done);
+      if (dmask == 0xffffffffu) break;
+      const int ec = c0 + lane;
+      const float4 box = ec < cnt ? s_box[ec] : empty_box();
+      uint32_t mine = quarter_todo<T>(tg, box, ec < cnt);
+      if (((dmask >> (lane & 24)) & 0xffu) == 0xffu) mine = 0;  // quarter finished
+      while (__any_sync(0xffffffffu, mine != 0)) {
+        if (mine == 0) continue;
+        const int k = c0 + __ffs(mine) - 1;
+        mine &= mine - 1;
         if (done) continue;
         const float4 A = s_a[k], B = s_b[k];
         PairEval e;
@@ -163,8 +185,15 @@ __device__ __forceinline__ void fwd_tile(const RasterArgs &a, int64_t gt, float4
 
 // Persistent forward rasteriser: each block takes work items from the queue
 // (longest tile lists first) until it is empty.
+// Minimum resident blocks per SM requested from the register allocator: six
+// 256-thread blocks (40 registers) for the forward, five (48) for the backward.
+template <int T>
+constexpr int fwd_min_blocks() { return T == 16 ? 6 : (T == 8 ? 16 : 1); }
+template <int T>
+constexpr int bwd_min_blocks() { return T == 16 ? 5 : (T == 8 ? 12 : 1); }
+
 template <int T, int BATCH>
-__global__ void __launch_bounds__(T *T) raster_fwd_kernel(RasterArgs a) {
+__global__ void __launch_bounds__(T *T, fwd_min_blocks<T>()) raster_fwd_kernel(RasterArgs a) {
   __shared__ float4 s_a[BATCH], s_b[BATCH], s_box[BATCH];
   __shared__ uint32_t s_item;
   for (;;) {
@@ -180,34 +209,32 @@ __global__ void __launch_bounds__(T *T) raster_fwd_kernel(RasterArgs a) {
   }
 }
 
-// Sum 8 per-lane values over the warp with 9 shuffles. Afterwards lanes whose
-// two low bits are 0 hold component ((l >> 4) & 1) * 4 + ((l >> 3) & 1) * 2 +
-// ((l >> 2) & 1) in v[0]; the function returns that index.
-__device__ __forceinline__ int warp_reduce8(float v[8]) {
+// Sum 8 per-lane values over each group of 8 lanes (a quarter) with 7
+// shuffles. Afterwards lane l of the quarter holds in v[0] the quarter's total
+// of component ((l >> 2) & 1) * 4 + ((l >> 1) & 1) * 2 + (l & 1), returned.
+__device__ __forceinline__ int quarter_reduce8(float v[8]) {
   const int lane = threadIdx.x & 31;
-  bool hi = lane & 16;
+  bool hi = lane & 4;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     float send = hi ? v[k] : v[k + 4];
     float keep = hi ? v[k + 4] : v[k];
-    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
   }
-  hi = lane & 8;
+  hi = lane & 2;
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
     float send = hi ? v[k] : v[k + 2];
     float keep = hi ? v[k + 2] : v[k];
-    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
   }
-  hi = lane & 4;
+  hi = lane & 1;
   {
     float send = hi ? v[0] : v[1];
     float keep = hi ? v[1] : v[0];
-    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
   }
-  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
-  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
-  return ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+  return ((lane >> 2) & 1) * 4 + ((lane >> 1) & 1) * 2 + (lane & 1);
 }
 
 template <int BATCH>
@@ -246,9 +273,12 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs &a, int64_t gt, BwdSme
   if (last) atomicMax(&s_max, last);
   __syncthreads();
   const uint32_t max_last = s_max;
-  uint32_t warp_last = last;
+  // last list position any pixel of each quarter added (every lane learns all four)
+  uint32_t qlast = last;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) warp_last = max(warp_last, __shfl_xor_sync(0xffffffffu, warp_last, o));
+  for (int o = 4; o > 0; o >>= 1) qlast = max(qlast, __shfl_xor_sync(0xffffffffu, qlast, o));
+  const uint32_t ql0 = __shfl_sync(0xffffffffu, qlast, 0), ql1 = __shfl_sync(0xffffffffu, qlast, 8);
+  const uint32_t ql2 = __shfl_sync(0xffffffffu, qlast, 16), ql3 = __shfl_sync(0xffffffffu, qlast, 24);
   float S = 0.f;
   for (int64_t hi = max_last; hi > 0; hi -= BATCH) {
     const int64_t lo = hi > BATCH ? hi - BATCH : 0;
@@ -272,50 +302,60 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs &a, int64_t gt, BwdSme
     }
     __syncthreads();
     const int cnt = (int)(hi - lo);
+    const int lane = threadIdx.x & 31;
     for (int c0 = 0; c0 < cnt; c0 += 32) {
-     // each lane tests one entry: inside the warp's box and before the last
-     // Gaussian any lane of the warp added
-     const int ec = c0 + (threadIdx.x & 31);
-     uint32_t todo = __ballot_sync(0xffffffffu, ec < cnt && (uint32_t)(hi - 1 - ec) < warp_last &&
-                                                    !tg.misses(s_box[ec]));
-     while (todo) {
-      const int k = c0 + __ffs(todo) - 1;
-      todo &= todo - 1;
-      const uint32_t pos = (uint32_t)(hi - 1 - k);
-      float gv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      bool act = pos < last;
-      if (act) {
-        const float4 A = s_a[k], B = s_b[k];
-        PairEval e;
-        act = eval_pair(A.x, A.y, A.z, A.w, B.x, B.y, px, py, a.P, e);
+      // each lane tests one entry against the four quarters: inside the
+      // quarter's box and before the last Gaussian the quarter added
+      const int ec = c0 + lane;
+      const bool ok = ec < cnt;
+      const float4 box = ok ? s_box[ec] : empty_box();
+      const uint32_t pe = (uint32_t)(hi - 1 - ec);
+      const uint32_t m0 = __ballot_sync(0xffffffffu, ok && pe < ql0 && !tg.misses_q(box, 0));
+      const uint32_t m1 = __ballot_sync(0xffffffffu, ok && pe < ql1 && !tg.misses_q(box, 1));
+      const uint32_t m2 = __ballot_sync(0xffffffffu, ok && pe < ql2 && !tg.misses_q(box, 2));
+      const uint32_t m3 = __ballot_sync(0xffffffffu, ok && pe < ql3 && !tg.misses_q(box, 3));
+      const int qi = lane >> 3;
+      uint32_t mine = qi == 0 ? m0 : (qi == 1 ? m1 : (qi == 2 ? m2 : m3));
+      while (__any_sync(0xffffffffu, mine != 0)) {
+        const bool has = mine != 0;
+        const int k = has ? c0 + __ffs(mine) - 1 : c0;
+        if (has) mine &= mine - 1;
+        const uint32_t pos = (uint32_t)(hi - 1 - k);
+        float gv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        bool act = has && pos < last;
         if (act) {
-          // 1 / (1 - sigma) with sigma <= alpha_max < 1: the fast reciprocal's
-          // relative error (~1 ulp) is far inside the gradient tolerance
-          const float inv_om = __frcp_rn(__fsub_rn(1.f, e.sigma));
-          Tr = Tr * inv_om;  // transmittance before this Gaussian
-          const float c = B.z;
-          const float dC_dsigma = fmaf(c, Tr, -S * inv_om);
-          S = fmaf(c * e.sigma, Tr, S);
-          const float gs = g * dC_dsigma;
-          float gq = 0.f;
-          if (!(e.aG > a.P.alpha_max)) {
-            gv[5] = gs * e.G;
-            gq = -0.5f * gs * B.y * e.G;
+          const float4 A = s_a[k], B = s_b[k];
+          PairEval e;
+          act = eval_pair(A.x, A.y, A.z, A.w, B.x, B.y, px, py, a.P, e);
+          if (act) {
+            // 1 / (1 - sigma) with sigma <= alpha_max < 1: the fast reciprocal's
+            // relative error (~1 ulp) is far inside the gradient tolerance
+            const float inv_om = __frcp_rn(__fsub_rn(1.f, e.sigma));
+            Tr = Tr * inv_om;  // transmittance before this Gaussian
+            const float c = B.z;
+            const float dC_dsigma = fmaf(c, Tr, -S * inv_om);
+            S = fmaf(c * e.sigma, Tr, S);
+            const float gs = g * dC_dsigma;
+            float gq = 0.f;
+            if (!(e.aG > a.P.alpha_max)) {
+              gv[5] = gs * e.G;
+              gq = -0.5f * gs * B.y * e.G;
+            }
+            const float gq2 = gq + gq;
+            gv[0] = gq2 * e.tx;
+            gv[1] = gq2 * e.ty;
+            gv[2] = gq * e.dx * e.dx;
+            gv[3] = gq2 * e.dx * e.dy;
+            gv[4] = gq * e.dy * e.dy;
+            gv[6] = g * e.sigma * Tr;
           }
-          const float gq2 = gq + gq;
-          gv[0] = gq2 * e.tx;
-          gv[1] = gq2 * e.ty;
-          gv[2] = gq * e.dx * e.dx;
-          gv[3] = gq2 * e.dx * e.dy;
-          gv[4] = gq * e.dy * e.dy;
-          gv[6] = g * e.sigma * Tr;
+        }
+        // sum the quarter's 8 lanes (each quarter has its own entry k)
+        if (__any_sync(0xffffffffu, act)) {
+          const int comp = quarter_reduce8(gv);
+          if (has && gv[0] != 0.f) atomicAdd(&s_acc[k][comp], gv[0]);
         }
       }
-      if (__any_sync(0xffffffffu, act)) {
-        const int comp = warp_reduce8(gv);
-        if ((threadIdx.x & 3) == 0) atomicAdd(&s_acc[k][comp], gv[0]);
-      }
-     }
     }
     __syncthreads();
     for (int e = tid; e < cnt; e += NT) {
@@ -333,7 +373,7 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs &a, int64_t gt, BwdSme
 }
 
 template <int T, int BATCH>
-__global__ void __launch_bounds__(T *T) raster_bwd_kernel(RasterArgs a) {
+__global__ void __launch_bounds__(T *T, bwd_min_blocks<T>()) raster_bwd_kernel(RasterArgs a) {
   __shared__ BwdSmem<BATCH> sm;
   __shared__ uint32_t s_item;
   for (;;) {
