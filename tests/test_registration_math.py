@@ -1,0 +1,43 @@
+"""Pose parameterisation and error measures of the registration driver (no GPU)."""
+import numpy as np
+import torch
+
+from paper_2406_02518_gb300 import registration as reg
+
+
+def test_rodrigues_and_errors_on_cpu_tensors():
+    w = torch.tensor([[0.0, 0.0, 0.0], [0.1, -0.2, 0.3]], dtype=torch.float64)
+    R = reg.rodrigues(w).numpy()
+    assert np.allclose(R[0], np.eye(3))
+    assert np.allclose(R[1] @ R[1].T, np.eye(3), atol=1e-12)
+    assert abs(reg.rotation_error_deg(R[1], np.eye(3)) - np.degrees(np.linalg.norm(w[1]))) < 1e-9
+
+
+def test_compose_is_a_rotation_about_the_isocenter():
+    R0 = torch.eye(3, dtype=torch.float64)[None]
+    t0 = torch.tensor([[0.0, 0.0, 800.0]], dtype=torch.float64)
+    w = torch.tensor([[0.0, 0.0, 0.2]], dtype=torch.float64)
+    d = torch.zeros((1, 3), dtype=torch.float64)
+    P = reg.compose(R0, t0, w, d, 10.0)[0].numpy()
+    # the isocenter (world origin) stays at t0; a point on the x axis rotates about z
+    assert np.allclose(P[:, 3], [0, 0, 800])
+    x = P[:, :3] @ np.array([10.0, 0, 0]) + P[:, 3]
+    assert np.allclose(x, [10 * np.cos(0.2), 10 * np.sin(0.2), 800])
+    P2 = reg.compose(R0, t0, torch.zeros_like(w), torch.tensor([[1.0, 0, 0]], dtype=torch.float64), 10.0)
+    assert np.allclose(P2[0, :, 3].numpy(), [10, 0, 800])
+    assert abs(reg.translation_error_mm(P, P2[0].numpy()) - 10) < 1e-9
+
+
+
+def test_rodrigues_gradient_is_finite_at_identity():
+    w = torch.zeros((2, 3), dtype=torch.float64, requires_grad=True)
+    R = reg.rodrigues(w)
+    (R * torch.arange(9, dtype=torch.float64).view(3, 3)).sum().backward()
+    assert torch.isfinite(w.grad).all()
+    # d exp([w]x) / dw at 0 is the generator: compare with finite differences
+    eps = 1e-6
+    for i in range(3):
+        wp = torch.zeros(3, dtype=torch.float64)
+        wp[i] = eps
+        fd = ((reg.rodrigues(wp) - reg.rodrigues(-wp)) / (2 * eps) * torch.arange(9, dtype=torch.float64).view(3, 3)).sum()
+        assert abs(float(fd) - float(w.grad[0, i])) < 1e-6
