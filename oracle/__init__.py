@@ -101,7 +101,9 @@ class _Pack:
                          o=_d(scene.opacity_logits), f=_d(scene.feat), b=_d(scene.b_iso),
                          B=_d(scene.B_dir), T=_d(views.world_to_cam), det=_d(views.detector))
         a = self.arrs
-        self.scene = _Scene(scene.n, scene.n_iso, scene.feat.shape[1], 1, _p(a["means"]),
+        kl = int(np.asarray(scene.B_dir).shape[0])
+        L = {3: 1, 8: 2, 15: 3, 24: 4}[kl]
+        self.scene = _Scene(scene.n, scene.n_iso, scene.feat.shape[1], L, _p(a["means"]),
                             _p(a["ls"]), _p(a["q"]), _p(a["o"]), _p(a["f"]), _p(a["b"]),
                             _p(a["B"]))
         self.views = _Views(views.n_views, views.height, views.width, _p(a["T"]), _p(a["det"]))
@@ -230,7 +232,7 @@ def render_backward(scene, views, settings, dL_dC, pix=None, depth32=None, threa
     n, k, V = scene.n, scene.feat.shape[1], views.n_views
     out = dict(means=np.zeros((n, 3)), log_scales=np.zeros((n, 3)), quats=np.zeros((n, 4)),
                opacity_logits=np.zeros(n), feat=np.zeros((n, k)), b_iso=np.zeros(k),
-               B_dir=np.zeros((3, k)), pose=np.zeros((V, 3, 4)))
+               B_dir=np.zeros(np.asarray(scene.B_dir).shape), pose=np.zeros((V, 3, 4)))
     g2 = np.zeros((V, n, 7)) if want_2d else None
     rc = lib().or_render_backward(
         C.byref(pk.scene), C.byref(pk.views), C.byref(pk.cfg), _p(depth32), m, _p(pix), _p(g),

@@ -39,14 +39,14 @@ extern "C" {
 /* ---------------- FP64 renderer ---------------- */
 
 typedef struct {
-  int32_t n, n_iso, k, L;        /* L = 1 only (k_L = L(L+2) = 3) */
+  int32_t n, n_iso, k, L;        /* k <= 64 features; degree 1 <= L <= 4, k_L = L(L+2) */
   const double *means;           /* [n][3] */
   const double *log_scales;      /* [n][3] */
   const double *quats;           /* [n][4] (w, x, y, z), any non-zero norm */
   const double *opacity_logits;  /* [n] */
   const double *feat;            /* [n][k]; row i is f_iso if i < n_iso else f_dir */
   const double *b_iso;           /* [k] */
-  const double *B_dir;           /* [k_L][k] row-major */
+  const double *B_dir;           /* [k_L][k] row-major, rows ordered (l, m = -l..l) */
 } or_scene;
 
 typedef struct {

@@ -38,8 +38,86 @@
 #include "ddgs_oracle.h"
 
 #define KMAX 64
-/* sqrt(3 / (4 pi)): normalisation of the real degree-1 harmonics. */
-#define OR_C1 0.48860251190291992
+#define LMAX 4
+#define KLMAX (LMAX * (LMAX + 2))
+#define OR_PI 3.14159265358979323846
+
+/* ---- real spherical harmonics of degrees 1..L (Eq. 3's Y without degree 0) ----
+ * For a unit direction (x, y, z), degree l, order m (-l..l):
+ *   Y_lm = (-1)^m N_l|m| sqrt(2)^[m != 0] D^|m| P_l(z) * { Re (x+iy)^|m|  (m > 0)
+ *                                                        { 1              (m = 0)
+ *                                                        { Im (x+iy)^|m|  (m < 0)
+ * with P_l the Legendre polynomial, D^m its m-th derivative, and
+ * N_lm = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!). sin^m(theta) e^{i m phi} =
+ * (x+iy)^m on the unit sphere, so this is the usual real harmonic with the
+ * Condon-Shortley sign (-1)^m; at l = 1 it is sqrt(3/(4 pi)) (-y, z, -x).
+ * Index of (l, m): l^2 - 1 + (m + l). The functions are polynomials in (x, y, z);
+ * dY[j][c] is their derivative along component c. */
+static void legendre_coeffs(int l, double c[LMAX + 1]) {
+  double p0[LMAX + 1] = {0}, p1[LMAX + 1] = {0}, p2[LMAX + 1];
+  p0[0] = 1.0;
+  p1[1] = 1.0;
+  if (l == 0) { memcpy(c, p0, sizeof p0); return; }
+  for (int n = 1; n < l; ++n) {  /* (n+1) P_{n+1} = (2n+1) z P_n - n P_{n-1} */
+    for (int i = 0; i <= LMAX; ++i) {
+      double zp = i > 0 ? p1[i - 1] : 0.0;
+      p2[i] = ((2 * n + 1) * zp - n * p0[i]) / (n + 1);
+    }
+    memcpy(p0, p1, sizeof p0);
+    memcpy(p1, p2, sizeof p1);
+  }
+  memcpy(c, p1, sizeof p1);
+}
+
+static double poly_deriv_eval(const double c[LMAX + 1], int m, double z) {
+  /* value at z of the m-th derivative of sum_i c_i z^i */
+  double acc = 0.0, zp = 1.0;
+  for (int i = m; i <= LMAX; ++i) {
+    double f = 1.0;
+    for (int j = 0; j < m; ++j) f *= (i - j);
+    acc += c[i] * f * zp;
+    zp *= z;
+  }
+  return acc;
+}
+
+static double factorial(int n) {
+  double f = 1.0;
+  for (int i = 2; i <= n; ++i) f *= i;
+  return f;
+}
+
+static void real_sh(int L, const double d[3], double *Y, double (*dY)[3]) {
+  const double x = d[0], y = d[1], z = d[2];
+  /* Re/Im of (x + i y)^m and their derivatives */
+  double re[LMAX + 1], im[LMAX + 1];
+  re[0] = 1.0; im[0] = 0.0;
+  for (int m = 1; m <= LMAX; ++m) {
+    re[m] = re[m - 1] * x - im[m - 1] * y;
+    im[m] = re[m - 1] * y + im[m - 1] * x;
+  }
+  for (int l = 1; l <= L; ++l) {
+    double c[LMAX + 1];
+    legendre_coeffs(l, c);
+    for (int m = -l; m <= l; ++m) {
+      const int am = m < 0 ? -m : m;
+      const double N = sqrt((2.0 * l + 1.0) / (4.0 * OR_PI) * factorial(l - am) / factorial(l + am)) *
+                       (am ? sqrt(2.0) : 1.0) * ((am & 1) ? -1.0 : 1.0);
+      const double Q = poly_deriv_eval(c, am, z), dQ = poly_deriv_eval(c, am + 1, z);
+      double A, dAx, dAy;
+      if (m > 0) { A = re[am]; dAx = am * re[am - 1]; dAy = -am * im[am - 1]; }
+      else if (m < 0) { A = im[am]; dAx = am * im[am - 1]; dAy = am * re[am - 1]; }
+      else { A = 1.0; dAx = 0.0; dAy = 0.0; }
+      const int j = l * l - 1 + (m + l);
+      Y[j] = N * Q * A;
+      if (dY) {
+        dY[j][0] = N * Q * dAx;
+        dY[j][1] = N * Q * dAy;
+        dY[j][2] = N * dQ * A;
+      }
+    }
+  }
+}
 
 typedef struct {
   int valid, near_cull;
@@ -47,7 +125,7 @@ typedef struct {
   double W[3][3], t[3], xc[3], fu, fv;
   double J[2][3], A[2][3], cov[3], det, conic[3];
   double u, v, alpha, color;
-  double d[3], dnorm, dhat[3], Y[3], h[3];
+  double d[3], dnorm, dhat[3], Y[KLMAX], h[KLMAX], dY[KLMAX][3];
 } g64;
 
 static double sigmoid(double x) { return 1.0 / (1.0 + exp(-x)); }
@@ -98,12 +176,10 @@ static void project64(const or_scene *sc, const or_views *vw,
       g->d[c] = mu[c] + g->W[0][c] * g->t[0] + g->W[1][c] * g->t[1] + g->W[2][c] * g->t[2];
     g->dnorm = sqrt(g->d[0] * g->d[0] + g->d[1] * g->d[1] + g->d[2] * g->d[2]);
     for (int c = 0; c < 3; ++c) g->dhat[c] = g->d[c] / g->dnorm;
-    /* real SH of degree 1, order m = -1, 0, 1: C1 * (-y, z, -x) */
-    g->Y[0] = -OR_C1 * g->dhat[1];
-    g->Y[1] = OR_C1 * g->dhat[2];
-    g->Y[2] = -OR_C1 * g->dhat[0];
+    const int kL = sc->L * (sc->L + 2);
+    real_sh(sc->L, g->dhat, g->Y, g->dY);
     double zl = 0;
-    for (int m = 0; m < 3; ++m) {
+    for (int m = 0; m < kL; ++m) {
       double hm = 0;
       for (int n = 0; n < k; ++n) hm += sc->B_dir[m * k + n] * f[n];
       g->h[m] = hm;
@@ -149,7 +225,7 @@ static void project64(const or_scene *sc, const or_views *vw,
  * color) of Gaussian i in view v into parameter and pose gradients. */
 typedef struct {
   double mu[3], ls[3], q[4], logit, f[KMAX];
-  double b_iso[KMAX], B_dir[3 * KMAX];
+  double b_iso[KMAX], B_dir[KLMAX * KMAX];
   double pose[12];
 } grad_acc;
 
@@ -168,14 +244,17 @@ static void backprop64(const or_scene *sc, int64_t i, const g64 *g,
       out->b_iso[n] += dzl * f[n];
     }
   } else {
-    double dY[3], dh[3];
-    for (int m = 0; m < 3; ++m) { dY[m] = dzl * g->h[m]; dh[m] = dzl * g->Y[m]; }
-    for (int m = 0; m < 3; ++m)
+    const int kL = sc->L * (sc->L + 2);
+    double dY[KLMAX], dh[KLMAX];
+    for (int m = 0; m < kL; ++m) { dY[m] = dzl * g->h[m]; dh[m] = dzl * g->Y[m]; }
+    for (int m = 0; m < kL; ++m)
       for (int n = 0; n < k; ++n) {
         out->B_dir[m * k + n] += dh[m] * f[n];
         out->f[n] += sc->B_dir[m * k + n] * dh[m];
       }
-    double ddh[3] = {-OR_C1 * dY[2], -OR_C1 * dY[0], OR_C1 * dY[1]};
+    double ddh[3] = {0, 0, 0};
+    for (int m = 0; m < kL; ++m)
+      for (int c3 = 0; c3 < 3; ++c3) ddh[c3] += dY[m] * g->dY[m][c3];
     double dot = ddh[0] * g->dhat[0] + ddh[1] * g->dhat[1] + ddh[2] * g->dhat[2];
     double dd[3];
     for (int c = 0; c < 3; ++c) dd[c] = (ddh[c] - g->dhat[c] * dot) / g->dnorm;
@@ -436,7 +515,7 @@ static void pixel_at(const or_views *vw, const int32_t *pix, int64_t p,
 static int check_args(const or_scene *sc, const or_views *vw, int64_t n_pix,
                       const int32_t *pix) {
   if (!sc || !vw) return 1;
-  if (sc->k < 1 || sc->k > KMAX || sc->L != 1) return 1;
+  if (sc->k < 1 || sc->k > KMAX || sc->L < 1 || sc->L > LMAX) return 1;
   if (sc->n_iso < 0 || sc->n_iso > sc->n) return 1;
   if (!pix && n_pix != (int64_t)vw->n_views * vw->height * vw->width) return 1;
   for (int64_t p = 0; pix && p < n_pix; ++p)
@@ -568,12 +647,13 @@ int or_render_backward(const or_scene *sc, const or_views *vw,
   /* chain rule per Gaussian (summed over views) and per view (over Gaussians) */
   const int64_t V = vw->n_views;
   double *pose = (double *)calloc((size_t)(V * 12 + 1), sizeof(double));
-  double *gb = (double *)calloc((size_t)(4 * k), sizeof(double));
+  const int kL = sc->L * (sc->L + 2);
+  double *gb = (double *)calloc((size_t)((1 + kL) * k), sizeof(double));
   if (!pose || !gb) { free(g2); free(pose); free(gb); return 2; }
 #pragma omp parallel
   {
     double *pose_l = (double *)calloc((size_t)(V * 12 + 1), sizeof(double));
-    double *gb_l = (double *)calloc((size_t)(4 * k), sizeof(double));
+    double *gb_l = (double *)calloc((size_t)((1 + kL) * k), sizeof(double));
 #pragma omp for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
       grad_acc acc;
@@ -593,19 +673,19 @@ int or_render_backward(const or_scene *sc, const or_views *vw,
       if (g_opacity_logits) g_opacity_logits[i] = acc.logit;
       if (g_feat) for (int c = 0; c < k; ++c) g_feat[(int64_t)k * i + c] = acc.f[c];
       for (int c = 0; c < k; ++c) gb_l[c] += acc.b_iso[c];
-      for (int c = 0; c < 3 * k; ++c) gb_l[k + c] += acc.B_dir[c];
+      for (int c = 0; c < kL * k; ++c) gb_l[k + c] += acc.B_dir[c];
     }
 #pragma omp critical
     {
       for (int64_t c = 0; c < V * 12; ++c) pose[c] += pose_l[c];
-      for (int c = 0; c < 4 * k; ++c) gb[c] += gb_l[c];
+      for (int c = 0; c < (1 + kL) * k; ++c) gb[c] += gb_l[c];
     }
     free(pose_l);
     free(gb_l);
   }
   if (g_pose) memcpy(g_pose, pose, sizeof(double) * (size_t)(V * 12));
   if (g_b_iso) memcpy(g_b_iso, gb, sizeof(double) * (size_t)k);
-  if (g_B_dir) memcpy(g_B_dir, gb + k, sizeof(double) * (size_t)(3 * k));
+  if (g_B_dir) memcpy(g_B_dir, gb + k, sizeof(double) * (size_t)(kL * k));
   free(pose);
   free(gb);
   free(g2);

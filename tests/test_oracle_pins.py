@@ -468,3 +468,112 @@ def test_count_inside_matches_brute_force():
             dx, dy = u - jj, v - ii
             ref += (a * dx * dx + 2 * b * dx * dy + c * dy * dy) <= st.q_max
     assert np.array_equal(n_in[0], ref) and ref.sum() > 50
+
+
+# ---------------------------------------------------------------------------
+# Degrees L = 2, 3 of the direction decomposition (Eq. 3, Table 2)
+# ---------------------------------------------------------------------------
+
+def _lattice(m_pts):
+    k = np.arange(m_pts) + 0.5
+    zz = 1 - 2 * k / m_pts
+    ph = math.pi * (1 + 5 ** 0.5) * k
+    return np.stack([np.sqrt(1 - zz ** 2) * np.cos(ph), np.sqrt(1 - zz ** 2) * np.sin(ph), zz], 1)
+
+
+def _sh_values(dirs, L, return_dirs=False):
+    """Y_j(d) of the oracle for every direction, recovered from the radiosity
+    sigmoid(beta Y_j) of one direction-dependent Gaussian at the isocenter.
+    The cameras are float32, so the directions the oracle sees are returned too."""
+    kl = L * (L + 2)
+    beta = 0.5
+    Y = np.zeros((dirs.shape[0], kl))
+    poses = []
+    for dv in dirs:
+        x = np.cross([0.3, 0.5, 0.8], dv)
+        x /= np.linalg.norm(x)
+        poses.append(_pose(np.stack([x, np.cross(dv, x), dv]), [0, 0, 3.0]))
+    views = _views(poses, 6.0, 0.1, 2, 2)
+    for j in range(kl):
+        B = np.zeros((kl, 8))
+        B[j, 0] = beta
+        feat = np.zeros((1, 8))
+        feat[0, 0] = 1.0
+        sc = _scene(np.zeros((1, 3)), np.full((1, 3), -3.0), [[1.0, 0, 0, 0]], [0.0], feat, 0,
+                    B_dir=B)
+        c = oracle.project64(sc, views, syn.Settings(near_plane=0.3))[:, 0, 6]
+        Y[:, j] = np.log(c / (1 - c)) / beta
+    if return_dirs:
+        T = views.world_to_cam.astype(np.float64)
+        d = np.einsum("vji,vj->vi", T[:, :, :3], T[:, :, 3])  # mu - S = W^T t at mu = 0
+        return Y, d / np.linalg.norm(d, axis=1, keepdims=True)
+    return Y
+
+
+def test_harmonics_to_degree_three_are_orthonormal_with_closed_form_zonals():
+    dirs = _lattice(6000)
+    Y, deff = _sh_values(dirs, 3, return_dirs=True)
+    gram = 4 * math.pi * (Y.T @ Y) / dirs.shape[0]
+    assert np.abs(gram - np.eye(15)).max() < 3e-3, np.abs(gram - np.eye(15)).max()
+    z = deff[:, 2]
+    # m = 0 members: sqrt((2l+1)/4pi) P_l(z)
+    assert np.allclose(Y[:, 1], math.sqrt(3 / (4 * math.pi)) * z, atol=1e-9)
+    assert np.allclose(Y[:, 5], math.sqrt(5 / (16 * math.pi)) * (3 * z ** 2 - 1), atol=1e-9)
+    assert np.allclose(Y[:, 11], math.sqrt(7 / (16 * math.pi)) * (5 * z ** 3 - 3 * z), atol=1e-9)
+
+
+def test_harmonic_degrees_have_parity_and_are_closed_under_rotation():
+    rng = np.random.default_rng(4)
+    dirs = _lattice(300)
+    Y = _sh_values(dirs, 3)
+    Yn = _sh_values(-dirs, 3)
+    for l in (1, 2, 3):
+        sl = slice(l * l - 1, l * l - 1 + 2 * l + 1)
+        assert np.allclose(Yn[:, sl], (-1) ** l * Y[:, sl], atol=1e-6)
+    Q = Rotation.random(random_state=rng).as_matrix()
+    YQ = _sh_values(dirs @ Q.T, 3)
+    for l in (1, 2, 3):
+        sl = slice(l * l - 1, l * l - 1 + 2 * l + 1)
+        D, res, *_ = np.linalg.lstsq(Y[:, sl], YQ[:, sl], rcond=None)
+        # the degree-l span is closed under rotation (up to the float32 cameras'
+        # ~1e-7 direction error) and the map is orthogonal
+        assert np.abs(Y[:, sl] @ D - YQ[:, sl]).max() < 1e-6
+        assert np.allclose(D.T @ D, np.eye(2 * l + 1), atol=1e-6)
+
+
+def test_analytic_gradient_matches_central_differences_degree_three():
+    R1 = Rotation.from_euler("zyx", [25, -15, 10], degrees=True).as_matrix()
+    views = _views([_pose(np.eye(3), [0.02, -0.03, 2.0]), _pose(R1, [0.1, 0.05, 2.3])], 4.0, 0.2,
+                   18, 22)
+    st = syn.Settings(near_plane=0.2, t_min=1e-3)
+    rng = np.random.default_rng(1)
+    for seed in range(23, 80):  # the first scene with no decision near a cutoff
+        sc = syn.uniform_cloud(5, seed=seed, extent=0.5, log_scale_range=(-2.2, -1.4),
+                               alpha_range=(0.2, 0.7), dir_frac=0.6, dir_std=1.0, k=4)
+        sc = dataclasses.replace(sc, B_dir=(rng.standard_normal((15, 4)) / 2).astype(np.float32))
+        if oracle.render(sc, views, st)["flags"].max() == 0:
+            break
+    assert oracle.render(sc, views, st)["flags"].max() == 0
+    depth32 = oracle.project32(sc, views, st)["depth"]
+    w = rng.uniform(-1, 1, (2, 18, 22))
+    g = oracle.render_backward(sc, views, st, w, depth32=depth32)
+    sc64 = dataclasses.replace(sc, **{f: getattr(sc, f).astype(np.float64) for f in
+                                      ("means", "feat", "B_dir")})
+    v64 = dataclasses.replace(views, world_to_cam=views.world_to_cam.astype(np.float64))
+    for name, arr in (("means", sc64.means), ("feat", sc64.feat), ("B_dir", sc64.B_dir),
+                      ("pose", v64.world_to_cam)):
+        G = g[name].reshape(-1)
+        scale = np.abs(G).max()
+        for idx in range(arr.size):
+            x0 = arr.reshape(-1)[idx]
+            h = 1e-6 * max(1.0, abs(x0))
+            vals = []
+            for sgn in (1, -1):
+                a2 = arr.copy()
+                a2.reshape(-1)[idx] = x0 + sgn * h
+                if name == "pose":
+                    vals.append(_loss(sc64, dataclasses.replace(v64, world_to_cam=a2), st, w, depth32))
+                else:
+                    vals.append(_loss(dataclasses.replace(sc64, **{name: a2}), v64, st, w, depth32))
+            fd = (vals[0] - vals[1]) / (2 * h)
+            assert abs(fd - G[idx]) <= 1e-6 * scale + 1e-9, (name, idx, fd, G[idx])
