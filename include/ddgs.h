@@ -17,8 +17,9 @@
  *   - No call aborts, throws or prints. Each returns a ddgs_status. Errors
  *     found while kernels run (capacity overflow in the no-sync mode) are
  *     latched in the workspace and returned by ddgs_sync_status().
- *   - Feature dimension k = 8 and harmonic degree L = 1 (k_L = L(L+2) = 3),
- *     the paper's evaluation setting (Sec. 4.1).
+ *   - Feature dimension k (1..32, default 8) and harmonic degree L (1..3,
+ *     default 1; k_L = L(L+2)) per cloud: k = 8, L = 1 is the paper's
+ *     evaluation setting (Sec. 4.1); Table 2 uses L = 3, Table 5 k = 1..32.
  *
  * Geometry (the paper fixes cone-beam X-ray imaging but not its
  * parameterisation; this is the library's reading). The X-ray source is the
@@ -37,8 +38,10 @@
 extern "C" {
 #endif
 
-#define DDGS_FEAT_DIM 8   /* k: features per Gaussian (Sec. 4.1) */
-#define DDGS_SH_DIM 3     /* k_L = L(L+2) at L = 1 (Sec. 3.2, after Eq. 3) */
+#define DDGS_FEAT_DIM 8   /* default k: features per Gaussian (Sec. 4.1) */
+#define DDGS_SH_DIM 3     /* default k_L = L(L+2) at L = 1 (Sec. 3.2, after Eq. 3) */
+#define DDGS_MAX_FEAT_DIM 32
+#define DDGS_MAX_SH_DEGREE 3
 
 typedef enum {
   DDGS_OK = 0,
@@ -62,11 +65,14 @@ typedef struct {
   const float *log_scales;     /* [n][3] */
   const float *quats;          /* [n][4] (w, x, y, z), any non-zero norm */
   const float *opacity_logits; /* [n] */
-  const float *feat_iso;       /* [n_iso][8] f_iso (Eq. 3); may be NULL if n_iso == 0 */
-  const void *feat_dir;        /* [n - n_iso][8] f_dir (Eq. 3); float32 or bfloat16 */
+  const float *feat_iso;       /* [n_iso][k] f_iso (Eq. 3); may be NULL if n_iso == 0 */
+  const void *feat_dir;        /* [n - n_iso][k] f_dir (Eq. 3); float32 or bfloat16 */
   int32_t feat_dir_bf16;       /* 0: feat_dir is float32, 1: bfloat16 */
-  const float *b_iso;          /* [8] shared isotropic basis b_iso (Eq. 3) */
-  const float *B_dir;          /* [3][8] shared direction basis B_dir (Eq. 3), row-major */
+  const float *b_iso;          /* [k] shared isotropic basis b_iso (Eq. 3) */
+  const float *B_dir;          /* [k_L][k] shared direction basis B_dir (Eq. 3), row-major;
+                                  rows ordered by degree l = 1..L, order m = -l..l */
+  int32_t feat_dim;            /* k, 1..32 (0 = 8); rows of 8 must be 16-byte aligned */
+  int32_t sh_degree;           /* L, 1..3 (0 = 1) */
 } ddgs_gaussians;
 
 /* n_views cone-beam views sharing one detector size. */
@@ -201,10 +207,12 @@ typedef struct {
   const float *feat_iso;           /* [sum iso_counts][8], request order, 16-byte aligned */
   const void *feat_dir;            /* [N - sum iso_counts][8], float32 or bfloat16 */
   int32_t feat_dir_bf16;
-  const float *b_iso;              /* [R][8] */
-  const float *B_dir;              /* [R][3][8] */
+  const float *b_iso;              /* [R][k] */
+  const float *B_dir;              /* [R][k_L][k] */
   const float *world_to_cam;       /* [V][3][4], views in request order */
   const float *detector;           /* [V][5] */
+  int32_t feat_dim;                /* k for every request, 1..32 (0 = 8) */
+  int32_t sh_degree;               /* L for every request, 1..3 (0 = 1) */
 } ddgs_batch;
 
 /* ddgs_render over a batch (same rule, Eq. 1 and Eq. 3, per view). Outputs are
@@ -216,7 +224,7 @@ ddgs_status ddgs_render_batched(const ddgs_batch *b, const ddgs_config *cfg,
                                 uint32_t *n_last, void *stream);
 
 /* ddgs_render_backward over a batch. Gradient layouts follow the batch's
- * arrays: per-Gaussian fields [N][...], b_iso [R][8], B_dir [R][3][8],
+ * arrays: per-Gaussian fields [N][...], b_iso [R][k], B_dir [R][k_L][k],
  * world_to_cam [V][3][4]. Must follow the ddgs_render_batched that filled ws
  * with the same batch. */
 ddgs_status ddgs_render_batched_backward(const ddgs_batch *b, const ddgs_config *cfg,

@@ -47,7 +47,8 @@ class _Gaussians(C.Structure):
     _fields_ = [("n", C.c_int64), ("n_iso", C.c_int64), ("means", C.c_void_p),
                 ("log_scales", C.c_void_p), ("quats", C.c_void_p), ("opacity_logits", C.c_void_p),
                 ("feat_iso", C.c_void_p), ("feat_dir", C.c_void_p), ("feat_dir_bf16", C.c_int32),
-                ("b_iso", C.c_void_p), ("B_dir", C.c_void_p)]
+                ("b_iso", C.c_void_p), ("B_dir", C.c_void_p), ("feat_dim", C.c_int32),
+                ("sh_degree", C.c_int32)]
 
 
 class _Views(C.Structure):
@@ -67,7 +68,8 @@ class _Batch(C.Structure):
                 ("widths", C.c_void_p), ("means", C.c_void_p), ("log_scales", C.c_void_p),
                 ("quats", C.c_void_p), ("opacity_logits", C.c_void_p), ("feat_iso", C.c_void_p),
                 ("feat_dir", C.c_void_p), ("feat_dir_bf16", C.c_int32), ("b_iso", C.c_void_p),
-                ("B_dir", C.c_void_p), ("world_to_cam", C.c_void_p), ("detector", C.c_void_p)]
+                ("B_dir", C.c_void_p), ("world_to_cam", C.c_void_p), ("detector", C.c_void_p),
+                ("feat_dim", C.c_int32), ("sh_degree", C.c_int32)]
 
 
 class _Grads(C.Structure):
@@ -161,13 +163,21 @@ class Cloud:
     def n_iso(self):
         return self.feat_iso.shape[0]
 
+    @property
+    def feat_dim(self):
+        return int(self.b_iso.shape[-1])
+
+    @property
+    def sh_degree(self):
+        return {3: 1, 8: 2, 15: 3}[int(self.B_dir.shape[-2])]
+
     def struct(self) -> _Gaussians:
         bf16 = self.feat_dir.dtype == torch.bfloat16
         return _Gaussians(self.n, self.n_iso, _ptr(self.means), _ptr(self.log_scales),
                           _ptr(self.quats), _ptr(self.opacity_logits),
                           _ptr(self.feat_iso) if self.n_iso else None,
                           _ptr(self.feat_dir) if self.n > self.n_iso else None, int(bf16),
-                          _ptr(self.b_iso), _ptr(self.B_dir))
+                          _ptr(self.b_iso), _ptr(self.B_dir), self.feat_dim, self.sh_degree)
 
 
 @dataclasses.dataclass
@@ -479,10 +489,12 @@ class Batch:
         bf16 = self.feat_dir.dtype == torch.bfloat16
         R = self.n_requests
         p = lambda t: _ptr(t) if t.numel() else None
+        c0 = self.clouds[0] if self.clouds else None
         return _Batch(R, self.n.ctypes.data, self.n_iso.ctypes.data, self.nv.ctypes.data,
                       self.H.ctypes.data, self.W.ctypes.data, p(self.means), p(self.log_scales),
                       p(self.quats), p(self.opacity_logits), p(self.feat_iso), p(self.feat_dir),
-                      int(bf16), p(self.b_iso), p(self.B_dir), p(self.world_to_cam), p(self.detector))
+                      int(bf16), p(self.b_iso), p(self.B_dir), p(self.world_to_cam), p(self.detector),
+                      c0.feat_dim if c0 else 8, c0.sh_degree if c0 else 1)
 
     def view_slice(self, flat: torch.Tensor, v: int) -> torch.Tensor:
         a, b = int(self.pixel_offsets[v]), int(self.pixel_offsets[v + 1])

@@ -53,12 +53,16 @@ ddgs_status check_inputs(const ddgs_gaussians *g, const ddgs_views *v, const ddg
   if (c->tile != 8 && c->tile != 16 && c->tile != 32) return DDGS_ERR_INVALID_ARG;
   if (!(c->q_max > 0) || !(c->alpha_max > 0) || !(c->t_min >= 0) || !(c->dilation >= 0))
     return DDGS_ERR_INVALID_ARG;
+  if (g->feat_dim < 0 || g->feat_dim > DDGS_MAX_FEAT_DIM || g->sh_degree < 0 ||
+      g->sh_degree > DDGS_MAX_SH_DEGREE)
+    return DDGS_ERR_INVALID_ARG;
   if (g->n > 0) {
     if (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->b_iso || !g->B_dir)
       return DDGS_ERR_INVALID_ARG;
     if (!aligned16(g->quats)) return DDGS_ERR_INVALID_ARG;
-    if (g->n_iso > 0 && (!g->feat_iso || !aligned16(g->feat_iso))) return DDGS_ERR_INVALID_ARG;
-    if (g->n > g->n_iso && (!g->feat_dir || !aligned16(g->feat_dir))) return DDGS_ERR_INVALID_ARG;
+    const bool vec = g->feat_dim == 0 || g->feat_dim == ddgs::K;  // 16-byte rows read as vectors
+    if (g->n_iso > 0 && (!g->feat_iso || (vec && !aligned16(g->feat_iso)))) return DDGS_ERR_INVALID_ARG;
+    if (g->n > g->n_iso && (!g->feat_dir || (vec && !aligned16(g->feat_dir)))) return DDGS_ERR_INVALID_ARG;
   }
   if (v->n_views > 0 && (!v->world_to_cam || !v->detector)) return DDGS_ERR_INVALID_ARG;
   return DDGS_OK;
@@ -494,8 +498,10 @@ ddgs_status backward_common(const ddgs_gaussians &g, const ddgs_views &v, const 
   if ((out->quats && !aligned16(out->quats)) || (out->feat_iso && !aligned16(out->feat_iso)) ||
       (out->feat_dir && !aligned16(out->feat_dir)))
     return DDGS_ERR_INVALID_ARG;
-  if (out->b_iso) CK(cudaMemsetAsync(out->b_iso, 0, (size_t)s.R * ddgs::K * sizeof(float), s_));
-  if (out->B_dir) CK(cudaMemsetAsync(out->B_dir, 0, (size_t)s.R * 3 * ddgs::K * sizeof(float), s_));
+  const int kf = g.feat_dim ? g.feat_dim : ddgs::K, lsh = g.sh_degree ? g.sh_degree : 1;
+  if (out->b_iso) CK(cudaMemsetAsync(out->b_iso, 0, (size_t)s.R * kf * sizeof(float), s_));
+  if (out->B_dir)
+    CK(cudaMemsetAsync(out->B_dir, 0, (size_t)s.R * lsh * (lsh + 2) * kf * sizeof(float), s_));
   if (out->world_to_cam)
     CK(cudaMemsetAsync(out->world_to_cam, 0, (size_t)s.V * 12 * sizeof(float), s_));
   if (s.n_total == 0) return DDGS_OK;  // parameter gradients empty, pose/basis zero
@@ -522,6 +528,10 @@ ddgs_status single_layout(const ddgs_gaussians *g, const ddgs_views *v, const dd
 
 ddgs_status check_batch(const ddgs_batch *b, const ddgs_config *c) {
   if (!b || !c || b->n_requests < 0) return DDGS_ERR_INVALID_ARG;
+  if (b->feat_dim < 0 || b->feat_dim > DDGS_MAX_FEAT_DIM || b->sh_degree < 0 ||
+      b->sh_degree > DDGS_MAX_SH_DEGREE)
+    return DDGS_ERR_INVALID_ARG;
+  const bool vec = b->feat_dim == 0 || b->feat_dim == ddgs::K;
   if (c->tile != 8 && c->tile != 16 && c->tile != 32) return DDGS_ERR_INVALID_ARG;
   if (!(c->q_max > 0) || !(c->alpha_max > 0) || !(c->t_min >= 0) || !(c->dilation >= 0))
     return DDGS_ERR_INVALID_ARG;
@@ -539,8 +549,8 @@ ddgs_status check_batch(const ddgs_batch *b, const ddgs_config *c) {
     if (!b->means || !b->log_scales || !b->quats || !b->opacity_logits || !b->b_iso || !b->B_dir ||
         !aligned16(b->quats))
       return DDGS_ERR_INVALID_ARG;
-    if (ni > 0 && (!b->feat_iso || !aligned16(b->feat_iso))) return DDGS_ERR_INVALID_ARG;
-    if (n > ni && (!b->feat_dir || !aligned16(b->feat_dir))) return DDGS_ERR_INVALID_ARG;
+    if (ni > 0 && (!b->feat_iso || (vec && !aligned16(b->feat_iso)))) return DDGS_ERR_INVALID_ARG;
+    if (n > ni && (!b->feat_dir || (vec && !aligned16(b->feat_dir)))) return DDGS_ERR_INVALID_ARG;
   }
   return DDGS_OK;
 }
@@ -550,6 +560,7 @@ void batch_structs(const ddgs_batch *b, ddgs_gaussians &g, ddgs_views &v) {
   g.means = b->means; g.log_scales = b->log_scales; g.quats = b->quats;
   g.opacity_logits = b->opacity_logits; g.feat_iso = b->feat_iso; g.feat_dir = b->feat_dir;
   g.feat_dir_bf16 = b->feat_dir_bf16; g.b_iso = b->b_iso; g.B_dir = b->B_dir;
+  g.feat_dim = b->feat_dim; g.sh_degree = b->sh_degree;
   v = ddgs_views{};
   v.world_to_cam = b->world_to_cam;
   v.detector = b->detector;

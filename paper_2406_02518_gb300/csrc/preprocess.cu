@@ -207,6 +207,81 @@ __device__ __forceinline__ void load_feat(const float *feat_iso, const void *fea
   }
 }
 
+// ---- generic radiosity: runtime feature dimension k <= 32, degree L <= 3 ----
+constexpr int KG = 32;   // largest feature dimension of the generic kernels
+constexpr int KLG = 15;  // largest k_L = L(L+2) (L = 3)
+
+__device__ __forceinline__ float load_feat1(const float *feat_iso, const void *feat_dir, int bf16,
+                                            const ReqTab &rq, int64_t l, int K, int k) {
+  if (l < rq.n_iso) return feat_iso[(rq.iso_row + l) * K + k];
+  const int64_t idx = (rq.dir_row + l - rq.n_iso) * K + k;
+  if (bf16) {
+    const unsigned short u = static_cast<const unsigned short *>(feat_dir)[idx];
+    return __uint_as_float((uint32_t)u << 16);
+  }
+  return static_cast<const float *>(feat_dir)[idx];
+}
+
+// Real spherical harmonics of degrees 1..L for a unit direction, Y_lm =
+// (-1)^m N_lm sqrt(2)^[m != 0] D^|m| P_l(z) * (Re (x+iy)^|m| for m > 0, 1 for
+// m = 0, Im (x+iy)^|m| for m < 0), N_lm = sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!),
+// ordered (l, m = -l..l). Row j of the table holds m and the coefficients of
+// the z polynomial; each block builds it from these definitions.
+struct ShTable {
+  float c[KLG][4];
+  int m[KLG];
+};
+
+__device__ void sh_table_row(int j, ShTable &t) {
+  int l = 1;
+  while ((l + 1) * (l + 1) - 1 <= j) ++l;
+  const int m = j - (l * l - 1) - l, am = m < 0 ? -m : m;
+  double p0[4] = {1, 0, 0, 0}, p1[4] = {0, 1, 0, 0};
+  for (int n = 1; n < l; ++n) {  // (n+1) P_{n+1} = (2n+1) z P_n - n P_{n-1}
+    double p2[4];
+    for (int i = 0; i < 4; ++i) p2[i] = ((2 * n + 1) * (i ? p1[i - 1] : 0.0) - n * p0[i]) / (n + 1);
+    for (int i = 0; i < 4; ++i) { p0[i] = p1[i]; p1[i] = p2[i]; }
+  }
+  double fl = 1, fh = 1;  // (l-|m|)!, (l+|m|)!
+  for (int i = 2; i <= l - am; ++i) fl *= i;
+  for (int i = 2; i <= l + am; ++i) fh *= i;
+  const double norm = sqrt((2.0 * l + 1.0) / (4.0 * 3.14159265358979323846) * fl / fh) *
+                      (am ? 1.4142135623730951 : 1.0) * ((am & 1) ? -1.0 : 1.0);
+  for (int i = 0; i < 4; ++i) {
+    double d = 0;
+    if (i + am < 4) {
+      d = p1[i + am];
+      for (int q = 0; q < am; ++q) d *= (i + am - q);
+    }
+    t.c[j][i] = (float)(norm * d);
+  }
+  t.m[j] = m;
+}
+
+// Y[j] and, if dY is given, the derivative of Y[j] along x, y, z.
+__device__ __forceinline__ void sh_eval(const ShTable &t, int kL, float x, float y, float z, float *Y,
+                                        float (*dY)[3]) {
+  const float re[4] = {1.f, x, x * x - y * y, x * (x * x - y * y) - y * (2.f * x * y)};
+  const float im[4] = {0.f, y, 2.f * x * y, x * (2.f * x * y) + y * (x * x - y * y)};
+#pragma unroll
+  for (int j = 0; j < KLG; ++j) {
+    if (j >= kL) break;
+    const int m = t.m[j], am = m < 0 ? -m : m;
+    const float *c = t.c[j];
+    const float Q = fmaf(fmaf(fmaf(c[3], z, c[2]), z, c[1]), z, c[0]);
+    float A = 1.f, dAx = 0.f, dAy = 0.f;
+    if (m > 0) { A = re[am]; dAx = am * re[am - 1]; dAy = -am * im[am - 1]; }
+    else if (m < 0) { A = im[am]; dAx = am * im[am - 1]; dAy = am * re[am - 1]; }
+    Y[j] = Q * A;
+    if (dY) {
+      const float dQ = fmaf(fmaf(3.f * c[3], z, 2.f * c[2]), z, c[1]);
+      dY[j][0] = Q * dAx;
+      dY[j][1] = Q * dAy;
+      dY[j][2] = dQ * A;
+    }
+  }
+}
+
 struct PreArgs {
   const float *means, *log_scales, *quats, *logits, *feat_iso;
   const void *feat_dir;
@@ -214,6 +289,7 @@ struct PreArgs {
   const float *b_iso, *B_dir, *world_to_cam, *detector;
   float dilation, near_plane, q_max;
   RenderShape s;
+  int K, L;          // feature dimension and harmonic degree
   float4 *rec0, *rec1;
   uint4 *bin_info;  // (rect lo, rect hi, depth bits, tiles touched)
   uint32_t *blk_total;
@@ -246,9 +322,15 @@ struct BlockReq {
   }
 };
 
+// GEN = false: k = 8, L = 1 (the paper's evaluation setting) with vector
+// feature loads; GEN = true: any k <= 32 and L <= 3.
+template <bool GEN>
 __global__ void __launch_bounds__(PRE_THREADS) preprocess_fwd_kernel(PreArgs a) {
+  constexpr int KS = GEN ? KG : K, KLS = GEN ? KLG : 3;
+  const int Kr = GEN ? a.K : K, kL = GEN ? a.L * (a.L + 2) : 3;
   __shared__ ViewConst sv[VIEW_CHUNK];
-  __shared__ float s_b[K], s_B[3 * K];
+  __shared__ float s_b[KS], s_B[KLS * KS];
+  __shared__ ShTable s_sh;
   __shared__ uint32_t s_red[PRE_THREADS / 32];
   const int tid = threadIdx.x;
   const RenderShape &s = a.s;
@@ -261,12 +343,15 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_fwd_kernel(PreArgs a) 
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     atomicMin(a.t0, t);
   }
-  if (tid < K) s_b[tid] = a.b_iso[br.r * K + tid];
-  if (tid < 3 * K) s_B[tid] = a.B_dir[br.r * 3 * K + tid];
+  for (int e = tid; e < Kr; e += PRE_THREADS) s_b[e] = a.b_iso[(int64_t)br.r * Kr + e];
+  for (int e = tid; e < kL * Kr; e += PRE_THREADS) s_B[e] = a.B_dir[(int64_t)br.r * kL * Kr + e];
+  if (GEN && tid < kL) sh_table_row(tid, s_sh);
   __syncthreads();
 
   GaussGeom gg;
-  float mu[3] = {0, 0, 0}, alpha = 0.f, c_iso = 0.f, h[3] = {0, 0, 0};
+  float mu[3] = {0, 0, 0}, alpha = 0.f, c_iso = 0.f, h[KLS];
+#pragma unroll
+  for (int m = 0; m < KLS; ++m) h[m] = 0.f;
   bool is_dir = false;
   if (live) {
     mu[0] = a.means[3 * i]; mu[1] = a.means[3 * i + 1]; mu[2] = a.means[3 * i + 2];
@@ -275,22 +360,37 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_fwd_kernel(PreArgs a) 
     float q[4] = {q4.x, q4.y, q4.z, q4.w};
     gauss_geom(ls, q, gg);
     alpha = sigmoidf_(a.logits[i]);
-    float f[K];
-    load_feat(a.feat_iso, a.feat_dir, a.feat_dir_bf16, rq, br.l, f);
     is_dir = br.l >= rq.n_iso;
-    if (!is_dir) {
-      float zl = 0.f;
+    if (!GEN) {
+      float f[K];
+      load_feat(a.feat_iso, a.feat_dir, a.feat_dir_bf16, rq, br.l, f);
+      if (!is_dir) {
+        float zl = 0.f;
 #pragma unroll
-      for (int k = 0; k < K; ++k) zl = fmaf(s_b[k], f[k], zl);
-      c_iso = sigmoidf_(zl);
-    } else {
+        for (int k = 0; k < K; ++k) zl = fmaf(s_b[k], f[k], zl);
+        c_iso = sigmoidf_(zl);
+      } else {
 #pragma unroll
-      for (int m = 0; m < 3; ++m) {
-        float acc = 0.f;
+        for (int m = 0; m < 3; ++m) {
+          float acc = 0.f;
 #pragma unroll
-        for (int k = 0; k < K; ++k) acc = fmaf(s_B[m * K + k], f[k], acc);
-        h[m] = acc;
+          for (int k = 0; k < K; ++k) acc = fmaf(s_B[m * K + k], f[k], acc);
+          h[m] = acc;
+        }
       }
+    } else {
+      float zl = 0.f;
+      for (int k = 0; k < Kr; ++k) {
+        const float fk = load_feat1(a.feat_iso, a.feat_dir, a.feat_dir_bf16, rq, br.l, Kr, k);
+        if (!is_dir) {
+          zl = fmaf(s_b[k], fk, zl);
+        } else {
+#pragma unroll
+          for (int m = 0; m < KLS; ++m)
+            if (m < kL) h[m] = fmaf(s_B[m * Kr + k], fk, h[m]);
+        }
+      }
+      if (!is_dir) c_iso = sigmoidf_(zl);
     }
   }
 
@@ -322,7 +422,17 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_fwd_kernel(PreArgs a) 
       if (is_dir) {
         float d0 = mu[0] + vc.wt[0], d1 = mu[1] + vc.wt[1], d2 = mu[2] + vc.wt[2];
         float inv = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
-        float zl = SH_C1 * (-d1 * inv * h[0] + d2 * inv * h[1] - d0 * inv * h[2]);
+        float zl;
+        if (!GEN) {
+          zl = SH_C1 * (-d1 * inv * h[0] + d2 * inv * h[1] - d0 * inv * h[2]);
+        } else {
+          float Y[KLS];
+          sh_eval(s_sh, kL, d0 * inv, d1 * inv, d2 * inv, Y, nullptr);
+          zl = 0.f;
+#pragma unroll
+          for (int m = 0; m < KLS; ++m)
+            if (m < kL) zl = fmaf(Y[m], h[m], zl);
+        }
         colour = sigmoidf_(zl);
       }
       a.rec0[rec] = make_float4(p.u, p.v, ca, cb);
@@ -412,6 +522,7 @@ struct PreBwdArgs {
   const float *b_iso, *B_dir, *world_to_cam, *detector;
   float dilation, near_plane;
   RenderShape s;
+  int K, L;
   const float4 *grad2d;
   ddgs_grads out;
   int want_param, want_basis, want_pose;
@@ -452,26 +563,34 @@ __device__ __forceinline__ int warp_reduce16(float v[16]) {
   return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
 }
 
+template <bool GEN>
 __global__ void __launch_bounds__(PRE_THREADS) preprocess_bwd_kernel(PreBwdArgs a) {
+  constexpr int KS = GEN ? KG : K, KLS = GEN ? KLG : 3;
+  const int Kr = GEN ? a.K : K, kL = GEN ? a.L * (a.L + 2) : 3;
   __shared__ ViewConst sv[VIEW_CHUNK];
   __shared__ float s_pose[VIEW_CHUNK][12];
-  __shared__ float s_b[K], s_B[3 * K], s_basis[4 * K];
+  __shared__ float s_b[KS], s_B[KLS * KS], s_basis[(1 + KLS) * KS];
+  __shared__ ShTable s_sh;
   const int tid = threadIdx.x, lane = tid & 31;
   const RenderShape &s = a.s;
   const BlockReq br(s);
   const ReqTab &rq = br.rq;
   const bool live = br.live;
   const int64_t i = rq.g_off + br.l;
-  if (tid < K) s_b[tid] = a.b_iso[br.r * K + tid];
-  if (tid < 3 * K) s_B[tid] = a.B_dir[br.r * 3 * K + tid];
-  if (tid < 4 * K) s_basis[tid] = 0.f;
+  for (int e = tid; e < Kr; e += PRE_THREADS) s_b[e] = a.b_iso[(int64_t)br.r * Kr + e];
+  for (int e = tid; e < kL * Kr; e += PRE_THREADS) s_B[e] = a.B_dir[(int64_t)br.r * kL * Kr + e];
+  for (int e = tid; e < (1 + kL) * Kr; e += PRE_THREADS) s_basis[e] = 0.f;
+  if (GEN && tid < kL) sh_table_row(tid, s_sh);
   __syncthreads();
 
   GaussGeom gg;
-  float mu[3] = {0, 0, 0}, alpha = 0.f, c_iso = 0.f, h[3] = {0, 0, 0}, f[K];
+  constexpr int KF = GEN ? 1 : K;  // features kept in registers (fast path only)
+  float mu[3] = {0, 0, 0}, alpha = 0.f, c_iso = 0.f, h[KLS], f[KF];
   bool is_dir = false;
 #pragma unroll
-  for (int k = 0; k < K; ++k) f[k] = 0.f;
+  for (int k = 0; k < KF; ++k) f[k] = 0.f;
+#pragma unroll
+  for (int m = 0; m < KLS; ++m) h[m] = 0.f;
   if (live) {
     mu[0] = a.means[3 * i]; mu[1] = a.means[3 * i + 1]; mu[2] = a.means[3 * i + 2];
     float ls[3] = {a.log_scales[3 * i], a.log_scales[3 * i + 1], a.log_scales[3 * i + 2]};
@@ -479,26 +598,43 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_bwd_kernel(PreBwdArgs 
     float q[4] = {q4.x, q4.y, q4.z, q4.w};
     gauss_geom(ls, q, gg);
     alpha = sigmoidf_(a.logits[i]);
-    load_feat(a.feat_iso, a.feat_dir, a.feat_dir_bf16, rq, br.l, f);
     is_dir = br.l >= rq.n_iso;
-    if (!is_dir) {
-      float zl = 0.f;
+    if (!GEN) {
+      load_feat(a.feat_iso, a.feat_dir, a.feat_dir_bf16, rq, br.l, f);
+      if (!is_dir) {
+        float zl = 0.f;
 #pragma unroll
-      for (int k = 0; k < K; ++k) zl = fmaf(s_b[k], f[k], zl);
-      c_iso = sigmoidf_(zl);
-    } else {
+        for (int k = 0; k < KF; ++k) zl = fmaf(s_b[k], f[k], zl);
+        c_iso = sigmoidf_(zl);
+      } else {
 #pragma unroll
-      for (int m = 0; m < 3; ++m) {
-        float acc = 0.f;
+        for (int m = 0; m < 3; ++m) {
+          float acc = 0.f;
 #pragma unroll
-        for (int k = 0; k < K; ++k) acc = fmaf(s_B[m * K + k], f[k], acc);
-        h[m] = acc;
+          for (int k = 0; k < KF; ++k) acc = fmaf(s_B[m * KF + k], f[k], acc);
+          h[m] = acc;
+        }
       }
+    } else {
+      float zl = 0.f;
+      for (int k = 0; k < Kr; ++k) {
+        const float fk = load_feat1(a.feat_iso, a.feat_dir, a.feat_dir_bf16, rq, br.l, Kr, k);
+        if (!is_dir) {
+          zl = fmaf(s_b[k], fk, zl);
+        } else {
+#pragma unroll
+          for (int m = 0; m < KLS; ++m)
+            if (m < kL) h[m] = fmaf(s_B[m * Kr + k], fk, h[m]);
+        }
+      }
+      if (!is_dir) c_iso = sigmoidf_(zl);
     }
   }
 
   float dSig[6] = {0, 0, 0, 0, 0, 0}, dmu[3] = {0, 0, 0};
-  float dz_iso = 0.f, dh[3] = {0, 0, 0}, galpha = 0.f;
+  float dz_iso = 0.f, dh[KLS], galpha = 0.f;
+#pragma unroll
+  for (int m = 0; m < KLS; ++m) dh[m] = 0.f;
 
   for (int v0 = 0; v0 < rq.n_views; v0 += VIEW_CHUNK) {
     const int nv = min(VIEW_CHUNK, rq.n_views - v0);
@@ -534,12 +670,34 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_bwd_kernel(PreBwdArgs 
             float nrm = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
             float inv = 1.f / nrm;
             float dh_[3] = {d[0] * inv, d[1] * inv, d[2] * inv};
-            float Y[3] = {-SH_C1 * dh_[1], SH_C1 * dh_[2], -SH_C1 * dh_[0]};
-            float c = sigmoidf_(Y[0] * h[0] + Y[1] * h[1] + Y[2] * h[2]);
-            float dz = g1.z * c * (1.f - c);
-            dh[0] += dz * Y[0]; dh[1] += dz * Y[1]; dh[2] += dz * Y[2];
-            float dY[3] = {dz * h[0], dz * h[1], dz * h[2]};
-            float ddh[3] = {-SH_C1 * dY[2], -SH_C1 * dY[0], SH_C1 * dY[1]};
+            float ddh[3];
+            if (!GEN) {
+              float Y[3] = {-SH_C1 * dh_[1], SH_C1 * dh_[2], -SH_C1 * dh_[0]};
+              float c = sigmoidf_(Y[0] * h[0] + Y[1] * h[1] + Y[2] * h[2]);
+              float dz = g1.z * c * (1.f - c);
+              dh[0] += dz * Y[0]; dh[1] += dz * Y[1]; dh[2] += dz * Y[2];
+              float dY[3] = {dz * h[0], dz * h[1], dz * h[2]};
+              ddh[0] = -SH_C1 * dY[2]; ddh[1] = -SH_C1 * dY[0]; ddh[2] = SH_C1 * dY[1];
+            } else {
+              float Y[KLS], dYd[KLS][3];
+              sh_eval(s_sh, kL, dh_[0], dh_[1], dh_[2], Y, dYd);
+              float zl = 0.f;
+#pragma unroll
+              for (int m = 0; m < KLS; ++m)
+                if (m < kL) zl = fmaf(Y[m], h[m], zl);
+              const float c = sigmoidf_(zl);
+              const float dz = g1.z * c * (1.f - c);
+              ddh[0] = ddh[1] = ddh[2] = 0.f;
+#pragma unroll
+              for (int m = 0; m < KLS; ++m) {
+                if (m >= kL) break;
+                dh[m] += dz * Y[m];
+                const float w = dz * h[m];
+                ddh[0] = fmaf(w, dYd[m][0], ddh[0]);
+                ddh[1] = fmaf(w, dYd[m][1], ddh[1]);
+                ddh[2] = fmaf(w, dYd[m][2], ddh[2]);
+              }
+            }
             float dot = ddh[0] * dh_[0] + ddh[1] * dh_[1] + ddh[2] * dh_[2];
             float dd[3] = {(ddh[0] - dh_[0] * dot) * inv, (ddh[1] - dh_[1] * dot) * inv,
                            (ddh[2] - dh_[2] * dot) * inv};
@@ -638,22 +796,35 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_bwd_kernel(PreBwdArgs 
     if (a.out.means) {
       a.out.means[3 * i] = dmu[0]; a.out.means[3 * i + 1] = dmu[1]; a.out.means[3 * i + 2] = dmu[2];
     }
-    float gf[K];
-    if (!is_dir) {
+    if (!GEN) {
+      float gf[K];
+      if (!is_dir) {
 #pragma unroll
-      for (int k = 0; k < K; ++k) gf[k] = dz_iso * s_b[k];
-      if (a.out.feat_iso) {
-        float4 *o = reinterpret_cast<float4 *>(a.out.feat_iso + (rq.iso_row + br.l) * K);
-        o[0] = make_float4(gf[0], gf[1], gf[2], gf[3]);
-        o[1] = make_float4(gf[4], gf[5], gf[6], gf[7]);
+        for (int k = 0; k < K; ++k) gf[k] = dz_iso * s_b[k];
+        if (a.out.feat_iso) {
+          float4 *o = reinterpret_cast<float4 *>(a.out.feat_iso + (rq.iso_row + br.l) * K);
+          o[0] = make_float4(gf[0], gf[1], gf[2], gf[3]);
+          o[1] = make_float4(gf[4], gf[5], gf[6], gf[7]);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k) gf[k] = s_B[k] * dh[0] + s_B[K + k] * dh[1] + s_B[2 * K + k] * dh[2];
+        if (a.out.feat_dir) {
+          float4 *o = reinterpret_cast<float4 *>(a.out.feat_dir + (rq.dir_row + br.l - rq.n_iso) * K);
+          o[0] = make_float4(gf[0], gf[1], gf[2], gf[3]);
+          o[1] = make_float4(gf[4], gf[5], gf[6], gf[7]);
+        }
       }
-    } else {
+    } else if (!is_dir) {
+      if (a.out.feat_iso)
+        for (int k = 0; k < Kr; ++k) a.out.feat_iso[(rq.iso_row + br.l) * Kr + k] = dz_iso * s_b[k];
+    } else if (a.out.feat_dir) {
+      for (int k = 0; k < Kr; ++k) {
+        float acc = 0.f;
 #pragma unroll
-      for (int k = 0; k < K; ++k) gf[k] = s_B[k] * dh[0] + s_B[K + k] * dh[1] + s_B[2 * K + k] * dh[2];
-      if (a.out.feat_dir) {
-        float4 *o = reinterpret_cast<float4 *>(a.out.feat_dir + (rq.dir_row + br.l - rq.n_iso) * K);
-        o[0] = make_float4(gf[0], gf[1], gf[2], gf[3]);
-        o[1] = make_float4(gf[4], gf[5], gf[6], gf[7]);
+        for (int m = 0; m < KLS; ++m)
+          if (m < kL) acc = fmaf(s_B[m * Kr + k], dh[m], acc);
+        a.out.feat_dir[(rq.dir_row + br.l - rq.n_iso) * Kr + k] = acc;
       }
     }
     if (a.out.log_scales || a.out.quats) {
@@ -696,7 +867,32 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_bwd_kernel(PreBwdArgs 
       }
     }
   }
-  if (a.want_basis) {
+  if (a.want_basis && GEN) {
+    // b_iso gradient: dz_iso f (isotropic); B_dir gradient: dh f^T (directional)
+    if (live) {
+      for (int k = 0; k < Kr; ++k) {
+        const float fk = load_feat1(a.feat_iso, a.feat_dir, a.feat_dir_bf16, rq, br.l, Kr, k);
+        if (!is_dir) {
+          if (dz_iso != 0.f) atomicAdd(&s_basis[k], dz_iso * fk);
+        } else {
+#pragma unroll
+          for (int m = 0; m < KLS; ++m)
+            if (m < kL && dh[m] != 0.f) atomicAdd(&s_basis[Kr + m * Kr + k], dh[m] * fk);
+        }
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < (1 + kL) * Kr; e += PRE_THREADS) {
+      const float x = s_basis[e];
+      if (x == 0.f) continue;
+      if (e < Kr) {
+        if (a.out.b_iso) atomicAdd(a.out.b_iso + (int64_t)br.r * Kr + e, x);
+      } else if (a.out.B_dir) {
+        atomicAdd(a.out.B_dir + (int64_t)br.r * kL * Kr + (e - Kr), x);
+      }
+    }
+  }
+  if (a.want_basis && !GEN) {
     // b_iso gradient: dz_iso f (isotropic); B_dir gradient: dh f^T (directional)
     float v32[4 * K];
 #pragma unroll
@@ -730,13 +926,18 @@ void launch_preprocess_fwd(const ddgs_gaussians &g, const ddgs_views &v, const d
   a.feat_iso = g.feat_iso; a.feat_dir = g.feat_dir; a.feat_dir_bf16 = g.feat_dir_bf16;
   a.b_iso = g.b_iso; a.B_dir = g.B_dir; a.world_to_cam = v.world_to_cam; a.detector = v.detector;
   a.dilation = c.dilation; a.near_plane = c.near_plane; a.q_max = c.q_max;
+  a.K = g.feat_dim ? g.feat_dim : K;
+  a.L = g.sh_degree ? g.sh_degree : 1;
   a.s = s;
   a.rec0 = ws.rec0; a.rec1 = ws.rec1; a.bin_info = reinterpret_cast<uint4 *>(ws.rect);
   a.blk_total = ws.blk_total;
   a.t0 = ws.req_time;
   if (s.n_blocks > 0) {
     LaunchScope ls(KID_PREPROCESS_FWD, st);
-    preprocess_fwd_kernel<<<(unsigned)s.n_blocks, PRE_THREADS, 0, st>>>(a);
+    if (a.K == K && a.L == 1)
+      preprocess_fwd_kernel<false><<<(unsigned)s.n_blocks, PRE_THREADS, 0, st>>>(a);
+    else
+      preprocess_fwd_kernel<true><<<(unsigned)s.n_blocks, PRE_THREADS, 0, st>>>(a);
   }
 }
 
@@ -763,6 +964,8 @@ void launch_preprocess_bwd(const ddgs_gaussians &g, const ddgs_views &v, const d
   a.feat_iso = g.feat_iso; a.feat_dir = g.feat_dir; a.feat_dir_bf16 = g.feat_dir_bf16;
   a.b_iso = g.b_iso; a.B_dir = g.B_dir; a.world_to_cam = v.world_to_cam; a.detector = v.detector;
   a.dilation = c.dilation; a.near_plane = c.near_plane;
+  a.K = g.feat_dim ? g.feat_dim : K;
+  a.L = g.sh_degree ? g.sh_degree : 1;
   a.s = s;
   a.grad2d = ws.grad2d;
   a.out = out;
@@ -772,7 +975,10 @@ void launch_preprocess_bwd(const ddgs_gaussians &g, const ddgs_views &v, const d
   a.want_pose = out.world_to_cam ? 1 : 0;
   if (s.n_blocks > 0) {
     LaunchScope ls(KID_PREPROCESS_BWD, st);
-    preprocess_bwd_kernel<<<(unsigned)s.n_blocks, PRE_THREADS, 0, st>>>(a);
+    if (a.K == K && a.L == 1)
+      preprocess_bwd_kernel<false><<<(unsigned)s.n_blocks, PRE_THREADS, 0, st>>>(a);
+    else
+      preprocess_bwd_kernel<true><<<(unsigned)s.n_blocks, PRE_THREADS, 0, st>>>(a);
   }
 }
 

@@ -92,6 +92,9 @@ extern "C" ddgs_status ddgs_render_static(const ddgs_gaussians *g, const ddgs_vi
                                           uint32_t *n_last, void *stream) {
   // argument checks (as ddgs_render)
   if (!g || !v || !c) return DDGS_ERR_INVALID_ARG;
+  if (g->feat_dim < 0 || g->feat_dim > DDGS_MAX_FEAT_DIM || g->sh_degree < 0 ||
+      g->sh_degree > DDGS_MAX_SH_DEGREE)
+    return DDGS_ERR_INVALID_ARG;
   if (g->n < 0 || g->n_iso < 0 || g->n_iso > g->n || v->n_views < 0 || v->height <= 0 ||
       v->width <= 0 || v->height > 65535 * 8 || v->width > 65535 * 8)
     return DDGS_ERR_INVALID_ARG;
@@ -100,8 +103,10 @@ extern "C" ddgs_status ddgs_render_static(const ddgs_gaussians *g, const ddgs_vi
     return DDGS_ERR_INVALID_ARG;
   if (g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->b_iso ||
                    !g->B_dir || !aligned16(g->quats) ||
-                   (g->n_iso > 0 && (!g->feat_iso || !aligned16(g->feat_iso))) ||
-                   (g->n > g->n_iso && (!g->feat_dir || !aligned16(g->feat_dir)))))
+                   (g->n_iso > 0 && !g->feat_iso) || (g->n > g->n_iso && !g->feat_dir) ||
+                   ((g->feat_dim == 0 || g->feat_dim == 8) &&
+                    ((g->n_iso > 0 && !aligned16(g->feat_iso)) ||
+                     (g->n > g->n_iso && !aligned16(g->feat_dir))))))
     return DDGS_ERR_INVALID_ARG;
   if (v->n_views > 0 && (!v->world_to_cam || !v->detector || !image || !t_final || !n_last))
     return DDGS_ERR_INVALID_ARG;

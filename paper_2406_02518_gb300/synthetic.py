@@ -96,15 +96,15 @@ def logit(p: np.ndarray) -> np.ndarray:
 
 
 def features(rng: np.random.Generator, n: int, n_iso: int, k: int = K_FEAT,
-             dir_std: float = 0.1, bf16_dir: bool = False):
-    """f_iso ~ U(0,1), f_dir ~ N(0, dir_std^2), b_iso, B_dir ~ N(0,1)/sqrt(k)."""
+             dir_std: float = 0.1, bf16_dir: bool = False, sh_degree: int = L_DEG):
+    """f_iso ~ U(0,1), f_dir ~ N(0, dir_std^2), b_iso [k], B_dir [L(L+2), k] ~ N(0,1)/sqrt(k)."""
     feat = np.empty((n, k), dtype=np.float32)
     feat[:n_iso] = rng.uniform(0.0, 1.0, (n_iso, k))
     feat[n_iso:] = rng.normal(0.0, dir_std, (n - n_iso, k))
     if bf16_dir:
         feat[n_iso:] = round_to_bf16(feat[n_iso:])
     b_iso = _f32(rng.standard_normal(k) / math.sqrt(k))
-    B_dir = _f32(rng.standard_normal((3, k)) / math.sqrt(k))
+    B_dir = _f32(rng.standard_normal((sh_degree * (sh_degree + 2), k)) / math.sqrt(k))
     return feat, b_iso, B_dir
 
 
@@ -184,7 +184,7 @@ def detector(n_views: int, sdd: float, pitch: float, off=(0.0, 0.0)) -> np.ndarr
 def uniform_cloud(n: int = 4096, seed: int = 0, k: int = K_FEAT,
                   dir_frac: float = 0.2, extent: float = 1.0,
                   log_scale_range=(-4.0, -2.0), alpha_range=(0.1, 0.9),
-                  dir_std: float = 0.1) -> Scene:
+                  dir_std: float = 0.1, sh_degree: int = L_DEG) -> Scene:
     """Means U[-extent, extent]^3, log-scales U(range), uniform unit quaternions,
     alpha U(range) stored as logits, f_iso U(0,1), f_dir N(0, dir_std^2);
     the last floor(dir_frac * n) Gaussians are direction-dependent."""
@@ -194,7 +194,7 @@ def uniform_cloud(n: int = 4096, seed: int = 0, k: int = K_FEAT,
     log_scales = _f32(rng.uniform(log_scale_range[0], log_scale_range[1], (n, 3)))
     quats = random_quats(rng, n)
     alpha = rng.uniform(alpha_range[0], alpha_range[1], n)
-    feat, b_iso, B_dir = features(rng, n, n - n_dir, k, dir_std)
+    feat, b_iso, B_dir = features(rng, n, n - n_dir, k, dir_std, sh_degree=sh_degree)
     return Scene(means, log_scales, quats, _f32(logit(alpha)), feat, n - n_dir,
                  b_iso, B_dir)
 
@@ -300,7 +300,8 @@ def body_voxels(ph: Phantom) -> np.ndarray:
 
 def gaussians_from_phantom(ph: Phantom, n_gauss: int, seed: int = 0,
                            k: int = K_FEAT, dir_frac: float = 0.2,
-                           bf16_dir: bool = False, candidates=None) -> Scene:
+                           bf16_dir: bool = False, candidates=None,
+                           sh_degree: int = L_DEG) -> Scene:
     """One candidate per voxel above -800 HU, subsampled without replacement to
     n_gauss. mu = voxel centre; log_s = log(voxel/2) + U(-1/4, 1/4);
     uniform unit quaternions; alpha = clip(0.05 + 0.9 (HU + 800) / 2300, 0.05,
@@ -319,7 +320,7 @@ def gaussians_from_phantom(ph: Phantom, n_gauss: int, seed: int = 0,
     log_s = np.log(0.5 * ph.voxel) + rng.uniform(-0.25, 0.25, (n_gauss, 3))
     quats = random_quats(rng, n_gauss)
     alpha = np.clip(0.05 + 0.9 * (hu + 800.0) / 2300.0, 0.05, 0.95)
-    feat, b_iso, B_dir = features(rng, n_gauss, n_gauss - n_dir, k, 0.1, bf16_dir)
+    feat, b_iso, B_dir = features(rng, n_gauss, n_gauss - n_dir, k, 0.1, bf16_dir, sh_degree)
     return Scene(_f32(mu), _f32(log_s), quats, _f32(logit(alpha)), feat,
                  n_gauss - n_dir, b_iso, B_dir, bf16_dir)
 

@@ -371,3 +371,30 @@ def test_large_fit_workload_sampled_pixels(ws):
     _sampled_check(scene, views, st, ws, [0, 5], 640, 6, bf16=True,
                    grads=("means", "log_scales", "quats", "opacity_logits", "feat_iso", "feat_dir",
                           "b_iso", "B_dir", "pose"))
+
+
+@pytest.mark.parametrize("k,L,bf16", [(1, 1, False), (4, 2, False), (8, 3, False), (16, 3, True),
+                                      (32, 1, False), (8, 2, True)])
+def test_feature_dimension_and_degree_variants(k, L, bf16, ws):
+    """Tables 2 and 5 of the paper vary k (1..32) and the degree L (1, 3): the
+    generic kernels against the oracle, image and every gradient."""
+    scene = syn.uniform_cloud(1500, seed=50 + k + L, dir_frac=0.5, dir_std=1.0, k=k, sh_degree=L)
+    if bf16:
+        scene.feat[scene.n_iso:] = syn.round_to_bf16(scene.feat[scene.n_iso:])
+    views = _two_views(45, 60, 8.0 / 56)
+    st = syn.Settings(near_plane=0.2)
+    cloud, gv, cfg, img, tf, nl = _run(scene, views, st, ws, bf16=bf16)
+    assert cloud.feat_dim == k and cloud.sh_degree == L
+    bins = _bins(ws, scene, views, st)
+    compare_binning(bins, oracle.bin32(scene, views, st))
+    ids = last_ids(nl.cpu().numpy().view(np.uint32), bins, views, st.tile)
+    check_image(scene, views, st, img.cpu().numpy(), tf.cpu().numpy(), ids)
+    ref = oracle.render(scene, views, st)
+    w = _masked_weights(ref, 3)
+    g = B.render_backward(cloud, gv, cfg, ws, torch.as_tensor(w, dtype=torch.float32, device="cuda"),
+                          tf, nl)
+    gr = oracle.render_backward(scene, views, st, w)
+    gpu = {n: t.float().cpu().numpy() for n, t in g.items()}
+    gpu["feat"] = np.concatenate([gpu.pop("feat_iso").reshape(-1, k), gpu.pop("feat_dir").reshape(-1, k)])
+    gpu["pose"] = gpu.pop("world_to_cam")
+    compare_grads(gpu, gr, GRAD_NAMES)
