@@ -40,7 +40,8 @@ class _Scene(C.Structure):
     _fields_ = [("n", C.c_int32), ("n_iso", C.c_int32), ("k", C.c_int32), ("L", C.c_int32),
                 ("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
                 ("opacity_logits", C.c_void_p), ("feat", C.c_void_p),
-                ("b_iso", C.c_void_p), ("B_dir", C.c_void_p)]
+                ("b_iso", C.c_void_p), ("B_dir", C.c_void_p),
+                ("entangled", C.c_int32), ("per_pixel", C.c_int32)]
 
 
 class _Views(C.Structure):
@@ -105,7 +106,7 @@ class _Pack:
         L = {3: 1, 8: 2, 15: 3, 24: 4}[kl]
         self.scene = _Scene(scene.n, scene.n_iso, scene.feat.shape[1], L, _p(a["means"]),
                             _p(a["ls"]), _p(a["q"]), _p(a["o"]), _p(a["f"]), _p(a["b"]),
-                            _p(a["B"]))
+                            _p(a["B"]), int(bool(scene.entangled)), int(bool(scene.per_pixel)))
         self.views = _Views(views.n_views, views.height, views.width, _p(a["T"]), _p(a["det"]))
         s = settings
         self.cfg = _Config(s.tile, s.dilation, s.near_plane, s.alpha_min, s.alpha_max,
@@ -233,7 +234,8 @@ def render_backward(scene, views, settings, dL_dC, pix=None, depth32=None, threa
     out = dict(means=np.zeros((n, 3)), log_scales=np.zeros((n, 3)), quats=np.zeros((n, 4)),
                opacity_logits=np.zeros(n), feat=np.zeros((n, k)), b_iso=np.zeros(k),
                B_dir=np.zeros(np.asarray(scene.B_dir).shape), pose=np.zeros((V, 3, 4)))
-    g2 = np.zeros((V, n, 7)) if want_2d else None
+    kl = int(np.asarray(scene.B_dir).shape[0])
+    g2 = np.zeros((V, n, 7 + kl)) if want_2d else None
     rc = lib().or_render_backward(
         C.byref(pk.scene), C.byref(pk.views), C.byref(pk.cfg), _p(depth32), m, _p(pix), _p(g),
         _p(out["means"]), _p(out["log_scales"]), _p(out["quats"]), _p(out["opacity_logits"]),

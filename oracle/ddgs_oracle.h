@@ -21,6 +21,13 @@
  *   Gaussians  [0, n_iso) are isotropic (Eq. 3, c = sigmoid(b_iso . f)),
  *              [n_iso, n) are direction-dependent
  *              (Eq. 3, c = sigmoid(Y_1..L(d) . B_dir f)).
+ *   Variants   (ablations of Sec. 4.4 / Table 3 and the ray-angle reading of
+ *              Eq. 3): "entangled" gives every Gaussian both terms,
+ *              c = sigmoid(b_iso . f + Y(d) . B_dir f) ("direct-entangled",
+ *              co-located as in usual spherical-harmonic splatting);
+ *              "per_pixel" takes d as the direction of the pixel's own ray
+ *              (source to pixel centre) instead of source to the Gaussian's
+ *              mean, so c varies across the Gaussian's footprint.
  *   Pose       world -> camera rigid transform [R | t], 3x4 row-major. The
  *              X-ray source sits at the camera origin; the detector plane is
  *              z = sdd; pixel (row i, col j) has centre (j + 1/2, i + 1/2).
@@ -47,6 +54,8 @@ typedef struct {
   const double *feat;            /* [n][k]; row i is f_iso if i < n_iso else f_dir */
   const double *b_iso;           /* [k] */
   const double *B_dir;           /* [k_L][k] row-major, rows ordered (l, m = -l..l) */
+  int32_t entangled;             /* 1: every Gaussian carries both terms of Eq. 3 */
+  int32_t per_pixel;             /* 1: d is the pixel's ray direction */
 } or_scene;
 
 typedef struct {
@@ -98,7 +107,8 @@ int or_render_backward(const or_scene *s, const or_views *vw,
                        double *g_opacity_logits, double *g_feat,
                        double *g_b_iso, double *g_B_dir,
                        double *g_pose /* [V][12] */,
-                       double *g_2d /* [V][n][7]: u, v, conic a, b, c, alpha, color */,
+                       double *g_2d /* [V][n][7 + k_L]: u, v, conic a, b, c, alpha,
+                                       logit z, then sum of dL/dz Y_m (= dL/dh_m) */,
                        int n_threads);
 
 /* Per requested pixel: the number of projected Gaussians with q <= q_max at

@@ -13,6 +13,13 @@
  *     with Y the real spherical harmonics of degrees 1..L (no degree 0), so
  *     k_L = L(L+2). The ray angles are those of the unit direction from the
  *     X-ray source to the Gaussian's mean, in world coordinates.
+ *     Written per pair (pixel p, Gaussian j) as c = sigmoid(z), z = a_j +
+ *     Y(d) . h_j with a_j = b_iso . f_j for a Gaussian with an isotropic
+ *     term (else 0) and h_j = B_dir f_j for one with a directional term (else
+ *     0). Variants: "entangled" gives every Gaussian both terms (the
+ *     direct-entangled ablation of Table 3); "per_pixel" takes d as the unit
+ *     direction of pixel p's ray (source to pixel centre) rather than of the
+ *     Gaussian's mean.
  *   - Image-plane projections mu-hat, Sigma-hat (text of Eq. 1): perspective
  *     projection of the mean onto the detector and the local affine
  *     (Jacobian) projection of Sigma, plus a dilation d on the diagonal.
@@ -124,7 +131,9 @@ typedef struct {
   double qn[4], qnorm, s[3], R[3][3], M[3][3], Sig[3][3];
   double W[3][3], t[3], xc[3], fu, fv;
   double J[2][3], A[2][3], cov[3], det, conic[3];
-  double u, v, alpha, color;
+  double u, v, alpha, color;  /* color: per-Gaussian direction only */
+  int has_iso, has_dir;
+  double a;                   /* isotropic logit b_iso . f (0 without that term) */
   double d[3], dnorm, dhat[3], Y[KLMAX], h[KLMAX], dY[KLMAX][3];
 } g64;
 
@@ -166,27 +175,32 @@ static void project64(const or_scene *sc, const or_views *vw,
   /* opacity and radiosity do not depend on culling */
   g->alpha = sigmoid(sc->opacity_logits[i]);
   const double *f = sc->feat + (int64_t)k * i;
-  if (i < sc->n_iso) {
-    double zl = 0;
-    for (int n = 0; n < k; ++n) zl += sc->b_iso[n] * f[n];
-    g->color = sigmoid(zl);
-  } else {
-    /* source position S = -W^T t; direction mu - S = mu + W^T t */
-    for (int c = 0; c < 3; ++c)
-      g->d[c] = mu[c] + g->W[0][c] * g->t[0] + g->W[1][c] * g->t[1] + g->W[2][c] * g->t[2];
-    g->dnorm = sqrt(g->d[0] * g->d[0] + g->d[1] * g->d[1] + g->d[2] * g->d[2]);
-    for (int c = 0; c < 3; ++c) g->dhat[c] = g->d[c] / g->dnorm;
+  g->has_iso = sc->entangled || i < sc->n_iso;
+  g->has_dir = sc->entangled || i >= sc->n_iso;
+  double zl = 0;
+  if (g->has_iso) {
+    for (int n = 0; n < k; ++n) g->a += sc->b_iso[n] * f[n];
+    zl = g->a;
+  }
+  if (g->has_dir) {
     const int kL = sc->L * (sc->L + 2);
-    real_sh(sc->L, g->dhat, g->Y, g->dY);
-    double zl = 0;
     for (int m = 0; m < kL; ++m) {
       double hm = 0;
       for (int n = 0; n < k; ++n) hm += sc->B_dir[m * k + n] * f[n];
       g->h[m] = hm;
-      zl += g->Y[m] * hm;
     }
-    g->color = sigmoid(zl);
+    if (!sc->per_pixel) {
+      /* source position S = -W^T t; direction mu - S = mu + W^T t */
+      for (int c = 0; c < 3; ++c)
+        g->d[c] = mu[c] + g->W[0][c] * g->t[0] + g->W[1][c] * g->t[1] + g->W[2][c] * g->t[2];
+      g->dnorm = sqrt(g->d[0] * g->d[0] + g->d[1] * g->d[1] + g->d[2] * g->d[2]);
+      for (int c = 0; c < 3; ++c) g->dhat[c] = g->d[c] / g->dnorm;
+      real_sh(sc->L, g->dhat, g->Y, g->dY);
+      for (int m = 0; m < kL; ++m) zl += g->Y[m] * g->h[m];
+    }
   }
+  /* with per-pixel directions a directional Gaussian has no single colour */
+  g->color = (g->has_dir && sc->per_pixel) ? NAN : sigmoid(zl);
 
   double zc = g->xc[2], sdd = dp[0];
   double tol_n = 1e-6 * fabs(cfg->near_plane) + 1e-12, tol_f = 1e-6 * sdd;
@@ -221,8 +235,10 @@ static void project64(const or_scene *sc, const or_views *vw,
   g->valid = 1;
 }
 
-/* Back-propagate the 2D gradient gg[7] = d/d(u, v, conic a, b, c, alpha,
- * color) of Gaussian i in view v into parameter and pose gradients. */
+/* Back-propagate the 2D gradient gg[7 + k_L] = d/d(u, v, conic a, b, c,
+ * alpha), the summed gradient of the colour logit z, and dL/dh_m (the sums of
+ * dL/dz Y_m over the pixels) of Gaussian i in view v into parameter and pose
+ * gradients. */
 typedef struct {
   double mu[3], ls[3], q[4], logit, f[KMAX];
   double b_iso[KMAX], B_dir[KLMAX * KMAX];
@@ -236,22 +252,28 @@ static void backprop64(const or_scene *sc, int64_t i, const g64 *g,
   const double *f = sc->feat + (int64_t)k * i;
   double dW[3][3] = {{0}}, dt[3] = {0}, dmu[3] = {0};
 
-  /* radiosity, Eq. 3 */
-  double dzl = gg[6] * g->color * (1 - g->color);
-  if (i < sc->n_iso) {
+  /* radiosity, Eq. 3: z = a + Y(d) . h, a = b_iso . f, h = B_dir f */
+  const double dzl = gg[6];
+  if (g->has_iso) {
     for (int n = 0; n < k; ++n) {
       out->f[n] += dzl * sc->b_iso[n];
       out->b_iso[n] += dzl * f[n];
     }
-  } else {
+  }
+  if (g->has_dir) {
     const int kL = sc->L * (sc->L + 2);
-    double dY[KLMAX], dh[KLMAX];
-    for (int m = 0; m < kL; ++m) { dY[m] = dzl * g->h[m]; dh[m] = dzl * g->Y[m]; }
+    const double *dh = gg + 7;
     for (int m = 0; m < kL; ++m)
       for (int n = 0; n < k; ++n) {
         out->B_dir[m * k + n] += dh[m] * f[n];
         out->f[n] += sc->B_dir[m * k + n] * dh[m];
       }
+  }
+  if (g->has_dir && !sc->per_pixel) {
+    /* the direction of the mean: d = mu - S */
+    const int kL = sc->L * (sc->L + 2);
+    double dY[KLMAX];
+    for (int m = 0; m < kL; ++m) dY[m] = dzl * g->h[m];
     double ddh[3] = {0, 0, 0};
     for (int m = 0; m < kL; ++m)
       for (int c3 = 0; c3 < 3; ++c3) ddh[c3] += dY[m] * g->dY[m][c3];
@@ -431,13 +453,22 @@ static void free_view(view_cache *vc) {
 typedef struct {
   int32_t i;
   int clamped;
-  double sigma, G, T, dx, dy;
+  double sigma, G, T, dx, dy, color;
 } contrib;
 
+/* Colour of Gaussian g at a pixel: Yp = Y(pixel ray) with per-pixel
+ * directions, NULL otherwise. */
+static double pair_color(const g64 *g, const double *Yp, int kL) {
+  if (!Yp || !g->has_dir) return g->color;
+  double z = g->a;
+  for (int m = 0; m < kL; ++m) z += Yp[m] * g->h[m];
+  return sigmoid(z);
+}
+
 static int64_t walk_pixel(const view_cache *vc, const or_config *cfg, double px,
-                          double py, unsigned flip_mask, double *C_out,
-                          double *T_out, int32_t *last_out, int32_t *flags_out,
-                          int32_t *nflag_out, contrib *rec) {
+                          double py, const double *Yp, int kL, unsigned flip_mask,
+                          double *C_out, double *T_out, int32_t *last_out,
+                          int32_t *flags_out, int32_t *nflag_out, contrib *rec) {
   double T = 1.0, C = 0.0;
   int32_t last = -1, flags = vc->near_cull ? OR_NEAR_CULL : 0;
   int nflag = 0;
@@ -476,6 +507,7 @@ static int64_t walk_pixel(const view_cache *vc, const or_config *cfg, double px,
       stop = DECIDE(stop);
     }
     if (stop) break;
+    const double color = pair_color(g, Yp, kL);
     if (rec) {
       rec[cnt].i = vc->order[j];
       rec[cnt].clamped = clamped;
@@ -484,8 +516,9 @@ static int64_t walk_pixel(const view_cache *vc, const or_config *cfg, double px,
       rec[cnt].T = T;
       rec[cnt].dx = dx;
       rec[cnt].dy = dy;
+      rec[cnt].color = color;
     }
-    C += g->color * sigma * T;
+    C += color * sigma * T;
     T = Tn;
     last = vc->order[j];
     ++cnt;
@@ -497,6 +530,23 @@ static int64_t walk_pixel(const view_cache *vc, const or_config *cfg, double px,
   if (flags_out) *flags_out = flags;
   if (nflag_out) *nflag_out = nflag;
   return cnt;
+}
+
+/* Unit direction (world frame) of the ray from the source through the centre
+ * (px, py) of a detector pixel of view v: in camera coordinates the pixel
+ * sits at rc = ((px - c_u) pitch_u, (py - c_v) pitch_v, sdd); the world
+ * direction is W^T rc. Also returns rc and |W^T rc| for the backward pass. */
+static void pixel_ray(const or_views *vw, int64_t v, double px, double py,
+                      double rc[3], double dhat[3], double *dnorm) {
+  const double *T = vw->world_to_cam + 12 * v;
+  const double *dp = vw->detector + 5 * v;
+  rc[0] = (px - (0.5 * vw->width + dp[3])) * dp[1];
+  rc[1] = (py - (0.5 * vw->height + dp[4])) * dp[2];
+  rc[2] = dp[0];
+  double d[3];
+  for (int c = 0; c < 3; ++c) d[c] = T[c] * rc[0] + T[4 + c] * rc[1] + T[8 + c] * rc[2];
+  *dnorm = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  for (int c = 0; c < 3; ++c) dhat[c] = d[c] / *dnorm;
 }
 
 /* Pixel list helpers: either explicit (v,row,col) triples or all pixels. */
@@ -553,6 +603,7 @@ int or_render(const or_scene *sc, const or_views *vw, const or_config *cfg,
               int32_t *n_flagged, int n_threads) {
   if (check_args(sc, vw, n_pix, pix)) return 1;
   SET_THREADS(n_threads);
+  const int kL = sc->L * (sc->L + 2);
   for (int64_t v = 0; v < vw->n_views; ++v) {
     view_cache vc;
     if (build_view(sc, vw, cfg, depth32, v, &vc)) return 2;
@@ -564,7 +615,13 @@ int or_render(const or_scene *sc, const or_views *vw, const or_config *cfg,
       double C, T;
       int32_t last, fl, nf;
       unsigned mask = flip_masks ? flip_masks[p] : 0u;
-      int64_t cnt = walk_pixel(&vc, cfg, col + 0.5, row + 0.5, mask, &C, &T, &last, &fl, &nf, NULL);
+      double Yp[KLMAX], rc[3], dh[3], dn;
+      if (sc->per_pixel) {
+        pixel_ray(vw, v, col + 0.5, row + 0.5, rc, dh, &dn);
+        real_sh(sc->L, dh, Yp, NULL);
+      }
+      int64_t cnt = walk_pixel(&vc, cfg, col + 0.5, row + 0.5, sc->per_pixel ? Yp : NULL, kL,
+                               mask, &C, &T, &last, &fl, &nf, NULL);
       if (image) image[p] = C;
       if (t_final) t_final[p] = T;
       if (last_id) last_id[p] = last;
@@ -588,9 +645,13 @@ int or_render_backward(const or_scene *sc, const or_views *vw,
   SET_THREADS(n_threads);
   const int64_t n = sc->n;
   const int k = sc->k;
+  const int kL = sc->L * (sc->L + 2), G2 = 7 + kL;
+  const int64_t V = vw->n_views;
   /* 2D gradients per (view, Gaussian) */
-  double *g2 = (double *)calloc((size_t)(vw->n_views * n * 7 + 1), sizeof(double));
-  if (!g2) return 2;
+  double *g2 = (double *)calloc((size_t)(V * n * G2 + 1), sizeof(double));
+  /* pose gradient through the per-pixel ray directions */
+  double *pose_ray = (double *)calloc((size_t)(V * 12 + 1), sizeof(double));
+  if (!g2 || !pose_ray) { free(g2); free(pose_ray); return 2; }
   for (int64_t v = 0; v < vw->n_views; ++v) {
     view_cache vc;
     if (build_view(sc, vw, cfg, depth32, v, &vc)) { free(g2); return 2; }
@@ -608,18 +669,33 @@ int or_render_backward(const or_scene *sc, const or_views *vw,
         int64_t pv, row, col;
         pixel_at(vw, pix, p, &pv, &row, &col);
         if (pv != v || dL_dC[p] == 0.0) continue;
-        int64_t cnt = walk_pixel(&vc, cfg, col + 0.5, row + 0.5, 0u, NULL, NULL, NULL, NULL, NULL, rec);
+        double Yp[KLMAX], dYp[KLMAX][3], rc[3], dhat[3], dn, gY[KLMAX] = {0};
+        if (sc->per_pixel) {
+          pixel_ray(vw, v, col + 0.5, row + 0.5, rc, dhat, &dn);
+          real_sh(sc->L, dhat, Yp, dYp);
+        }
+        int64_t cnt = walk_pixel(&vc, cfg, col + 0.5, row + 0.5, sc->per_pixel ? Yp : NULL, kL,
+                                 0u, NULL, NULL, NULL, NULL, NULL, rec);
         double gC = dL_dC[p];
         /* S = sum over later Gaussians of c sigma T (suffix sum) */
         double S = 0.0;
         for (int64_t j = cnt - 1; j >= 0; --j) {
           const contrib *r = &rec[j];
           const g64 *g = &vc.g[r->i];
+          const double c = r->color;
           double dC_dc = r->sigma * r->T;
-          double dC_dsigma = g->color * r->T - S / (1 - r->sigma);
-          S += g->color * r->sigma * r->T;
+          double dC_dsigma = c * r->T - S / (1 - r->sigma);
+          S += c * r->sigma * r->T;
           double gs = gC * dC_dsigma;
-          double gg[7] = {0, 0, 0, 0, 0, 0, gC * dC_dc};
+          /* colour logit z = a + Y(d) . h */
+          const double dz = gC * dC_dc * c * (1 - c);
+          double gg[7 + KLMAX] = {0, 0, 0, 0, 0, 0, dz};
+          if (g->has_dir) {
+            const double *Y = sc->per_pixel ? Yp : g->Y;
+            for (int m = 0; m < kL; ++m) gg[7 + m] = dz * Y[m];
+            if (sc->per_pixel)
+              for (int m = 0; m < kL; ++m) gY[m] += dz * g->h[m];
+          }
           if (!r->clamped) {
             gg[5] = gs * r->G;
             double gq = gs * g->alpha * r->G * -0.5;
@@ -630,26 +706,36 @@ int or_render_backward(const or_scene *sc, const or_views *vw,
             gg[3] = gq * 2 * dx * dy;
             gg[4] = gq * dy * dy;
           }
-          double *dst = g2 + 7 * (v * n + r->i);
-          for (int c = 0; c < 7; ++c) {
+          double *dst = g2 + G2 * (v * n + r->i);
+          for (int e = 0; e < G2; ++e) {
 #pragma omp atomic
-            dst[c] += gg[c];
+            dst[e] += gg[e];
           }
+        }
+        if (sc->per_pixel && cnt > 0) {
+          /* Y(dhat), dhat = d / |d|, d = W^T rc: dL/dW[r][c] = rc[r] dL/dd[c] */
+          double ddh[3] = {0, 0, 0};
+          for (int m = 0; m < kL; ++m)
+            for (int c3 = 0; c3 < 3; ++c3) ddh[c3] += gY[m] * dYp[m][c3];
+          double dot = ddh[0] * dhat[0] + ddh[1] * dhat[1] + ddh[2] * dhat[2];
+          for (int r = 0; r < 3; ++r)
+            for (int c3 = 0; c3 < 3; ++c3) {
+#pragma omp atomic
+              pose_ray[12 * v + 4 * r + c3] += rc[r] * (ddh[c3] - dhat[c3] * dot) / dn;
+            }
         }
       }
       free(rec);
     }
     free_view(&vc);
-    if (fail) { free(g2); return 2; }
+    if (fail) { free(g2); free(pose_ray); return 2; }
   }
-  if (g_2d) memcpy(g_2d, g2, sizeof(double) * (size_t)(vw->n_views * n * 7));
+  if (g_2d) memcpy(g_2d, g2, sizeof(double) * (size_t)(V * n * G2));
 
   /* chain rule per Gaussian (summed over views) and per view (over Gaussians) */
-  const int64_t V = vw->n_views;
-  double *pose = (double *)calloc((size_t)(V * 12 + 1), sizeof(double));
-  const int kL = sc->L * (sc->L + 2);
+  double *pose = pose_ray;
   double *gb = (double *)calloc((size_t)((1 + kL) * k), sizeof(double));
-  if (!pose || !gb) { free(g2); free(pose); free(gb); return 2; }
+  if (!gb) { free(g2); free(pose); return 2; }
 #pragma omp parallel
   {
     double *pose_l = (double *)calloc((size_t)(V * 12 + 1), sizeof(double));
@@ -659,8 +745,10 @@ int or_render_backward(const or_scene *sc, const or_views *vw,
       grad_acc acc;
       memset(&acc, 0, sizeof acc);
       for (int64_t v = 0; v < V; ++v) {
-        const double *gg = g2 + 7 * (v * n + i);
-        if (!(gg[0] || gg[1] || gg[2] || gg[3] || gg[4] || gg[5] || gg[6])) continue;
+        const double *gg = g2 + G2 * (v * n + i);
+        int any = 0;
+        for (int e = 0; e < G2; ++e) any |= gg[e] != 0.0;
+        if (!any) continue;
         g64 g;
         project64(sc, vw, cfg, v, i, &g);
         memset(acc.pose, 0, sizeof acc.pose);

@@ -38,6 +38,10 @@ class Scene:
     b_iso: np.ndarray
     B_dir: np.ndarray
     feat_dir_bf16: bool = False  # dir rows are exactly bf16-representable
+    # Eq. 3 variants: every Gaussian carries both terms (direct-entangled,
+    # Table 3); the ray angles are the pixel ray's rather than the mean's
+    entangled: bool = False
+    per_pixel: bool = False
 
     @property
     def n(self) -> int:

@@ -577,3 +577,144 @@ def test_analytic_gradient_matches_central_differences_degree_three():
                     vals.append(_loss(dataclasses.replace(sc64, **{name: a2}), v64, st, w, depth32))
             fd = (vals[0] - vals[1]) / (2 * h)
             assert abs(fd - G[idx]) <= 1e-6 * scale + 1e-9, (name, idx, fd, G[idx])
+
+
+# ---------------------------------------------------------------------------
+# Eq. 3 variants: direct-entangled radiosity (Table 3) and per-pixel ray angles
+# ---------------------------------------------------------------------------
+
+def _logit(c):
+    return np.log(c) - np.log1p(-c)
+
+
+def test_entangled_logit_is_sum_of_the_two_terms():
+    # co-located terms (direct-entangled, Table 3): the logit of c is b_iso . f
+    # + Y(d) . B_dir f, i.e. the isotropic-only logit plus the direction-only one
+    sc = syn.uniform_cloud(40, seed=31, dir_frac=0.5, dir_std=1.0)
+    R = Rotation.from_euler("zyx", [30, -20, 10], degrees=True).as_matrix()
+    views = _views([_pose(np.eye(3), [0, 0, 2.0]), _pose(R, [0.1, -0.2, 2.5])], 4.0, 1 / 8, 8, 8)
+    st = syn.Settings(near_plane=0.2)
+    ent = oracle.project64(dataclasses.replace(sc, entangled=True), views, st)[..., 6]
+    iso = oracle.project64(dataclasses.replace(sc, n_iso=sc.n), views, st)[..., 6]
+    dr = oracle.project64(dataclasses.replace(sc, n_iso=0), views, st)[..., 6]
+    assert np.abs(_logit(ent) - (_logit(iso) + _logit(dr))).max() < 1e-9
+    assert np.abs(ent - iso).max() > 1e-3 and np.abs(ent - dr).max() > 1e-3
+
+
+def test_entangled_reduces_to_either_term_alone():
+    sc = syn.uniform_cloud(300, seed=32, dir_frac=0.3, dir_std=1.0)
+    views = _views(_pose(np.eye(3), [0, 0, 2.0]), 4.0, 1 / 8, 40, 40)
+    st = syn.Settings(near_plane=0.2)
+    no_dir = dataclasses.replace(sc, B_dir=np.zeros_like(sc.B_dir))
+    a = oracle.render(dataclasses.replace(no_dir, entangled=True), views, st)["image"]
+    b = oracle.render(dataclasses.replace(no_dir, n_iso=sc.n), views, st)["image"]
+    assert np.array_equal(a, b)
+    no_iso = dataclasses.replace(sc, b_iso=np.zeros_like(sc.b_iso))
+    a = oracle.render(dataclasses.replace(no_iso, entangled=True), views, st)["image"]
+    b = oracle.render(dataclasses.replace(no_iso, n_iso=0), views, st)["image"]
+    assert np.abs(a - b).max() < 1e-15
+
+
+def _centred_views(sc, st, poses, sdd, pitch, H, W):
+    """Views whose principal points are shifted so that Gaussian 0's mean
+    projects exactly onto the centre of pixel (H//2, W//2)."""
+    # float64 poses: exactly orthonormal, so -W^T t is the source position
+    P64 = np.stack([syn.pose_matrix(R, t) for R, t in poses]).astype(np.float64)
+    views = syn.Views(P64, syn.detector(len(poses), sdd, pitch).astype(np.float64), H, W)
+    P = oracle.project64(sc, views, st)
+    det = views.detector.astype(np.float64).copy()
+    det[:, 3] += (W // 2 + 0.5) - P[:, 0, 0]
+    det[:, 4] += (H // 2 + 0.5) - P[:, 0, 1]
+    return dataclasses.replace(views, detector=det)
+
+
+def test_per_pixel_direction_equals_mean_direction_on_the_ray_through_the_mean():
+    # at the pixel whose ray passes through a Gaussian's mean, the pixel ray's
+    # direction and the source-to-mean direction coincide, so the two readings
+    # of the ray angles give the same colour there and differ elsewhere
+    rng = np.random.default_rng(5)
+    n = 1
+    sc = _scene(rng.uniform(-0.2, 0.2, (n, 3)), np.full((n, 3), -1.6), [[0.9, 0.1, -0.3, 0.2]],
+                [0.4], rng.normal(0, 1, (n, 8)), 0, B_dir=rng.normal(0, 1, (3, 8)))
+    st = syn.Settings(near_plane=0.2)
+    Rs = [Rotation.from_euler("zyx", a, degrees=True).as_matrix()
+          for a in ([0, 0, 0], [35, -20, 15], [-50, 40, 5])]
+    views = _centred_views(sc, st, [(R, np.array([0.05, -0.1, 2.0])) for R in Rs], 4.0, 0.05, 31, 31)
+    d32 = np.ones((3, 1), np.float32)  # one Gaussian: the depth order is trivial
+    pg = oracle.render(sc, views, st, depth32=d32)["image"]
+    pp = oracle.render(dataclasses.replace(sc, per_pixel=True), views, st, depth32=d32)["image"]
+    assert np.abs(pp[:, 15, 15] - pg[:, 15, 15]).max() < 1e-12
+    assert pg[:, 15, 15].min() > 0.05
+    inside = pg > 1e-3
+    assert np.abs(pp - pg)[inside].max() > 1e-4
+
+
+def test_per_pixel_colour_follows_the_source_to_detector_geometry():
+    # C(p) / sigma(p) at each pixel is sigmoid(Y_1(d_p) . B f), with d_p from
+    # the source S = -R^T t to the pixel's point on the detector plane
+    rng = np.random.default_rng(6)
+    sc = _scene([[0.05, -0.02, 0.1]], [[-1.5, -1.7, -1.6]], [[0.8, -0.2, 0.4, 0.1]], [0.0],
+                rng.normal(0, 1, (1, 8)), 0, B_dir=rng.normal(0, 1, (3, 8)))
+    R = Rotation.from_euler("zyx", [20, 25, -30], degrees=True).as_matrix()
+    t = np.array([0.1, 0.05, 2.2])
+    H = W = 25
+    views = _views(_pose(R, t), 4.4, 0.06, H, W, off=(0.7, -1.3))
+    st = syn.Settings(near_plane=0.2)
+    pg = oracle.render(sc, views, st)
+    pp = oracle.render(dataclasses.replace(sc, per_pixel=True), views, st)["image"][0]
+    c_mean = oracle.project64(sc, views, st)[0, 0, 6]
+    sigma = pg["image"][0] / c_mean
+    Rf, tf = views.world_to_cam[0, :, :3].astype(np.float64), views.world_to_cam[0, :, 3].astype(np.float64)
+    S = -Rf.T @ tf
+    h = sc.B_dir.astype(np.float64) @ sc.feat[0].astype(np.float64)
+    det = views.detector[0].astype(np.float64)
+    ok = pg["n_contrib"][0] > 0
+    assert ok.sum() > 20
+    for i, j in zip(*np.nonzero(ok)):
+        Pc = np.array([(j + 0.5 - (W / 2 + det[3])) * det[1], (i + 0.5 - (H / 2 + det[4])) * det[2],
+                       det[0]])
+        d = Rf.T @ (Pc - tf) - S
+        d /= np.linalg.norm(d)
+        Y1 = math.sqrt(3 / (4 * math.pi)) * np.array([-d[1], d[2], -d[0]])
+        assert abs(pp[i, j] - sigma[i, j] * _sigmoid(Y1 @ h)) < 1e-12
+
+
+def _fd_check(sc, views, st, names, seed=3):
+    depth32 = oracle.project32(sc, views, st)["depth"]
+    rng = np.random.default_rng(seed)
+    w = rng.uniform(-1, 1, (views.n_views, views.height, views.width))
+    g = oracle.render_backward(sc, views, st, w, depth32=depth32)
+    sc64 = dataclasses.replace(sc, **{f: getattr(sc, f).astype(np.float64) for f in
+                                      ("means", "log_scales", "quats", "opacity_logits",
+                                       "feat", "b_iso", "B_dir")})
+    v64 = dataclasses.replace(views, world_to_cam=views.world_to_cam.astype(np.float64))
+    checked = 0
+    for name in names:
+        arr = v64.world_to_cam if name == "pose" else getattr(sc64, name)
+        G = g[name].reshape(-1)
+        scale = np.abs(G).max()
+        assert scale > 0, name
+        for idx in range(arr.size):
+            x0 = arr.reshape(-1)[idx]
+            hh = 1e-6 * max(1.0, abs(x0))
+            vals = []
+            for sgn in (1, -1):
+                a2 = arr.copy()
+                a2.reshape(-1)[idx] = x0 + sgn * hh
+                if name == "pose":
+                    vals.append(_loss(sc64, dataclasses.replace(v64, world_to_cam=a2), st, w, depth32))
+                else:
+                    vals.append(_loss(dataclasses.replace(sc64, **{name: a2}), v64, st, w, depth32))
+            fd = (vals[0] - vals[1]) / (2 * hh)
+            assert abs(fd - G[idx]) <= 1e-6 * scale + 1e-9, (name, idx, fd, G[idx])
+            checked += 1
+    return checked
+
+
+@pytest.mark.parametrize("entangled,per_pixel", [(True, False), (False, True), (True, True)])
+def test_variant_gradients_match_central_differences(entangled, per_pixel):
+    sc, views, st = _fd_scene()
+    sc = dataclasses.replace(sc, entangled=entangled, per_pixel=per_pixel)
+    assert oracle.render(sc, views, st)["flags"].max() == 0
+    n = _fd_check(sc, views, st, ("means", "feat", "b_iso", "B_dir", "opacity_logits", "pose"))
+    assert n > 100
