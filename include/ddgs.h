@@ -73,6 +73,13 @@ typedef struct {
                                   rows ordered by degree l = 1..L, order m = -l..l */
   int32_t feat_dim;            /* k, 1..32 (0 = 8); rows of 8 must be 16-byte aligned */
   int32_t sh_degree;           /* L, 1..3 (0 = 1) */
+  int32_t entangled;           /* 1: every Gaussian carries both terms of Eq. 3,
+                                  c = sigmoid(b_iso . f + Y(d) . B_dir f) (the
+                                  direct-entangled ablation of Table 3); f is the
+                                  Gaussian's row of feat_iso or feat_dir */
+  int32_t per_pixel;           /* 1: Y is evaluated at the direction of each pixel's
+                                  ray (source to pixel centre) instead of the
+                                  source-to-mean direction; needs L = 1 */
 } ddgs_gaussians;
 
 /* n_views cone-beam views sharing one detector size. */
@@ -140,9 +147,14 @@ ddgs_status ddgs_workspace_reserve(ddgs_workspace *ws, int64_t records,
  * transmittance would drop below t_min. mu-hat, Sigma-hat are the perspective
  * projection of the mean and the Jacobian projection of Sigma (+ dilation).
  * Radiosity (Eq. 3): c = sigmoid(b_iso . f) for isotropic Gaussians and
- * c = sigmoid(Y_1(d) . B_dir f) for direction-dependent ones, with d the unit
- * direction from the source to the mean in world coordinates and
- * Y_1(d) = sqrt(3/(4 pi)) (-d_y, d_z, -d_x).
+ * c = sigmoid(Y_1..L(d) . B_dir f) for direction-dependent ones, with d the
+ * unit direction from the source to the mean in world coordinates and Y the
+ * real spherical harmonics of degrees 1..L (Y_1(d) = sqrt(3/(4 pi)) (-d_y,
+ * d_z, -d_x)). With g->entangled every Gaussian uses both terms; with
+ * g->per_pixel d is the pixel ray's direction, so c varies across a
+ * Gaussian's footprint. A per_pixel render with cfg->no_sync needs the
+ * workspace to have held a per_pixel render before (its extra per-record
+ * storage is allocated then).
  * Outputs (device, [n_views][height][width], overwritten):
  *   image   C(p) (background 0, no log transform; App. A.1)
  *   t_final transmittance after the last Gaussian added
@@ -160,7 +172,7 @@ ddgs_status ddgs_render(const ddgs_gaussians *g, const ddgs_views *v,
  * writes dL/d(every input) into the non-NULL fields of *out. The blending
  * state is recomputed from the sorted lists, walking each pixel back to front
  * (T_before = T_after / (1 - sigma)). Must follow the ddgs_render that filled
- * ws, with the same g, v and cfg. */
+ * ws, with the same g, v and cfg (a different g->per_pixel is rejected). */
 ddgs_status ddgs_render_backward(const ddgs_gaussians *g, const ddgs_views *v,
                                  const ddgs_config *cfg, ddgs_workspace *ws,
                                  const float *dL_dimage, const float *t_final,
@@ -183,7 +195,8 @@ ddgs_status ddgs_render_backward(const ddgs_gaussians *g, const ddgs_views *v,
  * device, with that device current); make that first call before any stream
  * capture. The call synchronises the stream once to read the pair count.
  * Every call on a device shares the array and each clears what must start at
- * zero; calls whose GPU work overlaps (other streams or host threads) race. */
+ * zero; calls whose GPU work overlaps (other streams or host threads) race.
+ * g->per_pixel is not supported here (DDGS_ERR_INVALID_ARG). */
 ddgs_status ddgs_render_static(const ddgs_gaussians *g, const ddgs_views *v,
                                const ddgs_config *cfg, float *image,
                                float *t_final, uint32_t *n_last, void *stream);
@@ -213,6 +226,7 @@ typedef struct {
   const float *detector;           /* [V][5] */
   int32_t feat_dim;                /* k for every request, 1..32 (0 = 8) */
   int32_t sh_degree;               /* L for every request, 1..3 (0 = 1) */
+  int32_t entangled, per_pixel;    /* Eq. 3 variants, as in ddgs_gaussians */
 } ddgs_batch;
 
 /* ddgs_render over a batch (same rule, Eq. 1 and Eq. 3, per view). Outputs are

@@ -48,7 +48,7 @@ class _Gaussians(C.Structure):
                 ("log_scales", C.c_void_p), ("quats", C.c_void_p), ("opacity_logits", C.c_void_p),
                 ("feat_iso", C.c_void_p), ("feat_dir", C.c_void_p), ("feat_dir_bf16", C.c_int32),
                 ("b_iso", C.c_void_p), ("B_dir", C.c_void_p), ("feat_dim", C.c_int32),
-                ("sh_degree", C.c_int32)]
+                ("sh_degree", C.c_int32), ("entangled", C.c_int32), ("per_pixel", C.c_int32)]
 
 
 class _Views(C.Structure):
@@ -69,7 +69,8 @@ class _Batch(C.Structure):
                 ("quats", C.c_void_p), ("opacity_logits", C.c_void_p), ("feat_iso", C.c_void_p),
                 ("feat_dir", C.c_void_p), ("feat_dir_bf16", C.c_int32), ("b_iso", C.c_void_p),
                 ("B_dir", C.c_void_p), ("world_to_cam", C.c_void_p), ("detector", C.c_void_p),
-                ("feat_dim", C.c_int32), ("sh_degree", C.c_int32)]
+                ("feat_dim", C.c_int32), ("sh_degree", C.c_int32), ("entangled", C.c_int32),
+                ("per_pixel", C.c_int32)]
 
 
 class _Grads(C.Structure):
@@ -154,6 +155,10 @@ class Cloud:
     feat_dir: torch.Tensor
     b_iso: torch.Tensor
     B_dir: torch.Tensor
+    # Eq. 3 variants: both terms in every Gaussian (direct-entangled, Table 3);
+    # harmonics evaluated at each pixel's ray direction
+    entangled: bool = False
+    per_pixel: bool = False
 
     @property
     def n(self):
@@ -177,7 +182,8 @@ class Cloud:
                           _ptr(self.quats), _ptr(self.opacity_logits),
                           _ptr(self.feat_iso) if self.n_iso else None,
                           _ptr(self.feat_dir) if self.n > self.n_iso else None, int(bf16),
-                          _ptr(self.b_iso), _ptr(self.B_dir), self.feat_dim, self.sh_degree)
+                          _ptr(self.b_iso), _ptr(self.B_dir), self.feat_dim, self.sh_degree,
+                          int(self.entangled), int(self.per_pixel))
 
 
 @dataclasses.dataclass
@@ -222,7 +228,8 @@ def cloud_from_arrays(scene, device="cuda", feat_dir_bf16: Optional[bool] = None
     if bf:
         fd = fd.to(torch.bfloat16)
     return Cloud(t(scene.means), t(scene.log_scales), t(scene.quats), t(scene.opacity_logits),
-                 t(scene.feat[:scene.n_iso]), fd.contiguous(), t(scene.b_iso), t(scene.B_dir))
+                 t(scene.feat[:scene.n_iso]), fd.contiguous(), t(scene.b_iso), t(scene.B_dir),
+                 bool(scene.entangled), bool(scene.per_pixel))
 
 
 def views_from_arrays(views, device="cuda") -> Views:
@@ -388,14 +395,15 @@ class RenderFunction(torch.autograd.Function):
 
     Inputs: the cloud's tensors and the poses; returns the image [V, H, W].
     The backward recomputes the blending state from the workspace's sorted
-    lists (it must run before the next render on the same workspace)."""
+    lists (it must run before the next render on the same workspace).
+    `variant` = (entangled, per_pixel) selects an Eq. 3 variant."""
 
     @staticmethod
     def forward(ctx, means, log_scales, quats, opacity_logits, feat_iso, feat_dir, b_iso, B_dir,
-                world_to_cam, detector, height, width, cfg, ws):
+                world_to_cam, detector, height, width, cfg, ws, variant=(False, False)):
         cloud = Cloud(means.contiguous(), log_scales.contiguous(), quats.contiguous(),
                       opacity_logits.contiguous(), feat_iso.contiguous(), feat_dir.contiguous(),
-                      b_iso.contiguous(), B_dir.contiguous())
+                      b_iso.contiguous(), B_dir.contiguous(), bool(variant[0]), bool(variant[1]))
         views = Views(world_to_cam.contiguous(), detector.contiguous(), height, width)
         img, tf, nl = render(cloud, views, cfg, ws)
         ctx.cloud, ctx.views, ctx.cfg, ctx.ws = cloud, views, cfg, ws
@@ -415,7 +423,7 @@ class RenderFunction(torch.autograd.Function):
         out = [g.get(n) for n in names]
         if out[5] is not None and ctx.feat_dir_dtype != torch.float32:
             out[5] = out[5].to(ctx.feat_dir_dtype)
-        return (*out, None, None, None, None, None)
+        return (*out, None, None, None, None, None, None)
 
 
 def render_differentiable(cloud: Cloud, views: Views, cfg: Config, ws: Workspace):
@@ -494,7 +502,8 @@ class Batch:
                       self.H.ctypes.data, self.W.ctypes.data, p(self.means), p(self.log_scales),
                       p(self.quats), p(self.opacity_logits), p(self.feat_iso), p(self.feat_dir),
                       int(bf16), p(self.b_iso), p(self.B_dir), p(self.world_to_cam), p(self.detector),
-                      c0.feat_dim if c0 else 8, c0.sh_degree if c0 else 1)
+                      c0.feat_dim if c0 else 8, c0.sh_degree if c0 else 1,
+                      int(c0.entangled) if c0 else 0, int(c0.per_pixel) if c0 else 0)
 
     def view_slice(self, flat: torch.Tensor, v: int) -> torch.Tensor:
         a, b = int(self.pixel_offsets[v]), int(self.pixel_offsets[v + 1])

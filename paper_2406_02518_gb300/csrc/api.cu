@@ -56,6 +56,9 @@ ddgs_status check_inputs(const ddgs_gaussians *g, const ddgs_views *v, const ddg
   if (g->feat_dim < 0 || g->feat_dim > DDGS_MAX_FEAT_DIM || g->sh_degree < 0 ||
       g->sh_degree > DDGS_MAX_SH_DEGREE)
     return DDGS_ERR_INVALID_ARG;
+  if ((g->entangled != 0 && g->entangled != 1) || (g->per_pixel != 0 && g->per_pixel != 1) ||
+      (g->per_pixel && g->sh_degree > 1))
+    return DDGS_ERR_INVALID_ARG;
   if (g->n > 0) {
     if (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->b_iso || !g->B_dir)
       return DDGS_ERR_INVALID_ARG;
@@ -195,6 +198,12 @@ ddgs_status ensure_records(ddgs_workspace *ws, const ddgs::RenderShape &s) {
     if ((st = grow(ws->rect, ws->rec_cap, cap, 0, sizeof(uint4)))) return st;
     if ((st = grow(ws->grad2d, ws->rec_cap, 2 * cap, 0, sizeof(float4)))) return st;
     ws->rec_cap = cap;
+  }
+  if (ws->rec2 && ws->pix_cap < ws->rec_cap) {  // per-pixel storage follows the records
+    ddgs_status st;
+    if ((st = grow(ws->rec2, ws->pix_cap, ws->rec_cap, 0, sizeof(float4)))) return st;
+    if ((st = grow(ws->grad_h, ws->pix_cap, ws->rec_cap, 0, sizeof(float4)))) return st;
+    ws->pix_cap = ws->rec_cap;
   }
   if (blk > ws->blk_cap || !ws->blk_total) {
     int64_t cap = blk + blk / 4 + 64;
@@ -393,7 +402,7 @@ ddgs_status ddgs_workspace_destroy(ddgs_workspace *ws) {
   void *dev[] = {ws->rec0, ws->rec1, ws->rect, ws->tiles_touched, ws->grad2d, ws->blk_total,
                  ws->blk_offset, ws->keys[0], ws->keys[1], ws->vals[0], ws->vals[1], ws->hist,
                  ws->digit_total, ws->ranges, ws->d_pairs, ws->d_status, ws->d_req, ws->d_view,
-                 ws->order, ws->lpt_counts, ws->queue, ws->req_time};
+                 ws->order, ws->lpt_counts, ws->queue, ws->req_time, ws->rec2, ws->grad_h};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (ws->h_pairs) cudaFreeHost(ws->h_pairs);
@@ -437,8 +446,14 @@ ddgs_status render_common(const ddgs_gaussians &g, const ddgs_views &v, const dd
     if (s.records > ws->rec_cap || s.n_blocks > ws->blk_cap || s.total_tiles > ws->tile_cap ||
         !ws->keys[0])
       return DDGS_ERR_CAPACITY;
-  } else if ((st = ensure_records(ws, s))) {
-    return st;
+    if (g.per_pixel && (!ws->rec2 || ws->pix_cap < s.records)) return DDGS_ERR_CAPACITY;
+  } else {
+    if ((st = ensure_records(ws, s))) return st;
+    if (g.per_pixel && !ws->rec2) {
+      if ((st = grow(ws->rec2, ws->pix_cap, ws->rec_cap, 0, sizeof(float4)))) return st;
+      if ((st = grow(ws->grad_h, ws->pix_cap, ws->rec_cap, 0, sizeof(float4)))) return st;
+      ws->pix_cap = ws->rec_cap;
+    }
   }
   if ((st = upload_layout(ws, L, c->no_sync != 0, s_))) return st;
   ws->have_render = false;
@@ -477,9 +492,13 @@ ddgs_status render_common(const ddgs_gaussians &g, const ddgs_views &v, const dd
     ddgs::launch_tile_order(s, *ws, s_);
     CK(cudaGetLastError());
     ddgs::RasterParams P{c->alpha_min, c->alpha_max, c->t_min, c->q_max};
-    ddgs::launch_raster_fwd(s, P, *ws, image, t_final, n_last, s_);
+    ddgs::PixelRays pr;
+    pr.world_to_cam = v.world_to_cam;
+    pr.detector = v.detector;
+    ddgs::launch_raster_fwd(s, P, *ws, image, t_final, n_last, g.per_pixel ? &pr : nullptr, s_);
     CK(cudaGetLastError());
   }
+  ws->last_per_pixel = g.per_pixel != 0;
   ws->shape = s;
   ws->pair_bound = bound;
   ws->have_render = true;
@@ -490,7 +509,9 @@ ddgs_status backward_common(const ddgs_gaussians &g, const ddgs_views &v, const 
                             Layout &L, ddgs_workspace *ws, const float *dL_dimage,
                             const float *t_final, const uint32_t *n_last, const ddgs_grads *out,
                             cudaStream_t s_) {
-  if (!ws || !out || !ws->have_render || L.hash != ws->last_hash) return DDGS_ERR_INVALID_ARG;
+  if (!ws || !out || !ws->have_render || L.hash != ws->last_hash ||
+      (g.per_pixel != 0) != ws->last_per_pixel)
+    return DDGS_ERR_INVALID_ARG;
   ddgs::RenderShape &s = L.shape;
   s.req = ws->d_req;
   s.view = ws->d_view;
@@ -507,9 +528,15 @@ ddgs_status backward_common(const ddgs_gaussians &g, const ddgs_views &v, const 
   if (s.n_total == 0) return DDGS_OK;  // parameter gradients empty, pose/basis zero
   // with no views the backward preprocess still writes the (zero) gradients
   if (s.records > 0) CK(cudaMemsetAsync(ws->grad2d, 0, (size_t)s.records * 2 * sizeof(float4), s_));
+  if (s.records > 0 && g.per_pixel)
+    CK(cudaMemsetAsync(ws->grad_h, 0, (size_t)s.records * sizeof(float4), s_));
   ddgs::RasterParams P{c->alpha_min, c->alpha_max, c->t_min, c->q_max};
   if (s.records > 0 && s.total_tiles > 0 && ws->pair_bound > 0) {
-    ddgs::launch_raster_bwd(s, P, *ws, dL_dimage, t_final, n_last, s_);
+    ddgs::PixelRays pr;
+    pr.world_to_cam = v.world_to_cam;
+    pr.detector = v.detector;
+    pr.pose_grad = out->world_to_cam;
+    ddgs::launch_raster_bwd(s, P, *ws, dL_dimage, t_final, n_last, g.per_pixel ? &pr : nullptr, s_);
     CK(cudaGetLastError());
   }
   ddgs::launch_preprocess_bwd(g, v, *c, s, *ws, *out, s_);
@@ -530,6 +557,9 @@ ddgs_status check_batch(const ddgs_batch *b, const ddgs_config *c) {
   if (!b || !c || b->n_requests < 0) return DDGS_ERR_INVALID_ARG;
   if (b->feat_dim < 0 || b->feat_dim > DDGS_MAX_FEAT_DIM || b->sh_degree < 0 ||
       b->sh_degree > DDGS_MAX_SH_DEGREE)
+    return DDGS_ERR_INVALID_ARG;
+  if ((b->entangled != 0 && b->entangled != 1) || (b->per_pixel != 0 && b->per_pixel != 1) ||
+      (b->per_pixel && b->sh_degree > 1))
     return DDGS_ERR_INVALID_ARG;
   const bool vec = b->feat_dim == 0 || b->feat_dim == ddgs::K;
   if (c->tile != 8 && c->tile != 16 && c->tile != 32) return DDGS_ERR_INVALID_ARG;
@@ -561,6 +591,7 @@ void batch_structs(const ddgs_batch *b, ddgs_gaussians &g, ddgs_views &v) {
   g.opacity_logits = b->opacity_logits; g.feat_iso = b->feat_iso; g.feat_dir = b->feat_dir;
   g.feat_dir_bf16 = b->feat_dir_bf16; g.b_iso = b->b_iso; g.B_dir = b->B_dir;
   g.feat_dim = b->feat_dim; g.sh_degree = b->sh_degree;
+  g.entangled = b->entangled; g.per_pixel = b->per_pixel;
   v = ddgs_views{};
   v.world_to_cam = b->world_to_cam;
   v.detector = b->detector;

@@ -132,7 +132,13 @@ struct ddgs_workspace {
   float4 *rec1 = nullptr;        // (conic c, alpha, colour, depth)
   uint2 *rect = nullptr;         // (tx0 | ty0 << 16, tx1 | ty1 << 16)
   uint32_t *tiles_touched = nullptr;
-  float4 *grad2d = nullptr;      // [records][2]: (u, v, ca, cb), (cc, alpha, colour, 0)
+  float4 *grad2d = nullptr;      // [records][2]: (u, v, ca, cb), (cc, alpha, colour, 0);
+                                 // with per-pixel directions the colour slot holds dL/dz
+  // per-pixel directions only (allocated by the first such render)
+  float4 *rec2 = nullptr;        // (a, h_0, h_1, h_2): colour logit z = a + Y(ray) . h
+  float4 *grad_h = nullptr;      // (dL/dh_0, dL/dh_1, dL/dh_2, 0)
+  int64_t pix_cap = 0;
+  bool last_per_pixel = false;   // mode of the last forward render
   // scan
   uint32_t *blk_total = nullptr;
   uint64_t *blk_offset = nullptr;
@@ -200,12 +206,20 @@ int64_t sort_blocks(uint64_t pair_bound);
 cudaError_t prepare_sort_kernels();  // once per device, before any capture
 
 // raster.cu
+// Per-pixel ray angles (Eq. 3 variant): the views' poses and detectors, and
+// the backward pass's pose-gradient output (may be null). A null PixelRays
+// selects the per-Gaussian colours of the records.
+struct PixelRays {
+  const float *world_to_cam = nullptr, *detector = nullptr;
+  float *pose_grad = nullptr;
+};
 void launch_tile_order(const RenderShape &s, ddgs_workspace &ws, cudaStream_t st);
 void launch_raster_fwd(const RenderShape &s, const RasterParams &p, ddgs_workspace &ws,
-                       float *image, float *t_final, uint32_t *n_last, cudaStream_t st);
+                       float *image, float *t_final, uint32_t *n_last, const PixelRays *pr,
+                       cudaStream_t st);
 void launch_raster_bwd(const RenderShape &s, const RasterParams &p, ddgs_workspace &ws,
                        const float *dL_dimage, const float *t_final, const uint32_t *n_last,
-                       cudaStream_t st);
+                       const PixelRays *pr, cudaStream_t st);
 
 // api.cu
 void launch_l1_loss(const float *image, const float *target, int per_view, int V, int64_t hw,

@@ -290,7 +290,9 @@ struct PreArgs {
   float dilation, near_plane, q_max;
   RenderShape s;
   int K, L;          // feature dimension and harmonic degree
-  float4 *rec0, *rec1;
+  int entangled;     // every Gaussian carries both terms of Eq. 3
+  int per_pixel;     // Y at the pixel rays: write (a, h) to rec2 instead of a colour
+  float4 *rec0, *rec1, *rec2;
   uint4 *bin_info;  // (rect lo, rect hi, depth bits, tiles touched)
   uint32_t *blk_total;
   unsigned long long *t0;  // batch start (min over blocks of %globaltimer), or null
@@ -323,7 +325,11 @@ struct BlockReq {
 };
 
 // GEN = false: k = 8, L = 1 (the paper's evaluation setting) with vector
-// feature loads; GEN = true: any k <= 32 and L <= 3.
+// feature loads; GEN = true: any k <= 32 and L <= 3, and the Eq. 3 variants.
+// Generic radiosity: logit z = a + Y(d) . h, a = b_iso . f for a Gaussian with
+// the isotropic term (every one of the isotropic range; all when entangled),
+// h = B_dir f for one with the directional term. With per-pixel directions
+// the record carries (a, h) and the rasteriser evaluates Y per pixel.
 template <bool GEN>
 __global__ void __launch_bounds__(PRE_THREADS) preprocess_fwd_kernel(PreArgs a) {
   constexpr int KS = GEN ? KG : K, KLS = GEN ? KLG : 3;
@@ -352,7 +358,7 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_fwd_kernel(PreArgs a) 
   float mu[3] = {0, 0, 0}, alpha = 0.f, c_iso = 0.f, h[KLS];
 #pragma unroll
   for (int m = 0; m < KLS; ++m) h[m] = 0.f;
-  bool is_dir = false;
+  bool is_dir = false, has_dir = false;
   if (live) {
     mu[0] = a.means[3 * i]; mu[1] = a.means[3 * i + 1]; mu[2] = a.means[3 * i + 2];
     float ls[3] = {a.log_scales[3 * i], a.log_scales[3 * i + 1], a.log_scales[3 * i + 2]};
@@ -379,18 +385,20 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_fwd_kernel(PreArgs a) 
         }
       }
     } else {
+      // c_iso holds the isotropic logit a here
+      const bool has_iso = !is_dir || a.entangled;
+      has_dir = is_dir || a.entangled;
       float zl = 0.f;
       for (int k = 0; k < Kr; ++k) {
         const float fk = load_feat1(a.feat_iso, a.feat_dir, a.feat_dir_bf16, rq, br.l, Kr, k);
-        if (!is_dir) {
-          zl = fmaf(s_b[k], fk, zl);
-        } else {
+        if (has_iso) zl = fmaf(s_b[k], fk, zl);
+        if (has_dir) {
 #pragma unroll
           for (int m = 0; m < KLS; ++m)
             if (m < kL) h[m] = fmaf(s_B[m * Kr + k], fk, h[m]);
         }
       }
-      if (!is_dir) c_iso = sigmoidf_(zl);
+      c_iso = zl;
     }
   }
 
@@ -419,16 +427,22 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_fwd_kernel(PreArgs a) 
       total += tt;
       const float ca = divr(p.cov[2], p.det), cb = divr(-p.cov[1], p.det), cc = divr(p.cov[0], p.det);
       float colour = c_iso;
-      if (is_dir) {
-        float d0 = mu[0] + vc.wt[0], d1 = mu[1] + vc.wt[1], d2 = mu[2] + vc.wt[2];
-        float inv = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
-        float zl;
-        if (!GEN) {
-          zl = SH_C1 * (-d1 * inv * h[0] + d2 * inv * h[1] - d0 * inv * h[2]);
-        } else {
+      if (!GEN) {
+        if (is_dir) {
+          float d0 = mu[0] + vc.wt[0], d1 = mu[1] + vc.wt[1], d2 = mu[2] + vc.wt[2];
+          float inv = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+          colour = sigmoidf_(SH_C1 * (-d1 * inv * h[0] + d2 * inv * h[1] - d0 * inv * h[2]));
+        }
+      } else if (a.per_pixel) {
+        a.rec2[rec] = make_float4(c_iso, h[0], h[1], h[2]);  // L = 1: k_L = 3
+        colour = 0.f;
+      } else {
+        float zl = c_iso;
+        if (has_dir) {
+          float d0 = mu[0] + vc.wt[0], d1 = mu[1] + vc.wt[1], d2 = mu[2] + vc.wt[2];
+          float inv = rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
           float Y[KLS];
           sh_eval(s_sh, kL, d0 * inv, d1 * inv, d2 * inv, Y, nullptr);
-          zl = 0.f;
 #pragma unroll
           for (int m = 0; m < KLS; ++m)
             if (m < kL) zl = fmaf(Y[m], h[m], zl);
@@ -523,7 +537,9 @@ struct PreBwdArgs {
   float dilation, near_plane;
   RenderShape s;
   int K, L;
+  int entangled, per_pixel;
   const float4 *grad2d;
+  const float4 *grad_h;  // per_pixel: dL/dh summed over pixels
   ddgs_grads out;
   int want_param, want_basis, want_pose;
 };
@@ -586,7 +602,7 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_bwd_kernel(PreBwdArgs 
   GaussGeom gg;
   constexpr int KF = GEN ? 1 : K;  // features kept in registers (fast path only)
   float mu[3] = {0, 0, 0}, alpha = 0.f, c_iso = 0.f, h[KLS], f[KF];
-  bool is_dir = false;
+  bool is_dir = false, has_iso = false, has_dir = false;
 #pragma unroll
   for (int k = 0; k < KF; ++k) f[k] = 0.f;
 #pragma unroll
@@ -616,18 +632,20 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_bwd_kernel(PreBwdArgs 
         }
       }
     } else {
+      // c_iso holds the isotropic logit a here
+      has_iso = !is_dir || a.entangled;
+      has_dir = is_dir || a.entangled;
       float zl = 0.f;
       for (int k = 0; k < Kr; ++k) {
         const float fk = load_feat1(a.feat_iso, a.feat_dir, a.feat_dir_bf16, rq, br.l, Kr, k);
-        if (!is_dir) {
-          zl = fmaf(s_b[k], fk, zl);
-        } else {
+        if (has_iso) zl = fmaf(s_b[k], fk, zl);
+        if (has_dir) {
 #pragma unroll
           for (int m = 0; m < KLS; ++m)
             if (m < kL) h[m] = fmaf(s_B[m * Kr + k], fk, h[m]);
         }
       }
-      if (!is_dir) c_iso = sigmoidf_(zl);
+      c_iso = zl;
     }
   }
 
@@ -652,8 +670,9 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_bwd_kernel(PreBwdArgs 
       if (live) {
         const int64_t rec = vc.rec_off + br.l;
         const float4 g0 = a.grad2d[2 * rec], g1 = a.grad2d[2 * rec + 1];
+        const float4 gh = (GEN && a.per_pixel) ? a.grad_h[rec] : make_float4(0.f, 0.f, 0.f, 0.f);
         any = (g0.x != 0.f) | (g0.y != 0.f) | (g0.z != 0.f) | (g0.w != 0.f) | (g1.x != 0.f) |
-              (g1.y != 0.f) | (g1.z != 0.f);
+              (g1.y != 0.f) | (g1.z != 0.f) | (gh.x != 0.f) | (gh.y != 0.f) | (gh.z != 0.f);
         ViewProj p;
         if (any) {
           view_proj(mu, gg.S, vc, a.dilation, a.near_plane, p);
@@ -662,32 +681,44 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_bwd_kernel(PreBwdArgs 
         if (any) {
           const float gu = g0.x, gv = g0.y, gca = g0.z, gcb = g0.w, gcc = g1.x;
           galpha += g1.y;
-          // radiosity (Eq. 3)
-          if (!is_dir) {
-            dz_iso += g1.z * c_iso * (1.f - c_iso);
-          } else {
-            float d[3] = {mu[0] + vc.wt[0], mu[1] + vc.wt[1], mu[2] + vc.wt[2]};
-            float nrm = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-            float inv = 1.f / nrm;
-            float dh_[3] = {d[0] * inv, d[1] * inv, d[2] * inv};
-            float ddh[3];
-            if (!GEN) {
+          // radiosity (Eq. 3); dir_grad: the colour depends on the mean's direction
+          bool dir_grad = false;
+          float d[3], inv = 0.f, dh_[3], ddh[3] = {0.f, 0.f, 0.f};
+          if (!GEN) {
+            if (!is_dir) {
+              dz_iso += g1.z * c_iso * (1.f - c_iso);
+            } else {
+              dir_grad = true;
+              d[0] = mu[0] + vc.wt[0]; d[1] = mu[1] + vc.wt[1]; d[2] = mu[2] + vc.wt[2];
+              inv = 1.f / sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+              dh_[0] = d[0] * inv; dh_[1] = d[1] * inv; dh_[2] = d[2] * inv;
               float Y[3] = {-SH_C1 * dh_[1], SH_C1 * dh_[2], -SH_C1 * dh_[0]};
               float c = sigmoidf_(Y[0] * h[0] + Y[1] * h[1] + Y[2] * h[2]);
               float dz = g1.z * c * (1.f - c);
               dh[0] += dz * Y[0]; dh[1] += dz * Y[1]; dh[2] += dz * Y[2];
               float dY[3] = {dz * h[0], dz * h[1], dz * h[2]};
               ddh[0] = -SH_C1 * dY[2]; ddh[1] = -SH_C1 * dY[0]; ddh[2] = SH_C1 * dY[1];
-            } else {
-              float Y[KLS], dYd[KLS][3];
+            }
+          } else if (a.per_pixel) {
+            // the rasteriser summed dL/dz (g1.z) and dL/dh (gh) over the pixels
+            if (has_iso) dz_iso += g1.z;
+            if (has_dir) { dh[0] += gh.x; dh[1] += gh.y; dh[2] += gh.z; }
+          } else {
+            float zl = c_iso, Y[KLS], dYd[KLS][3];
+            if (has_dir) {
+              d[0] = mu[0] + vc.wt[0]; d[1] = mu[1] + vc.wt[1]; d[2] = mu[2] + vc.wt[2];
+              inv = 1.f / sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+              dh_[0] = d[0] * inv; dh_[1] = d[1] * inv; dh_[2] = d[2] * inv;
               sh_eval(s_sh, kL, dh_[0], dh_[1], dh_[2], Y, dYd);
-              float zl = 0.f;
 #pragma unroll
               for (int m = 0; m < KLS; ++m)
                 if (m < kL) zl = fmaf(Y[m], h[m], zl);
-              const float c = sigmoidf_(zl);
-              const float dz = g1.z * c * (1.f - c);
-              ddh[0] = ddh[1] = ddh[2] = 0.f;
+            }
+            const float c = sigmoidf_(zl);
+            const float dz = g1.z * c * (1.f - c);
+            if (has_iso) dz_iso += dz;
+            if (has_dir) {
+              dir_grad = true;
 #pragma unroll
               for (int m = 0; m < KLS; ++m) {
                 if (m >= kL) break;
@@ -698,6 +729,8 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_bwd_kernel(PreBwdArgs 
                 ddh[2] = fmaf(w, dYd[m][2], ddh[2]);
               }
             }
+          }
+          if (dir_grad) {
             float dot = ddh[0] * dh_[0] + ddh[1] * dh_[1] + ddh[2] * dh_[2];
             float dd[3] = {(ddh[0] - dh_[0] * dot) * inv, (ddh[1] - dh_[1] * dot) * inv,
                            (ddh[2] - dh_[2] * dot) * inv};
@@ -815,17 +848,22 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_bwd_kernel(PreBwdArgs 
           o[1] = make_float4(gf[4], gf[5], gf[6], gf[7]);
         }
       }
-    } else if (!is_dir) {
-      if (a.out.feat_iso)
-        for (int k = 0; k < Kr; ++k) a.out.feat_iso[(rq.iso_row + br.l) * Kr + k] = dz_iso * s_b[k];
-    } else if (a.out.feat_dir) {
-      for (int k = 0; k < Kr; ++k) {
-        float acc = 0.f;
+    } else {
+      // f feeds a = b_iso . f and/or h = B_dir f; the row lives in the
+      // Gaussian's own range
+      float *dst = !is_dir ? (a.out.feat_iso ? a.out.feat_iso + (rq.iso_row + br.l) * Kr : nullptr)
+                           : (a.out.feat_dir ? a.out.feat_dir + (rq.dir_row + br.l - rq.n_iso) * Kr
+                                             : nullptr);
+      if (dst)
+        for (int k = 0; k < Kr; ++k) {
+          float acc = has_iso ? dz_iso * s_b[k] : 0.f;
+          if (has_dir) {
 #pragma unroll
-        for (int m = 0; m < KLS; ++m)
-          if (m < kL) acc = fmaf(s_B[m * Kr + k], dh[m], acc);
-        a.out.feat_dir[(rq.dir_row + br.l - rq.n_iso) * Kr + k] = acc;
-      }
+            for (int m = 0; m < KLS; ++m)
+              if (m < kL) acc = fmaf(s_B[m * Kr + k], dh[m], acc);
+          }
+          dst[k] = acc;
+        }
     }
     if (a.out.log_scales || a.out.quats) {
       // Sigma = M M^T: dM = 2 dSigma M ; M = R diag(s)
@@ -872,9 +910,8 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_bwd_kernel(PreBwdArgs 
     if (live) {
       for (int k = 0; k < Kr; ++k) {
         const float fk = load_feat1(a.feat_iso, a.feat_dir, a.feat_dir_bf16, rq, br.l, Kr, k);
-        if (!is_dir) {
-          if (dz_iso != 0.f) atomicAdd(&s_basis[k], dz_iso * fk);
-        } else {
+        if (has_iso && dz_iso != 0.f) atomicAdd(&s_basis[k], dz_iso * fk);
+        if (has_dir) {
 #pragma unroll
           for (int m = 0; m < KLS; ++m)
             if (m < kL && dh[m] != 0.f) atomicAdd(&s_basis[Kr + m * Kr + k], dh[m] * fk);
@@ -928,13 +965,16 @@ void launch_preprocess_fwd(const ddgs_gaussians &g, const ddgs_views &v, const d
   a.dilation = c.dilation; a.near_plane = c.near_plane; a.q_max = c.q_max;
   a.K = g.feat_dim ? g.feat_dim : K;
   a.L = g.sh_degree ? g.sh_degree : 1;
+  a.entangled = g.entangled ? 1 : 0;
+  a.per_pixel = g.per_pixel ? 1 : 0;
   a.s = s;
-  a.rec0 = ws.rec0; a.rec1 = ws.rec1; a.bin_info = reinterpret_cast<uint4 *>(ws.rect);
+  a.rec0 = ws.rec0; a.rec1 = ws.rec1; a.rec2 = ws.rec2;
+  a.bin_info = reinterpret_cast<uint4 *>(ws.rect);
   a.blk_total = ws.blk_total;
   a.t0 = ws.req_time;
   if (s.n_blocks > 0) {
     LaunchScope ls(KID_PREPROCESS_FWD, st);
-    if (a.K == K && a.L == 1)
+    if (a.K == K && a.L == 1 && !a.entangled && !a.per_pixel)
       preprocess_fwd_kernel<false><<<(unsigned)s.n_blocks, PRE_THREADS, 0, st>>>(a);
     else
       preprocess_fwd_kernel<true><<<(unsigned)s.n_blocks, PRE_THREADS, 0, st>>>(a);
@@ -966,8 +1006,11 @@ void launch_preprocess_bwd(const ddgs_gaussians &g, const ddgs_views &v, const d
   a.dilation = c.dilation; a.near_plane = c.near_plane;
   a.K = g.feat_dim ? g.feat_dim : K;
   a.L = g.sh_degree ? g.sh_degree : 1;
+  a.entangled = g.entangled ? 1 : 0;
+  a.per_pixel = g.per_pixel ? 1 : 0;
   a.s = s;
   a.grad2d = ws.grad2d;
+  a.grad_h = ws.grad_h;
   a.out = out;
   a.want_param = (out.means || out.log_scales || out.quats || out.opacity_logits || out.feat_iso ||
                   out.feat_dir) ? 1 : 0;
@@ -975,7 +1018,7 @@ void launch_preprocess_bwd(const ddgs_gaussians &g, const ddgs_views &v, const d
   a.want_pose = out.world_to_cam ? 1 : 0;
   if (s.n_blocks > 0) {
     LaunchScope ls(KID_PREPROCESS_BWD, st);
-    if (a.K == K && a.L == 1)
+    if (a.K == K && a.L == 1 && !a.entangled && !a.per_pixel)
       preprocess_bwd_kernel<false><<<(unsigned)s.n_blocks, PRE_THREADS, 0, st>>>(a);
     else
       preprocess_bwd_kernel<true><<<(unsigned)s.n_blocks, PRE_THREADS, 0, st>>>(a);

@@ -20,7 +20,15 @@
 // The per-pixel 2D gradients of one Gaussian are summed over the warp with
 // shuffles, over the block in shared memory, and reach global memory with one
 // vector atomic per (tile, Gaussian).
+//
+// PIX = true renders the Eq. 3 variant whose ray angles are each pixel's own:
+// a record then carries (a, h) instead of a colour, and the pair's colour is
+// c = sigmoid(a + Y_1(d_p) . h) with d_p the pixel ray's unit direction. The
+// backward pass sums dL/dz (z the logit) and dL/dh per (tile, Gaussian) and
+// adds the pose gradient through each pixel's ray.
+#include <map>
 #include <mutex>
+#include <utility>
 
 #include "ddgs_internal.cuh"
 
@@ -41,7 +49,42 @@ struct RasterArgs {
   const uint32_t *order;     // global tiles, longest list first
   uint32_t *counter;         // work-queue head (zero at launch)
   unsigned long long *req_end;  // [R]: latest %globaltimer of a finished tile, or null
+  // per-pixel ray angles only
+  const float4 *rec2;        // (a, h_0, h_1, h_2) per record
+  float4 *grad_h;            // dL/dh per record
+  const float *world_to_cam, *detector;
+  float *pose_grad;          // [V][12] or null
 };
+
+__device__ __forceinline__ float sigmoid_r(float x) { return 1.f / (1.f + __expf(-x)); }
+
+// The ray through pixel centre (px, py) of a view: rc = ((px - c_u) pitch_u,
+// (py - c_v) pitch_v, sdd) in camera coordinates, world direction d = W^T rc,
+// and Y_1 of d / |d| (real harmonics of degree 1: sqrt(3/(4 pi)) (-y, z, -x)).
+struct PixRay {
+  float rc[3], dh[3], inv, Y[3];
+};
+
+__device__ __forceinline__ void pixel_ray(const float *pose, const float *det, int H, int W,
+                                          float px, float py, PixRay &r) {
+  const float cu = 0.5f * (float)W + det[3], cv = 0.5f * (float)H + det[4];
+  r.rc[0] = (px - cu) * det[1];
+  r.rc[1] = (py - cv) * det[2];
+  r.rc[2] = det[0];
+  float d[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) d[c] = pose[c] * r.rc[0] + pose[4 + c] * r.rc[1] + pose[8 + c] * r.rc[2];
+  r.inv = 1.f / sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) r.dh[c] = d[c] * r.inv;
+  r.Y[0] = -SH_C1 * r.dh[1];
+  r.Y[1] = SH_C1 * r.dh[2];
+  r.Y[2] = -SH_C1 * r.dh[0];
+}
+
+__device__ __forceinline__ float pixel_colour(const PixRay &r, float4 z) {
+  return sigmoid_r(fmaf(r.Y[2], z.w, fmaf(r.Y[1], z.z, fmaf(r.Y[0], z.y, z.x))));
+}
 
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
@@ -114,15 +157,17 @@ __device__ __forceinline__ uint32_t quarter_todo(const TileGeom<T> &tg, float4 b
 
 // One (view, tile) work item of the forward pass; BATCH list entries are
 // staged in shared memory per round.
-template <int T, int BATCH>
+template <int T, int BATCH, bool PIX>
 __device__ __forceinline__ void fwd_tile(const RasterArgs &a, int64_t gt, float4 *s_a, float4 *s_b,
-                                         float4 *s_box) {
+                                         float4 *s_box, float4 *s_c) {
   constexpr int NT = T * T;
   const int tid = threadIdx.x;
   const TileGeom<T> tg(a.s, gt);
   const uint2 range = a.ranges[tg.gtile];
   const int64_t rec_base = tg.rec_base;
   const float px = tg.px + 0.5f, py = tg.py + 0.5f;
+  PixRay ray;
+  if (PIX) pixel_ray(a.world_to_cam + 12 * tg.v, a.detector + 5 * tg.v, tg.H, tg.W, px, py, ray);
   float Tr = 1.f, C = 0.f;
   uint32_t last = 0;
   bool done = !tg.inside;
@@ -138,6 +183,7 @@ __device__ __forceinline__ void fwd_tile(const RasterArgs &a, int64_t gt, float4
           s_a[e] = r0;
           s_b[e] = r1;
           s_box[e] = ellipse_box(r0, r1, a.P.q_max);
+          if (PIX) s_c[e] = a.rec2[r];
         } else {
           s_box[e] = empty_box();  // only after a capacity overflow
         }
@@ -169,7 +215,8 @@ __device__ __forceinline__ void fwd_tile(const RasterArgs &a, int64_t gt, float4
           done = true;
           continue;
         }
-        C = fmaf(B.z * e.sigma, Tr, C);
+        const float col = PIX ? pixel_colour(ray, s_c[k]) : B.z;
+        C = fmaf(col * e.sigma, Tr, C);
         Tr = Tn;
         last = b0 + (uint32_t)k - range.x + 1u;
       }
@@ -192,9 +239,9 @@ constexpr int fwd_min_blocks() { return T == 16 ? 6 : (T == 8 ? 16 : 1); }
 template <int T>
 constexpr int bwd_min_blocks() { return T == 16 ? 5 : (T == 8 ? 12 : 1); }
 
-template <int T, int BATCH>
+template <int T, int BATCH, bool PIX>
 __global__ void __launch_bounds__(T *T, fwd_min_blocks<T>()) raster_fwd_kernel(RasterArgs a) {
-  __shared__ float4 s_a[BATCH], s_b[BATCH], s_box[BATCH];
+  __shared__ float4 s_a[BATCH], s_b[BATCH], s_box[BATCH], s_c[PIX ? BATCH : 1];
   __shared__ uint32_t s_item;
   for (;;) {
     __syncthreads();  // the previous item is finished by every thread
@@ -203,7 +250,7 @@ __global__ void __launch_bounds__(T *T, fwd_min_blocks<T>()) raster_fwd_kernel(R
     const uint32_t item = s_item;
     if (item >= (uint32_t)a.s.total_tiles) break;
     const int64_t gt = a.order[item];
-    fwd_tile<T, BATCH>(a, gt, s_a, s_b, s_box);
+    fwd_tile<T, BATCH, PIX>(a, gt, s_a, s_b, s_box, s_c);
     if (a.req_end && threadIdx.x == 0)
       atomicMax(a.req_end + a.s.view[find_view(a.s.view, a.s.V, gt)].req, global_ns());
   }
@@ -237,20 +284,55 @@ __device__ __forceinline__ int quarter_reduce8(float v[8]) {
   return ((lane >> 2) & 1) * 4 + ((lane >> 1) & 1) * 2 + (lane & 1);
 }
 
-template <int BATCH>
+// Sum 16 per-lane values over each quarter (8 lanes) with 14 shuffles. Lane l
+// of the quarter ends with components c and c + 1 in v[0], v[1], where
+// c = ((l >> 2) & 1) * 8 + ((l >> 1) & 1) * 4 + (l & 1) * 2 is returned.
+__device__ __forceinline__ int quarter_reduce16(float v[16]) {
+  const int lane = threadIdx.x & 31;
+  bool hi = lane & 4;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    float send = hi ? v[k] : v[k + 8];
+    float keep = hi ? v[k + 8] : v[k];
+    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  hi = lane & 2;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    float send = hi ? v[k] : v[k + 4];
+    float keep = hi ? v[k + 4] : v[k];
+    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+  }
+  hi = lane & 1;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    float send = hi ? v[k] : v[k + 2];
+    float keep = hi ? v[k + 2] : v[k];
+    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
+  }
+  return ((lane >> 2) & 1) * 8 + ((lane >> 1) & 1) * 4 + (lane & 1) * 2;
+}
+
+// Accumulated components per (tile, Gaussian): u, v, conic a, b, c, alpha and
+// the colour (or, with PIX, the logit z and h_0..h_2).
+template <bool PIX>
+constexpr int n_acc() { return PIX ? 12 : 8; }
+
+template <int BATCH, bool PIX>
 struct BwdSmem {
-  float4 a[BATCH], b[BATCH], box[BATCH];
+  float4 a[BATCH], b[BATCH], box[BATCH], c[PIX ? BATCH : 1];
   uint32_t id[BATCH];
-  float acc[BATCH][8];
+  float acc[BATCH][n_acc<PIX>()];
+  float pose[PIX ? 12 : 1];  // per-tile pose gradient through the pixel rays
   uint32_t max_last;
 };
 
 // One (view, tile) work item of the backward pass.
-template <int T, int BATCH>
-__device__ __forceinline__ void bwd_tile(const RasterArgs &a, int64_t gt, BwdSmem<BATCH> &sm) {
-  float4 *s_a = sm.a, *s_b = sm.b, *s_box = sm.box;
+template <int T, int BATCH, bool PIX>
+__device__ __forceinline__ void bwd_tile(const RasterArgs &a, int64_t gt, BwdSmem<BATCH, PIX> &sm) {
+  float4 *s_a = sm.a, *s_b = sm.b, *s_box = sm.box, *s_c = sm.c;
   uint32_t *s_id = sm.id;
-  float (*s_acc)[8] = sm.acc;
+  float (*s_acc)[n_acc<PIX>()] = sm.acc;
   uint32_t &s_max = sm.max_last;
   constexpr int NT = T * T;
   const int tid = threadIdx.x;
@@ -258,6 +340,9 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs &a, int64_t gt, BwdSme
   const uint2 range = a.ranges[tg.gtile];
   const int64_t rec_base = tg.rec_base;
   const float px = tg.px + 0.5f, py = tg.py + 0.5f;
+  PixRay ray;
+  float gY[3] = {0.f, 0.f, 0.f};  // dL/dY_1 of this pixel's ray
+  if (PIX) pixel_ray(a.world_to_cam + 12 * tg.v, a.detector + 5 * tg.v, tg.H, tg.W, px, py, ray);
   float Tr = 1.f, g = 0.f;
   uint32_t last = 0;
   if (tg.inside) {
@@ -292,13 +377,14 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs &a, int64_t gt, BwdSme
           s_a[e] = r0;
           s_b[e] = r1;
           s_box[e] = ellipse_box(r0, r1, a.P.q_max);
+          if (PIX) s_c[e] = a.rec2[r];
         } else {
           s_box[e] = empty_box();  // only after a capacity overflow
         }
         s_id[e] = id;
       }
 #pragma unroll
-      for (int c = 0; c < 8; ++c) s_acc[e][c] = 0.f;
+      for (int c = 0; c < n_acc<PIX>(); ++c) s_acc[e][c] = 0.f;
     }
     __syncthreads();
     const int cnt = (int)(hi - lo);
@@ -321,7 +407,9 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs &a, int64_t gt, BwdSme
         const int k = has ? c0 + __ffs(mine) - 1 : c0;
         if (has) mine &= mine - 1;
         const uint32_t pos = (uint32_t)(hi - 1 - k);
-        float gv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        float gv[PIX ? 16 : 8];
+#pragma unroll
+        for (int c = 0; c < (PIX ? 16 : 8); ++c) gv[c] = 0.f;
         bool act = has && pos < last;
         if (act) {
           const float4 A = s_a[k], B = s_b[k];
@@ -332,7 +420,9 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs &a, int64_t gt, BwdSme
             // relative error (~1 ulp) is far inside the gradient tolerance
             const float inv_om = __frcp_rn(__fsub_rn(1.f, e.sigma));
             Tr = Tr * inv_om;  // transmittance before this Gaussian
-            const float c = B.z;
+            float4 cz;
+            if (PIX) cz = s_c[k];
+            const float c = PIX ? pixel_colour(ray, cz) : B.z;
             const float dC_dsigma = fmaf(c, Tr, -S * inv_om);
             S = fmaf(c * e.sigma, Tr, S);
             const float gs = g * dC_dsigma;
@@ -347,35 +437,87 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs &a, int64_t gt, BwdSme
             gv[2] = gq * e.dx * e.dx;
             gv[3] = gq2 * e.dx * e.dy;
             gv[4] = gq * e.dy * e.dy;
-            gv[6] = g * e.sigma * Tr;
+            const float dcol = g * e.sigma * Tr;  // dL/dc
+            if (PIX) {
+              const float dz = dcol * c * (1.f - c);
+              gv[6] = dz;
+              gv[7] = dz * ray.Y[0];
+              gv[8] = dz * ray.Y[1];
+              gv[9] = dz * ray.Y[2];
+              gY[0] = fmaf(dz, cz.y, gY[0]);
+              gY[1] = fmaf(dz, cz.z, gY[1]);
+              gY[2] = fmaf(dz, cz.w, gY[2]);
+            } else {
+              gv[6] = dcol;
+            }
           }
         }
         // sum the quarter's 8 lanes (each quarter has its own entry k)
         if (__any_sync(0xffffffffu, act)) {
-          const int comp = quarter_reduce8(gv);
-          if (has && gv[0] != 0.f) atomicAdd(&s_acc[k][comp], gv[0]);
+          if (PIX) {
+            const int comp = quarter_reduce16(gv);
+            if (has && comp < 10) {
+              if (gv[0] != 0.f) atomicAdd(&s_acc[k][comp], gv[0]);
+              if (gv[1] != 0.f) atomicAdd(&s_acc[k][comp + 1], gv[1]);
+            }
+          } else {
+            const int comp = quarter_reduce8(gv);
+            if (has && gv[0] != 0.f) atomicAdd(&s_acc[k][comp], gv[0]);
+          }
         }
       }
     }
     __syncthreads();
     for (int e = tid; e < cnt; e += NT) {
       const float *acc = s_acc[e];
-      const bool nz = (acc[0] != 0.f) | (acc[1] != 0.f) | (acc[2] != 0.f) | (acc[3] != 0.f) |
-                      (acc[4] != 0.f) | (acc[5] != 0.f) | (acc[6] != 0.f);
+      bool nz = (acc[0] != 0.f) | (acc[1] != 0.f) | (acc[2] != 0.f) | (acc[3] != 0.f) |
+                (acc[4] != 0.f) | (acc[5] != 0.f) | (acc[6] != 0.f);
+      if (PIX) nz |= (acc[7] != 0.f) | (acc[8] != 0.f) | (acc[9] != 0.f);
       if (nz) {
         float4 *dst = a.grad2d + 2 * (rec_base + s_id[e]);
         atomicAdd(dst, make_float4(acc[0], acc[1], acc[2], acc[3]));
         atomicAdd(dst + 1, make_float4(acc[4], acc[5], acc[6], 0.f));
+        if (PIX) atomicAdd(a.grad_h + rec_base + s_id[e], make_float4(acc[7], acc[8], acc[9], 0.f));
       }
     }
     __syncthreads();
   }
+  if (PIX && a.pose_grad) {
+    // Y_1(d / |d|), d = W^T rc: dL/dW[r][c] = rc[r] dL/dd[c]
+    float w9[9];
+    const bool mine = tg.inside && ((gY[0] != 0.f) | (gY[1] != 0.f) | (gY[2] != 0.f));
+    const float ddh[3] = {-SH_C1 * gY[2], -SH_C1 * gY[0], SH_C1 * gY[1]};
+    const float dot = ddh[0] * ray.dh[0] + ddh[1] * ray.dh[1] + ddh[2] * ray.dh[2];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float dd = mine ? (ddh[c] - ray.dh[c] * dot) * ray.inv : 0.f;
+#pragma unroll
+      for (int r = 0; r < 3; ++r) w9[3 * r + c] = ray.rc[r] * dd;
+    }
+    if (__any_sync(0xffffffffu, mine)) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) w9[i] += __shfl_xor_sync(0xffffffffu, w9[i], o);
+      }
+      if ((tid & 31) == 0)
+#pragma unroll
+        for (int i = 0; i < 9; ++i) atomicAdd(&sm.pose[i], w9[i]);
+    }
+    __syncthreads();
+    if (tid < 9) {
+      const float x = sm.pose[tid];
+      if (x != 0.f) atomicAdd(a.pose_grad + 12 * (int64_t)tg.v + 4 * (tid / 3) + tid % 3, x);
+      sm.pose[tid] = 0.f;
+    }
+  }
 }
 
-template <int T, int BATCH>
+template <int T, int BATCH, bool PIX>
 __global__ void __launch_bounds__(T *T, bwd_min_blocks<T>()) raster_bwd_kernel(RasterArgs a) {
-  __shared__ BwdSmem<BATCH> sm;
+  __shared__ BwdSmem<BATCH, PIX> sm;
   __shared__ uint32_t s_item;
+  if (PIX && threadIdx.x < 12) sm.pose[threadIdx.x] = 0.f;
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1u);
@@ -383,7 +525,7 @@ __global__ void __launch_bounds__(T *T, bwd_min_blocks<T>()) raster_bwd_kernel(R
     const uint32_t item = s_item;
     if (item >= (uint32_t)a.s.total_tiles) break;
     const int64_t gt = a.order[item];
-    bwd_tile<T, BATCH>(a, gt, sm);
+    bwd_tile<T, BATCH, PIX>(a, gt, sm);
     if (a.req_end && threadIdx.x == 0)
       atomicMax(a.req_end + a.s.view[find_view(a.s.view, a.s.V, gt)].req, global_ns());
   }
@@ -444,57 +586,58 @@ int device_sms() {
   return sms[dev];
 }
 
-// Resident blocks per SM of a kernel (cached; the query is not a stream
-// operation, so it is also legal while a stream is being captured).
-template <class Kern>
-int blocks_per_sm(Kern k, int threads) {
+// Resident blocks per SM of a kernel, cached per (device, kernel); the query
+// is not a stream operation, so it is also legal while a stream is captured.
+int blocks_per_sm(void (*k)(RasterArgs), int threads) {
   static std::mutex mu;
-  static int cache[64] = {};
+  static std::map<std::pair<int, const void *>, int> cache;
   int dev = 0;
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lk(mu);
-  if (dev >= 0 && dev < 64 && cache[dev]) return cache[dev];
+  const auto key = std::make_pair(dev, reinterpret_cast<const void *>(k));
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, 0) != cudaSuccess || n < 1) n = 1;
-  if (dev >= 0 && dev < 64) cache[dev] = n;
+  cache[key] = n;
   return n;
 }
 
-template <int T, int BATCH>
+template <int T, int BATCH, bool PIX>
 void launch_fwd_t(const RasterArgs &a, cudaStream_t st) {
   if (a.s.total_tiles <= 0) return;
-  auto k = raster_fwd_kernel<T, BATCH>;
+  auto k = raster_fwd_kernel<T, BATCH, PIX>;
   int64_t grid = (int64_t)blocks_per_sm(k, T * T) * device_sms();
   if (grid > a.s.total_tiles) grid = a.s.total_tiles;
   LaunchScope ls(KID_RASTER_FWD, st);
   k<<<(unsigned)grid, T * T, 0, st>>>(a);
 }
 
-template <int T, int BATCH>
+template <int T, int BATCH, bool PIX>
 void launch_bwd_t(const RasterArgs &a, cudaStream_t st) {
   if (a.s.total_tiles <= 0) return;
-  auto k = raster_bwd_kernel<T, BATCH>;
+  auto k = raster_bwd_kernel<T, BATCH, PIX>;
   int64_t grid = (int64_t)blocks_per_sm(k, T * T) * device_sms();
   if (grid > a.s.total_tiles) grid = a.s.total_tiles;
   LaunchScope ls(KID_RASTER_BWD, st);
   k<<<(unsigned)grid, T * T, 0, st>>>(a);
 }
 
-template <int BATCH>
+template <int BATCH, bool PIX>
 void fwd_dispatch(const RasterArgs &a, int tile, cudaStream_t st) {
   switch (tile) {
-    case 8: launch_fwd_t<8, BATCH>(a, st); break;
-    case 16: launch_fwd_t<16, BATCH>(a, st); break;
-    default: launch_fwd_t<32, BATCH>(a, st); break;
+    case 8: launch_fwd_t<8, BATCH, PIX>(a, st); break;
+    case 16: launch_fwd_t<16, BATCH, PIX>(a, st); break;
+    default: launch_fwd_t<32, BATCH, PIX>(a, st); break;
   }
 }
 
-template <int BATCH>
+template <int BATCH, bool PIX>
 void bwd_dispatch(const RasterArgs &a, int tile, cudaStream_t st) {
   switch (tile) {
-    case 8: launch_bwd_t<8, BATCH>(a, st); break;
-    case 16: launch_bwd_t<16, BATCH>(a, st); break;
-    default: launch_bwd_t<32, BATCH>(a, st); break;
+    case 8: launch_bwd_t<8, BATCH, PIX>(a, st); break;
+    case 16: launch_bwd_t<16, BATCH, PIX>(a, st); break;
+    default: launch_bwd_t<32, BATCH, PIX>(a, st); break;
   }
 }
 
@@ -517,7 +660,8 @@ void launch_tile_order(const RenderShape &s, ddgs_workspace &ws, cudaStream_t st
 }
 
 void launch_raster_fwd(const RenderShape &s, const RasterParams &p, ddgs_workspace &ws,
-                       float *image, float *t_final, uint32_t *n_last, cudaStream_t st) {
+                       float *image, float *t_final, uint32_t *n_last, const PixelRays *pr,
+                       cudaStream_t st) {
   RasterArgs a{};
   a.s = s;
   a.P = p;
@@ -532,14 +676,23 @@ void launch_raster_fwd(const RenderShape &s, const RasterParams &p, ddgs_workspa
   a.counter = ws.queue;
   a.req_end = ws.req_time ? ws.req_time + 1 : nullptr;
   cudaMemsetAsync(ws.queue, 0, sizeof(uint32_t), st);
-  if (ws.batch_depth == 128) fwd_dispatch<128>(a, s.tile, st);
-  else if (ws.batch_depth == 512) fwd_dispatch<512>(a, s.tile, st);
-  else fwd_dispatch<256>(a, s.tile, st);
+  if (pr) {  // per-pixel ray angles: one staging depth
+    a.rec2 = ws.rec2;
+    a.world_to_cam = pr->world_to_cam;
+    a.detector = pr->detector;
+    fwd_dispatch<256, true>(a, s.tile, st);
+  } else if (ws.batch_depth == 128) {
+    fwd_dispatch<128, false>(a, s.tile, st);
+  } else if (ws.batch_depth == 512) {
+    fwd_dispatch<512, false>(a, s.tile, st);
+  } else {
+    fwd_dispatch<256, false>(a, s.tile, st);
+  }
 }
 
 void launch_raster_bwd(const RenderShape &s, const RasterParams &p, ddgs_workspace &ws,
                        const float *dL_dimage, const float *t_final, const uint32_t *n_last,
-                       cudaStream_t st) {
+                       const PixelRays *pr, cudaStream_t st) {
   RasterArgs a{};
   a.s = s;
   a.P = p;
@@ -555,9 +708,20 @@ void launch_raster_bwd(const RenderShape &s, const RasterParams &p, ddgs_workspa
   a.counter = ws.queue + 1;
   a.req_end = ws.req_time ? ws.req_time + 1 + s.R : nullptr;
   cudaMemsetAsync(ws.queue + 1, 0, sizeof(uint32_t), st);
-  if (ws.batch_depth == 128) bwd_dispatch<128>(a, s.tile, st);
-  else if (ws.batch_depth == 512) bwd_dispatch<512>(a, s.tile, st);
-  else bwd_dispatch<256>(a, s.tile, st);
+  if (pr) {  // per-pixel ray angles: one staging depth
+    a.rec2 = ws.rec2;
+    a.grad_h = ws.grad_h;
+    a.world_to_cam = pr->world_to_cam;
+    a.detector = pr->detector;
+    a.pose_grad = pr->pose_grad;
+    bwd_dispatch<256, true>(a, s.tile, st);
+  } else if (ws.batch_depth == 128) {
+    bwd_dispatch<128, false>(a, s.tile, st);
+  } else if (ws.batch_depth == 512) {
+    bwd_dispatch<512, false>(a, s.tile, st);
+  } else {
+    bwd_dispatch<256, false>(a, s.tile, st);
+  }
 }
 
 }  // namespace ddgs

@@ -95,6 +95,8 @@ extern "C" ddgs_status ddgs_render_static(const ddgs_gaussians *g, const ddgs_vi
   if (g->feat_dim < 0 || g->feat_dim > DDGS_MAX_FEAT_DIM || g->sh_degree < 0 ||
       g->sh_degree > DDGS_MAX_SH_DEGREE)
     return DDGS_ERR_INVALID_ARG;
+  // per-pixel ray angles need per-record storage the static scratch does not hold
+  if ((g->entangled != 0 && g->entangled != 1) || g->per_pixel != 0) return DDGS_ERR_INVALID_ARG;
   if (g->n < 0 || g->n_iso < 0 || g->n_iso > g->n || v->n_views < 0 || v->height <= 0 ||
       v->width <= 0 || v->height > 65535 * 8 || v->width > 65535 * 8)
     return DDGS_ERR_INVALID_ARG;
@@ -207,7 +209,7 @@ extern "C" ddgs_status ddgs_render_static(const ddgs_gaussians *g, const ddgs_vi
     ddgs::launch_tile_ranges(s, pairs, ws, cs);
     ddgs::launch_tile_order(s, ws, cs);
     ddgs::RasterParams P{c->alpha_min, c->alpha_max, c->t_min, c->q_max};
-    ddgs::launch_raster_fwd(s, P, ws, image, t_final, n_last, cs);
+    ddgs::launch_raster_fwd(s, P, ws, image, t_final, n_last, nullptr, cs);
   }
   return cudaGetLastError() == cudaSuccess ? DDGS_OK : DDGS_ERR_CUDA;
 }

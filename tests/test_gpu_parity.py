@@ -398,3 +398,47 @@ def test_feature_dimension_and_degree_variants(k, L, bf16, ws):
     gpu["feat"] = np.concatenate([gpu.pop("feat_iso").reshape(-1, k), gpu.pop("feat_dir").reshape(-1, k)])
     gpu["pose"] = gpu.pop("world_to_cam")
     compare_grads(gpu, gr, GRAD_NAMES)
+
+
+@pytest.mark.parametrize("entangled,per_pixel,tile,bf16", [
+    (True, False, 16, False), (False, True, 16, False), (True, True, 16, False),
+    (False, True, 8, False), (True, True, 32, True)])
+def test_radiosity_variants(entangled, per_pixel, tile, bf16, ws):
+    """Eq. 3 variants (direct-entangled terms, Table 3; ray angles per pixel)
+    against the oracle: binning, image and every gradient, the pose included."""
+    scene = syn.uniform_cloud(1500, seed=60 + tile, dir_frac=0.4, dir_std=1.0)
+    scene = dataclasses.replace(scene, entangled=entangled, per_pixel=per_pixel)
+    if bf16:
+        scene.feat[scene.n_iso:] = syn.round_to_bf16(scene.feat[scene.n_iso:])
+    views = _two_views(45, 60, 8.0 / 56)
+    st = syn.Settings(near_plane=0.2, tile=tile)
+    cloud, gv, cfg, img, tf, nl = _run(scene, views, st, ws, bf16=bf16)
+    assert cloud.entangled == entangled and cloud.per_pixel == per_pixel
+    bins = _bins(ws, scene, views, st)
+    compare_binning(bins, oracle.bin32(scene, views, st))
+    ids = last_ids(nl.cpu().numpy().view(np.uint32), bins, views, st.tile)
+    check_image(scene, views, st, img.cpu().numpy(), tf.cpu().numpy(), ids)
+    ref = oracle.render(scene, views, st)
+    w = _masked_weights(ref, 3)
+    g = B.render_backward(cloud, gv, cfg, ws, torch.as_tensor(w, dtype=torch.float32, device="cuda"),
+                          tf, nl)
+    gr = oracle.render_backward(scene, views, st, w)
+    gpu = {n: t.float().cpu().numpy() for n, t in g.items()}
+    gpu["feat"] = np.concatenate([gpu.pop("feat_iso").reshape(-1, 8), gpu.pop("feat_dir").reshape(-1, 8)])
+    gpu["pose"] = gpu.pop("world_to_cam")
+    compare_grads(gpu, gr, GRAD_NAMES)
+
+
+def test_per_pixel_mode_must_match_between_forward_and_backward(ws):
+    scene = syn.uniform_cloud(300, seed=70, dir_frac=0.5)
+    views = _two_views(32, 32, 8.0 / 30)
+    st = syn.Settings(near_plane=0.2)
+    cloud, gv, cfg, img, tf, nl = _run(scene, views, st, ws)
+    other = dataclasses.replace(cloud, per_pixel=True)
+    with pytest.raises(RuntimeError):
+        B.render_backward(other, gv, cfg, ws, torch.ones_like(img), tf, nl)
+    # degree 3 has no per-pixel path
+    sc3 = syn.uniform_cloud(300, seed=71, dir_frac=0.5, sh_degree=3)
+    c3 = dataclasses.replace(B.cloud_from_arrays(sc3), per_pixel=True)
+    with pytest.raises(RuntimeError):
+        B.render(c3, gv, cfg, ws)
