@@ -48,6 +48,12 @@ def shard_seed(rank: int) -> int:
     return 1000 + rank
 
 
+# Eq. 3 variants of the radiosity (Scene fields)
+VARIANTS = {"disentangled": {}, "entangled": {"entangled": True},
+            "per-pixel": {"per_pixel": True},
+            "entangled-per-pixel": {"entangled": True, "per_pixel": True}}
+
+
 def workload(rank: int = 0, n_gauss=N_GAUSS, n_views=N_VIEWS, size=SIZE, grid=GRID):
     from paper_2406_02518_gb300 import synthetic as syn
     scene, views, st = syn.registration_workload(n_gauss, n_views, size, grid, seed=0)
@@ -173,6 +179,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     scene, views, st = workload(0)
+    scene = dataclasses.replace(scene, **VARIANTS[args.variant])
     # The L1 target (the AP view) is rendered by the oracle at each step's
     # sampled pixels, outside the timed part of the step.
     import dataclasses
@@ -266,6 +273,7 @@ def run_ours(args):
         raise RuntimeError("needs an sm_103 (GB300) device")
 
     scene, views, st = workload(rank, size=args.size, n_gauss=args.n_gauss, n_views=args.views)
+    scene = dataclasses.replace(scene, **VARIANTS[args.variant])
     H, W, V = views.height, views.width, views.n_views
     cloud = B.cloud_from_arrays(scene)
     gv = B.views_from_arrays(views)
@@ -298,6 +306,8 @@ def run_ours(args):
         from paper_2406_02518_gb300 import autotune as at
         props = torch.cuda.get_device_properties(dev)
         key = at.workload_key(props.name, props.multi_processor_count, H * W, scene.n, V)
+        if args.variant != "disentangled":
+            key += "|" + args.variant
         tuned = at.tune(tune_step, key, force=args.autotune == "force")
         st = dataclasses.replace(st, tile=tuned["tile"])
     cfg = B.config_from_settings(st, batch_depth=tuned["batch_depth"] if tuned else 256)
@@ -504,7 +514,7 @@ def run_ours(args):
                        "l2": "working set larger than L2 (records 2.6 GB, pairs 1.1 GB per step)",
                        "graph": "batched step replayed from one CUDA graph",
                        "tile": st.tile, "batch_depth": cfg.batch_depth,
-                       "autotune": tuned},
+                       "radiosity": args.variant, "autotune": tuned},
             "plain": {"value": plain_value, "ms_per_step": ms_plain,
                       "how": "64 x (ddgs_render + ddgs_l1_loss + ddgs_render_backward), 1 view each"},
             "batched_over_plain": value / plain_value,
@@ -697,6 +707,9 @@ def main():
                     help="tune (tile, staging depth) before timing (cached per workload class)")
     ap.add_argument("--workload", choices=["registration", "uneven", "registration-loop"],
                     default="registration")
+    ap.add_argument("--variant", choices=sorted(VARIANTS), default="disentangled",
+                    help="Eq. 3 radiosity: the paper's disentangled sets, the direct-entangled "
+                         "ablation (Table 3), or harmonics at each pixel's ray")
     ap.add_argument("--iters", type=int, default=300)
     ap.add_argument("--requests", type=int, default=256)
     args = ap.parse_args()
