@@ -285,6 +285,27 @@ def voxel_centres(ph: Phantom, flat_idx: np.ndarray) -> np.ndarray:
     return (idx + 0.5) * ph.voxel - ph.fov / 2
 
 
+def phantom_volume(ph: Phantom) -> np.ndarray:
+    """The phantom sampled at its voxel centres as a CT volume: int16 HU,
+    [z][y][x] with x fastest (one z slice at a time)."""
+    n = ph.n
+    c = (np.arange(n) + 0.5) * ph.voxel - ph.fov / 2
+    yy, xx = np.meshgrid(c, c, indexing="ij")
+    out = np.empty((n, n, n), np.int16)
+    for iz in range(n):
+        pts = np.stack([xx.ravel(), yy.ravel(), np.full(n * n, c[iz])], 1)
+        out[iz] = np.clip(np.rint(phantom_hu(ph, pts)), -32768, 32767).reshape(n, n)
+    return out
+
+
+def volume_geometry(ph: Phantom):
+    """(spacing, origin) of phantom_volume: voxel size per axis and the world
+    position of voxel (0, 0, 0)'s centre, mm."""
+    v = float(ph.voxel)
+    o = -ph.fov / 2 + 0.5 * v
+    return (v, v, v), (o, o, o)
+
+
 def body_voxels(ph: Phantom) -> np.ndarray:
     """Flat indices of the voxels whose HU exceeds -800 (the body ellipsoid)."""
     n = ph.n
