@@ -255,6 +255,46 @@ ddgs_status ddgs_l1_loss(const float *image, const float *target,
                          int32_t target_per_view, int32_t n_views, int64_t hw,
                          float *loss, float *dL_dimage, void *stream);
 
+/* ---- initialisation: radiodensity-aware dual sampling (RADS, Sec. 3.3) ---- */
+
+/* A CT volume: integer radiodensities (HU) on a regular grid. */
+typedef struct {
+  int32_t nx, ny, nz;   /* voxels along x (fastest), y, z; nx * ny * nz * 3 < 2^32 */
+  const int16_t *hu;    /* device [nz][ny][nx], 16-byte aligned */
+  float spacing[3];     /* voxel size along x, y, z (mm) */
+  float origin[3];      /* world position of voxel (0, 0, 0)'s centre (mm) */
+} ddgs_volume;
+
+/* Initial point cloud of Sec. 3.3, with the sizes of Sec. 4.1 (n1 = 15000,
+ * n2 = 10000):
+ *   P^mc  marching-cubes points at the isolevel (min + max) / 2 of the volume:
+ *         on every grid edge whose end voxels lie on opposite sides of it (a
+ *         voxel is above when 2 HU > min + max), the point at the linear
+ *         interpolation t = (level - HU_0) / (HU_1 - HU_0) along the edge.
+ *         min(n1, crossings) of them are kept uniformly without replacement:
+ *         edge e (= 3 * voxel + axis, voxel = (z ny + y) nx + x, axis 0/1/2 =
+ *         +x/+y/+z neighbour) has the key (splitmix64(seed, e) >> 32) << 32 | e
+ *         and the smallest keys win; kept points are written in edge order.
+ *   P^dw  n2 voxel centres drawn independently with probability proportional
+ *         to HU - min: draw j maps u = splitmix64(~seed, j) to the target
+ *         floor(u * W / 2^64) (W the total weight) and takes the voxel whose
+ *         cumulative-weight interval holds it. No draws if W = 0.
+ * splitmix64(s, i) is output number i + 1 of SplitMix64 (Steele, Lea and
+ * Flood 2014) seeded with s. Scales follow the 3D Gaussian splatting default:
+ * log_s = log sqrt(max(mean squared distance to the 3 nearest other points,
+ * 1e-7)), the same on the three axes.
+ * Outputs (device, caller-owned, at least n1 + n2 rows): means [][3] (P^mc
+ * kept, then P^dw in draw order, packed), log_scales [][3]; optional
+ * kept_edges [n1] and draw_voxels [n2] (int64 edge ids / voxel indices, may
+ * be NULL). counts (host [3]): points of P^mc kept, points of P^dw, crossings
+ * found. The cloud has counts[0] + counts[1] points; Sec. 3.3 makes the first
+ * counts[0] + counts[1] - counts[1] / 2 isotropic and the rest direction-
+ * dependent. Synchronises the stream (to size the crossing list). */
+ddgs_status ddgs_rads(const ddgs_volume *vol, int32_t n1, int32_t n2, uint64_t seed,
+                      ddgs_workspace *ws, float *means, float *log_scales,
+                      int64_t *kept_edges, int64_t *draw_voxels, int64_t *counts,
+                      void *stream);
+
 /* Number of (Gaussian, tile) pairs of the last render, read from the host
  * mirror written by that render (valid after the stream has synchronised). */
 ddgs_status ddgs_workspace_pairs(const ddgs_workspace *ws, int64_t *pairs);

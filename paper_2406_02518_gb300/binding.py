@@ -31,7 +31,7 @@ EXPORTS = ["ddgs_workspace_create", "ddgs_workspace_destroy", "ddgs_workspace_re
            "ddgs_status_string", "ddgs_last_cuda_error", "ddgs_device_supported",
            "ddgs_kernel_launches", "ddgs_profiler_enable", "ddgs_profiler_collect",
            "ddgs_profiler_kernel_name", "ddgs_render_static", "ddgs_render_batched",
-           "ddgs_render_batched_backward", "ddgs_request_times"]
+           "ddgs_render_batched_backward", "ddgs_request_times", "ddgs_rads"]
 
 
 class DDGSError(RuntimeError):
@@ -111,6 +111,7 @@ def load(path: Optional[str] = None):
     lib.ddgs_render_batched.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     lib.ddgs_render_batched_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
     lib.ddgs_request_times.argtypes = [vp, vp, vp, vp]
+    lib.ddgs_rads.argtypes = [vp, i32, i32, C.c_uint64, vp, vp, vp, vp, vp, vp, vp]
     lib.ddgs_kernel_launches.restype = i64
     lib.ddgs_profiler_enable.argtypes = [i32]
     lib.ddgs_profiler_collect.argtypes = [i32, vp, vp, vp]
@@ -547,3 +548,43 @@ def render_batched_backward(batch: Batch, cfg: Config, ws: Workspace, dL_dimage,
                                             _ptr(n_last), C.byref(gs), _stream()),
            "ddgs_render_batched_backward")
     return grads
+
+
+class _Volume(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("hu", C.c_void_p),
+                ("spacing", C.c_float * 3), ("origin", C.c_float * 3)]
+
+
+def rads(hu: torch.Tensor, spacing, origin, n1: int = 15000, n2: int = 10000, seed: int = 0,
+         ws: Optional[Workspace] = None, debug: bool = False) -> dict:
+    """ddgs_rads (Sec. 3.3): the initial cloud of a CT volume hu [nz, ny, nx]
+    (int16 HU, device). Returns means [n, 3], log_scales [n, 3], n_iso and the
+    counts; with debug, also the kept edge ids and drawn voxel indices."""
+    lib = load()
+    assert hu.dtype == torch.int16 and hu.dim() == 3 and hu.is_contiguous()
+    nz, ny, nx = hu.shape
+    dev = hu.device
+    vol = _Volume(nx, ny, nz, _ptr(hu), (C.c_float * 3)(*spacing), (C.c_float * 3)(*origin))
+    n = max(n1 + n2, 1)
+    means = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    log_scales = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    kept = torch.empty(max(n1, 1), dtype=torch.int64, device=dev) if debug else None
+    draws = torch.empty(max(n2, 1), dtype=torch.int64, device=dev) if debug else None
+    counts = (C.c_int64 * 3)()
+    own = ws is None
+    ws = ws or Workspace()
+    try:
+        _check(lib.ddgs_rads(C.byref(vol), n1, n2, C.c_uint64(seed & (2 ** 64 - 1)), ws.handle,
+                             _ptr(means), _ptr(log_scales), _ptr(kept), _ptr(draws),
+                             C.addressof(counts), _stream()), "ddgs_rads")
+    finally:
+        if own:
+            torch.cuda.current_stream().synchronize()
+            ws.close()
+    m1, m2, M = int(counts[0]), int(counts[1]), int(counts[2])
+    out = dict(means=means[:m1 + m2], log_scales=log_scales[:m1 + m2], n_mc=m1, n_dw=m2,
+               n_crossings=M, n_iso=m1 + m2 - m2 // 2)
+    if debug:
+        out["kept_edges"] = kept[:m1]
+        out["draw_voxels"] = draws[:m2]
+    return out

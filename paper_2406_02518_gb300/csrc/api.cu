@@ -25,6 +25,14 @@ ddgs_status cuda_fail(cudaError_t e, const char *what) {
     if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
   } while (0)
 
+}  // namespace
+
+namespace ddgs {
+ddgs_status cuda_status(cudaError_t e, const char *what) { return cuda_fail(e, what); }
+}  // namespace ddgs
+
+namespace {
+
 template <class Tp>
 ddgs_status grow(Tp *&p, int64_t &cap_field, int64_t need, int64_t cur_cap, size_t elem) {
   (void)cap_field;
@@ -250,7 +258,8 @@ std::vector<cudaEvent_t> g_pool;
 const char *const KERNEL_NAMES[ddgs::KID_COUNT] = {
     "preprocess_fwd", "scan_blocks", "emit_keys", "radix_upsweep", "radix_scan",
     "radix_downsweep", "tile_ranges", "raster_fwd", "l1_loss", "raster_bwd",
-    "preprocess_bwd", "debug_copy", "tile_order"};
+    "preprocess_bwd", "debug_copy", "tile_order", "rads_minmax", "rads_count", "rads_scan",
+    "rads_emit", "rads_select", "rads_draw", "rads_knn"};
 
 cudaEvent_t pool_event() {  // caller holds g_prof_mu
   if (!g_pool.empty()) {
@@ -402,7 +411,8 @@ ddgs_status ddgs_workspace_destroy(ddgs_workspace *ws) {
   void *dev[] = {ws->rec0, ws->rec1, ws->rect, ws->tiles_touched, ws->grad2d, ws->blk_total,
                  ws->blk_offset, ws->keys[0], ws->keys[1], ws->vals[0], ws->vals[1], ws->hist,
                  ws->digit_total, ws->ranges, ws->d_pairs, ws->d_status, ws->d_req, ws->d_view,
-                 ws->order, ws->lpt_counts, ws->queue, ws->req_time, ws->rec2, ws->grad_h};
+                 ws->order, ws->lpt_counts, ws->queue, ws->req_time, ws->rec2, ws->grad_h,
+                 ws->rads_keys, ws->rads_buf};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (ws->h_pairs) cudaFreeHost(ws->h_pairs);

@@ -168,6 +168,11 @@ struct ddgs_workspace {
   bool have_render = false;
   uint64_t pair_bound = 0;       // grid bound used for the pair kernels
   int64_t last_hash = 0;         // identifies the batch layout of the last render
+  // initialisation (rads.cu): crossing keys and per-chunk scratch
+  uint64_t *rads_keys = nullptr;
+  int64_t rads_key_cap = 0;
+  unsigned char *rads_buf = nullptr;
+  int64_t rads_buf_cap = 0;
 };
 
 namespace ddgs {
@@ -176,8 +181,12 @@ namespace ddgs {
 enum KernelId : int {
   KID_PREPROCESS_FWD = 0, KID_SCAN_BLOCKS, KID_EMIT_KEYS, KID_RADIX_UPSWEEP, KID_RADIX_SCAN,
   KID_RADIX_DOWNSWEEP, KID_TILE_RANGES, KID_RASTER_FWD, KID_L1_LOSS, KID_RASTER_BWD,
-  KID_PREPROCESS_BWD, KID_DEBUG, KID_TILE_ORDER, KID_COUNT
+  KID_PREPROCESS_BWD, KID_DEBUG, KID_TILE_ORDER, KID_RADS_MINMAX, KID_RADS_COUNT, KID_RADS_SCAN,
+  KID_RADS_EMIT, KID_RADS_SELECT, KID_RADS_DRAW, KID_RADS_KNN, KID_COUNT
 };
+
+// Records a failed CUDA call for ddgs_last_cuda_error and maps it to a status.
+ddgs_status cuda_status(cudaError_t e, const char *what);
 
 // Brackets one kernel launch: counts it and, when profiling, records events.
 struct LaunchScope {

@@ -1,0 +1,587 @@
+// rads.cu -- radiodensity-aware dual sampling (RADS, Sec. 3.3): the initial
+// point cloud of a DDGS model from a CT volume.
+//
+//   P^mc  marching-cubes points of the isolevel (min + max) / 2 (Sec. 4.1):
+//         one point on every grid edge whose two end voxels lie on opposite
+//         sides of it, at the linear interpolation along the edge; n1 of them
+//         kept uniformly without replacement (the n1 smallest counter-based
+//         keys), in edge order.
+//   P^dw  n2 voxel centres drawn with probability proportional to HU - min.
+//   Scales: the 3D Gaussian splatting default, the root mean squared distance
+//         to the 3 nearest other points.
+//
+// Every pass over the volume is a memory-bound sweep: blocks own chunks of
+// 4096 consecutive voxels; a warp walks 512 of them lane-interleaved (voxel
+// base + 32 i + lane), so each load of the voxel and of its +x/+y/+z
+// neighbours is one coalesced 64-byte request, and the per-warp crossing
+// order is the global edge order. The crossing list is sized by one host
+// synchronisation; the n1-th smallest key is found by an 8-pass radix select
+// (8 bits a pass) and the kept crossings are compacted in order.
+#include <algorithm>
+#include <climits>
+
+#include "ddgs_internal.cuh"
+
+namespace ddgs {
+namespace {
+
+constexpr int RT = 256;         // threads per block of the sweeps
+constexpr int RI = 16;          // voxels (keys) per lane
+constexpr int RCH = RT * RI;    // voxels (keys) per block: 4096
+constexpr int KNN_T = 128;      // threads per block of the neighbour search
+
+// Output number i + 1 of SplitMix64 (Steele, Lea and Flood, OOPSLA 2014)
+// seeded with `seed`: the state after i + 1 golden-gamma steps, finalised.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+struct RadsState {
+  int32_t hu_min, hu_max;
+  uint64_t prefix;   // radix select: the wanted key's digits found so far
+  uint64_t rank;     // its rank among the keys sharing that prefix
+  uint32_t hist[256];
+};
+
+struct Vol {
+  const int16_t *hu;
+  int32_t nx, ny, nz;
+  int64_t nvox;
+  float sx, sy, sz, ox, oy, oz;
+};
+
+__device__ __forceinline__ int warp_min(int x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = min(x, __shfl_xor_sync(0xffffffffu, x, o));
+  return x;
+}
+__device__ __forceinline__ int warp_max(int x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(0xffffffffu, x, o));
+  return x;
+}
+template <class Tv>
+__device__ __forceinline__ Tv warp_sum(Tv x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+template <class Tv>
+__device__ __forceinline__ Tv warp_incl_scan(Tv x) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const Tv y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+// ---- pass 1: min and max of the volume ----
+__global__ void __launch_bounds__(RT) rads_minmax_kernel(Vol v, RadsState *st) {
+  int lo = INT_MAX, hi = INT_MIN;
+  const int64_t n8 = v.nvox / 8, stride = (int64_t)gridDim.x * blockDim.x;
+  const uint4 *p = reinterpret_cast<const uint4 *>(v.hu);  // 8 voxels, little-endian
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n8; i += stride) {
+    const uint4 q = p[i];
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int a = (int)(int16_t)(w[k] & 0xffffu), b = (int)(int16_t)(w[k] >> 16);
+      lo = min(lo, min(a, b));
+      hi = max(hi, max(a, b));
+    }
+  }
+  for (int64_t i = n8 * 8 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < v.nvox; i += stride) {
+    const int a = v.hu[i];
+    lo = min(lo, a);
+    hi = max(hi, a);
+  }
+  lo = warp_min(lo);
+  hi = warp_max(hi);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(&st->hu_min, lo);
+    atomicMax(&st->hu_max, hi);
+  }
+}
+
+// Lane-interleaved walk of one warp's 512 voxels: voxel c0 + 32 i + lane.
+struct VoxelWalk {
+  int64_t v;
+  int32_t x, y, z;
+  __device__ __forceinline__ VoxelWalk(const Vol &vol, int64_t first) : v(first) {
+    const int64_t plane = (int64_t)vol.nx * vol.ny;
+    z = (int32_t)(first / plane);
+    const int64_t r = first - (int64_t)z * plane;
+    y = (int32_t)(r / vol.nx);
+    x = (int32_t)(r - (int64_t)y * vol.nx);
+  }
+  __device__ __forceinline__ void advance(const Vol &vol) {
+    v += 32;
+    x += 32;
+    while (x >= vol.nx) {
+      x -= vol.nx;
+      if (++y == vol.ny) { y = 0; ++z; }
+    }
+  }
+};
+
+// Crossing edges (bit a = edge to the +a neighbour) of a voxel inside the
+// volume; a voxel is above the isolevel when 2 HU > lam2 = min + max.
+__device__ __forceinline__ uint32_t crossing_bits(const Vol &vol, const VoxelWalk &w, int lam2,
+                                                  int &hu) {
+  hu = vol.hu[w.v];
+  const bool a = 2 * hu > lam2;
+  uint32_t bits = 0;
+  if (w.x + 1 < vol.nx) bits |= (uint32_t)((2 * (int)vol.hu[w.v + 1] > lam2) != a);
+  if (w.y + 1 < vol.ny) bits |= (uint32_t)((2 * (int)vol.hu[w.v + vol.nx] > lam2) != a) << 1;
+  if (w.z + 1 < vol.nz)
+    bits |= (uint32_t)((2 * (int)vol.hu[w.v + (int64_t)vol.nx * vol.ny] > lam2) != a) << 2;
+  return bits;
+}
+
+// ---- pass 2: crossings and weight per chunk ----
+__global__ void __launch_bounds__(RT) rads_count_kernel(Vol vol, const RadsState *st,
+                                                        uint32_t *cnt, uint64_t *wsum) {
+  __shared__ uint32_t s_c[RT / 32];
+  __shared__ uint64_t s_w[RT / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int mn = st->hu_min, lam2 = st->hu_min + st->hu_max;
+  const int64_t first = (int64_t)blockIdx.x * RCH + wid * (32 * RI) + lane;
+  uint32_t c = 0;
+  uint64_t ws = 0;
+  if (first < vol.nvox) {
+    VoxelWalk w(vol, first);
+    for (int i = 0; i < RI && w.v < vol.nvox; ++i, w.advance(vol)) {
+      int hu;
+      c += __popc(crossing_bits(vol, w, lam2, hu));
+      ws += (uint64_t)(hu - mn);
+    }
+  }
+  c = warp_sum(c);
+  ws = warp_sum(ws);
+  if (lane == 0) { s_c[wid] = c; s_w[wid] = ws; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t tc = 0;
+    uint64_t tw = 0;
+    for (int k = 0; k < RT / 32; ++k) { tc += s_c[k]; tw += s_w[k]; }
+    cnt[blockIdx.x] = tc;
+    wsum[blockIdx.x] = tw;
+  }
+}
+
+// ---- exclusive scan of per-chunk values (one block): out[0..n], out[n] = total ----
+template <class Tin>
+__global__ void __launch_bounds__(1024) rads_scan_kernel(const Tin *in, int64_t n, uint64_t *out) {
+  __shared__ uint64_t s_part[1024];
+  const int t = threadIdx.x;
+  const int64_t per = (n + 1023) / 1024, lo = t * per, hi = min(n, lo + per);
+  uint64_t sum = 0;
+  for (int64_t i = lo; i < hi; ++i) sum += (uint64_t)in[i];
+  s_part[t] = sum;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {  // Hillis-Steele inclusive scan of the parts
+    const uint64_t y = t >= o ? s_part[t - o] : 0;
+    __syncthreads();
+    s_part[t] += y;
+    __syncthreads();
+  }
+  uint64_t run = s_part[t] - sum;
+  for (int64_t i = lo; i < hi; ++i) {
+    out[i] = run;
+    run += (uint64_t)in[i];
+  }
+  if (t == 1023) out[n] = s_part[1023];
+}
+
+__device__ __forceinline__ uint64_t edge_key(uint64_t seed, uint64_t e) {
+  return ((splitmix64(seed, e) >> 32) << 32) | e;
+}
+
+// ---- pass 3: the keys of every crossing, in edge order ----
+__global__ void __launch_bounds__(RT) rads_emit_kernel(Vol vol, const RadsState *st,
+                                                       const uint64_t *coff, uint64_t seed,
+                                                       uint64_t *keys, uint64_t cap) {
+  __shared__ uint32_t s_c[RT / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lam2 = st->hu_min + st->hu_max;
+  const int64_t first = (int64_t)blockIdx.x * RCH + wid * (32 * RI) + lane;
+  uint64_t allbits = 0;  // 3 bits per iteration
+  uint32_t c = 0;
+  if (first < vol.nvox) {
+    VoxelWalk w(vol, first);
+    for (int i = 0; i < RI && w.v < vol.nvox; ++i, w.advance(vol)) {
+      int hu;
+      const uint32_t b = crossing_bits(vol, w, lam2, hu);
+      allbits |= (uint64_t)b << (3 * i);
+      c += __popc(b);
+    }
+  }
+  const uint32_t wc = warp_sum(c);
+  if (lane == 0) s_c[wid] = wc;
+  __syncthreads();
+  uint64_t run = coff[blockIdx.x];
+  for (int k = 0; k < wid; ++k) run += s_c[k];
+  if (wc == 0) return;  // warp-uniform: nothing for this warp to write
+  for (int i = 0; i < RI; ++i) {
+    const uint32_t b = (uint32_t)(allbits >> (3 * i)) & 7u;
+    const uint32_t n = __popc(b);
+    const uint32_t incl = warp_incl_scan(n);
+    uint64_t o = run + (incl - n);
+    const uint64_t v = (uint64_t)first + 32ull * i;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (b & (1u << a)) {
+        if (o < cap) keys[o] = edge_key(seed, 3ull * v + a);
+        ++o;
+      }
+    run += __shfl_sync(0xffffffffu, incl, 31);
+  }
+}
+
+// ---- radix select of the rank-th smallest key, 8 bits a pass from the top ----
+__global__ void rads_select_init_kernel(RadsState *st, uint64_t rank) {
+  if (threadIdx.x == 0) { st->prefix = 0; st->rank = rank; }
+  st->hist[threadIdx.x] = 0;
+}
+
+__global__ void __launch_bounds__(RT) rads_hist_kernel(const uint64_t *keys, int64_t m,
+                                                       RadsState *st, int shift) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const uint64_t mask = shift >= 56 ? 0ull : (~0ull << (shift + 8));
+  const uint64_t prefix = st->prefix;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = keys[i];
+    if ((k & mask) == prefix) atomicAdd(&h[(k >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  if (h[threadIdx.x]) atomicAdd(&st->hist[threadIdx.x], h[threadIdx.x]);
+}
+
+__global__ void rads_pick_kernel(RadsState *st, int shift) {  // one block of 256 threads
+  __shared__ uint32_t s[256];
+  const int d = threadIdx.x;
+  const uint32_t h = st->hist[d];
+  s[d] = h;
+  __syncthreads();
+  for (int o = 1; o < 256; o <<= 1) {
+    const uint32_t y = d >= o ? s[d - o] : 0;
+    __syncthreads();
+    s[d] += y;
+    __syncthreads();
+  }
+  const uint64_t excl = s[d] - h, rank = st->rank;
+  __syncthreads();
+  if (h && excl <= rank && rank < excl + h) {
+    st->prefix |= (uint64_t)d << shift;
+    st->rank = rank - excl;
+  }
+  st->hist[d] = 0;
+}
+
+// ---- compaction of the kept crossings (key <= limit), in edge order ----
+__global__ void __launch_bounds__(RT) rads_keep_count_kernel(const uint64_t *keys, int64_t m,
+                                                             const RadsState *st, int all,
+                                                             uint32_t *cnt) {
+  __shared__ uint32_t s_c[RT / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint64_t limit = all ? ~0ull : st->prefix;
+  const int64_t first = (int64_t)blockIdx.x * RCH + wid * (32 * RI) + lane;
+  uint32_t c = 0;
+  for (int i = 0; i < RI; ++i) {
+    const int64_t j = first + 32 * i;
+    c += (j < m && keys[j] <= limit) ? 1u : 0u;
+  }
+  c = warp_sum(c);
+  if (lane == 0) s_c[wid] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int k = 0; k < RT / 32; ++k) t += s_c[k];
+    cnt[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(RT) rads_keep_emit_kernel(Vol vol, const uint64_t *keys,
+                                                            int64_t m, const RadsState *st,
+                                                            int all, const uint64_t *off,
+                                                            int64_t n_out, float *means,
+                                                            int64_t *kept_edges) {
+  __shared__ uint32_t s_c[RT / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint64_t limit = all ? ~0ull : st->prefix;
+  const int lam2 = st->hu_min + st->hu_max;
+  const int64_t first = (int64_t)blockIdx.x * RCH + wid * (32 * RI) + lane;
+  uint32_t sel = 0;  // bit i: this lane's key of iteration i is kept
+  for (int i = 0; i < RI; ++i) {
+    const int64_t j = first + 32 * i;
+    if (j < m && keys[j] <= limit) sel |= 1u << i;
+  }
+  const uint32_t wc = warp_sum((uint32_t)__popc(sel));
+  if (lane == 0) s_c[wid] = wc;
+  __syncthreads();
+  uint64_t run = off[blockIdx.x];
+  for (int k = 0; k < wid; ++k) run += s_c[k];
+  const uint64_t plane = (uint64_t)vol.nx * vol.ny;
+  for (int i = 0; i < RI; ++i) {
+    const bool kept = (sel >> i) & 1u;
+    const uint32_t bal = __ballot_sync(0xffffffffu, kept);
+    if (kept) {
+      const uint64_t o = run + __popc(bal & ((1u << lane) - 1u));
+      if (o < (uint64_t)n_out) {
+        const uint64_t e = keys[first + 32 * i] & 0xffffffffull;
+        const uint64_t v = e / 3;
+        const int axis = (int)(e - 3 * v);
+        const uint64_t z = v / plane, r = v - z * plane, y = r / vol.nx, x = r - y * vol.nx;
+        const uint64_t step = axis == 0 ? 1ull : (axis == 1 ? (uint64_t)vol.nx : plane);
+        const float f0 = (float)vol.hu[v], f1 = (float)vol.hu[v + step];
+        const float t = (0.5f * (float)lam2 - f0) / (f1 - f0);
+        float c[3] = {(float)x, (float)y, (float)z};
+        c[axis] += t;
+        means[3 * o] = fmaf(vol.sx, c[0], vol.ox);
+        means[3 * o + 1] = fmaf(vol.sy, c[1], vol.oy);
+        means[3 * o + 2] = fmaf(vol.sz, c[2], vol.oz);
+        if (kept_edges) kept_edges[o] = (int64_t)e;
+      }
+    }
+    run += __popc(bal);
+  }
+}
+
+// ---- P^dw: one warp per draw ----
+__global__ void __launch_bounds__(RT) rads_draw_kernel(Vol vol, const RadsState *st,
+                                                       const uint64_t *woff, int64_t nblk,
+                                                       int32_t n2, uint64_t seed, int64_t row0,
+                                                       float *means, int64_t *draw_voxels) {
+  const int lane = threadIdx.x & 31;
+  const int64_t j = (int64_t)blockIdx.x * (RT / 32) + (threadIdx.x >> 5);
+  if (j >= n2) return;
+  const uint64_t total = woff[nblk];
+  const uint64_t target = __umul64hi(splitmix64(~seed, (uint64_t)j), total);
+  // the chunk whose weight interval [woff[c], woff[c+1]) holds the target
+  int64_t lo = 0, hi = nblk;
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (woff[mid] <= target) lo = mid; else hi = mid;
+  }
+  const uint64_t rem = target - woff[lo];
+  const int mn = st->hu_min;
+  uint64_t run = 0;
+  int64_t found = -1;
+  for (int i = 0; i < RCH / 32; ++i) {
+    const int64_t v = lo * RCH + 32 * i + lane;
+    const uint64_t w = v < vol.nvox ? (uint64_t)((int)vol.hu[v] - mn) : 0ull;
+    const uint64_t incl = warp_incl_scan(w);
+    const uint32_t past = __ballot_sync(0xffffffffu, run + incl > rem);
+    if (past) {
+      found = lo * RCH + 32 * i + (__ffs(past) - 1);
+      break;
+    }
+    run += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  if (lane != 0 || found < 0) return;  // found < 0 cannot happen while target < total
+  const uint64_t plane = (uint64_t)vol.nx * vol.ny;
+  const uint64_t z = (uint64_t)found / plane, r = (uint64_t)found - z * plane;
+  const uint64_t y = r / vol.nx, x = r - y * vol.nx;
+  const int64_t o = row0 + j;
+  means[3 * o] = fmaf(vol.sx, (float)x, vol.ox);
+  means[3 * o + 1] = fmaf(vol.sy, (float)y, vol.oy);
+  means[3 * o + 2] = fmaf(vol.sz, (float)z, vol.oz);
+  if (draw_voxels) draw_voxels[j] = found;
+}
+
+// ---- scales: mean squared distance to the 3 nearest other points ----
+__global__ void __launch_bounds__(KNN_T) rads_knn_kernel(const float *means, int64_t n,
+                                                         float *log_scales) {
+  __shared__ float4 s_p[KNN_T];
+  const int64_t i = (int64_t)blockIdx.x * KNN_T + threadIdx.x;
+  float qx = 0.f, qy = 0.f, qz = 0.f;
+  if (i < n) { qx = means[3 * i]; qy = means[3 * i + 1]; qz = means[3 * i + 2]; }
+  const float inf = __int_as_float(0x7f800000);
+  float b0 = inf, b1 = inf, b2 = inf;  // b0 <= b1 <= b2
+  for (int64_t t0 = 0; t0 < n; t0 += KNN_T) {
+    __syncthreads();
+    const int64_t jj = t0 + threadIdx.x;
+    if (jj < n) s_p[threadIdx.x] = make_float4(means[3 * jj], means[3 * jj + 1], means[3 * jj + 2], 0.f);
+    __syncthreads();
+    const int cnt = (int)min((int64_t)KNN_T, n - t0);
+    for (int k = 0; k < cnt; ++k) {
+      const float4 p = s_p[k];
+      const float dx = p.x - qx, dy = p.y - qy, dz = p.z - qz;
+      float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+      if (t0 + k == i) d2 = inf;  // not itself
+      if (d2 < b2) {
+        if (d2 < b1) {
+          b2 = b1;
+          if (d2 < b0) { b1 = b0; b0 = d2; } else { b1 = d2; }
+        } else {
+          b2 = d2;
+        }
+      }
+    }
+  }
+  if (i >= n) return;
+  const int kk = n - 1 < 3 ? (int)(n - 1) : 3;
+  float m = 0.f;
+  if (kk >= 1) m += b0;
+  if (kk >= 2) m += b1;
+  if (kk >= 3) m += b2;
+  m = kk > 0 ? m / (float)kk : 0.f;
+  const float ls = 0.5f * logf(fmaxf(m, 1e-7f));
+  log_scales[3 * i] = ls;
+  log_scales[3 * i + 1] = ls;
+  log_scales[3 * i + 2] = ls;
+}
+
+}  // namespace
+}  // namespace ddgs
+
+#define RCK(call)                                                  \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) return ddgs::cuda_status(e_, #call);    \
+  } while (0)
+
+namespace {
+
+ddgs_status grow_bytes(unsigned char *&p, int64_t &cap, int64_t need) {
+  if (need <= cap && p) return DDGS_OK;
+  if (p) RCK(cudaFree(p));
+  p = nullptr;
+  const int64_t c = need + need / 4 + 4096;
+  RCK(cudaMalloc(reinterpret_cast<void **>(&p), (size_t)c));
+  cap = c;
+  return DDGS_OK;
+}
+
+int64_t align256(int64_t x) { return (x + 255) & ~int64_t(255); }
+
+}  // namespace
+
+extern "C" ddgs_status ddgs_rads(const ddgs_volume *vol, int32_t n1, int32_t n2, uint64_t seed,
+                                 ddgs_workspace *ws, float *means, float *log_scales,
+                                 int64_t *kept_edges, int64_t *draw_voxels, int64_t *counts,
+                                 void *stream) {
+  using namespace ddgs;
+  if (!vol || !ws || !counts || !vol->hu || n1 < 0 || n2 < 0) return DDGS_ERR_INVALID_ARG;
+  if (vol->nx < 1 || vol->ny < 1 || vol->nz < 1) return DDGS_ERR_INVALID_ARG;
+  const int64_t nvox = (int64_t)vol->nx * vol->ny * vol->nz;
+  if (nvox * 3 >= (int64_t(1) << 32)) return DDGS_ERR_INVALID_ARG;  // edge ids fill the key's low word
+  if ((reinterpret_cast<uintptr_t>(vol->hu) & 15u) != 0) return DDGS_ERR_INVALID_ARG;
+  if ((int64_t)n1 + n2 > 0 && (!means || !log_scales)) return DDGS_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Vol v{vol->hu, vol->nx, vol->ny, vol->nz, nvox, vol->spacing[0], vol->spacing[1],
+        vol->spacing[2], vol->origin[0], vol->origin[1], vol->origin[2]};
+  const int64_t nblk = (nvox + RCH - 1) / RCH;
+
+  // scratch: state | cnt u32[nblk] | wsum u64[nblk] | coff u64[nblk+1] | woff u64[nblk+1]
+  const int64_t o_cnt = align256(sizeof(RadsState)), o_ws = o_cnt + align256(4 * nblk),
+                o_coff = o_ws + align256(8 * nblk), o_woff = o_coff + align256(8 * (nblk + 1)),
+                bytes = o_woff + align256(8 * (nblk + 1));
+  ddgs_status s;
+  if ((s = grow_bytes(ws->rads_buf, ws->rads_buf_cap, bytes))) return s;
+  unsigned char *b = ws->rads_buf;
+  RadsState *state = reinterpret_cast<RadsState *>(b);
+  uint32_t *cnt = reinterpret_cast<uint32_t *>(b + o_cnt);
+  uint64_t *wsum = reinterpret_cast<uint64_t *>(b + o_ws);
+  uint64_t *coff = reinterpret_cast<uint64_t *>(b + o_coff);
+  uint64_t *woff = reinterpret_cast<uint64_t *>(b + o_woff);
+
+  RCK(cudaMemsetAsync(&state->hu_min, 0x7f, sizeof(int32_t), st));  // > any int16
+  RCK(cudaMemsetAsync(&state->hu_max, 0x80, sizeof(int32_t), st));  // < any int16
+  {
+    LaunchScope ls(KID_RADS_MINMAX, st);
+    const int64_t want = (nvox / 8 + RT - 1) / RT;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, 152 * 8));
+    rads_minmax_kernel<<<grid, RT, 0, st>>>(v, state);
+  }
+  {
+    LaunchScope ls(KID_RADS_COUNT, st);
+    rads_count_kernel<<<(unsigned)nblk, RT, 0, st>>>(v, state, cnt, wsum);
+  }
+  {
+    LaunchScope ls(KID_RADS_SCAN, st);
+    rads_scan_kernel<uint32_t><<<1, 1024, 0, st>>>(cnt, nblk, coff);
+  }
+  {
+    LaunchScope ls(KID_RADS_SCAN, st);
+    rads_scan_kernel<uint64_t><<<1, 1024, 0, st>>>(wsum, nblk, woff);
+  }
+  RCK(cudaGetLastError());
+  uint64_t tot[2] = {0, 0};
+  RCK(cudaMemcpyAsync(&tot[0], coff + nblk, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+  RCK(cudaMemcpyAsync(&tot[1], woff + nblk, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+  RCK(cudaStreamSynchronize(st));
+  const int64_t M = (int64_t)tot[0];
+  const int64_t m1 = std::min<int64_t>(n1, M), m2 = tot[1] > 0 ? n2 : 0;
+
+  if (m1 > 0) {
+    // keys u64[M] | off u64[nkb+1] | cnt u32[nkb]
+    const int64_t nkb = (M + RCH - 1) / RCH;
+    const int64_t k_off = align256(8 * M), k_cnt = k_off + align256(8 * (nkb + 1)),
+                  kbytes = k_cnt + align256(4 * nkb);
+    unsigned char *kb = reinterpret_cast<unsigned char *>(ws->rads_keys);
+    if ((s = grow_bytes(kb, ws->rads_key_cap, kbytes))) return s;
+    ws->rads_keys = reinterpret_cast<uint64_t *>(kb);
+    uint64_t *keys = ws->rads_keys;
+    uint64_t *koff = reinterpret_cast<uint64_t *>(kb + k_off);
+    uint32_t *kcnt = reinterpret_cast<uint32_t *>(kb + k_cnt);
+    {
+      LaunchScope ls(KID_RADS_EMIT, st);
+      rads_emit_kernel<<<(unsigned)nblk, RT, 0, st>>>(v, state, coff, seed, keys, (uint64_t)M);
+    }
+    const int all = M <= n1 ? 1 : 0;
+    if (!all) {
+      {
+        LaunchScope ls(KID_RADS_SELECT, st);
+        rads_select_init_kernel<<<1, 256, 0, st>>>(state, (uint64_t)(n1 - 1));
+      }
+      const unsigned hg = (unsigned)std::max<int64_t>(1, std::min<int64_t>((M + RT - 1) / RT, 152 * 4));
+      for (int shift = 56; shift >= 0; shift -= 8) {
+        {
+          LaunchScope ls(KID_RADS_SELECT, st);
+          rads_hist_kernel<<<hg, RT, 0, st>>>(keys, M, state, shift);
+        }
+        LaunchScope ls(KID_RADS_SELECT, st);
+        rads_pick_kernel<<<1, 256, 0, st>>>(state, shift);
+      }
+    }
+    {
+      LaunchScope ls(KID_RADS_SELECT, st);
+      rads_keep_count_kernel<<<(unsigned)nkb, RT, 0, st>>>(keys, M, state, all, kcnt);
+    }
+    {
+      LaunchScope ls(KID_RADS_SELECT, st);
+      rads_scan_kernel<uint32_t><<<1, 1024, 0, st>>>(kcnt, nkb, koff);
+    }
+    {
+      LaunchScope ls(KID_RADS_SELECT, st);
+      rads_keep_emit_kernel<<<(unsigned)nkb, RT, 0, st>>>(v, keys, M, state, all, koff, m1, means,
+                                                          kept_edges);
+    }
+    RCK(cudaGetLastError());
+  }
+  if (m2 > 0) {
+    LaunchScope ls(KID_RADS_DRAW, st);
+    rads_draw_kernel<<<(unsigned)((m2 + RT / 32 - 1) / (RT / 32)), RT, 0, st>>>(
+        v, state, woff, nblk, (int32_t)m2, seed, m1, means, draw_voxels);
+    RCK(cudaGetLastError());
+  }
+  const int64_t n = m1 + m2;
+  if (n > 0) {
+    LaunchScope ls(KID_RADS_KNN, st);
+    rads_knn_kernel<<<(unsigned)((n + KNN_T - 1) / KNN_T), KNN_T, 0, st>>>(means, n, log_scales);
+    RCK(cudaGetLastError());
+  }
+  counts[0] = m1;
+  counts[1] = m2;
+  counts[2] = M;
+  return DDGS_OK;
+}

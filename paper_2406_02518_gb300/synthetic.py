@@ -258,22 +258,26 @@ def make_phantom(n: int, seed: int = 0, fov: float = 256.0,
     return Phantom(n, fov / n, structs, tuple(body), float(rng.uniform(0, 80)))
 
 
+def _apply_structure(hu: np.ndarray, pts: np.ndarray, inside: np.ndarray, st) -> np.ndarray:
+    kind, c, axes, R, val, wall = st
+    loc = (pts - c) @ R  # coordinates in the structure frame
+    r2 = np.sum((loc / axes) ** 2, axis=1)
+    if kind == "bone":
+        inner = np.maximum(axes - wall, 1.0)
+        m = (r2 <= 1.0) & (np.sum((loc / inner) ** 2, axis=1) > 1.0) & inside
+        return np.where(m, val, hu)
+    if kind == "organ":
+        return np.where((r2 <= 1.0) & inside, val, hu)
+    return np.where((r2 <= 1.0) & inside, hu + val, hu)  # lesion: additive over its host
+
+
 def phantom_hu(ph: Phantom, pts: np.ndarray) -> np.ndarray:
     """HU at world points pts [M,3] (mm, isocenter at the origin)."""
     body = np.array(ph.body_axes)
     inside = np.sum((pts / body) ** 2, axis=1) <= 1.0
     hu = np.where(inside, ph.body_hu, -1000.0)
-    for kind, c, axes, R, val, wall in ph.structures:
-        loc = (pts - c) @ R  # coordinates in the structure frame
-        r2 = np.sum((loc / axes) ** 2, axis=1)
-        if kind == "bone":
-            inner = np.maximum(axes - wall, 1.0)
-            m = (r2 <= 1.0) & (np.sum((loc / inner) ** 2, axis=1) > 1.0) & inside
-            hu = np.where(m, val, hu)
-        elif kind == "organ":
-            hu = np.where((r2 <= 1.0) & inside, val, hu)
-        else:  # lesion: additive over its host
-            hu = np.where((r2 <= 1.0) & inside, hu + val, hu)
+    for st in ph.structures:
+        hu = _apply_structure(hu, pts, inside, st)
     return hu
 
 
@@ -287,14 +291,26 @@ def voxel_centres(ph: Phantom, flat_idx: np.ndarray) -> np.ndarray:
 
 def phantom_volume(ph: Phantom) -> np.ndarray:
     """The phantom sampled at its voxel centres as a CT volume: int16 HU,
-    [z][y][x] with x fastest (one z slice at a time)."""
+    [z][y][x] with x fastest. Same values as phantom_hu at the centres; each
+    structure is evaluated only on the points of a box around its bounding
+    sphere (it cannot change any other point)."""
     n = ph.n
     c = (np.arange(n) + 0.5) * ph.voxel - ph.fov / 2
     yy, xx = np.meshgrid(c, c, indexing="ij")
+    body = np.array(ph.body_axes)
     out = np.empty((n, n, n), np.int16)
     for iz in range(n):
         pts = np.stack([xx.ravel(), yy.ravel(), np.full(n * n, c[iz])], 1)
-        out[iz] = np.clip(np.rint(phantom_hu(ph, pts)), -32768, 32767).reshape(n, n)
+        inside = np.sum((pts / body) ** 2, axis=1) <= 1.0
+        hu = np.where(inside, ph.body_hu, -1000.0)
+        for st in ph.structures:
+            ctr, r = st[1], float(np.max(st[2])) * 1.001 + ph.voxel
+            if abs(c[iz] - ctr[2]) > r:
+                continue
+            sel = np.flatnonzero((np.abs(pts[:, 0] - ctr[0]) <= r) & (np.abs(pts[:, 1] - ctr[1]) <= r))
+            if sel.size:
+                hu[sel] = _apply_structure(hu[sel], pts[sel], inside[sel], st)
+        out[iz] = np.clip(np.rint(hu), -32768, 32767).reshape(n, n)
     return out
 
 

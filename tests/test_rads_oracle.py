@@ -210,3 +210,13 @@ def test_rads_on_the_phantom():
     # P^dw points are centres of voxels denser than the minimum
     assert np.all(hu.reshape(-1)[r["draw_voxels"]] > hu.min())
     assert np.all(np.isfinite(r["log_scales"]))
+
+
+def test_phantom_volume_equals_the_phantom_at_voxel_centres():
+    n = 48
+    ph = syn.make_phantom(n, seed=2, lesions=10)
+    v = syn.phantom_volume(ph)
+    c = (np.arange(n) + 0.5) * ph.voxel - ph.fov / 2
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    ref = syn.phantom_hu(ph, np.stack([x.ravel(), y.ravel(), z.ravel()], 1))
+    assert np.array_equal(v, np.rint(ref).reshape(n, n, n).astype(np.int16))
