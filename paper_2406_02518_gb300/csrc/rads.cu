@@ -28,7 +28,10 @@ namespace {
 constexpr int RT = 256;         // threads per block of the sweeps
 constexpr int RI = 16;          // voxels (keys) per lane
 constexpr int RCH = RT * RI;    // voxels (keys) per block: 4096
+constexpr int SUB = 32 * RI;    // voxels per warp (sub-chunk): 512
+constexpr int NSUB = RT / 32;   // sub-chunks per chunk
 constexpr int KNN_T = 128;      // threads per block of the neighbour search
+constexpr int SEL_BINS = 2048;  // radix select: 11-bit digits
 
 // Output number i + 1 of SplitMix64 (Steele, Lea and Flood, OOPSLA 2014)
 // seeded with `seed`: the state after i + 1 golden-gamma steps, finalised.
@@ -43,7 +46,8 @@ struct RadsState {
   int32_t hu_min, hu_max;
   uint64_t prefix;   // radix select: the wanted key's digits found so far
   uint64_t rank;     // its rank among the keys sharing that prefix
-  uint32_t hist[256];
+  uint32_t done;     // blocks finished in the current select pass
+  uint32_t hist[SEL_BINS];
 };
 
 struct Vol {
@@ -143,18 +147,76 @@ __device__ __forceinline__ uint32_t crossing_bits(const Vol &vol, const VoxelWal
   return bits;
 }
 
-// ---- pass 2: crossings and weight per chunk ----
+// 8 consecutive voxels of one row (rows are a multiple of 8 voxels on the
+// vector path): int16 values from one 16-byte load, little-endian.
+__device__ __forceinline__ void unpack8(const uint4 q, int h[8]) {
+  const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    h[2 * k] = (int)(int16_t)(w[k] & 0xffffu);
+    h[2 * k + 1] = (int)(int16_t)(w[k] >> 16);
+  }
+}
+
+__device__ __forceinline__ uint32_t above_mask(const int h[8], int lam2) {
+  uint32_t m = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) m |= (uint32_t)(2 * h[j] > lam2) << j;
+  return m;
+}
+
+// Crossing bits of voxels v0 .. v0 + 7 (v0 a multiple of 8, nx a multiple of
+// 8): bit 3 j + a for voxel j and axis a, so that the edge id is 3 v0 + bit.
+// Adds the group's weights (HU - min) to wsum.
+__device__ __forceinline__ uint32_t group_bits(const Vol &vol, int64_t v0, int lam2, int mn,
+                                               uint64_t &wsum) {
+  const int64_t plane = (int64_t)vol.nx * vol.ny;
+  const int64_t z = v0 / plane, r = v0 - z * plane, y = r / vol.nx, x0 = r - y * vol.nx;
+  const uint4 *p = reinterpret_cast<const uint4 *>(vol.hu);
+  int h[8];
+  unpack8(p[v0 >> 3], h);
+  uint32_t ws = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) ws += (uint32_t)(h[j] - mn);
+  wsum += ws;
+  const uint32_t ab = above_mask(h, lam2);
+  uint32_t bx = (ab ^ (ab >> 1)) & 0x7fu, by = 0, bz = 0;
+  if (x0 + 8 < vol.nx) bx |= ((ab >> 7) ^ (uint32_t)(2 * (int)vol.hu[v0 + 8] > lam2)) << 7;
+  int hn[8];
+  if (y + 1 < vol.ny) {
+    unpack8(p[(v0 + vol.nx) >> 3], hn);
+    by = ab ^ above_mask(hn, lam2);
+  }
+  if (z + 1 < vol.nz) {
+    unpack8(p[(v0 + plane) >> 3], hn);
+    bz = ab ^ above_mask(hn, lam2);
+  }
+  uint32_t bits = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    bits |= (((bx >> j) & 1u) << (3 * j)) | (((by >> j) & 1u) << (3 * j + 1)) |
+            (((bz >> j) & 1u) << (3 * j + 2));
+  return bits;
+}
+
+// ---- pass 2: crossings per chunk and weight per warp sub-chunk (512 voxels) ----
+template <bool VEC>
 __global__ void __launch_bounds__(RT) rads_count_kernel(Vol vol, const RadsState *st,
-                                                        uint32_t *cnt, uint64_t *wsum) {
+                                                        uint32_t *cnt, uint64_t *wsub) {
   __shared__ uint32_t s_c[RT / 32];
-  __shared__ uint64_t s_w[RT / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int mn = st->hu_min, lam2 = st->hu_min + st->hu_max;
-  const int64_t first = (int64_t)blockIdx.x * RCH + wid * (32 * RI) + lane;
+  const int64_t sub0 = (int64_t)blockIdx.x * RCH + wid * SUB;
   uint32_t c = 0;
   uint64_t ws = 0;
-  if (first < vol.nvox) {
-    VoxelWalk w(vol, first);
+  if (VEC) {
+#pragma unroll
+    for (int i = 0; i < SUB / 256; ++i) {
+      const int64_t v0 = sub0 + 256 * i + 8 * lane;
+      if (v0 < vol.nvox) c += __popc(group_bits(vol, v0, lam2, mn, ws));
+    }
+  } else if (sub0 + lane < vol.nvox) {
+    VoxelWalk w(vol, sub0 + lane);
     for (int i = 0; i < RI && w.v < vol.nvox; ++i, w.advance(vol)) {
       int hu;
       c += __popc(crossing_bits(vol, w, lam2, hu));
@@ -163,39 +225,45 @@ __global__ void __launch_bounds__(RT) rads_count_kernel(Vol vol, const RadsState
   }
   c = warp_sum(c);
   ws = warp_sum(ws);
-  if (lane == 0) { s_c[wid] = c; s_w[wid] = ws; }
+  if (lane == 0) {
+    s_c[wid] = c;
+    wsub[(int64_t)blockIdx.x * NSUB + wid] = ws;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     uint32_t tc = 0;
-    uint64_t tw = 0;
-    for (int k = 0; k < RT / 32; ++k) { tc += s_c[k]; tw += s_w[k]; }
+    for (int k = 0; k < RT / 32; ++k) tc += s_c[k];
     cnt[blockIdx.x] = tc;
-    wsum[blockIdx.x] = tw;
   }
 }
 
-// ---- exclusive scan of per-chunk values (one block): out[0..n], out[n] = total ----
-template <class Tin>
+// ---- exclusive scan (one block, coalesced 1024-entry tiles): out[0..n],
+// out[n] = total; entry i is the sum of in[G i .. G i + G) ----
+template <class Tin, int G>
 __global__ void __launch_bounds__(1024) rads_scan_kernel(const Tin *in, int64_t n, uint64_t *out) {
-  __shared__ uint64_t s_part[1024];
-  const int t = threadIdx.x;
-  const int64_t per = (n + 1023) / 1024, lo = t * per, hi = min(n, lo + per);
-  uint64_t sum = 0;
-  for (int64_t i = lo; i < hi; ++i) sum += (uint64_t)in[i];
-  s_part[t] = sum;
+  __shared__ uint64_t s_w[32];
+  __shared__ uint64_t s_carry;
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  if (t == 0) s_carry = 0;
   __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {  // Hillis-Steele inclusive scan of the parts
-    const uint64_t y = t >= o ? s_part[t - o] : 0;
+  for (int64_t base = 0; base < n; base += 1024) {
+    const int64_t i = base + t;
+    uint64_t x = 0;
+    if (i < n)
+#pragma unroll
+      for (int k = 0; k < G; ++k) x += (uint64_t)in[i * G + k];
+    const uint64_t inc = warp_incl_scan(x);
+    if (lane == 31) s_w[wid] = inc;
     __syncthreads();
-    s_part[t] += y;
+    if (wid == 0) s_w[lane] = warp_incl_scan(s_w[lane]);
+    __syncthreads();
+    const uint64_t carry = s_carry;
+    if (i < n) out[i] = carry + (wid ? s_w[wid - 1] : 0ull) + inc - x;
+    __syncthreads();
+    if (t == 0) s_carry = carry + s_w[31];
     __syncthreads();
   }
-  uint64_t run = s_part[t] - sum;
-  for (int64_t i = lo; i < hi; ++i) {
-    out[i] = run;
-    run += (uint64_t)in[i];
-  }
-  if (t == 1023) out[n] = s_part[1023];
+  if (t == 0) out[n] = s_carry;
 }
 
 __device__ __forceinline__ uint64_t edge_key(uint64_t seed, uint64_t e) {
@@ -203,87 +271,132 @@ __device__ __forceinline__ uint64_t edge_key(uint64_t seed, uint64_t e) {
 }
 
 // ---- pass 3: the keys of every crossing, in edge order ----
+template <bool VEC>
 __global__ void __launch_bounds__(RT) rads_emit_kernel(Vol vol, const RadsState *st,
                                                        const uint64_t *coff, uint64_t seed,
                                                        uint64_t *keys, uint64_t cap) {
   __shared__ uint32_t s_c[RT / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int lam2 = st->hu_min + st->hu_max;
-  const int64_t first = (int64_t)blockIdx.x * RCH + wid * (32 * RI) + lane;
-  uint64_t allbits = 0;  // 3 bits per iteration
+  const int mn = st->hu_min, lam2 = st->hu_min + st->hu_max;
+  const int64_t sub0 = (int64_t)blockIdx.x * RCH + wid * SUB;
+  constexpr int NIT = VEC ? SUB / 256 : RI;
+  constexpr int BPI = VEC ? 24 : 3;  // crossing bits per lane and iteration
+  uint32_t bits[NIT];
   uint32_t c = 0;
-  if (first < vol.nvox) {
-    VoxelWalk w(vol, first);
-    for (int i = 0; i < RI && w.v < vol.nvox; ++i, w.advance(vol)) {
-      int hu;
-      const uint32_t b = crossing_bits(vol, w, lam2, hu);
-      allbits |= (uint64_t)b << (3 * i);
-      c += __popc(b);
+  uint64_t ws = 0;
+#pragma unroll
+  for (int i = 0; i < NIT; ++i) bits[i] = 0;
+  if (VEC) {
+#pragma unroll
+    for (int i = 0; i < NIT; ++i) {
+      const int64_t v0 = sub0 + 256 * i + 8 * lane;
+      if (v0 < vol.nvox) {
+        bits[i] = group_bits(vol, v0, lam2, mn, ws);
+        c += __popc(bits[i]);
+      }
+    }
+  } else if (sub0 + lane < vol.nvox) {
+    VoxelWalk w(vol, sub0 + lane);
+#pragma unroll
+    for (int i = 0; i < NIT; ++i) {
+      if (w.v < vol.nvox) {
+        int hu;
+        bits[i] = crossing_bits(vol, w, lam2, hu);
+        c += __popc(bits[i]);
+        w.advance(vol);
+      }
     }
   }
+  (void)BPI;
   const uint32_t wc = warp_sum(c);
   if (lane == 0) s_c[wid] = wc;
   __syncthreads();
   uint64_t run = coff[blockIdx.x];
   for (int k = 0; k < wid; ++k) run += s_c[k];
   if (wc == 0) return;  // warp-uniform: nothing for this warp to write
-  for (int i = 0; i < RI; ++i) {
-    const uint32_t b = (uint32_t)(allbits >> (3 * i)) & 7u;
-    const uint32_t n = __popc(b);
+#pragma unroll
+  for (int i = 0; i < NIT; ++i) {
+    const uint32_t n = __popc(bits[i]);
     const uint32_t incl = warp_incl_scan(n);
     uint64_t o = run + (incl - n);
-    const uint64_t v = (uint64_t)first + 32ull * i;
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-      if (b & (1u << a)) {
-        if (o < cap) keys[o] = edge_key(seed, 3ull * v + a);
-        ++o;
-      }
+    // first edge id of this lane's voxels in iteration i: 3 v0 (+ bit index)
+    const uint64_t e0 = VEC ? 3ull * (uint64_t)(sub0 + 256 * i + 8 * lane)
+                            : 3ull * (uint64_t)(sub0 + 32 * i + lane);
+    uint32_t b = bits[i];
+    while (b) {
+      const int k = __ffs(b) - 1;
+      b &= b - 1;
+      if (o < cap) keys[o] = edge_key(seed, e0 + (uint64_t)k);
+      ++o;
+    }
     run += __shfl_sync(0xffffffffu, incl, 31);
   }
 }
 
-// ---- radix select of the rank-th smallest key, 8 bits a pass from the top ----
+// ---- radix select of the rank-th smallest key: 11-bit digits from the top;
+// the last block of each pass picks the digit ----
 __global__ void rads_select_init_kernel(RadsState *st, uint64_t rank) {
-  if (threadIdx.x == 0) { st->prefix = 0; st->rank = rank; }
-  st->hist[threadIdx.x] = 0;
+  if (threadIdx.x == 0) {
+    st->prefix = 0;
+    st->rank = rank;
+    st->done = 0;
+  }
+  for (int k = threadIdx.x; k < SEL_BINS; k += blockDim.x) st->hist[k] = 0;
 }
 
-__global__ void __launch_bounds__(RT) rads_hist_kernel(const uint64_t *keys, int64_t m,
-                                                       RadsState *st, int shift) {
-  __shared__ uint32_t h[256];
-  h[threadIdx.x] = 0;
+__global__ void __launch_bounds__(RT) rads_select_pass_kernel(const uint64_t *keys, int64_t m,
+                                                              RadsState *st, int shift,
+                                                              int width) {
+  __shared__ uint32_t h[SEL_BINS];
+  __shared__ uint32_t s_sum[RT];
+  __shared__ bool s_last;
+  const int t = threadIdx.x;
+  for (int k = t; k < SEL_BINS; k += RT) h[k] = 0;
   __syncthreads();
-  const uint64_t mask = shift >= 56 ? 0ull : (~0ull << (shift + 8));
+  const uint64_t mask = shift + width >= 64 ? 0ull : (~0ull << (shift + width));
   const uint64_t prefix = st->prefix;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  const uint32_t dmask = (1u << width) - 1u;
+  for (int64_t i = (int64_t)blockIdx.x * RT + t; i < m; i += (int64_t)gridDim.x * RT) {
     const uint64_t k = keys[i];
-    if ((k & mask) == prefix) atomicAdd(&h[(k >> shift) & 255u], 1u);
+    if ((k & mask) == prefix) atomicAdd(&h[(uint32_t)(k >> shift) & dmask], 1u);
   }
   __syncthreads();
-  if (h[threadIdx.x]) atomicAdd(&st->hist[threadIdx.x], h[threadIdx.x]);
-}
-
-__global__ void rads_pick_kernel(RadsState *st, int shift) {  // one block of 256 threads
-  __shared__ uint32_t s[256];
-  const int d = threadIdx.x;
-  const uint32_t h = st->hist[d];
-  s[d] = h;
+  for (int k = t; k < SEL_BINS; k += RT)
+    if (h[k]) atomicAdd(&st->hist[k], h[k]);
+  __threadfence();
   __syncthreads();
-  for (int o = 1; o < 256; o <<= 1) {
-    const uint32_t y = d >= o ? s[d - o] : 0;
+  if (t == 0) s_last = atomicAdd(&st->done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // the last block: the digit whose count interval holds the rank
+  constexpr int PER = SEL_BINS / RT;  // 8 bins per thread
+  uint32_t hv[PER], sum = 0;
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    hv[k] = __ldcg(&st->hist[t * PER + k]);
+    sum += hv[k];
+  }
+  s_sum[t] = sum;
+  const uint64_t rank = st->rank;
+  __syncthreads();
+  for (int o = 1; o < RT; o <<= 1) {
+    const uint32_t y = t >= o ? s_sum[t - o] : 0u;
     __syncthreads();
-    s[d] += y;
+    s_sum[t] += y;
     __syncthreads();
   }
-  const uint64_t excl = s[d] - h, rank = st->rank;
-  __syncthreads();
-  if (h && excl <= rank && rank < excl + h) {
-    st->prefix |= (uint64_t)d << shift;
-    st->rank = rank - excl;
+  uint64_t excl = s_sum[t] - sum;
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    if (hv[k] && excl <= rank && rank < excl + hv[k]) {
+      st->prefix = prefix | ((uint64_t)(t * PER + k) << shift);
+      st->rank = rank - excl;
+    }
+    excl += hv[k];
   }
-  st->hist[d] = 0;
+  for (int k = 0; k < PER; ++k) st->hist[t * PER + k] = 0;
+  if (t == 0) st->done = 0;
 }
 
 // ---- compaction of the kept crossings (key <= limit), in edge order ----
@@ -356,13 +469,15 @@ __global__ void __launch_bounds__(RT) rads_keep_emit_kernel(Vol vol, const uint6
 }
 
 // ---- P^dw: one warp per draw ----
+template <bool VEC>
 __global__ void __launch_bounds__(RT) rads_draw_kernel(Vol vol, const RadsState *st,
-                                                       const uint64_t *woff, int64_t nblk,
-                                                       int32_t n2, uint64_t seed, int64_t row0,
-                                                       float *means, int64_t *draw_voxels) {
+                                                       const uint64_t *woff, const uint64_t *wsub,
+                                                       int64_t nblk, int32_t n2, uint64_t seed,
+                                                       int64_t row0, float *means,
+                                                       int64_t *draw_voxels) {
   const int lane = threadIdx.x & 31;
   const int64_t j = (int64_t)blockIdx.x * (RT / 32) + (threadIdx.x >> 5);
-  if (j >= n2) return;
+  if (j >= n2) return;  // warp-uniform
   const uint64_t total = woff[nblk];
   const uint64_t target = __umul64hi(splitmix64(~seed, (uint64_t)j), total);
   // the chunk whose weight interval [woff[c], woff[c+1]) holds the target
@@ -371,20 +486,57 @@ __global__ void __launch_bounds__(RT) rads_draw_kernel(Vol vol, const RadsState 
     const int64_t mid = (lo + hi) >> 1;
     if (woff[mid] <= target) lo = mid; else hi = mid;
   }
-  const uint64_t rem = target - woff[lo];
+  uint64_t rem = target - woff[lo];
+  // then the warp sub-chunk (512 voxels) inside it
+  const uint64_t wsl = lane < NSUB ? wsub[lo * NSUB + lane] : 0ull;
+  const uint64_t winc = warp_incl_scan(wsl);
+  const uint32_t sub_past = __ballot_sync(0xffffffffu, lane < NSUB && winc > rem);
+  const int s = sub_past ? __ffs(sub_past) - 1 : NSUB - 1;
+  rem -= __shfl_sync(0xffffffffu, winc - wsl, s);
+  const int64_t sub0 = lo * RCH + (int64_t)s * SUB;
   const int mn = st->hu_min;
   uint64_t run = 0;
   int64_t found = -1;
-  for (int i = 0; i < RCH / 32; ++i) {
-    const int64_t v = lo * RCH + 32 * i + lane;
-    const uint64_t w = v < vol.nvox ? (uint64_t)((int)vol.hu[v] - mn) : 0ull;
-    const uint64_t incl = warp_incl_scan(w);
-    const uint32_t past = __ballot_sync(0xffffffffu, run + incl > rem);
-    if (past) {
-      found = lo * RCH + 32 * i + (__ffs(past) - 1);
-      break;
+  if (VEC) {
+    const uint4 *p = reinterpret_cast<const uint4 *>(vol.hu);
+    for (int i = 0; i < SUB / 256; ++i) {
+      const int64_t v0 = sub0 + 256 * i + 8 * lane;
+      int h[8];
+      uint64_t wl = 0;
+      if (v0 < vol.nvox) {
+        unpack8(p[v0 >> 3], h);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) wl += (uint64_t)(h[k] - mn);
+      }
+      const uint64_t incl = warp_incl_scan(wl);
+      const uint32_t past = __ballot_sync(0xffffffffu, run + incl > rem);
+      if (past) {
+        const int L = __ffs(past) - 1;
+        int64_t f = -1;
+        if (lane == L) {
+          uint64_t acc = run + incl - wl;
+          for (int k = 0; k < 8; ++k) {
+            acc += (uint64_t)(h[k] - mn);
+            if (acc > rem) { f = v0 + k; break; }
+          }
+        }
+        found = __shfl_sync(0xffffffffu, f, L);
+        break;
+      }
+      run += __shfl_sync(0xffffffffu, incl, 31);
     }
-    run += __shfl_sync(0xffffffffu, incl, 31);
+  } else {
+    for (int i = 0; i < SUB / 32; ++i) {
+      const int64_t v = sub0 + 32 * i + lane;
+      const uint64_t w = v < vol.nvox ? (uint64_t)((int)vol.hu[v] - mn) : 0ull;
+      const uint64_t incl = warp_incl_scan(w);
+      const uint32_t past = __ballot_sync(0xffffffffu, run + incl > rem);
+      if (past) {
+        found = sub0 + 32 * i + (__ffs(past) - 1);
+        break;
+      }
+      run += __shfl_sync(0xffffffffu, incl, 31);
+    }
   }
   if (lane != 0 || found < 0) return;  // found < 0 cannot happen while target < total
   const uint64_t plane = (uint64_t)vol.nx * vol.ny;
@@ -397,26 +549,29 @@ __global__ void __launch_bounds__(RT) rads_draw_kernel(Vol vol, const RadsState 
   if (draw_voxels) draw_voxels[j] = found;
 }
 
-// ---- scales: mean squared distance to the 3 nearest other points ----
-__global__ void __launch_bounds__(KNN_T) rads_knn_kernel(const float *means, int64_t n,
-                                                         float *log_scales) {
+// ---- scales: the 3 nearest other points, candidates split over gridDim.y ----
+__global__ void __launch_bounds__(KNN_T) rads_knn_part_kernel(const float *means, int64_t n,
+                                                              int64_t slice, float *part) {
   __shared__ float4 s_p[KNN_T];
   const int64_t i = (int64_t)blockIdx.x * KNN_T + threadIdx.x;
+  const int64_t c0 = (int64_t)blockIdx.y * slice, c1 = min(n, c0 + slice);
   float qx = 0.f, qy = 0.f, qz = 0.f;
   if (i < n) { qx = means[3 * i]; qy = means[3 * i + 1]; qz = means[3 * i + 2]; }
   const float inf = __int_as_float(0x7f800000);
   float b0 = inf, b1 = inf, b2 = inf;  // b0 <= b1 <= b2
-  for (int64_t t0 = 0; t0 < n; t0 += KNN_T) {
+  for (int64_t t0 = c0; t0 < c1; t0 += KNN_T) {
     __syncthreads();
     const int64_t jj = t0 + threadIdx.x;
-    if (jj < n) s_p[threadIdx.x] = make_float4(means[3 * jj], means[3 * jj + 1], means[3 * jj + 2], 0.f);
+    if (jj < c1) s_p[threadIdx.x] = make_float4(means[3 * jj], means[3 * jj + 1], means[3 * jj + 2], 0.f);
     __syncthreads();
-    const int cnt = (int)min((int64_t)KNN_T, n - t0);
+    const int cnt = (int)min((int64_t)KNN_T, c1 - t0);
+    const int self = (i >= t0 && i < t0 + cnt) ? (int)(i - t0) : -1;
+#pragma unroll 4
     for (int k = 0; k < cnt; ++k) {
       const float4 p = s_p[k];
       const float dx = p.x - qx, dy = p.y - qy, dz = p.z - qz;
       float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-      if (t0 + k == i) d2 = inf;  // not itself
+      if (k == self) d2 = inf;  // not itself
       if (d2 < b2) {
         if (d2 < b1) {
           b2 = b1;
@@ -428,6 +583,31 @@ __global__ void __launch_bounds__(KNN_T) rads_knn_kernel(const float *means, int
     }
   }
   if (i >= n) return;
+  float *o = part + ((int64_t)blockIdx.y * n + i) * 3;
+  o[0] = b0;
+  o[1] = b1;
+  o[2] = b2;
+}
+
+__global__ void rads_knn_merge_kernel(const float *part, int64_t n, int slices, float *log_scales) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float inf = __int_as_float(0x7f800000);
+  float b0 = inf, b1 = inf, b2 = inf;
+  for (int s = 0; s < slices; ++s) {
+    const float *q = part + ((int64_t)s * n + i) * 3;
+    for (int k = 0; k < 3; ++k) {
+      const float d2 = q[k];
+      if (d2 < b2) {
+        if (d2 < b1) {
+          b2 = b1;
+          if (d2 < b0) { b1 = b0; b0 = d2; } else { b1 = d2; }
+        } else {
+          b2 = d2;
+        }
+      }
+    }
+  }
   const int kk = n - 1 < 3 ? (int)(n - 1) : 3;
   float m = 0.f;
   if (kk >= 1) m += b0;
@@ -480,19 +660,27 @@ extern "C" ddgs_status ddgs_rads(const ddgs_volume *vol, int32_t n1, int32_t n2,
   Vol v{vol->hu, vol->nx, vol->ny, vol->nz, nvox, vol->spacing[0], vol->spacing[1],
         vol->spacing[2], vol->origin[0], vol->origin[1], vol->origin[2]};
   const int64_t nblk = (nvox + RCH - 1) / RCH;
+  const bool vec = vol->nx % 8 == 0;  // rows of whole 16-byte vectors
+  const int64_t n_max = (int64_t)n1 + n2;
+  // candidate slices of the neighbour search: enough blocks to fill the GPU
+  const int64_t qblk = (n_max + KNN_T - 1) / KNN_T;
+  const int slices = (int)std::max<int64_t>(1, std::min<int64_t>(32, qblk ? (8 * 152 + qblk - 1) / qblk : 1));
 
-  // scratch: state | cnt u32[nblk] | wsum u64[nblk] | coff u64[nblk+1] | woff u64[nblk+1]
+  // scratch: state | cnt u32[nblk] | wsub u64[8 nblk] | coff u64[nblk+1] |
+  //          woff u64[nblk+1] | knn partial f32[slices][n1+n2][3]
   const int64_t o_cnt = align256(sizeof(RadsState)), o_ws = o_cnt + align256(4 * nblk),
-                o_coff = o_ws + align256(8 * nblk), o_woff = o_coff + align256(8 * (nblk + 1)),
-                bytes = o_woff + align256(8 * (nblk + 1));
+                o_coff = o_ws + align256(8 * NSUB * nblk), o_woff = o_coff + align256(8 * (nblk + 1)),
+                o_knn = o_woff + align256(8 * (nblk + 1)),
+                bytes = o_knn + align256(12 * (int64_t)slices * std::max<int64_t>(n_max, 1));
   ddgs_status s;
   if ((s = grow_bytes(ws->rads_buf, ws->rads_buf_cap, bytes))) return s;
   unsigned char *b = ws->rads_buf;
   RadsState *state = reinterpret_cast<RadsState *>(b);
   uint32_t *cnt = reinterpret_cast<uint32_t *>(b + o_cnt);
-  uint64_t *wsum = reinterpret_cast<uint64_t *>(b + o_ws);
+  uint64_t *wsub = reinterpret_cast<uint64_t *>(b + o_ws);
   uint64_t *coff = reinterpret_cast<uint64_t *>(b + o_coff);
   uint64_t *woff = reinterpret_cast<uint64_t *>(b + o_woff);
+  float *knn_part = reinterpret_cast<float *>(b + o_knn);
 
   RCK(cudaMemsetAsync(&state->hu_min, 0x7f, sizeof(int32_t), st));  // > any int16
   RCK(cudaMemsetAsync(&state->hu_max, 0x80, sizeof(int32_t), st));  // < any int16
@@ -504,15 +692,16 @@ extern "C" ddgs_status ddgs_rads(const ddgs_volume *vol, int32_t n1, int32_t n2,
   }
   {
     LaunchScope ls(KID_RADS_COUNT, st);
-    rads_count_kernel<<<(unsigned)nblk, RT, 0, st>>>(v, state, cnt, wsum);
+    if (vec) rads_count_kernel<true><<<(unsigned)nblk, RT, 0, st>>>(v, state, cnt, wsub);
+    else rads_count_kernel<false><<<(unsigned)nblk, RT, 0, st>>>(v, state, cnt, wsub);
   }
   {
     LaunchScope ls(KID_RADS_SCAN, st);
-    rads_scan_kernel<uint32_t><<<1, 1024, 0, st>>>(cnt, nblk, coff);
+    rads_scan_kernel<uint32_t, 1><<<1, 1024, 0, st>>>(cnt, nblk, coff);
   }
   {
     LaunchScope ls(KID_RADS_SCAN, st);
-    rads_scan_kernel<uint64_t><<<1, 1024, 0, st>>>(wsum, nblk, woff);
+    rads_scan_kernel<uint64_t, NSUB><<<1, 1024, 0, st>>>(wsub, nblk, woff);
   }
   RCK(cudaGetLastError());
   uint64_t tot[2] = {0, 0};
@@ -535,22 +724,24 @@ extern "C" ddgs_status ddgs_rads(const ddgs_volume *vol, int32_t n1, int32_t n2,
     uint32_t *kcnt = reinterpret_cast<uint32_t *>(kb + k_cnt);
     {
       LaunchScope ls(KID_RADS_EMIT, st);
-      rads_emit_kernel<<<(unsigned)nblk, RT, 0, st>>>(v, state, coff, seed, keys, (uint64_t)M);
+      if (vec) rads_emit_kernel<true><<<(unsigned)nblk, RT, 0, st>>>(v, state, coff, seed, keys, (uint64_t)M);
+      else rads_emit_kernel<false><<<(unsigned)nblk, RT, 0, st>>>(v, state, coff, seed, keys, (uint64_t)M);
     }
     const int all = M <= n1 ? 1 : 0;
     if (!all) {
       {
         LaunchScope ls(KID_RADS_SELECT, st);
-        rads_select_init_kernel<<<1, 256, 0, st>>>(state, (uint64_t)(n1 - 1));
+        rads_select_init_kernel<<<1, RT, 0, st>>>(state, (uint64_t)(n1 - 1));
       }
-      const unsigned hg = (unsigned)std::max<int64_t>(1, std::min<int64_t>((M + RT - 1) / RT, 152 * 4));
-      for (int shift = 56; shift >= 0; shift -= 8) {
-        {
-          LaunchScope ls(KID_RADS_SELECT, st);
-          rads_hist_kernel<<<hg, RT, 0, st>>>(keys, M, state, shift);
-        }
+      const unsigned hg = (unsigned)std::max<int64_t>(1, std::min<int64_t>((M + RT - 1) / RT, 152 * 2));
+      // digits of 11 bits from the top: shifts 53, 42, 31, 20, 9 and a last 9-bit digit
+      for (int shift = 53; shift >= 0; shift -= 11) {
         LaunchScope ls(KID_RADS_SELECT, st);
-        rads_pick_kernel<<<1, 256, 0, st>>>(state, shift);
+        rads_select_pass_kernel<<<hg, RT, 0, st>>>(keys, M, state, shift, 11);
+      }
+      {
+        LaunchScope ls(KID_RADS_SELECT, st);
+        rads_select_pass_kernel<<<hg, RT, 0, st>>>(keys, M, state, 0, 9);
       }
     }
     {
@@ -559,7 +750,7 @@ extern "C" ddgs_status ddgs_rads(const ddgs_volume *vol, int32_t n1, int32_t n2,
     }
     {
       LaunchScope ls(KID_RADS_SELECT, st);
-      rads_scan_kernel<uint32_t><<<1, 1024, 0, st>>>(kcnt, nkb, koff);
+      rads_scan_kernel<uint32_t, 1><<<1, 1024, 0, st>>>(kcnt, nkb, koff);
     }
     {
       LaunchScope ls(KID_RADS_SELECT, st);
@@ -570,14 +761,27 @@ extern "C" ddgs_status ddgs_rads(const ddgs_volume *vol, int32_t n1, int32_t n2,
   }
   if (m2 > 0) {
     LaunchScope ls(KID_RADS_DRAW, st);
-    rads_draw_kernel<<<(unsigned)((m2 + RT / 32 - 1) / (RT / 32)), RT, 0, st>>>(
-        v, state, woff, nblk, (int32_t)m2, seed, m1, means, draw_voxels);
+    const unsigned g = (unsigned)((m2 + RT / 32 - 1) / (RT / 32));
+    if (vec)
+      rads_draw_kernel<true><<<g, RT, 0, st>>>(v, state, woff, wsub, nblk, (int32_t)m2, seed, m1,
+                                               means, draw_voxels);
+    else
+      rads_draw_kernel<false><<<g, RT, 0, st>>>(v, state, woff, wsub, nblk, (int32_t)m2, seed, m1,
+                                                means, draw_voxels);
     RCK(cudaGetLastError());
   }
   const int64_t n = m1 + m2;
   if (n > 0) {
-    LaunchScope ls(KID_RADS_KNN, st);
-    rads_knn_kernel<<<(unsigned)((n + KNN_T - 1) / KNN_T), KNN_T, 0, st>>>(means, n, log_scales);
+    const int64_t slice = (n + slices - 1) / slices;
+    {
+      LaunchScope ls(KID_RADS_KNN, st);
+      rads_knn_part_kernel<<<dim3((unsigned)((n + KNN_T - 1) / KNN_T), (unsigned)slices), KNN_T, 0, st>>>(
+          means, n, slice, knn_part);
+    }
+    {
+      LaunchScope ls(KID_RADS_KNN, st);
+      rads_knn_merge_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(knn_part, n, slices, log_scales);
+    }
     RCK(cudaGetLastError());
   }
   counts[0] = m1;

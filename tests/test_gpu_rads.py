@@ -57,8 +57,11 @@ def _check(hu, spacing, origin, n1, n2, seed, ws, pos_tol=2e-4):
     return g
 
 
-@pytest.mark.parametrize("shape,seed", [((37, 29, 23), 0), ((5, 64, 130), 1), ((17, 3, 41), 2)])
+@pytest.mark.parametrize("shape,seed", [((37, 29, 23), 0), ((5, 64, 130), 1), ((17, 3, 41), 2),
+                                        ((37, 29, 24), 3), ((3, 5, 16), 4), ((2, 1, 8), 5),
+                                        ((9, 70, 136), 6)])
 def test_random_volumes(shape, seed, ws):
+    """Rows of a multiple of 8 voxels take the 16-byte vector sweep; others the scalar one."""
     hu = np.random.default_rng(seed).integers(-1000, 2000, shape).astype(np.int16)
     _check(hu, (0.7, 1.1, 1.3), (-20.0, 5.0, 3.5), 500, 301, seed + 10, ws)
 
