@@ -31,6 +31,7 @@ constexpr int RCH = RT * RI;    // voxels (keys) per block: 4096
 constexpr int SUB = 32 * RI;    // voxels per warp (sub-chunk): 512
 constexpr int NSUB = RT / 32;   // sub-chunks per chunk
 constexpr int KNN_T = 128;      // threads per block of the neighbour search
+constexpr int KNN_Q = 2;        // queries per thread
 constexpr int SEL_BINS = 2048;  // radix select: 11-bit digits
 
 // Output number i + 1 of SplitMix64 (Steele, Lea and Flood, OOPSLA 2014)
@@ -170,8 +171,10 @@ __device__ __forceinline__ uint32_t above_mask(const int h[8], int lam2) {
 // Adds the group's weights (HU - min) to wsum.
 __device__ __forceinline__ uint32_t group_bits(const Vol &vol, int64_t v0, int lam2, int mn,
                                                uint64_t &wsum) {
-  const int64_t plane = (int64_t)vol.nx * vol.ny;
-  const int64_t z = v0 / plane, r = v0 - z * plane, y = r / vol.nx, x0 = r - y * vol.nx;
+  // voxel counts stay below 2^32 (edge ids fit 32 bits): 32-bit division
+  const uint32_t plane = (uint32_t)vol.nx * (uint32_t)vol.ny, vv = (uint32_t)v0;
+  const uint32_t z = vv / plane, r = vv - z * plane, y = r / (uint32_t)vol.nx,
+                 x0 = r - y * (uint32_t)vol.nx;
   const uint4 *p = reinterpret_cast<const uint4 *>(vol.hu);
   int h[8];
   unpack8(p[v0 >> 3], h);
@@ -181,13 +184,13 @@ __device__ __forceinline__ uint32_t group_bits(const Vol &vol, int64_t v0, int l
   wsum += ws;
   const uint32_t ab = above_mask(h, lam2);
   uint32_t bx = (ab ^ (ab >> 1)) & 0x7fu, by = 0, bz = 0;
-  if (x0 + 8 < vol.nx) bx |= ((ab >> 7) ^ (uint32_t)(2 * (int)vol.hu[v0 + 8] > lam2)) << 7;
+  if (x0 + 8 < (uint32_t)vol.nx) bx |= ((ab >> 7) ^ (uint32_t)(2 * (int)vol.hu[v0 + 8] > lam2)) << 7;
   int hn[8];
-  if (y + 1 < vol.ny) {
+  if (y + 1 < (uint32_t)vol.ny) {
     unpack8(p[(v0 + vol.nx) >> 3], hn);
     by = ab ^ above_mask(hn, lam2);
   }
-  if (z + 1 < vol.nz) {
+  if (z + 1 < (uint32_t)vol.nz) {
     unpack8(p[(v0 + plane) >> 3], hn);
     bz = ab ^ above_mask(hn, lam2);
   }
@@ -202,8 +205,10 @@ __device__ __forceinline__ uint32_t group_bits(const Vol &vol, int64_t v0, int l
 // ---- pass 2: crossings per chunk and weight per warp sub-chunk (512 voxels) ----
 template <bool VEC>
 __global__ void __launch_bounds__(RT) rads_count_kernel(Vol vol, const RadsState *st,
-                                                        uint32_t *cnt, uint64_t *wsub) {
+                                                        uint32_t *cnt, uint64_t *wsub,
+                                                        uint64_t *wsum) {
   __shared__ uint32_t s_c[RT / 32];
+  __shared__ uint64_t s_w[RT / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int mn = st->hu_min, lam2 = st->hu_min + st->hu_max;
   const int64_t sub0 = (int64_t)blockIdx.x * RCH + wid * SUB;
@@ -227,43 +232,78 @@ __global__ void __launch_bounds__(RT) rads_count_kernel(Vol vol, const RadsState
   ws = warp_sum(ws);
   if (lane == 0) {
     s_c[wid] = c;
+    s_w[wid] = ws;
     wsub[(int64_t)blockIdx.x * NSUB + wid] = ws;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     uint32_t tc = 0;
-    for (int k = 0; k < RT / 32; ++k) tc += s_c[k];
+    uint64_t tw = 0;
+    for (int k = 0; k < RT / 32; ++k) { tc += s_c[k]; tw += s_w[k]; }
     cnt[blockIdx.x] = tc;
+    wsum[blockIdx.x] = tw;
   }
 }
 
-// ---- exclusive scan (one block, coalesced 1024-entry tiles): out[0..n],
-// out[n] = total; entry i is the sum of in[G i .. G i + G) ----
-template <class Tin, int G>
-__global__ void __launch_bounds__(1024) rads_scan_kernel(const Tin *in, int64_t n, uint64_t *out) {
-  __shared__ uint64_t s_w[32];
-  __shared__ uint64_t s_carry;
-  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-  if (t == 0) s_carry = 0;
+// ---- exclusive scans of per-chunk values over many blocks: a[] (uint32)
+// and optionally b[] (uint64) into ao[0..n], bo[0..n] (ao[n], bo[n] = totals).
+// Local scans of 1024 entries, a one-block scan of their totals, then the add.
+constexpr int SCAN_T = 1024;
+
+__device__ __forceinline__ uint64_t block_excl_scan64(uint64_t x, uint64_t *s_w, uint64_t &total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint64_t inc = warp_incl_scan(x);
   __syncthreads();
-  for (int64_t base = 0; base < n; base += 1024) {
-    const int64_t i = base + t;
-    uint64_t x = 0;
-    if (i < n)
-#pragma unroll
-      for (int k = 0; k < G; ++k) x += (uint64_t)in[i * G + k];
-    const uint64_t inc = warp_incl_scan(x);
-    if (lane == 31) s_w[wid] = inc;
-    __syncthreads();
-    if (wid == 0) s_w[lane] = warp_incl_scan(s_w[lane]);
-    __syncthreads();
-    const uint64_t carry = s_carry;
-    if (i < n) out[i] = carry + (wid ? s_w[wid - 1] : 0ull) + inc - x;
-    __syncthreads();
-    if (t == 0) s_carry = carry + s_w[31];
-    __syncthreads();
+  if (lane == 31) s_w[wid] = inc;
+  __syncthreads();
+  if (wid == 0) s_w[lane] = warp_incl_scan(lane < (int)(blockDim.x >> 5) ? s_w[lane] : 0ull);
+  __syncthreads();
+  total = s_w[(blockDim.x >> 5) - 1];
+  return (wid ? s_w[wid - 1] : 0ull) + inc - x;
+}
+
+__global__ void __launch_bounds__(SCAN_T) rads_scan_local_kernel(const uint32_t *a, const uint64_t *b,
+                                                                 int64_t n, uint64_t *ao, uint64_t *bo,
+                                                                 uint64_t *tops) {
+  __shared__ uint64_t s_w[32];
+  const int64_t i = (int64_t)blockIdx.x * SCAN_T + threadIdx.x;
+  uint64_t ta, tb;
+  const uint64_t ea = block_excl_scan64(i < n ? (uint64_t)a[i] : 0ull, s_w, ta);
+  if (i < n) ao[i] = ea;
+  if (b) {
+    const uint64_t eb = block_excl_scan64(i < n ? b[i] : 0ull, s_w, tb);
+    if (i < n) bo[i] = eb;
   }
-  if (t == 0) out[n] = s_carry;
+  if (threadIdx.x == 0) {
+    tops[2 * blockIdx.x] = ta;
+    tops[2 * blockIdx.x + 1] = b ? tb : 0ull;
+  }
+}
+
+__global__ void __launch_bounds__(SCAN_T) rads_scan_tops_kernel(uint64_t *tops, int64_t nt, int64_t n,
+                                                                uint64_t *ao, uint64_t *bo) {
+  __shared__ uint64_t s_w[32];
+  const int t = threadIdx.x;  // nt <= SCAN_T
+  uint64_t ta, tb;
+  const uint64_t xa = t < nt ? tops[2 * t] : 0ull, xb = t < nt ? tops[2 * t + 1] : 0ull;
+  const uint64_t ea = block_excl_scan64(xa, s_w, ta);
+  const uint64_t eb = block_excl_scan64(xb, s_w, tb);
+  if (t < nt) {
+    tops[2 * t] = ea;
+    tops[2 * t + 1] = eb;
+  }
+  if (t == 0) {
+    ao[n] = ta;
+    if (bo) bo[n] = tb;
+  }
+}
+
+__global__ void __launch_bounds__(SCAN_T) rads_scan_add_kernel(const uint64_t *tops, int64_t n,
+                                                               uint64_t *ao, uint64_t *bo) {
+  const int64_t i = (int64_t)blockIdx.x * SCAN_T + threadIdx.x;
+  if (blockIdx.x == 0 || i >= n) return;
+  ao[i] += tops[2 * blockIdx.x];
+  if (bo) bo[i] += tops[2 * blockIdx.x + 1];
 }
 
 __device__ __forceinline__ uint64_t edge_key(uint64_t seed, uint64_t e) {
@@ -549,70 +589,84 @@ __global__ void __launch_bounds__(RT) rads_draw_kernel(Vol vol, const RadsState 
   if (draw_voxels) draw_voxels[j] = found;
 }
 
-// ---- scales: the 3 nearest other points, candidates split over gridDim.y ----
+// ---- scales: the 3 nearest other points, candidates split over gridDim.y.
+// Each thread serves KNN_Q queries; every list keeps the 4 smallest squared
+// distances, the point itself included (it contributes exactly one 0, the
+// smallest value), so no per-pair self test is needed: the merge drops it. ----
+__device__ __forceinline__ void insert4(float d2, float &b0, float &b1, float &b2, float &b3) {
+  if (d2 < b3) {
+    if (d2 < b2) {
+      b3 = b2;
+      if (d2 < b1) {
+        b2 = b1;
+        if (d2 < b0) { b1 = b0; b0 = d2; } else { b1 = d2; }
+      } else {
+        b2 = d2;
+      }
+    } else {
+      b3 = d2;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(KNN_T) rads_knn_part_kernel(const float *means, int64_t n,
                                                               int64_t slice, float *part) {
   __shared__ float4 s_p[KNN_T];
-  const int64_t i = (int64_t)blockIdx.x * KNN_T + threadIdx.x;
-  const int64_t c0 = (int64_t)blockIdx.y * slice, c1 = min(n, c0 + slice);
-  float qx = 0.f, qy = 0.f, qz = 0.f;
-  if (i < n) { qx = means[3 * i]; qy = means[3 * i + 1]; qz = means[3 * i + 2]; }
   const float inf = __int_as_float(0x7f800000);
-  float b0 = inf, b1 = inf, b2 = inf;  // b0 <= b1 <= b2
+  const int64_t c0 = (int64_t)blockIdx.y * slice, c1 = min(n, c0 + slice);
+  float q[KNN_Q][3], b[KNN_Q][4];
+  int64_t qi[KNN_Q];
+#pragma unroll
+  for (int u = 0; u < KNN_Q; ++u) {
+    qi[u] = (int64_t)blockIdx.x * (KNN_T * KNN_Q) + u * KNN_T + threadIdx.x;
+    const bool ok = qi[u] < n;
+    q[u][0] = ok ? means[3 * qi[u]] : 0.f;
+    q[u][1] = ok ? means[3 * qi[u] + 1] : 0.f;
+    q[u][2] = ok ? means[3 * qi[u] + 2] : 0.f;
+    b[u][0] = b[u][1] = b[u][2] = b[u][3] = inf;
+  }
   for (int64_t t0 = c0; t0 < c1; t0 += KNN_T) {
     __syncthreads();
     const int64_t jj = t0 + threadIdx.x;
     if (jj < c1) s_p[threadIdx.x] = make_float4(means[3 * jj], means[3 * jj + 1], means[3 * jj + 2], 0.f);
     __syncthreads();
     const int cnt = (int)min((int64_t)KNN_T, c1 - t0);
-    const int self = (i >= t0 && i < t0 + cnt) ? (int)(i - t0) : -1;
 #pragma unroll 4
     for (int k = 0; k < cnt; ++k) {
       const float4 p = s_p[k];
-      const float dx = p.x - qx, dy = p.y - qy, dz = p.z - qz;
-      float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-      if (k == self) d2 = inf;  // not itself
-      if (d2 < b2) {
-        if (d2 < b1) {
-          b2 = b1;
-          if (d2 < b0) { b1 = b0; b0 = d2; } else { b1 = d2; }
-        } else {
-          b2 = d2;
-        }
+#pragma unroll
+      for (int u = 0; u < KNN_Q; ++u) {
+        const float dx = p.x - q[u][0], dy = p.y - q[u][1], dz = p.z - q[u][2];
+        insert4(fmaf(dz, dz, fmaf(dy, dy, dx * dx)), b[u][0], b[u][1], b[u][2], b[u][3]);
       }
     }
   }
-  if (i >= n) return;
-  float *o = part + ((int64_t)blockIdx.y * n + i) * 3;
-  o[0] = b0;
-  o[1] = b1;
-  o[2] = b2;
+#pragma unroll
+  for (int u = 0; u < KNN_Q; ++u) {
+    if (qi[u] >= n) continue;
+    float4 *o = reinterpret_cast<float4 *>(part) + (int64_t)blockIdx.y * n + qi[u];
+    *o = make_float4(b[u][0], b[u][1], b[u][2], b[u][3]);
+  }
 }
 
 __global__ void rads_knn_merge_kernel(const float *part, int64_t n, int slices, float *log_scales) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float inf = __int_as_float(0x7f800000);
-  float b0 = inf, b1 = inf, b2 = inf;
+  float b0 = inf, b1 = inf, b2 = inf, b3 = inf;
   for (int s = 0; s < slices; ++s) {
-    const float *q = part + ((int64_t)s * n + i) * 3;
-    for (int k = 0; k < 3; ++k) {
-      const float d2 = q[k];
-      if (d2 < b2) {
-        if (d2 < b1) {
-          b2 = b1;
-          if (d2 < b0) { b1 = b0; b0 = d2; } else { b1 = d2; }
-        } else {
-          b2 = d2;
-        }
-      }
-    }
+    const float4 v = reinterpret_cast<const float4 *>(part)[(int64_t)s * n + i];
+    insert4(v.x, b0, b1, b2, b3);
+    insert4(v.y, b0, b1, b2, b3);
+    insert4(v.z, b0, b1, b2, b3);
+    insert4(v.w, b0, b1, b2, b3);
   }
+  // b0 is the point itself (0); the others are the nearest other points
   const int kk = n - 1 < 3 ? (int)(n - 1) : 3;
   float m = 0.f;
-  if (kk >= 1) m += b0;
-  if (kk >= 2) m += b1;
-  if (kk >= 3) m += b2;
+  if (kk >= 1) m += b1;
+  if (kk >= 2) m += b2;
+  if (kk >= 3) m += b3;
   m = kk > 0 ? m / (float)kk : 0.f;
   const float ls = 0.5f * logf(fmaxf(m, 1e-7f));
   log_scales[3 * i] = ls;
@@ -643,6 +697,26 @@ ddgs_status grow_bytes(unsigned char *&p, int64_t &cap, int64_t need) {
 
 int64_t align256(int64_t x) { return (x + 255) & ~int64_t(255); }
 
+// Exclusive scans of n per-chunk values (a, and b if not null) with totals at
+// [n]; n <= 1024 * 1024.
+void scan_chunks(const uint32_t *a, const uint64_t *b, int64_t n, uint64_t *ao, uint64_t *bo,
+                 uint64_t *tops, cudaStream_t st) {
+  using namespace ddgs;
+  const int64_t nt = (n + SCAN_T - 1) / SCAN_T;
+  {
+    LaunchScope ls(KID_RADS_SCAN, st);
+    rads_scan_local_kernel<<<(unsigned)nt, SCAN_T, 0, st>>>(a, b, n, ao, bo, tops);
+  }
+  {
+    LaunchScope ls(KID_RADS_SCAN, st);
+    rads_scan_tops_kernel<<<1, SCAN_T, 0, st>>>(tops, nt, n, ao, bo);
+  }
+  if (nt > 1) {
+    LaunchScope ls(KID_RADS_SCAN, st);
+    rads_scan_add_kernel<<<(unsigned)nt, SCAN_T, 0, st>>>(tops, n, ao, bo);
+  }
+}
+
 }  // namespace
 
 extern "C" ddgs_status ddgs_rads(const ddgs_volume *vol, int32_t n1, int32_t n2, uint64_t seed,
@@ -663,21 +737,24 @@ extern "C" ddgs_status ddgs_rads(const ddgs_volume *vol, int32_t n1, int32_t n2,
   const bool vec = vol->nx % 8 == 0;  // rows of whole 16-byte vectors
   const int64_t n_max = (int64_t)n1 + n2;
   // candidate slices of the neighbour search: enough blocks to fill the GPU
-  const int64_t qblk = (n_max + KNN_T - 1) / KNN_T;
+  const int64_t qblk = (n_max + KNN_T * KNN_Q - 1) / (KNN_T * KNN_Q);
   const int slices = (int)std::max<int64_t>(1, std::min<int64_t>(32, qblk ? (8 * 152 + qblk - 1) / qblk : 1));
 
-  // scratch: state | cnt u32[nblk] | wsub u64[8 nblk] | coff u64[nblk+1] |
-  //          woff u64[nblk+1] | knn partial f32[slices][n1+n2][3]
+  // scratch: state | cnt u32[nblk] | wsub u64[8 nblk] | wsum u64[nblk] | coff u64[nblk+1] |
+  //          woff u64[nblk+1] | scan tops u64[2][1024] | knn partial f32x4[slices][n1+n2]
   const int64_t o_cnt = align256(sizeof(RadsState)), o_ws = o_cnt + align256(4 * nblk),
-                o_coff = o_ws + align256(8 * NSUB * nblk), o_woff = o_coff + align256(8 * (nblk + 1)),
-                o_knn = o_woff + align256(8 * (nblk + 1)),
-                bytes = o_knn + align256(12 * (int64_t)slices * std::max<int64_t>(n_max, 1));
+                o_wsum = o_ws + align256(8 * NSUB * nblk), o_coff = o_wsum + align256(8 * nblk),
+                o_woff = o_coff + align256(8 * (nblk + 1)), o_tops = o_woff + align256(8 * (nblk + 1)),
+                o_knn = o_tops + align256(16 * SCAN_T),
+                bytes = o_knn + align256(16 * (int64_t)slices * std::max<int64_t>(n_max, 1));
   ddgs_status s;
   if ((s = grow_bytes(ws->rads_buf, ws->rads_buf_cap, bytes))) return s;
   unsigned char *b = ws->rads_buf;
   RadsState *state = reinterpret_cast<RadsState *>(b);
   uint32_t *cnt = reinterpret_cast<uint32_t *>(b + o_cnt);
   uint64_t *wsub = reinterpret_cast<uint64_t *>(b + o_ws);
+  uint64_t *wsum = reinterpret_cast<uint64_t *>(b + o_wsum);
+  uint64_t *tops = reinterpret_cast<uint64_t *>(b + o_tops);
   uint64_t *coff = reinterpret_cast<uint64_t *>(b + o_coff);
   uint64_t *woff = reinterpret_cast<uint64_t *>(b + o_woff);
   float *knn_part = reinterpret_cast<float *>(b + o_knn);
@@ -692,17 +769,10 @@ extern "C" ddgs_status ddgs_rads(const ddgs_volume *vol, int32_t n1, int32_t n2,
   }
   {
     LaunchScope ls(KID_RADS_COUNT, st);
-    if (vec) rads_count_kernel<true><<<(unsigned)nblk, RT, 0, st>>>(v, state, cnt, wsub);
-    else rads_count_kernel<false><<<(unsigned)nblk, RT, 0, st>>>(v, state, cnt, wsub);
+    if (vec) rads_count_kernel<true><<<(unsigned)nblk, RT, 0, st>>>(v, state, cnt, wsub, wsum);
+    else rads_count_kernel<false><<<(unsigned)nblk, RT, 0, st>>>(v, state, cnt, wsub, wsum);
   }
-  {
-    LaunchScope ls(KID_RADS_SCAN, st);
-    rads_scan_kernel<uint32_t, 1><<<1, 1024, 0, st>>>(cnt, nblk, coff);
-  }
-  {
-    LaunchScope ls(KID_RADS_SCAN, st);
-    rads_scan_kernel<uint64_t, NSUB><<<1, 1024, 0, st>>>(wsub, nblk, woff);
-  }
+  scan_chunks(cnt, wsum, nblk, coff, woff, tops, st);
   RCK(cudaGetLastError());
   uint64_t tot[2] = {0, 0};
   RCK(cudaMemcpyAsync(&tot[0], coff + nblk, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
@@ -748,10 +818,7 @@ extern "C" ddgs_status ddgs_rads(const ddgs_volume *vol, int32_t n1, int32_t n2,
       LaunchScope ls(KID_RADS_SELECT, st);
       rads_keep_count_kernel<<<(unsigned)nkb, RT, 0, st>>>(keys, M, state, all, kcnt);
     }
-    {
-      LaunchScope ls(KID_RADS_SELECT, st);
-      rads_scan_kernel<uint32_t, 1><<<1, 1024, 0, st>>>(kcnt, nkb, koff);
-    }
+    scan_chunks(kcnt, nullptr, nkb, koff, nullptr, tops, st);
     {
       LaunchScope ls(KID_RADS_SELECT, st);
       rads_keep_emit_kernel<<<(unsigned)nkb, RT, 0, st>>>(v, keys, M, state, all, koff, m1, means,
@@ -775,8 +842,8 @@ extern "C" ddgs_status ddgs_rads(const ddgs_volume *vol, int32_t n1, int32_t n2,
     const int64_t slice = (n + slices - 1) / slices;
     {
       LaunchScope ls(KID_RADS_KNN, st);
-      rads_knn_part_kernel<<<dim3((unsigned)((n + KNN_T - 1) / KNN_T), (unsigned)slices), KNN_T, 0, st>>>(
-          means, n, slice, knn_part);
+      const unsigned qb = (unsigned)((n + KNN_T * KNN_Q - 1) / (KNN_T * KNN_Q));
+      rads_knn_part_kernel<<<dim3(qb, (unsigned)slices), KNN_T, 0, st>>>(means, n, slice, knn_part);
     }
     {
       LaunchScope ls(KID_RADS_KNN, st);
