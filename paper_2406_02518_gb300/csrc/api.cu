@@ -198,11 +198,10 @@ ddgs_status upload_layout(ddgs_workspace *ws, Layout &L, bool no_sync, cudaStrea
 
 ddgs_status ensure_records(ddgs_workspace *ws, const ddgs::RenderShape &s) {
   const int64_t blk = s.n_blocks;
-  if (s.records > ws->rec_cap || !ws->rec0) {
+  if (s.records > ws->rec_cap || !ws->rec) {
     int64_t cap = s.records + s.records / 4 + 1024;
     ddgs_status st;
-    if ((st = grow(ws->rec0, ws->rec_cap, cap, 0, sizeof(float4)))) return st;
-    if ((st = grow(ws->rec1, ws->rec_cap, cap, 0, sizeof(float4)))) return st;
+    if ((st = grow(ws->rec, ws->rec_cap, 2 * cap, 0, sizeof(float4)))) return st;
     if ((st = grow(ws->rect, ws->rec_cap, cap, 0, sizeof(uint4)))) return st;
     if ((st = grow(ws->grad2d, ws->rec_cap, 2 * cap, 0, sizeof(float4)))) return st;
     ws->rec_cap = cap;
@@ -383,7 +382,6 @@ ddgs_status ddgs_workspace_create(ddgs_workspace **out) {
       (e = cudaMalloc(&ws->d_pairs, sizeof(uint64_t))) != cudaSuccess ||
       (e = cudaMalloc(&ws->d_status, sizeof(int32_t))) != cudaSuccess ||
       (e = cudaMalloc(&ws->digit_total, ddgs::RADIX * sizeof(uint32_t))) != cudaSuccess ||
-      (e = cudaMalloc(&ws->lpt_counts, 128 * sizeof(uint32_t))) != cudaSuccess ||
       (e = cudaMalloc(&ws->queue, 2 * sizeof(uint32_t))) != cudaSuccess ||
       (e = cudaHostAlloc(&ws->h_pairs, sizeof(uint64_t), cudaHostAllocDefault)) != cudaSuccess ||
       (e = cudaMemset(ws->d_status, 0, sizeof(int32_t))) != cudaSuccess ||
@@ -408,10 +406,10 @@ ddgs_status ddgs_workspace_create(ddgs_workspace **out) {
 
 ddgs_status ddgs_workspace_destroy(ddgs_workspace *ws) {
   if (!ws) return DDGS_OK;
-  void *dev[] = {ws->rec0, ws->rec1, ws->rect, ws->tiles_touched, ws->grad2d, ws->blk_total,
+  void *dev[] = {ws->rec, ws->rect, ws->tiles_touched, ws->grad2d, ws->blk_total,
                  ws->blk_offset, ws->keys[0], ws->keys[1], ws->vals[0], ws->vals[1], ws->hist,
                  ws->digit_total, ws->ranges, ws->d_pairs, ws->d_status, ws->d_req, ws->d_view,
-                 ws->order, ws->lpt_counts, ws->queue, ws->req_time, ws->rec2, ws->grad_h,
+                 ws->order, ws->queue, ws->req_time, ws->rec2, ws->grad_h,
                  ws->rads_keys, ws->rads_buf};
   for (void *p : dev)
     if (p) cudaFree(p);

@@ -128,8 +128,8 @@ struct ddgs_workspace {
   int device = -1;
   int64_t rec_cap = 0, pair_cap = 0, tile_cap = 0, blk_cap = 0, sblk_cap = 0;
   // per (view, Gaussian) records
-  float4 *rec0 = nullptr;        // (u, v, conic a, conic b)
-  float4 *rec1 = nullptr;        // (conic c, alpha, colour, depth)
+  float4 *rec = nullptr;         // [records][2]: (u, v, conic a, conic b), (conic c, alpha,
+                                 // colour, depth): one 32-byte sector per gather
   uint2 *rect = nullptr;         // (tx0 | ty0 << 16, tx1 | ty1 << 16)
   uint32_t *tiles_touched = nullptr;
   float4 *grad2d = nullptr;      // [records][2]: (u, v, ca, cb), (cc, alpha, colour, 0);
@@ -150,7 +150,6 @@ struct ddgs_workspace {
   uint32_t *digit_total = nullptr;  // [RADIX]
   uint2 *ranges = nullptr;       // [tiles]
   uint32_t *order = nullptr;     // [tiles] work order of the persistent rasterisers
-  uint32_t *lpt_counts = nullptr;  // bucket counts and cursors of that order
   uint32_t *queue = nullptr;     // work-queue heads of the forward / backward rasterisers
   unsigned long long *req_time = nullptr;  // [1 + 2 R]: batch start, per-request fwd / bwd ends
   int batch_depth = 256;         // list entries staged per round in the rasterisers

@@ -292,7 +292,7 @@ struct PreArgs {
   int K, L;          // feature dimension and harmonic degree
   int entangled;     // every Gaussian carries both terms of Eq. 3
   int per_pixel;     // Y at the pixel rays: write (a, h) to rec2 instead of a colour
-  float4 *rec0, *rec1, *rec2;
+  float4 *rec, *rec2;  // rec: two float4 per record
   uint4 *bin_info;  // (rect lo, rect hi, depth bits, tiles touched)
   uint32_t *blk_total;
   unsigned long long *t0;  // batch start (min over blocks of %globaltimer), or null
@@ -449,8 +449,8 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_fwd_kernel(PreArgs a) 
         }
         colour = sigmoidf_(zl);
       }
-      a.rec0[rec] = make_float4(p.u, p.v, ca, cb);
-      a.rec1[rec] = make_float4(cc, alpha, colour, depth);
+      a.rec[2 * rec] = make_float4(p.u, p.v, ca, cb);
+      a.rec[2 * rec + 1] = make_float4(cc, alpha, colour, depth);
     }
   }
   uint32_t bt = block_sum_u32(total, s_red);
@@ -968,7 +968,7 @@ void launch_preprocess_fwd(const ddgs_gaussians &g, const ddgs_views &v, const d
   a.entangled = g.entangled ? 1 : 0;
   a.per_pixel = g.per_pixel ? 1 : 0;
   a.s = s;
-  a.rec0 = ws.rec0; a.rec1 = ws.rec1; a.rec2 = ws.rec2;
+  a.rec = ws.rec; a.rec2 = ws.rec2;
   a.bin_info = reinterpret_cast<uint4 *>(ws.rect);
   a.blk_total = ws.blk_total;
   a.t0 = ws.req_time;

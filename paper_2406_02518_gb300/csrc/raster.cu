@@ -38,7 +38,7 @@ namespace {
 struct RasterArgs {
   RenderShape s;
   RasterParams P;
-  const float4 *rec0, *rec1;
+  const float4 *rec;  // two float4 per record
   const uint32_t *vals;
   const uint2 *ranges;
   float4 *grad2d;
@@ -179,7 +179,7 @@ __device__ __forceinline__ void fwd_tile(const RasterArgs &a, int64_t gt, float4
         const uint32_t id = a.vals[j];
         if (id < tg.n_req) {
           const int64_t r = rec_base + id;
-          const float4 r0 = a.rec0[r], r1 = a.rec1[r];
+          const float4 r0 = a.rec[2 * r], r1 = a.rec[2 * r + 1];
           s_a[e] = r0;
           s_b[e] = r1;
           s_box[e] = ellipse_box(r0, r1, a.P.q_max);
@@ -373,7 +373,7 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs &a, int64_t gt, BwdSme
         const uint32_t id = a.vals[range.x + (uint32_t)pos_t];
         if (id < tg.n_req) {
           const int64_t r = rec_base + id;
-          const float4 r0 = a.rec0[r], r1 = a.rec1[r];
+          const float4 r0 = a.rec[2 * r], r1 = a.rec[2 * r + 1];
           s_a[e] = r0;
           s_b[e] = r1;
           s_box[e] = ellipse_box(r0, r1, a.P.q_max);
@@ -531,7 +531,10 @@ __global__ void __launch_bounds__(T *T, bwd_min_blocks<T>()) raster_bwd_kernel(R
   }
 }
 
-// ---- work order: tiles by descending list length (bucketed by log2) ----
+// ---- work order: view by view, and within a view the tiles by descending
+// list length (bucketed by log2). At any time the persistent blocks then work
+// on a few views, whose records and gradient accumulators stay in L2 while
+// the longest lists of each view still start first. ----
 
 constexpr int LPT_BUCKETS = 34;  // 0 = empty list, b = 1 + floor(log2(len))
 
@@ -540,36 +543,29 @@ __device__ __forceinline__ int lpt_bucket(uint2 r) {
   return len ? 33 - __clz(len) : 0;  // 1..33
 }
 
-__global__ void tile_bucket_count_kernel(const uint2 *ranges, int64_t n_tiles, uint32_t *counts) {
-  __shared__ uint32_t h[LPT_BUCKETS];
+// One block per view: a counting sort of the view's tiles by bucket, longest
+// bucket first, written to order[tile_base .. tile_base + tiles).
+__global__ void __launch_bounds__(256) tile_order_view_kernel(const ViewTab *view, const uint2 *ranges,
+                                                              uint32_t *order) {
+  __shared__ uint32_t h[LPT_BUCKETS], start[LPT_BUCKETS];
+  const int v = blockIdx.x;
+  const int64_t t0 = view[v].tile_base, nt = view[v + 1].tile_base - t0;
   for (int b = threadIdx.x; b < LPT_BUCKETS; b += blockDim.x) h[b] = 0;
   __syncthreads();
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles;
-       t += (int64_t)gridDim.x * blockDim.x)
-    atomicAdd(&h[lpt_bucket(ranges[t])], 1u);
+  for (int64_t t = threadIdx.x; t < nt; t += blockDim.x) atomicAdd(&h[lpt_bucket(ranges[t0 + t])], 1u);
   __syncthreads();
-  for (int b = threadIdx.x; b < LPT_BUCKETS; b += blockDim.x)
-    if (h[b]) atomicAdd(&counts[b], h[b]);
-}
-
-// counts[0..B) then cursors[0..B): every block derives the bucket starts
-// (longest bucket first) and claims slots with one atomic per tile.
-__global__ void tile_bucket_scatter_kernel(const uint2 *ranges, int64_t n_tiles,
-                                           const uint32_t *counts, uint32_t *cursors,
-                                           uint32_t *order) {
-  __shared__ uint32_t start[LPT_BUCKETS];
   if (threadIdx.x == 0) {
     uint32_t run = 0;
     for (int b = LPT_BUCKETS - 1; b >= 0; --b) {
       start[b] = run;
-      run += counts[b];
+      run += h[b];
+      h[b] = 0;  // reused as the bucket's cursor
     }
   }
   __syncthreads();
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int b = lpt_bucket(ranges[t]);
-    order[start[b] + atomicAdd(&cursors[b], 1u)] = (uint32_t)t;
+  for (int64_t t = threadIdx.x; t < nt; t += blockDim.x) {
+    const int b = lpt_bucket(ranges[t0 + t]);
+    order[t0 + start[b] + atomicAdd(&h[b], 1u)] = (uint32_t)(t0 + t);
   }
 }
 
@@ -644,19 +640,9 @@ void bwd_dispatch(const RasterArgs &a, int tile, cudaStream_t st) {
 }  // namespace
 
 void launch_tile_order(const RenderShape &s, ddgs_workspace &ws, cudaStream_t st) {
-  if (s.total_tiles <= 0) return;
-  cudaMemsetAsync(ws.lpt_counts, 0, 2 * LPT_BUCKETS * sizeof(uint32_t), st);
-  int64_t blocks = (s.total_tiles + 255) / 256;
-  if (blocks > 1024) blocks = 1024;
-  {
-    LaunchScope ls(KID_TILE_ORDER, st);
-    tile_bucket_count_kernel<<<(unsigned)blocks, 256, 0, st>>>(ws.ranges, s.total_tiles, ws.lpt_counts);
-  }
-  {
-    LaunchScope ls(KID_TILE_ORDER, st);
-    tile_bucket_scatter_kernel<<<(unsigned)blocks, 256, 0, st>>>(
-        ws.ranges, s.total_tiles, ws.lpt_counts, ws.lpt_counts + LPT_BUCKETS, ws.order);
-  }
+  if (s.total_tiles <= 0 || s.V <= 0) return;
+  LaunchScope ls(KID_TILE_ORDER, st);
+  tile_order_view_kernel<<<(unsigned)s.V, 256, 0, st>>>(s.view, ws.ranges, ws.order);
 }
 
 void launch_raster_fwd(const RenderShape &s, const RasterParams &p, ddgs_workspace &ws,
@@ -665,8 +651,7 @@ void launch_raster_fwd(const RenderShape &s, const RasterParams &p, ddgs_workspa
   RasterArgs a{};
   a.s = s;
   a.P = p;
-  a.rec0 = ws.rec0;
-  a.rec1 = ws.rec1;
+  a.rec = ws.rec;
   a.vals = ws.vals[ws.sorted];
   a.ranges = ws.ranges;
   a.image = image;
@@ -696,8 +681,7 @@ void launch_raster_bwd(const RenderShape &s, const RasterParams &p, ddgs_workspa
   RasterArgs a{};
   a.s = s;
   a.P = p;
-  a.rec0 = ws.rec0;
-  a.rec1 = ws.rec1;
+  a.rec = ws.rec;
   a.vals = ws.vals[ws.sorted];
   a.ranges = ws.ranges;
   a.grad2d = ws.grad2d;

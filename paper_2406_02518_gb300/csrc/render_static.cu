@@ -34,6 +34,8 @@ constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr size_t kOffRec0 = 0;
 constexpr size_t kOffRec1 = align256(kOffRec0 + kMaxRecords * sizeof(float4));
 constexpr size_t kOffInfo = align256(kOffRec1 + kMaxRecords * sizeof(float4));
+static_assert(kOffRec1 == kOffRec0 + kMaxRecords * sizeof(float4),
+              "the records are one interleaved array over both regions");
 constexpr size_t kOffBlkTotal = align256(kOffInfo + kMaxRecords * sizeof(uint4));
 constexpr size_t kOffBlkOffset = align256(kOffBlkTotal + kMaxBlocks * sizeof(uint32_t));
 constexpr size_t kOffKeys0 = align256(kOffBlkOffset + kMaxBlocks * sizeof(uint64_t));
@@ -46,8 +48,7 @@ constexpr size_t kOffRanges = align256(kOffDigit + ddgs::RADIX * sizeof(uint32_t
 constexpr size_t kOffPairs = align256(kOffRanges + kMaxTiles * sizeof(uint2));
 constexpr size_t kOffStatus = align256(kOffPairs + sizeof(uint64_t));
 constexpr size_t kOffOrder = align256(kOffStatus + sizeof(int32_t));
-constexpr size_t kOffLpt = align256(kOffOrder + kMaxTiles * sizeof(uint32_t));
-constexpr size_t kOffQueue = align256(kOffLpt + 128 * sizeof(uint32_t));
+constexpr size_t kOffQueue = align256(kOffOrder + kMaxTiles * sizeof(uint32_t));
 constexpr size_t kOffReq = align256(kOffQueue + 2 * sizeof(uint32_t));
 constexpr size_t kOffView = align256(kOffReq + 2 * sizeof(ddgs::ReqTab));
 constexpr size_t kScratchBytes = align256(kOffView + (kMaxViews + 1) * sizeof(ddgs::ViewTab));
@@ -156,8 +157,7 @@ extern "C" ddgs_status ddgs_render_static(const ddgs_gaussians *g, const ddgs_vi
   ws.tile_cap = kMaxTiles;
   ws.blk_cap = kMaxBlocks;
   ws.sblk_cap = kMaxSortBlocks;
-  ws.rec0 = reinterpret_cast<float4 *>(base + kOffRec0);
-  ws.rec1 = reinterpret_cast<float4 *>(base + kOffRec1);
+  ws.rec = reinterpret_cast<float4 *>(base + kOffRec0);  // rec0 and rec1 regions, contiguous
   ws.rect = reinterpret_cast<uint2 *>(base + kOffInfo);
   ws.blk_total = reinterpret_cast<uint32_t *>(base + kOffBlkTotal);
   ws.blk_offset = reinterpret_cast<uint64_t *>(base + kOffBlkOffset);
@@ -171,7 +171,6 @@ extern "C" ddgs_status ddgs_render_static(const ddgs_gaussians *g, const ddgs_vi
   ws.d_pairs = reinterpret_cast<uint64_t *>(base + kOffPairs);
   ws.d_status = reinterpret_cast<int32_t *>(base + kOffStatus);
   ws.order = reinterpret_cast<uint32_t *>(base + kOffOrder);
-  ws.lpt_counts = reinterpret_cast<uint32_t *>(base + kOffLpt);
   ws.queue = reinterpret_cast<uint32_t *>(base + kOffQueue);
   ws.req_time = nullptr;
   ws.batch_depth = (c->batch_depth == 128 || c->batch_depth == 512) ? c->batch_depth : 256;
