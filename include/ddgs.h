@@ -105,7 +105,9 @@ typedef struct {
                         capacities come from ddgs_workspace_reserve and an
                         overflow is latched as DDGS_ERR_CAPACITY */
   int32_t batch_depth; /* list entries a rasteriser block stages per round:
-                          128, 256 or 512 (other values = 256) */
+                          128, 256 or 512; 32: every warp streams its own
+                          8 x 4 pixel region's list 32 entries at a time, with
+                          no block-wide staging (other values = 256) */
 } ddgs_config;
 
 /* Gradient outputs of ddgs_render_backward. Every pointer may be NULL (that

@@ -2,7 +2,8 @@
 
 For a given workload the tuner times one full step (the caller's function,
 which renders and back-propagates with the candidate configuration) for every
-(tile, batch_depth) pair and keeps the fastest. Results are cached in a JSON
+(tile, batch_depth) pair and keeps the fastest. Depth 32 selects the
+warp-streamed rasterisers; the others are block-staged depths. Results are cached in a JSON
 file keyed by the GPU (name, SM count) and coarse buckets of the workload
 (largest detector, Gaussians, views), so a workload of the same class reuses
 the choice without re-timing.
@@ -16,7 +17,7 @@ import time
 from typing import Callable, Dict, Iterable, Optional, Tuple
 
 TILES = (8, 16, 32)
-DEPTHS = (128, 256, 512)
+DEPTHS = (32, 128, 256, 512)  # 32: warp-streamed rasterisers (no block staging)
 CANDIDATES = tuple((t, d) for t in TILES for d in DEPTHS)
 
 

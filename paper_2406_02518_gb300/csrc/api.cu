@@ -465,7 +465,8 @@ ddgs_status render_common(const ddgs_gaussians &g, const ddgs_views &v, const dd
   }
   if ((st = upload_layout(ws, L, c->no_sync != 0, s_))) return st;
   ws->have_render = false;
-  ws->batch_depth = (c->batch_depth == 128 || c->batch_depth == 512) ? c->batch_depth : 256;
+  ws->batch_depth = (c->batch_depth == 32 || c->batch_depth == 128 || c->batch_depth == 512)
+                        ? c->batch_depth : 256;
   // timing slots: batch start (min) and per-request ends (max)
   CK(cudaMemsetAsync(ws->req_time, 0xff, sizeof(unsigned long long), s_));
   CK(cudaMemsetAsync(ws->req_time + 1, 0, 2 * (size_t)s.R * sizeof(unsigned long long), s_));

@@ -1,6 +1,7 @@
 // ddgs_internal.cuh -- shared declarations of the sm_103a DRR splatting kernels.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -105,6 +106,24 @@ struct PairEval {
   float dx, dy, tx, ty, G, aG, sigma;
 };
 
+// Half-extents of the q <= q_max ellipse of a 2D covariance, sqrt(q_max
+// Sigma_xx) and sqrt(q_max Sigma_yy), widened by 1e-3 relative + 1e-3 px and
+// rounded up to binary16, packed into the record's fourth float (x in the low
+// half). The rasterisers cull with this box; rounding up keeps it conservative.
+__device__ __forceinline__ float box_halfwidths(const float cov[3], float q_max) {
+  const float ex = sqrtf(q_max * cov[0]) * 1.001f + 1e-3f;
+  const float ey = sqrtf(q_max * cov[2]) * 1.001f + 1e-3f;
+  const uint32_t hx = __half_as_ushort(__float2half_ru(ex));
+  const uint32_t hy = __half_as_ushort(__float2half_ru(ey));
+  return __uint_as_float(hx | (hy << 16));
+}
+
+__device__ __forceinline__ float2 unpack_halfwidths(float w) {
+  const uint32_t b = __float_as_uint(w);
+  return make_float2(__half2float(__ushort_as_half((unsigned short)(b & 0xffffu))),
+                     __half2float(__ushort_as_half((unsigned short)(b >> 16))));
+}
+
 // q = d^T K d computed as d . t with t = K d (t is reused by the gradients).
 __device__ __forceinline__ bool eval_pair(float u, float v, float ca, float cb, float cc,
                                           float alpha, float px, float py,
@@ -129,7 +148,8 @@ struct ddgs_workspace {
   int64_t rec_cap = 0, pair_cap = 0, tile_cap = 0, blk_cap = 0, sblk_cap = 0;
   // per (view, Gaussian) records
   float4 *rec = nullptr;         // [records][2]: (u, v, conic a, conic b), (conic c, alpha,
-                                 // colour, depth): one 32-byte sector per gather
+                                 // colour, packed box half-extents): one 32-byte sector
+                                 // per gather
   uint2 *rect = nullptr;         // (tx0 | ty0 << 16, tx1 | ty1 << 16)
   uint32_t *tiles_touched = nullptr;
   float4 *grad2d = nullptr;      // [records][2]: (u, v, ca, cb), (cc, alpha, colour, 0);

@@ -450,7 +450,7 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_fwd_kernel(PreArgs a) 
         colour = sigmoidf_(zl);
       }
       a.rec[2 * rec] = make_float4(p.u, p.v, ca, cb);
-      a.rec[2 * rec + 1] = make_float4(cc, alpha, colour, depth);
+      a.rec[2 * rec + 1] = make_float4(cc, alpha, colour, box_halfwidths(p.cov, a.q_max));
     }
   }
   uint32_t bt = block_sum_u32(total, s_red);

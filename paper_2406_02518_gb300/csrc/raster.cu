@@ -92,13 +92,12 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Conservative pixel-space box of the q <= q_max ellipse of a conic.
+// Pixel-space box of the q <= q_max ellipse: the record's packed
+// half-extents (computed from the 2D covariance by the preprocess).
 __device__ __forceinline__ float4 ellipse_box(float4 r0, float4 r1, float q_max) {
-  const float det = r0.z * r1.x - r0.w * r0.w;
-  const float cxx = r1.x / det, cyy = r0.z / det;
-  const float ex = sqrtf(q_max * cxx) * 1.001f + 1e-3f;
-  const float ey = sqrtf(q_max * cyy) * 1.001f + 1e-3f;
-  return make_float4(r0.x - ex, r0.x + ex, r0.y - ey, r0.y + ey);
+  (void)q_max;
+  const float2 e = unpack_halfwidths(r1.w);
+  return make_float4(r0.x - e.x, r0.x + e.x, r0.y - e.y, r0.y + e.y);
 }
 
 __device__ __forceinline__ float4 empty_box() {
@@ -111,7 +110,8 @@ struct TileGeom {
   int v, txi, tyi, px, py, wx0, wy0, H, W;
   bool inside;
   int64_t gtile, rec_base, img_off, n_req;
-  __device__ __forceinline__ TileGeom(const RenderShape &s, int64_t gt) {
+  // region: which 8 x 4 pixel block of the tile this warp owns
+  __device__ __forceinline__ TileGeom(const RenderShape &s, int64_t gt, int region) {
     gtile = gt;
     v = find_view(s.view, s.V, gt);
     const ViewTab vt = s.view[v];
@@ -124,8 +124,8 @@ struct TileGeom {
     tyi = (int)(local / vt.tiles_x);
     txi = (int)(local - (int64_t)tyi * vt.tiles_x);
     constexpr int WX = T / 8;
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int wx = w % WX, wy = w / WX;
+    const int lane = threadIdx.x & 31;
+    const int wx = region % WX, wy = region / WX;
     wx0 = txi * T + wx * 8;
     wy0 = tyi * T + wy * 4;
     // the warp's 8 x 4 pixels are four 4 x 2 quarters of 8 lanes each
@@ -162,7 +162,7 @@ __device__ __forceinline__ void fwd_tile(const RasterArgs &a, int64_t gt, float4
                                          float4 *s_box, float4 *s_c) {
   constexpr int NT = T * T;
   const int tid = threadIdx.x;
-  const TileGeom<T> tg(a.s, gt);
+  const TileGeom<T> tg(a.s, gt, threadIdx.x >> 5);
   const uint2 range = a.ranges[tg.gtile];
   const int64_t rec_base = tg.rec_base;
   const float px = tg.px + 0.5f, py = tg.py + 0.5f;
@@ -336,7 +336,7 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs &a, int64_t gt, BwdSme
   uint32_t &s_max = sm.max_last;
   constexpr int NT = T * T;
   const int tid = threadIdx.x;
-  const TileGeom<T> tg(a.s, gt);
+  const TileGeom<T> tg(a.s, gt, threadIdx.x >> 5);
   const uint2 range = a.ranges[tg.gtile];
   const int64_t rec_base = tg.rec_base;
   const float px = tg.px + 0.5f, py = tg.py + 0.5f;
@@ -531,6 +531,284 @@ __global__ void __launch_bounds__(T *T, bwd_min_blocks<T>()) raster_bwd_kernel(R
   }
 }
 
+// ---- warp-streamed rasterisers (staging depth 32) ----
+// Every warp takes its own (tile, 8 x 4 region) item from the queue, stages 32
+// list entries at a time in its own slice of shared memory and never waits
+// for the other warps of its block. Item i is region i % NW of tile
+// order[i / NW] (NW = regions per tile), so the regions of one tile are taken
+// together and share its list in L1/L2. The backward sums a batch's 2D
+// gradients per entry in the warp's slice and sends the non-zero sums to
+// global memory with vector atomics.
+
+constexpr int WARPS = 8;  // warps per block of the warp-streamed kernels
+
+__device__ __forceinline__ uint32_t warp_next_item(uint32_t *counter) {
+  uint32_t it = 0;
+  if ((threadIdx.x & 31) == 0) it = atomicAdd(counter, 1u);
+  return __shfl_sync(0xffffffffu, it, 0);
+}
+
+template <int T, bool PIX>
+__device__ __forceinline__ void fwd_warp_item(const RasterArgs &a, int64_t gt, int region, float4 *sA,
+                                              float4 *sB, float4 *sC) {
+  const int lane = threadIdx.x & 31;
+  const TileGeom<T> tg(a.s, gt, region);
+  const uint2 range = a.ranges[tg.gtile];
+  const float px = tg.px + 0.5f, py = tg.py + 0.5f;
+  PixRay ray;
+  if (PIX) pixel_ray(a.world_to_cam + 12 * tg.v, a.detector + 5 * tg.v, tg.H, tg.W, px, py, ray);
+  float Tr = 1.f, C = 0.f;
+  uint32_t last = 0;
+  bool done = !tg.inside;
+  for (uint32_t b0 = range.x; b0 < range.y; b0 += 32) {
+    const uint32_t dmask = __ballot_sync(0xffffffffu, done);
+    if (dmask == 0xffffffffu) break;
+    const uint32_t j = b0 + lane;
+    const bool ok = j < range.y;
+    float4 box = empty_box();
+    if (ok) {
+      const uint32_t id = a.vals[j];
+      if (id < tg.n_req) {  // else only after a capacity overflow
+        const int64_t r = tg.rec_base + id;
+        const float4 r0 = a.rec[2 * r], r1 = a.rec[2 * r + 1];
+        sA[lane] = r0;
+        sB[lane] = r1;
+        if (PIX) sC[lane] = a.rec2[r];
+        box = ellipse_box(r0, r1, a.P.q_max);
+      }
+    }
+    __syncwarp();
+    uint32_t mine = quarter_todo<T>(tg, box, ok);
+    if (((dmask >> (lane & 24)) & 0xffu) == 0xffu) mine = 0;  // quarter finished
+    while (__any_sync(0xffffffffu, mine != 0)) {
+      if (mine == 0) continue;
+      const int k = __ffs(mine) - 1;
+      mine &= mine - 1;
+      if (done) continue;
+      const float4 A = sA[k], B = sB[k];
+      PairEval e;
+      if (!eval_pair(A.x, A.y, A.z, A.w, B.x, B.y, px, py, a.P, e)) continue;
+      const float Tn = __fmul_rn(Tr, __fsub_rn(1.f, e.sigma));
+      if (Tn < a.P.t_min) {
+        done = true;
+        continue;
+      }
+      const float col = PIX ? pixel_colour(ray, sC[k]) : B.z;
+      C = fmaf(col * e.sigma, Tr, C);
+      Tr = Tn;
+      last = b0 + (uint32_t)k - range.x + 1u;
+    }
+    __syncwarp();  // the slice is rewritten by the next batch
+  }
+  if (tg.inside) {
+    const int64_t pix = tg.pixel();
+    a.image[pix] = C;
+    a.t_final[pix] = Tr;
+    a.n_last[pix] = last;
+  }
+}
+
+template <int T, bool PIX>
+// Resident blocks per SM asked of the register allocator: 5 (48 registers) for
+// the forward and 4 (64) for the backward; without block barriers fewer
+// resident warps keep the SM busy.
+__global__ void __launch_bounds__(WARPS * 32, 5) raster_fwd_warp_kernel(RasterArgs a) {
+  constexpr int NW = T * T / 32;
+  __shared__ float4 s_a[WARPS][32], s_b[WARPS][32], s_c[WARPS][PIX ? 32 : 1];
+  const int w = threadIdx.x >> 5;
+  const uint64_t n_items = (uint64_t)a.s.total_tiles * NW;
+  for (;;) {
+    const uint32_t item = warp_next_item(a.counter);
+    if (item >= n_items) break;
+    const int64_t gt = a.order[item / NW];
+    fwd_warp_item<T, PIX>(a, gt, (int)(item % NW), s_a[w], s_b[w], s_c[w]);
+    if (a.req_end && (threadIdx.x & 31) == 0)
+      atomicMax(a.req_end + a.s.view[find_view(a.s.view, a.s.V, gt)].req, global_ns());
+  }
+}
+
+template <int T, bool PIX>
+__device__ __forceinline__ void bwd_warp_item(const RasterArgs &a, int64_t gt, int region, float4 *sA,
+                                              float4 *sB, float4 *sC, uint32_t *sId,
+                                              float (*sAcc)[n_acc<PIX>()]) {
+  const int lane = threadIdx.x & 31;
+  const TileGeom<T> tg(a.s, gt, region);
+  const uint2 range = a.ranges[tg.gtile];
+  const float px = tg.px + 0.5f, py = tg.py + 0.5f;
+  PixRay ray;
+  float gY[3] = {0.f, 0.f, 0.f};
+  if (PIX) pixel_ray(a.world_to_cam + 12 * tg.v, a.detector + 5 * tg.v, tg.H, tg.W, px, py, ray);
+  float Tr = 1.f, g = 0.f;
+  uint32_t last = 0;
+  if (tg.inside) {
+    const int64_t pix = tg.pixel();
+    Tr = a.t_final_in[pix];
+    last = a.n_last_in[pix];
+    g = a.dL_dimage[pix];
+  }
+  if (g == 0.f) last = 0;  // nothing to propagate from this pixel
+  if (last > range.y - range.x) last = range.y - range.x;  // never read past the list
+  uint32_t max_last = last;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) max_last = max(max_last, __shfl_xor_sync(0xffffffffu, max_last, o));
+  uint32_t qlast = last;
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) qlast = max(qlast, __shfl_xor_sync(0xffffffffu, qlast, o));
+  const uint32_t ql0 = __shfl_sync(0xffffffffu, qlast, 0), ql1 = __shfl_sync(0xffffffffu, qlast, 8);
+  const uint32_t ql2 = __shfl_sync(0xffffffffu, qlast, 16), ql3 = __shfl_sync(0xffffffffu, qlast, 24);
+  float S = 0.f;
+  for (int64_t hi = max_last; hi > 0; hi -= 32) {
+    const int64_t lo = hi > 32 ? hi - 32 : 0;
+    const int cnt = (int)(hi - lo);
+    // lane e stages list position hi - 1 - e (batches run back to front)
+    const bool ok = lane < cnt;
+    float4 box = empty_box();
+    if (ok) {
+      const uint32_t id = a.vals[range.x + (uint32_t)(hi - 1 - lane)];
+      if (id < tg.n_req) {  // else only after a capacity overflow
+        const int64_t r = tg.rec_base + id;
+        const float4 r0 = a.rec[2 * r], r1 = a.rec[2 * r + 1];
+        sA[lane] = r0;
+        sB[lane] = r1;
+        if (PIX) sC[lane] = a.rec2[r];
+        box = ellipse_box(r0, r1, a.P.q_max);
+      }
+      sId[lane] = id;
+    }
+#pragma unroll
+    for (int c = 0; c < n_acc<PIX>(); ++c) sAcc[lane][c] = 0.f;
+    __syncwarp();
+    const uint32_t pe = (uint32_t)(hi - 1 - lane);
+    const uint32_t m0 = __ballot_sync(0xffffffffu, ok && pe < ql0 && !tg.misses_q(box, 0));
+    const uint32_t m1 = __ballot_sync(0xffffffffu, ok && pe < ql1 && !tg.misses_q(box, 1));
+    const uint32_t m2 = __ballot_sync(0xffffffffu, ok && pe < ql2 && !tg.misses_q(box, 2));
+    const uint32_t m3 = __ballot_sync(0xffffffffu, ok && pe < ql3 && !tg.misses_q(box, 3));
+    const int qi = lane >> 3;
+    uint32_t mine = qi == 0 ? m0 : (qi == 1 ? m1 : (qi == 2 ? m2 : m3));
+    while (__any_sync(0xffffffffu, mine != 0)) {
+      const bool has = mine != 0;
+      const int k = has ? __ffs(mine) - 1 : 0;
+      if (has) mine &= mine - 1;
+      const uint32_t pos = (uint32_t)(hi - 1 - k);
+      float gv[PIX ? 16 : 8];
+#pragma unroll
+      for (int c = 0; c < (PIX ? 16 : 8); ++c) gv[c] = 0.f;
+      bool act = has && pos < last;
+      if (act) {
+        const float4 A = sA[k], B = sB[k];
+        PairEval e;
+        act = eval_pair(A.x, A.y, A.z, A.w, B.x, B.y, px, py, a.P, e);
+        if (act) {
+          // 1 / (1 - sigma) with sigma <= alpha_max < 1
+          const float inv_om = __frcp_rn(__fsub_rn(1.f, e.sigma));
+          Tr = Tr * inv_om;  // transmittance before this Gaussian
+          float4 cz;
+          if (PIX) cz = sC[k];
+          const float c = PIX ? pixel_colour(ray, cz) : B.z;
+          const float dC_dsigma = fmaf(c, Tr, -S * inv_om);
+          S = fmaf(c * e.sigma, Tr, S);
+          const float gs = g * dC_dsigma;
+          float gq = 0.f;
+          if (!(e.aG > a.P.alpha_max)) {
+            gv[5] = gs * e.G;
+            gq = -0.5f * gs * B.y * e.G;
+          }
+          const float gq2 = gq + gq;
+          gv[0] = gq2 * e.tx;
+          gv[1] = gq2 * e.ty;
+          gv[2] = gq * e.dx * e.dx;
+          gv[3] = gq2 * e.dx * e.dy;
+          gv[4] = gq * e.dy * e.dy;
+          const float dcol = g * e.sigma * Tr;  // dL/dc
+          if (PIX) {
+            const float dz = dcol * c * (1.f - c);
+            gv[6] = dz;
+            gv[7] = dz * ray.Y[0];
+            gv[8] = dz * ray.Y[1];
+            gv[9] = dz * ray.Y[2];
+            gY[0] = fmaf(dz, cz.y, gY[0]);
+            gY[1] = fmaf(dz, cz.z, gY[1]);
+            gY[2] = fmaf(dz, cz.w, gY[2]);
+          } else {
+            gv[6] = dcol;
+          }
+        }
+      }
+      if (__any_sync(0xffffffffu, act)) {
+        if (PIX) {
+          const int comp = quarter_reduce16(gv);
+          if (has && comp < 10) {
+            if (gv[0] != 0.f) atomicAdd(&sAcc[k][comp], gv[0]);
+            if (gv[1] != 0.f) atomicAdd(&sAcc[k][comp + 1], gv[1]);
+          }
+        } else {
+          const int comp = quarter_reduce8(gv);
+          if (has && gv[0] != 0.f) atomicAdd(&sAcc[k][comp], gv[0]);
+        }
+      }
+    }
+    __syncwarp();
+    if (ok) {  // lane e sends entry e's sums
+      const float *acc = sAcc[lane];
+      bool nz = (acc[0] != 0.f) | (acc[1] != 0.f) | (acc[2] != 0.f) | (acc[3] != 0.f) |
+                (acc[4] != 0.f) | (acc[5] != 0.f) | (acc[6] != 0.f);
+      if (PIX) nz |= (acc[7] != 0.f) | (acc[8] != 0.f) | (acc[9] != 0.f);
+      if (nz) {
+        const int64_t r = tg.rec_base + sId[lane];
+        float4 *dst = a.grad2d + 2 * r;
+        atomicAdd(dst, make_float4(acc[0], acc[1], acc[2], acc[3]));
+        atomicAdd(dst + 1, make_float4(acc[4], acc[5], acc[6], 0.f));
+        if (PIX) atomicAdd(a.grad_h + r, make_float4(acc[7], acc[8], acc[9], 0.f));
+      }
+    }
+    __syncwarp();
+  }
+  if (PIX && a.pose_grad) {
+    // Y_1(d / |d|), d = W^T rc: dL/dW[r][c] = rc[r] dL/dd[c], summed over the warp
+    const bool mine = tg.inside && ((gY[0] != 0.f) | (gY[1] != 0.f) | (gY[2] != 0.f));
+    if (__any_sync(0xffffffffu, mine)) {
+      float w9[9];
+      const float ddh[3] = {-SH_C1 * gY[2], -SH_C1 * gY[0], SH_C1 * gY[1]};
+      const float dot = ddh[0] * ray.dh[0] + ddh[1] * ray.dh[1] + ddh[2] * ray.dh[2];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float dd = mine ? (ddh[c] - ray.dh[c] * dot) * ray.inv : 0.f;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) w9[3 * r + c] = ray.rc[r] * dd;
+      }
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) w9[i] += __shfl_xor_sync(0xffffffffu, w9[i], o);
+      }
+      if (lane < 9) {
+        float x = w9[0];
+#pragma unroll
+        for (int i = 1; i < 9; ++i) if (lane == i) x = w9[i];
+        if (x != 0.f) atomicAdd(a.pose_grad + 12 * (int64_t)tg.v + 4 * (lane / 3) + lane % 3, x);
+      }
+    }
+  }
+}
+
+template <int T, bool PIX>
+__global__ void __launch_bounds__(WARPS * 32, 4) raster_bwd_warp_kernel(RasterArgs a) {
+  constexpr int NW = T * T / 32;
+  __shared__ float4 s_a[WARPS][32], s_b[WARPS][32], s_c[WARPS][PIX ? 32 : 1];
+  __shared__ uint32_t s_id[WARPS][32];
+  __shared__ float s_acc[WARPS][32][n_acc<PIX>()];
+  const int w = threadIdx.x >> 5;
+  const uint64_t n_items = (uint64_t)a.s.total_tiles * NW;
+  for (;;) {
+    const uint32_t item = warp_next_item(a.counter);
+    if (item >= n_items) break;
+    const int64_t gt = a.order[item / NW];
+    bwd_warp_item<T, PIX>(a, gt, (int)(item % NW), s_a[w], s_b[w], s_c[w], s_id[w], s_acc[w]);
+    if (a.req_end && (threadIdx.x & 31) == 0)
+      atomicMax(a.req_end + a.s.view[find_view(a.s.view, a.s.V, gt)].req, global_ns());
+  }
+}
+
 // ---- work order: view by view, and within a view the tiles by descending
 // list length (bucketed by log2). At any time the persistent blocks then work
 // on a few views, whose records and gradient accumulators stay in L2 while
@@ -619,6 +897,51 @@ void launch_bwd_t(const RasterArgs &a, cudaStream_t st) {
   k<<<(unsigned)grid, T * T, 0, st>>>(a);
 }
 
+template <int T, bool PIX>
+void launch_fwd_warp_t(const RasterArgs &a, cudaStream_t st) {
+  auto k = raster_fwd_warp_kernel<T, PIX>;
+  const int64_t need = (a.s.total_tiles * (T * T / 32) + WARPS - 1) / WARPS;
+  int64_t grid = (int64_t)blocks_per_sm(k, WARPS * 32) * device_sms();
+  if (grid > need) grid = need;
+  LaunchScope ls(KID_RASTER_FWD, st);
+  k<<<(unsigned)grid, WARPS * 32, 0, st>>>(a);
+}
+
+template <int T, bool PIX>
+void launch_bwd_warp_t(const RasterArgs &a, cudaStream_t st) {
+  auto k = raster_bwd_warp_kernel<T, PIX>;
+  const int64_t need = (a.s.total_tiles * (T * T / 32) + WARPS - 1) / WARPS;
+  int64_t grid = (int64_t)blocks_per_sm(k, WARPS * 32) * device_sms();
+  if (grid > need) grid = need;
+  LaunchScope ls(KID_RASTER_BWD, st);
+  k<<<(unsigned)grid, WARPS * 32, 0, st>>>(a);
+}
+
+// The warp-streamed kernels count items in 32 bits.
+bool warp_mode(const RenderShape &s, const ddgs_workspace &ws) {
+  return ws.batch_depth == 32 && s.total_tiles * (int64_t)(s.tile * s.tile / 32) < (int64_t(1) << 32);
+}
+
+template <bool PIX>
+void fwd_warp_dispatch(const RasterArgs &a, int tile, cudaStream_t st) {
+  if (a.s.total_tiles <= 0) return;
+  switch (tile) {
+    case 8: launch_fwd_warp_t<8, PIX>(a, st); break;
+    case 16: launch_fwd_warp_t<16, PIX>(a, st); break;
+    default: launch_fwd_warp_t<32, PIX>(a, st); break;
+  }
+}
+
+template <bool PIX>
+void bwd_warp_dispatch(const RasterArgs &a, int tile, cudaStream_t st) {
+  if (a.s.total_tiles <= 0) return;
+  switch (tile) {
+    case 8: launch_bwd_warp_t<8, PIX>(a, st); break;
+    case 16: launch_bwd_warp_t<16, PIX>(a, st); break;
+    default: launch_bwd_warp_t<32, PIX>(a, st); break;
+  }
+}
+
 template <int BATCH, bool PIX>
 void fwd_dispatch(const RasterArgs &a, int tile, cudaStream_t st) {
   switch (tile) {
@@ -665,7 +988,10 @@ void launch_raster_fwd(const RenderShape &s, const RasterParams &p, ddgs_workspa
     a.rec2 = ws.rec2;
     a.world_to_cam = pr->world_to_cam;
     a.detector = pr->detector;
-    fwd_dispatch<256, true>(a, s.tile, st);
+    if (warp_mode(s, ws)) fwd_warp_dispatch<true>(a, s.tile, st);
+    else fwd_dispatch<256, true>(a, s.tile, st);
+  } else if (warp_mode(s, ws)) {
+    fwd_warp_dispatch<false>(a, s.tile, st);
   } else if (ws.batch_depth == 128) {
     fwd_dispatch<128, false>(a, s.tile, st);
   } else if (ws.batch_depth == 512) {
@@ -698,7 +1024,10 @@ void launch_raster_bwd(const RenderShape &s, const RasterParams &p, ddgs_workspa
     a.world_to_cam = pr->world_to_cam;
     a.detector = pr->detector;
     a.pose_grad = pr->pose_grad;
-    bwd_dispatch<256, true>(a, s.tile, st);
+    if (warp_mode(s, ws)) bwd_warp_dispatch<true>(a, s.tile, st);
+    else bwd_dispatch<256, true>(a, s.tile, st);
+  } else if (warp_mode(s, ws)) {
+    bwd_warp_dispatch<false>(a, s.tile, st);
   } else if (ws.batch_depth == 128) {
     bwd_dispatch<128, false>(a, s.tile, st);
   } else if (ws.batch_depth == 512) {

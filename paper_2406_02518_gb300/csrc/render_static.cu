@@ -173,7 +173,8 @@ extern "C" ddgs_status ddgs_render_static(const ddgs_gaussians *g, const ddgs_vi
   ws.order = reinterpret_cast<uint32_t *>(base + kOffOrder);
   ws.queue = reinterpret_cast<uint32_t *>(base + kOffQueue);
   ws.req_time = nullptr;
-  ws.batch_depth = (c->batch_depth == 128 || c->batch_depth == 512) ? c->batch_depth : 256;
+  ws.batch_depth = (c->batch_depth == 32 || c->batch_depth == 128 || c->batch_depth == 512)
+                       ? c->batch_depth : 256;
   ddgs::ReqTab *d_req = reinterpret_cast<ddgs::ReqTab *>(base + kOffReq);
   ddgs::ViewTab *d_view = reinterpret_cast<ddgs::ViewTab *>(base + kOffView);
   s.req = d_req;

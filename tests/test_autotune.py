@@ -12,7 +12,7 @@ def test_picks_fastest_and_caches(tmp_path):
 
     def step(tile, depth):
         calls.append((tile, depth))
-        return {8: 3.0, 16: 1.0, 32: 2.0}[tile] + (0.5 if depth == 128 else 0.0)
+        return {8: 3.0, 16: 1.0, 32: 2.0}[tile] + (0.5 if depth in (32, 128) else 0.0)
 
     r = at.tune(step, "k1", cache_path=path)
     assert (r["tile"], r["batch_depth"], r["cached"]) == (16, 256, False)
@@ -31,7 +31,7 @@ def test_failing_candidates_are_skipped(tmp_path):
         return float(tile + depth / 1000)
 
     r = at.tune(step, "k2", cache_path=str(tmp_path / "c.json"))
-    assert r["tile"] == 8 and r["batch_depth"] == 128
+    assert r["tile"] == 8 and r["batch_depth"] == 32
     assert r["timings"]["16x256"] is None
     with pytest.raises(RuntimeError):
         at.tune(lambda t, d: (_ for _ in ()).throw(ValueError("x")), "k3",

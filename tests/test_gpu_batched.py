@@ -128,8 +128,9 @@ def test_empty_batch_and_batch_without_views():
 
 
 def test_batch_depth_and_tile_variants_agree():
-    """The staging depth changes only how many list entries a block loads per
-    round, never the per-pixel order: images are bit-identical."""
+    """The staging depth (and warp-streamed staging) changes only how many list
+    entries are loaded per round, never the per-pixel order: images are
+    bit-identical."""
     sc = syn.uniform_cloud(3000, seed=41)
     views = syn.Views(np.ascontiguousarray(np.stack([
         syn.pose_matrix(np.eye(3), np.array([0.0, 0.0, 2.0])),
@@ -141,7 +142,7 @@ def test_batch_depth_and_tile_variants_agree():
     for tile in (8, 16, 32):
         st = syn.Settings(near_plane=0.2, tile=tile)
         outs = []
-        for depth in (128, 256, 512):
+        for depth in (32, 128, 256, 512):  # 32: warp-streamed
             img, tf, nl = B.render(cloud, gv, B.config_from_settings(st, batch_depth=depth), ws)
             outs.append((img.clone(), tf.clone(), nl.clone()))
         torch.cuda.synchronize()

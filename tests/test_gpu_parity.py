@@ -442,3 +442,29 @@ def test_per_pixel_mode_must_match_between_forward_and_backward(ws):
     c3 = dataclasses.replace(B.cloud_from_arrays(sc3), per_pixel=True)
     with pytest.raises(RuntimeError):
         B.render(c3, gv, cfg, ws)
+
+
+@pytest.mark.parametrize("case,per_pixel", [("ragged_100x75_2views", False), ("tile8", False),
+                                            ("tile32", False), ("strong_dir", True)])
+def test_warp_streamed_rasterisers(case, per_pixel, ws):
+    """Staging depth 32: every warp streams its own region's list. Image and
+    every gradient against the oracle."""
+    scene, views, st = CASES[case]()
+    scene = dataclasses.replace(scene, per_pixel=per_pixel)
+    cloud = B.cloud_from_arrays(scene)
+    gv = B.views_from_arrays(views)
+    cfg = B.config_from_settings(st, batch_depth=32)
+    img, tf, nl = B.render(cloud, gv, cfg, ws)
+    torch.cuda.synchronize()
+    bins = _bins(ws, scene, views, st)
+    ids = last_ids(nl.cpu().numpy().view(np.uint32), bins, views, st.tile)
+    check_image(scene, views, st, img.cpu().numpy(), tf.cpu().numpy(), ids)
+    ref = oracle.render(scene, views, st)
+    w = _masked_weights(ref, 5)
+    g = B.render_backward(cloud, gv, cfg, ws, torch.as_tensor(w, dtype=torch.float32, device="cuda"),
+                          tf, nl)
+    gr = oracle.render_backward(scene, views, st, w)
+    gpu = {n: t.float().cpu().numpy() for n, t in g.items()}
+    gpu["feat"] = np.concatenate([gpu.pop("feat_iso"), gpu.pop("feat_dir")])
+    gpu["pose"] = gpu.pop("world_to_cam")
+    compare_grads(gpu, gr, GRAD_NAMES)
