@@ -383,6 +383,8 @@ ddgs_status ddgs_workspace_create(ddgs_workspace **out) {
       (e = cudaMalloc(&ws->d_status, sizeof(int32_t))) != cudaSuccess ||
       (e = cudaMalloc(&ws->digit_total, ddgs::RADIX * sizeof(uint32_t))) != cudaSuccess ||
       (e = cudaMalloc(&ws->queue, 2 * sizeof(uint32_t))) != cudaSuccess ||
+      (e = cudaMalloc(&ws->sort_state, sizeof(ddgs::SortState))) != cudaSuccess ||
+      (e = cudaMemset(ws->sort_state, 0, sizeof(ddgs::SortState))) != cudaSuccess ||
       (e = cudaHostAlloc(&ws->h_pairs, sizeof(uint64_t), cudaHostAllocDefault)) != cudaSuccess ||
       (e = cudaMemset(ws->d_status, 0, sizeof(int32_t))) != cudaSuccess ||
       (e = cudaMemset(ws->d_pairs, 0, sizeof(uint64_t))) != cudaSuccess) {
@@ -409,7 +411,7 @@ ddgs_status ddgs_workspace_destroy(ddgs_workspace *ws) {
   void *dev[] = {ws->rec, ws->rect, ws->tiles_touched, ws->grad2d, ws->blk_total,
                  ws->blk_offset, ws->keys[0], ws->keys[1], ws->vals[0], ws->vals[1], ws->hist,
                  ws->digit_total, ws->ranges, ws->d_pairs, ws->d_status, ws->d_req, ws->d_view,
-                 ws->order, ws->queue, ws->req_time, ws->rec2, ws->grad_h,
+                 ws->order, ws->queue, ws->sort_state, ws->req_time, ws->rec2, ws->grad_h,
                  ws->rads_keys, ws->rads_buf};
   for (void *p : dev)
     if (p) cudaFree(p);
@@ -751,8 +753,15 @@ ddgs_status ddgs_debug_binning(const ddgs_workspace *ws, uint32_t *tiles_touched
   }
   uint64_t m = *ws->h_pairs;
   if (m > (uint64_t)ws->pair_cap) m = (uint64_t)ws->pair_cap;  // after an overflow
-  if (keys && m) CK(cudaMemcpyAsync(keys, ws->keys[ws->sorted], m * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s_));
-  if (vals && m) CK(cudaMemcpyAsync(vals, ws->vals[ws->sorted], m * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s_));
+  int32_t sorted = 0;  // the sort's result buffer, decided on the device
+  if ((keys || vals) && m) {
+    CK(cudaMemcpyAsync(&sorted, ws->sort_state->cur + ws->sort_passes, sizeof(int32_t),
+                       cudaMemcpyDeviceToHost, s_));
+    CK(cudaStreamSynchronize(s_));
+    sorted = sorted ? 1 : 0;
+  }
+  if (keys && m) CK(cudaMemcpyAsync(keys, ws->keys[sorted], m * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s_));
+  if (vals && m) CK(cudaMemcpyAsync(vals, ws->vals[sorted], m * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s_));
   if (ranges && s.total_tiles)
     CK(cudaMemcpyAsync(ranges, ws->ranges, (size_t)s.total_tiles * sizeof(uint2), cudaMemcpyDeviceToDevice, s_));
   return DDGS_OK;

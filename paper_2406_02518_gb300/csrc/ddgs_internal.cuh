@@ -56,6 +56,17 @@ struct ViewConst {
   int64_t tile_base, rec_off;
 };
 
+// Device-side state of one radix sort. A pass whose digit is the same in
+// every key leaves the order unchanged and is skipped (found from the AND and
+// OR of all keys during the first pass), so the buffer holding the keys before
+// each pass is tracked on the device: consumers read cur[passes].
+constexpr int MAX_SORT_PASSES = 8;  // 64-bit keys, 8-bit digits
+struct SortState {
+  unsigned long long key_and, key_or;
+  uint32_t skip;                     // bit p: pass p is skipped
+  int32_t cur[MAX_SORT_PASSES + 1];  // buffer (0 / 1) holding the keys before pass p
+};
+
 // Parameters shared by the rasterisers.
 struct RasterParams {
   float alpha_min, alpha_max, t_min, q_max;
@@ -165,7 +176,8 @@ struct ddgs_workspace {
   // pairs
   uint64_t *keys[2] = {nullptr, nullptr};
   uint32_t *vals[2] = {nullptr, nullptr};
-  int sorted = 0;                // which buffer holds the sorted pairs
+  ddgs::SortState *sort_state = nullptr;  // device: which buffer holds the sorted pairs
+  int sort_passes = 0;           // passes of the last sort: the result is cur[sort_passes]
   uint32_t *hist = nullptr;      // [RADIX][sort blocks]
   uint32_t *digit_total = nullptr;  // [RADIX]
   uint2 *ranges = nullptr;       // [tiles]

@@ -39,7 +39,8 @@ struct RasterArgs {
   RenderShape s;
   RasterParams P;
   const float4 *rec;  // two float4 per record
-  const uint32_t *vals;
+  const uint32_t *vals0, *vals1;  // sort buffers: the sorted values are in vals1 if *sorted
+  const int32_t *sorted;
   const uint2 *ranges;
   float4 *grad2d;
   float *image, *t_final;
@@ -164,6 +165,7 @@ __device__ __forceinline__ void fwd_tile(const RasterArgs &a, int64_t gt, float4
   const int tid = threadIdx.x;
   const TileGeom<T> tg(a.s, gt, threadIdx.x >> 5);
   const uint2 range = a.ranges[tg.gtile];
+  const uint32_t *vals = *a.sorted ? a.vals1 : a.vals0;
   const int64_t rec_base = tg.rec_base;
   const float px = tg.px + 0.5f, py = tg.py + 0.5f;
   PixRay ray;
@@ -176,7 +178,7 @@ __device__ __forceinline__ void fwd_tile(const RasterArgs &a, int64_t gt, float4
     for (int e = tid; e < BATCH; e += NT) {
       const uint32_t j = b0 + e;
       if (j < range.y) {
-        const uint32_t id = a.vals[j];
+        const uint32_t id = vals[j];
         if (id < tg.n_req) {
           const int64_t r = rec_base + id;
           const float4 r0 = a.rec[2 * r], r1 = a.rec[2 * r + 1];
@@ -338,6 +340,7 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs &a, int64_t gt, BwdSme
   const int tid = threadIdx.x;
   const TileGeom<T> tg(a.s, gt, threadIdx.x >> 5);
   const uint2 range = a.ranges[tg.gtile];
+  const uint32_t *vals = *a.sorted ? a.vals1 : a.vals0;
   const int64_t rec_base = tg.rec_base;
   const float px = tg.px + 0.5f, py = tg.py + 0.5f;
   PixRay ray;
@@ -370,7 +373,7 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs &a, int64_t gt, BwdSme
     for (int e = tid; e < BATCH; e += NT) {
       const int64_t pos_t = hi - 1 - e;  // batches run back to front
       if (pos_t >= lo) {
-        const uint32_t id = a.vals[range.x + (uint32_t)pos_t];
+        const uint32_t id = vals[range.x + (uint32_t)pos_t];
         if (id < tg.n_req) {
           const int64_t r = rec_base + id;
           const float4 r0 = a.rec[2 * r], r1 = a.rec[2 * r + 1];
@@ -554,6 +557,7 @@ __device__ __forceinline__ void fwd_warp_item(const RasterArgs &a, int64_t gt, i
   const int lane = threadIdx.x & 31;
   const TileGeom<T> tg(a.s, gt, region);
   const uint2 range = a.ranges[tg.gtile];
+  const uint32_t *vals = *a.sorted ? a.vals1 : a.vals0;
   const float px = tg.px + 0.5f, py = tg.py + 0.5f;
   PixRay ray;
   if (PIX) pixel_ray(a.world_to_cam + 12 * tg.v, a.detector + 5 * tg.v, tg.H, tg.W, px, py, ray);
@@ -567,7 +571,7 @@ __device__ __forceinline__ void fwd_warp_item(const RasterArgs &a, int64_t gt, i
     const bool ok = j < range.y;
     float4 box = empty_box();
     if (ok) {
-      const uint32_t id = a.vals[j];
+      const uint32_t id = vals[j];
       if (id < tg.n_req) {  // else only after a capacity overflow
         const int64_t r = tg.rec_base + id;
         const float4 r0 = a.rec[2 * r], r1 = a.rec[2 * r + 1];
@@ -634,6 +638,7 @@ __device__ __forceinline__ void bwd_warp_item(const RasterArgs &a, int64_t gt, i
   const int lane = threadIdx.x & 31;
   const TileGeom<T> tg(a.s, gt, region);
   const uint2 range = a.ranges[tg.gtile];
+  const uint32_t *vals = *a.sorted ? a.vals1 : a.vals0;
   const float px = tg.px + 0.5f, py = tg.py + 0.5f;
   PixRay ray;
   float gY[3] = {0.f, 0.f, 0.f};
@@ -664,7 +669,7 @@ __device__ __forceinline__ void bwd_warp_item(const RasterArgs &a, int64_t gt, i
     const bool ok = lane < cnt;
     float4 box = empty_box();
     if (ok) {
-      const uint32_t id = a.vals[range.x + (uint32_t)(hi - 1 - lane)];
+      const uint32_t id = vals[range.x + (uint32_t)(hi - 1 - lane)];
       if (id < tg.n_req) {  // else only after a capacity overflow
         const int64_t r = tg.rec_base + id;
         const float4 r0 = a.rec[2 * r], r1 = a.rec[2 * r + 1];
@@ -975,7 +980,9 @@ void launch_raster_fwd(const RenderShape &s, const RasterParams &p, ddgs_workspa
   a.s = s;
   a.P = p;
   a.rec = ws.rec;
-  a.vals = ws.vals[ws.sorted];
+  a.vals0 = ws.vals[0];
+  a.vals1 = ws.vals[1];
+  a.sorted = ws.sort_state->cur + ws.sort_passes;
   a.ranges = ws.ranges;
   a.image = image;
   a.t_final = t_final;
@@ -1008,7 +1015,9 @@ void launch_raster_bwd(const RenderShape &s, const RasterParams &p, ddgs_workspa
   a.s = s;
   a.P = p;
   a.rec = ws.rec;
-  a.vals = ws.vals[ws.sorted];
+  a.vals0 = ws.vals[0];
+  a.vals1 = ws.vals[1];
+  a.sorted = ws.sort_state->cur + ws.sort_passes;
   a.ranges = ws.ranges;
   a.grad2d = ws.grad2d;
   a.dL_dimage = dL_dimage;

@@ -48,7 +48,8 @@ constexpr size_t kOffRanges = align256(kOffDigit + ddgs::RADIX * sizeof(uint32_t
 constexpr size_t kOffPairs = align256(kOffRanges + kMaxTiles * sizeof(uint2));
 constexpr size_t kOffStatus = align256(kOffPairs + sizeof(uint64_t));
 constexpr size_t kOffOrder = align256(kOffStatus + sizeof(int32_t));
-constexpr size_t kOffQueue = align256(kOffOrder + kMaxTiles * sizeof(uint32_t));
+constexpr size_t kOffSortState = align256(kOffOrder + kMaxTiles * sizeof(uint32_t));
+constexpr size_t kOffQueue = align256(kOffSortState + sizeof(ddgs::SortState));
 constexpr size_t kOffReq = align256(kOffQueue + 2 * sizeof(uint32_t));
 constexpr size_t kOffView = align256(kOffReq + 2 * sizeof(ddgs::ReqTab));
 constexpr size_t kScratchBytes = align256(kOffView + (kMaxViews + 1) * sizeof(ddgs::ViewTab));
@@ -170,6 +171,7 @@ extern "C" ddgs_status ddgs_render_static(const ddgs_gaussians *g, const ddgs_vi
   ws.ranges = reinterpret_cast<uint2 *>(base + kOffRanges);
   ws.d_pairs = reinterpret_cast<uint64_t *>(base + kOffPairs);
   ws.d_status = reinterpret_cast<int32_t *>(base + kOffStatus);
+  ws.sort_state = reinterpret_cast<ddgs::SortState *>(base + kOffSortState);
   ws.order = reinterpret_cast<uint32_t *>(base + kOffOrder);
   ws.queue = reinterpret_cast<uint32_t *>(base + kOffQueue);
   ws.req_time = nullptr;

@@ -87,10 +87,12 @@ __device__ __forceinline__ uint64_t pair_count(const uint64_t *d_pairs, uint64_t
 }
 
 __global__ void __launch_bounds__(SORT_THREADS) radix_upsweep_kernel(
-    const uint64_t *keys, const uint64_t *d_pairs, uint64_t cap, int shift, uint32_t *hist,
-    uint32_t *digit_total, int64_t nblk) {
+    const uint64_t *keys0, const uint64_t *keys1, const uint64_t *d_pairs, uint64_t cap, int shift,
+    int pass, SortState *ss, uint32_t *hist, uint32_t *digit_total, int64_t nblk) {
   __shared__ uint32_t s_hist[SORT_THREADS / 32][RADIX];
   const int tid = threadIdx.x, wid = tid >> 5;
+  if (pass > 0 && ((ss->skip >> pass) & 1u)) return;  // block-uniform
+  const uint64_t *keys = ss->cur[pass] ? keys1 : keys0;
   for (int d = tid; d < (SORT_THREADS / 32) * RADIX; d += SORT_THREADS) (&s_hist[0][0])[d] = 0;
   const uint64_t m = pair_count(d_pairs, cap);
   const uint64_t start = (uint64_t)blockIdx.x * SORT_TILE;
@@ -115,10 +117,26 @@ __global__ void __launch_bounds__(SORT_THREADS) radix_upsweep_kernel(
       }
   }
   __syncthreads();
+  unsigned long long k_and = ~0ull, k_or = 0ull;
 #pragma unroll
   for (int r = 0; r < SORT_ITEMS; ++r) {
     const uint64_t j = start + 2 * ((uint64_t)(r >> 1) * SORT_THREADS + tid) + (r & 1);
-    if (j < m) atomicAdd(&s_hist[wid][(k[r] >> shift) & (RADIX - 1)], 1u);
+    if (j < m) {
+      atomicAdd(&s_hist[wid][(k[r] >> shift) & (RADIX - 1)], 1u);
+      k_and &= k[r];
+      k_or |= k[r];
+    }
+  }
+  if (pass == 0) {  // the bits that differ between keys decide which passes can be skipped
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      k_and &= __shfl_xor_sync(0xffffffffu, k_and, o);
+      k_or |= __shfl_xor_sync(0xffffffffu, k_or, o);
+    }
+    if ((tid & 31) == 0) {
+      atomicAnd(&ss->key_and, k_and);
+      atomicOr(&ss->key_or, k_or);
+    }
   }
   __syncthreads();
   for (int d = tid; d < RADIX; d += SORT_THREADS) {
@@ -132,11 +150,28 @@ __global__ void __launch_bounds__(SORT_THREADS) radix_upsweep_kernel(
 
 // One block per digit: offsets[d][b] = (keys of smaller digits) + (keys of
 // digit d in blocks before b).
+// Also decides whether the pass is skipped and which buffer the next pass reads.
 __global__ void __launch_bounds__(1024) radix_scan_kernel(uint32_t *hist, const uint32_t *digit_total,
-                                                          int64_t nblk) {
+                                                          int64_t nblk, SortState *ss, int pass,
+                                                          int passes) {
   __shared__ uint32_t s_warp[32];
   __shared__ uint32_t s_carry;
   const int d = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  uint32_t sk;
+  if (pass == 0) {  // the AND / OR of every key are complete: a digit that no key varies in
+    const unsigned long long diff = ss->key_and ^ ss->key_or;
+    sk = 0;
+    for (int p = 0; p < passes; ++p)
+      if (((diff >> (p * RADIX_BITS)) & (RADIX - 1)) == 0) sk |= 1u << p;
+  } else {
+    sk = ss->skip;
+  }
+  const bool skip = (sk >> pass) & 1u;
+  if (d == 0 && tid == 0) {
+    if (pass == 0) ss->skip = sk;
+    ss->cur[pass + 1] = skip ? ss->cur[pass] : ss->cur[pass] ^ 1;
+  }
+  if (skip) return;  // block-uniform
   if (tid == 0) {
     uint32_t b = 0;
     for (int e = 0; e < d; ++e) b += digit_total[e];
@@ -184,8 +219,14 @@ constexpr int DS_SEG = SORT_TILE / DS_WARPS;  // 512 keys per warp
 constexpr size_t DS_DYN_SMEM = SORT_TILE * (sizeof(uint64_t) + sizeof(uint32_t));
 
 __global__ void __launch_bounds__(SORT_THREADS) radix_downsweep_kernel(
-    const uint64_t *keys_in, const uint32_t *vals_in, uint64_t *keys_out, uint32_t *vals_out,
-    const uint64_t *d_pairs, uint64_t cap, int shift, const uint32_t *offsets, int64_t nblk) {
+    uint64_t *keys0, uint32_t *vals0, uint64_t *keys1, uint32_t *vals1, const uint64_t *d_pairs,
+    uint64_t cap, int shift, int pass, const SortState *ss, const uint32_t *offsets, int64_t nblk) {
+  if ((ss->skip >> pass) & 1u) return;  // block-uniform
+  const bool from1 = ss->cur[pass] != 0;
+  const uint64_t *keys_in = from1 ? keys1 : keys0;
+  const uint32_t *vals_in = from1 ? vals1 : vals0;
+  uint64_t *keys_out = from1 ? keys0 : keys1;
+  uint32_t *vals_out = from1 ? vals0 : vals1;
   extern __shared__ __align__(16) unsigned char ds_smem[];
   uint64_t *s_keys = reinterpret_cast<uint64_t *>(ds_smem);
   uint32_t *s_vals = reinterpret_cast<uint32_t *>(ds_smem + SORT_TILE * sizeof(uint64_t));
@@ -277,8 +318,10 @@ __global__ void __launch_bounds__(SORT_THREADS) radix_downsweep_kernel(
 
 // Tiles outside [0, n_tiles) can only come from a capacity overflow (stale
 // keys); they are ignored so that the render stays memory-safe.
-__global__ void tile_ranges_kernel(const uint64_t *keys, const uint64_t *d_pairs, uint64_t cap,
+__global__ void tile_ranges_kernel(const uint64_t *keys0, const uint64_t *keys1,
+                                   const int32_t *sorted, const uint64_t *d_pairs, uint64_t cap,
                                    uint2 *ranges, uint64_t n_tiles) {
+  const uint64_t *keys = *sorted ? keys1 : keys0;
   const uint64_t m = pair_count(d_pairs, cap);
   for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m;
        j += (uint64_t)gridDim.x * blockDim.x) {
@@ -320,7 +363,10 @@ void launch_radix_sort(const RenderShape &s, uint64_t pair_bound, ddgs_workspace
                        cudaStream_t st) {
   const int64_t nblk = sort_blocks(pair_bound);
   if (nblk > 0 && prepare_sort_kernels() != cudaSuccess) return;  // surfaces via cudaGetLastError
-  int cur = 0;
+  // state: key AND = all ones, key OR = 0, nothing skipped, keys in buffer 0
+  cudaMemsetAsync(ws.sort_state, 0, sizeof(SortState), st);
+  cudaMemsetAsync(&ws.sort_state->key_and, 0xff, sizeof(unsigned long long), st);
+  ws.sort_passes = 0;
   if (nblk > 0) {
     const int passes = (s.key_bits + RADIX_BITS - 1) / RADIX_BITS;
     for (int p = 0; p < passes; ++p) {
@@ -329,22 +375,23 @@ void launch_radix_sort(const RenderShape &s, uint64_t pair_bound, ddgs_workspace
       {
         LaunchScope ls(KID_RADIX_UPSWEEP, st);
         radix_upsweep_kernel<<<(unsigned)nblk, SORT_THREADS, 0, st>>>(
-            ws.keys[cur], ws.d_pairs, (uint64_t)ws.pair_cap, shift, ws.hist, ws.digit_total, nblk);
+            ws.keys[0], ws.keys[1], ws.d_pairs, (uint64_t)ws.pair_cap, shift, p, ws.sort_state,
+            ws.hist, ws.digit_total, nblk);
       }
       {
         LaunchScope ls(KID_RADIX_SCAN, st);
-        radix_scan_kernel<<<RADIX, 1024, 0, st>>>(ws.hist, ws.digit_total, nblk);
+        radix_scan_kernel<<<RADIX, 1024, 0, st>>>(ws.hist, ws.digit_total, nblk, ws.sort_state, p,
+                                                  passes);
       }
       {
         LaunchScope ls(KID_RADIX_DOWNSWEEP, st);
         radix_downsweep_kernel<<<(unsigned)nblk, SORT_THREADS, DS_DYN_SMEM, st>>>(
-            ws.keys[cur], ws.vals[cur], ws.keys[cur ^ 1], ws.vals[cur ^ 1], ws.d_pairs,
-            (uint64_t)ws.pair_cap, shift, ws.hist, nblk);
+            ws.keys[0], ws.vals[0], ws.keys[1], ws.vals[1], ws.d_pairs, (uint64_t)ws.pair_cap,
+            shift, p, ws.sort_state, ws.hist, nblk);
       }
-      cur ^= 1;
     }
+    ws.sort_passes = passes;
   }
-  ws.sorted = cur;
 }
 
 void launch_tile_ranges(const RenderShape &s, uint64_t pair_bound, ddgs_workspace &ws,
@@ -354,9 +401,9 @@ void launch_tile_ranges(const RenderShape &s, uint64_t pair_bound, ddgs_workspac
   int64_t blocks = (int64_t)((pair_bound + 255) / 256);
   if (blocks > 152 * 32) blocks = 152 * 32;
   LaunchScope ls(KID_TILE_RANGES, st);
-  tile_ranges_kernel<<<(unsigned)blocks, 256, 0, st>>>(ws.keys[ws.sorted], ws.d_pairs,
-                                                       (uint64_t)ws.pair_cap, ws.ranges,
-                                                       (uint64_t)s.total_tiles);
+  tile_ranges_kernel<<<(unsigned)blocks, 256, 0, st>>>(
+      ws.keys[0], ws.keys[1], ws.sort_state->cur + ws.sort_passes, ws.d_pairs, (uint64_t)ws.pair_cap,
+      ws.ranges, (uint64_t)s.total_tiles);
 }
 
 }  // namespace ddgs
