@@ -119,9 +119,8 @@ TRAFFIC = {
         "sources_sha256": {"raster.cu": "7f3925f559a8d20d1227736a48b433f3455802c4e693fc388bfaeaa8565859ca",
                            "ddgs_internal.cuh": "2bfbdd727ef2a53bfab1c85f75c74e10e12e758e455c51877001dee4f514857b"},
         "tile": 8, "batch_depth": 32, "views": 64, "gaussians": 500_000,
-        "bytes_per_launch": 4 * 730.6e6,
-        "how": "16-pose capture (730.6 MB) scaled by 4 to the 64-pose launch; "
-               "profiles/raster_bwd_warp_registration_500k_16poses_tile8.md",
+        "bytes_per_launch": 2460.0e6 + 579.1e6,
+        "how": "one-pass ncu capture of the 64-pose step; profiles/launches_registration_500k_64x256.md",
     },
 }
 
