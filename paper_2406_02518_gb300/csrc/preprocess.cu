@@ -492,25 +492,46 @@ struct EmitArgs {
 
 // K3: pairs in (block, view, Gaussian, tile row, tile column) order, so that
 // pairs of one view with equal keys appear in ascending Gaussian index. The
-// value is the Gaussian's index within its request.
+// value is the Gaussian's index within its request. A block's pairs of one
+// view are staged in shared memory and written out by consecutive threads
+// (direct writes when they exceed the staging area); the next view's
+// records are fetched before the block-wide scan of the current one.
+constexpr int EMIT_STAGE = 2048;  // pairs of one (block, view) staged at once
+
 __global__ void __launch_bounds__(PRE_THREADS) emit_keys_kernel(EmitArgs a) {
   __shared__ uint32_t s_warp[PRE_THREADS / 32];
+  __shared__ uint64_t s_keys[EMIT_STAGE];
+  __shared__ uint32_t s_vals[EMIT_STAGE];
   const RenderShape &s = a.s;
   const BlockReq br(s);
   const ReqTab &rq = br.rq;
   uint64_t base = a.blk_offset[blockIdx.x];
   bool overflow = false;
-  for (int v = rq.v_off; v < rq.v_off + rq.n_views; ++v) {
+  const int v_end = rq.v_off + rq.n_views;
+  uint4 next = (br.live && rq.n_views > 0) ? a.bin_info[s.view[rq.v_off].rec_off + br.l]
+                                            : make_uint4(0, 0, 0, 0);
+  for (int v = rq.v_off; v < v_end; ++v) {
     const ViewTab vt = s.view[v];
-    uint4 info = br.live ? a.bin_info[vt.rec_off + br.l] : make_uint4(0, 0, 0, 0);
+    const uint4 info = next;
+    if (br.live && v + 1 < v_end) next = a.bin_info[s.view[v + 1].rec_off + br.l];
     uint32_t total;
     const uint32_t excl = block_excl_scan(info.w, s_warp, &total);
+    const bool staged = total <= EMIT_STAGE;
     if (info.w) {
-      uint64_t off = base + excl;
-      if (off + info.w > a.cap) {
+      const int tx0 = info.x & 0xffff, ty0 = info.x >> 16, tx1 = info.y & 0xffff, ty1 = info.y >> 16;
+      uint32_t o = excl;
+      if (staged) {
+        for (int ty = ty0; ty <= ty1; ++ty)
+          for (int tx = tx0; tx <= tx1; ++tx) {
+            const uint64_t gt = (uint64_t)vt.tile_base + (uint64_t)ty * vt.tiles_x + tx;
+            s_keys[o] = (gt << 32) | info.z;
+            s_vals[o] = (uint32_t)br.l;
+            ++o;
+          }
+      } else if (base + excl + info.w > a.cap) {
         overflow = true;
       } else {
-        const int tx0 = info.x & 0xffff, ty0 = info.x >> 16, tx1 = info.y & 0xffff, ty1 = info.y >> 16;
+        uint64_t off = base + excl;
         for (int ty = ty0; ty <= ty1; ++ty)
           for (int tx = tx0; tx <= tx1; ++tx) {
             const uint64_t gt = (uint64_t)vt.tile_base + (uint64_t)ty * vt.tiles_x + tx;
@@ -519,6 +540,18 @@ __global__ void __launch_bounds__(PRE_THREADS) emit_keys_kernel(EmitArgs a) {
             ++off;
           }
       }
+    }
+    if (staged) {  // block-uniform
+      __syncthreads();
+      for (uint32_t e = threadIdx.x; e < total; e += PRE_THREADS) {
+        if (base + e < a.cap) {
+          a.keys[base + e] = s_keys[e];
+          a.vals[base + e] = s_vals[e];
+        } else {
+          overflow = true;
+        }
+      }
+      __syncthreads();  // the staging area is rewritten for the next view
     }
     base += total;
   }
