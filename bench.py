@@ -277,8 +277,8 @@ def algorithmic_bytes(kernel, s):
     """Algorithmic DRAM bytes per launch of an HBM-bound kernel."""
     M, N, V = s["pairs"], s["n"], s["views"]
     return {
-        "radix_downsweep": 24 * M,          # read + write 8 B key + 4 B value
-        "radix_upsweep": 8 * M,             # read keys
+        "radix_pass": 24 * M,               # read + write 8 B key + 4 B value
+        "radix_hist": 8 * M,                # read keys once for every pass's histogram
         "emit_keys": 16 * N * V + 12 * M,   # read binning record, write key + value
         "preprocess_fwd": 76 * N + 48 * N * V,  # read params once, write 48 B records
         "preprocess_bwd": 76 * N + 32 * N * V,  # read params once, read 2D gradients

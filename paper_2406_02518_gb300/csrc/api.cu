@@ -238,7 +238,7 @@ ddgs_status ensure_pairs(ddgs_workspace *ws, int64_t pairs) {
     if ((st = grow(ws->vals[b], ws->pair_cap, cap, 0, sizeof(uint32_t)))) return st;
   }
   const int64_t sb = ddgs::sort_blocks((uint64_t)cap);
-  if ((st = grow(ws->hist, ws->sblk_cap, sb * ddgs::RADIX, 0, sizeof(uint32_t)))) return st;
+  if ((st = grow(ws->lookback, ws->sblk_cap, sb * ddgs::RADIX, 0, sizeof(uint64_t)))) return st;
   ws->sblk_cap = sb;
   ws->pair_cap = cap;
   return DDGS_OK;
@@ -255,8 +255,8 @@ struct ProfRec {
 std::vector<ProfRec> g_pending;
 std::vector<cudaEvent_t> g_pool;
 const char *const KERNEL_NAMES[ddgs::KID_COUNT] = {
-    "preprocess_fwd", "scan_blocks", "emit_keys", "radix_upsweep", "radix_scan",
-    "radix_downsweep", "tile_ranges", "raster_fwd", "l1_loss", "raster_bwd",
+    "preprocess_fwd", "scan_blocks", "emit_keys", "radix_hist", "radix_plan",
+    "radix_pass", "tile_ranges", "raster_fwd", "l1_loss", "raster_bwd",
     "preprocess_bwd", "debug_copy", "tile_order", "rads_minmax", "rads_count", "rads_scan",
     "rads_emit", "rads_select", "rads_draw", "rads_knn"};
 
@@ -381,7 +381,6 @@ ddgs_status ddgs_workspace_create(ddgs_workspace **out) {
   if ((e = cudaGetDevice(&ws->device)) != cudaSuccess ||
       (e = cudaMalloc(&ws->d_pairs, sizeof(uint64_t))) != cudaSuccess ||
       (e = cudaMalloc(&ws->d_status, sizeof(int32_t))) != cudaSuccess ||
-      (e = cudaMalloc(&ws->digit_total, ddgs::RADIX * sizeof(uint32_t))) != cudaSuccess ||
       (e = cudaMalloc(&ws->queue, 2 * sizeof(uint32_t))) != cudaSuccess ||
       (e = cudaMalloc(&ws->sort_state, sizeof(ddgs::SortState))) != cudaSuccess ||
       (e = cudaMemset(ws->sort_state, 0, sizeof(ddgs::SortState))) != cudaSuccess ||
@@ -409,8 +408,8 @@ ddgs_status ddgs_workspace_create(ddgs_workspace **out) {
 ddgs_status ddgs_workspace_destroy(ddgs_workspace *ws) {
   if (!ws) return DDGS_OK;
   void *dev[] = {ws->rec, ws->rect, ws->tiles_touched, ws->grad2d, ws->blk_total,
-                 ws->blk_offset, ws->keys[0], ws->keys[1], ws->vals[0], ws->vals[1], ws->hist,
-                 ws->digit_total, ws->ranges, ws->d_pairs, ws->d_status, ws->d_req, ws->d_view,
+                 ws->blk_offset, ws->keys[0], ws->keys[1], ws->vals[0], ws->vals[1], ws->lookback,
+                 ws->ranges, ws->d_pairs, ws->d_status, ws->d_req, ws->d_view,
                  ws->order, ws->queue, ws->sort_state, ws->req_time, ws->rec2, ws->grad_h,
                  ws->rads_keys, ws->rads_buf};
   for (void *p : dev)

@@ -57,14 +57,16 @@ struct ViewConst {
 };
 
 // Device-side state of one radix sort. A pass whose digit is the same in
-// every key leaves the order unchanged and is skipped (found from the AND and
-// OR of all keys during the first pass), so the buffer holding the keys before
-// each pass is tracked on the device: consumers read cur[passes].
+// every key leaves the order unchanged and is skipped (found from the digit
+// histograms of the prepass), so the buffer holding the keys before each pass
+// is tracked on the device: consumers read cur[passes].
 constexpr int MAX_SORT_PASSES = 8;  // 64-bit keys, 8-bit digits
 struct SortState {
-  unsigned long long key_and, key_or;
-  uint32_t skip;                     // bit p: pass p is skipped
-  int32_t cur[MAX_SORT_PASSES + 1];  // buffer (0 / 1) holding the keys before pass p
+  uint32_t hist[MAX_SORT_PASSES][RADIX];  // keys per digit value, per pass
+  uint32_t off[MAX_SORT_PASSES][RADIX];   // first output position of each digit value
+  uint32_t ticket[MAX_SORT_PASSES];       // next tile of each pass
+  uint32_t skip;                          // bit p: pass p is skipped
+  int32_t cur[MAX_SORT_PASSES + 1];       // buffer (0 / 1) holding the keys before pass p
 };
 
 // Parameters shared by the rasterisers.
@@ -178,8 +180,7 @@ struct ddgs_workspace {
   uint32_t *vals[2] = {nullptr, nullptr};
   ddgs::SortState *sort_state = nullptr;  // device: which buffer holds the sorted pairs
   int sort_passes = 0;           // passes of the last sort: the result is cur[sort_passes]
-  uint32_t *hist = nullptr;      // [RADIX][sort blocks]
-  uint32_t *digit_total = nullptr;  // [RADIX]
+  uint64_t *lookback = nullptr;  // [sort tiles][RADIX] look-back words of the running pass
   uint2 *ranges = nullptr;       // [tiles]
   uint32_t *order = nullptr;     // [tiles] work order of the persistent rasterisers
   uint32_t *queue = nullptr;     // work-queue heads of the forward / backward rasterisers
@@ -210,8 +211,8 @@ namespace ddgs {
 
 // Kernel ids of the launch counter and profiler (api.cu).
 enum KernelId : int {
-  KID_PREPROCESS_FWD = 0, KID_SCAN_BLOCKS, KID_EMIT_KEYS, KID_RADIX_UPSWEEP, KID_RADIX_SCAN,
-  KID_RADIX_DOWNSWEEP, KID_TILE_RANGES, KID_RASTER_FWD, KID_L1_LOSS, KID_RASTER_BWD,
+  KID_PREPROCESS_FWD = 0, KID_SCAN_BLOCKS, KID_EMIT_KEYS, KID_RADIX_HIST, KID_RADIX_PLAN,
+  KID_RADIX_PASS, KID_TILE_RANGES, KID_RASTER_FWD, KID_L1_LOSS, KID_RASTER_BWD,
   KID_PREPROCESS_BWD, KID_DEBUG, KID_TILE_ORDER, KID_RADS_MINMAX, KID_RADS_COUNT, KID_RADS_SCAN,
   KID_RADS_EMIT, KID_RADS_SELECT, KID_RADS_DRAW, KID_RADS_KNN, KID_COUNT
 };

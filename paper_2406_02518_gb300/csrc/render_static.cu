@@ -42,9 +42,8 @@ constexpr size_t kOffKeys0 = align256(kOffBlkOffset + kMaxBlocks * sizeof(uint64
 constexpr size_t kOffKeys1 = align256(kOffKeys0 + kMaxPairs * sizeof(uint64_t));
 constexpr size_t kOffVals0 = align256(kOffKeys1 + kMaxPairs * sizeof(uint64_t));
 constexpr size_t kOffVals1 = align256(kOffVals0 + kMaxPairs * sizeof(uint32_t));
-constexpr size_t kOffHist = align256(kOffVals1 + kMaxPairs * sizeof(uint32_t));
-constexpr size_t kOffDigit = align256(kOffHist + kMaxSortBlocks * ddgs::RADIX * sizeof(uint32_t));
-constexpr size_t kOffRanges = align256(kOffDigit + ddgs::RADIX * sizeof(uint32_t));
+constexpr size_t kOffLookback = align256(kOffVals1 + kMaxPairs * sizeof(uint32_t));
+constexpr size_t kOffRanges = align256(kOffLookback + kMaxSortBlocks * ddgs::RADIX * sizeof(uint64_t));
 constexpr size_t kOffPairs = align256(kOffRanges + kMaxTiles * sizeof(uint2));
 constexpr size_t kOffStatus = align256(kOffPairs + sizeof(uint64_t));
 constexpr size_t kOffOrder = align256(kOffStatus + sizeof(int32_t));
@@ -166,8 +165,7 @@ extern "C" ddgs_status ddgs_render_static(const ddgs_gaussians *g, const ddgs_vi
   ws.keys[1] = reinterpret_cast<uint64_t *>(base + kOffKeys1);
   ws.vals[0] = reinterpret_cast<uint32_t *>(base + kOffVals0);
   ws.vals[1] = reinterpret_cast<uint32_t *>(base + kOffVals1);
-  ws.hist = reinterpret_cast<uint32_t *>(base + kOffHist);
-  ws.digit_total = reinterpret_cast<uint32_t *>(base + kOffDigit);
+  ws.lookback = reinterpret_cast<uint64_t *>(base + kOffLookback);
   ws.ranges = reinterpret_cast<uint2 *>(base + kOffRanges);
   ws.d_pairs = reinterpret_cast<uint64_t *>(base + kOffPairs);
   ws.d_status = reinterpret_cast<int32_t *>(base + kOffStatus);
