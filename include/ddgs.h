@@ -323,6 +323,15 @@ ddgs_status ddgs_debug_binning(const ddgs_workspace *ws, uint32_t *tiles_touched
  * kernels since the last call (DDGS_OK, DDGS_ERR_CAPACITY, DDGS_ERR_TIMEOUT). */
 ddgs_status ddgs_sync_status(ddgs_workspace *ws, void *stream);
 
+/* Test hook of the radix sort's bounded waits (no counterpart in the paper).
+ * The sort's passes take tiles of keys in order and each waits, with an
+ * iteration limit, for the digit counts of the tiles before it. With tile >= 0,
+ * the block holding that tile never publishes its counts. Later tiles then
+ * wait until the limit, the sort latches DDGS_ERR_TIMEOUT (read with
+ * ddgs_sync_status) and that render's binning is wrong, but its writes stay
+ * in bounds. -1 (the default) turns the hook off. Host only. */
+ddgs_status ddgs_debug_withhold_tile(ddgs_workspace *ws, int32_t tile);
+
 /* Floats of a cloud: n * (3 + 4 + 3 + 1 + k) + k + k_L * k, i.e. 19 per
  * Gaussian and a 32-float shared basis at k = 8, L = 1 (Sec. 4.2). Host only. */
 int64_t ddgs_parameter_count(int64_t n, int32_t k, int32_t L);

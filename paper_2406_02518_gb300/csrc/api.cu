@@ -778,6 +778,12 @@ ddgs_status ddgs_l1_loss(const float *image, const float *target, int32_t target
   return DDGS_OK;
 }
 
+ddgs_status ddgs_debug_withhold_tile(ddgs_workspace *ws, int32_t tile) {
+  if (!ws || tile < -1) return DDGS_ERR_INVALID_ARG;
+  ws->debug_withhold_tile = tile;
+  return DDGS_OK;
+}
+
 ddgs_status ddgs_sync_status(ddgs_workspace *ws, void *stream) {
   if (!ws) return DDGS_ERR_INVALID_ARG;
   cudaStream_t s_ = static_cast<cudaStream_t>(stream);

@@ -180,6 +180,7 @@ struct ddgs_workspace {
   uint32_t *vals[2] = {nullptr, nullptr};
   ddgs::SortState *sort_state = nullptr;  // device: which buffer holds the sorted pairs
   int sort_passes = 0;           // passes of the last sort: the result is cur[sort_passes]
+  int32_t debug_withhold_tile = -1;  // test hook of the sort's bounded look-back waits
   uint64_t *lookback = nullptr;  // [sort tiles][RADIX] look-back words of the running pass
   uint2 *ranges = nullptr;       // [tiles]
   uint32_t *order = nullptr;     // [tiles] work order of the persistent rasterisers

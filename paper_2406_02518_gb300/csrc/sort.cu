@@ -191,7 +191,8 @@ constexpr size_t DS_DYN_SMEM = SORT_TILE * (sizeof(uint64_t) + sizeof(uint32_t))
 
 __global__ void __launch_bounds__(SORT_THREADS) radix_pass_kernel(
     uint64_t *keys0, uint32_t *vals0, uint64_t *keys1, uint32_t *vals1, const uint64_t *d_pairs,
-    uint64_t cap, int shift, int pass, SortState *ss, uint64_t *lookback, int32_t *status) {
+    uint64_t cap, int shift, int pass, SortState *ss, uint64_t *lookback, int32_t *status,
+    int32_t withhold) {
   if ((ss->skip >> pass) & 1u) return;  // block-uniform
   extern __shared__ __align__(16) unsigned char ds_smem[];
   uint64_t *s_keys = reinterpret_cast<uint64_t *>(ds_smem);
@@ -234,7 +235,9 @@ __global__ void __launch_bounds__(SORT_THREADS) radix_pass_kernel(
     if (wid * DS_SEG + r * 32 + lane < count) atomicAdd(&s_hist[(key[r] >> shift) & (RADIX - 1)], 1u);
   __syncthreads();
   uint64_t *mine = lookback + (uint64_t)tile * RADIX + tid;
-  atomicExch(reinterpret_cast<unsigned long long *>(mine), (tile == 0 ? LB_PREFIX : LB_AGG) | s_hist[tid]);
+  const bool publish = (int64_t)tile != (int64_t)withhold;  // test hook: withhold = -1
+  if (publish)
+    atomicExch(reinterpret_cast<unsigned long long *>(mine), (tile == 0 ? LB_PREFIX : LB_AGG) | s_hist[tid]);
 #pragma unroll
   for (int r = 0; r < SORT_ITEMS; ++r) {
     const int li = wid * DS_SEG + r * 32 + lane;
@@ -292,7 +295,7 @@ __global__ void __launch_bounds__(SORT_THREADS) radix_pass_kernel(
         __nanosleep(32);
       }
     }
-    atomicExch(reinterpret_cast<unsigned long long *>(mine), LB_PREFIX | (excl + run));
+    if (publish) atomicExch(reinterpret_cast<unsigned long long *>(mine), LB_PREFIX | (excl + run));
   }
   uint32_t inc = run;
 #pragma unroll
@@ -403,7 +406,7 @@ void launch_radix_sort(const RenderShape &s, uint64_t pair_bound, ddgs_workspace
     LaunchScope ls(KID_RADIX_PASS, st);
     radix_pass_kernel<<<(unsigned)nblk, SORT_THREADS, DS_DYN_SMEM, st>>>(
         ws.keys[0], ws.vals[0], ws.keys[1], ws.vals[1], ws.d_pairs, (uint64_t)ws.pair_cap,
-        p * RADIX_BITS, p, ws.sort_state, ws.lookback, ws.d_status);
+        p * RADIX_BITS, p, ws.sort_state, ws.lookback, ws.d_status, ws.debug_withhold_tile);
   }
   ws.sort_passes = passes;
 }
