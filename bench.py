@@ -117,9 +117,9 @@ class Clocks:
 TRAFFIC = {
     "raster_bwd": {
         "sources_sha256": {"raster.cu": "7f3925f559a8d20d1227736a48b433f3455802c4e693fc388bfaeaa8565859ca",
-                           "ddgs_internal.cuh": "2bfbdd727ef2a53bfab1c85f75c74e10e12e758e455c51877001dee4f514857b"},
+                           "ddgs_internal.cuh": "b073281dd4262621b65c42bbee2253eee7c6efc36071e341d51a858465ac7332"},
         "tile": 8, "batch_depth": 32, "views": 64, "gaussians": 500_000,
-        "bytes_per_launch": 2460.0e6 + 579.1e6,
+        "bytes_per_launch": 2460.0e6 + 579.5e6,
         "how": "one-pass ncu capture of the 64-pose step; profiles/launches_registration_500k_64x256.md",
     },
 }
