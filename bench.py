@@ -277,12 +277,11 @@ def algorithmic_bytes(kernel, s):
     """Algorithmic DRAM bytes per launch of an HBM-bound kernel."""
     M, N, V = s["pairs"], s["n"], s["views"]
     return {
-        "radix_pass": 24 * M,               # read + write 8 B key + 4 B value
-        "radix_hist": 8 * M,                # read keys once for every pass's histogram
-        "emit_keys": 16 * N * V + 12 * M,   # read binning record, write key + value
+        "bin_count": 16 * N * V,            # read binning record
+        "bin_scatter": 16 * N * V + 8 * M,  # read binning record, write (depth, index)
+        "bin_sort": 12 * M,                 # read (depth, index), write index
         "preprocess_fwd": 76 * N + 48 * N * V,  # read params once, write 48 B records
         "preprocess_bwd": 76 * N + 32 * N * V,  # read params once, read 2D gradients
-        "tile_ranges": 8 * M,
     }.get(kernel)
 
 

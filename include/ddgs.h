@@ -48,7 +48,7 @@ typedef enum {
   DDGS_ERR_INVALID_ARG = 1,   /* a null pointer, negative size, bad tile ... */
   DDGS_ERR_CAPACITY = 2,      /* no-sync mode: pairs exceeded the reserved capacity */
   DDGS_ERR_NONFINITE = 3,     /* reserved */
-  DDGS_ERR_TIMEOUT = 4,       /* a bounded device wait gave up */
+  DDGS_ERR_TIMEOUT = 4,       /* reserved: a bounded device wait gave up */
   DDGS_ERR_CUDA = 5,          /* a CUDA runtime call failed (see ddgs_last_cuda_error) */
   DDGS_ERR_UNSUPPORTED = 6,   /* e.g. no sm_103 device */
   DDGS_ERR_OUT_OF_MEMORY = 7  /* workspace growth failed */
@@ -122,7 +122,7 @@ typedef struct {
 
 typedef struct ddgs_workspace ddgs_workspace;
 
-/* Workspace: per-(view, Gaussian) projections, sort buffers, tile ranges,
+/* Workspace: per-(view, Gaussian) projections, tile lists and their counters,
  * request/view tables and the device status word, on the device that is
  * current at creation. Owned by the library between create and destroy. One
  * workspace serves one render at a time; ddgs_render_backward reads what the
@@ -162,7 +162,8 @@ ddgs_status ddgs_workspace_reserve(ddgs_workspace *ws, int64_t records,
  *   t_final transmittance after the last Gaussian added
  *   n_last  1 + position, in the pixel's tile list, of the last Gaussian
  *           added (0 if none); needed by the backward pass.
- * Synchronises the stream once (to size the sort) unless cfg->no_sync. */
+ * Synchronises the stream once (to size the tile lists) unless cfg->no_sync.
+ * Pairs are limited to 2^31 - 1 per render (DDGS_ERR_CAPACITY beyond). */
 ddgs_status ddgs_render(const ddgs_gaussians *g, const ddgs_views *v,
                         const ddgs_config *cfg, ddgs_workspace *ws,
                         float *image, float *t_final, uint32_t *n_last,
@@ -320,17 +321,10 @@ ddgs_status ddgs_debug_binning(const ddgs_workspace *ws, uint32_t *tiles_touched
                                void *stream);
 
 /* Synchronise the stream, then return and clear the status latched by
- * kernels since the last call (DDGS_OK, DDGS_ERR_CAPACITY, DDGS_ERR_TIMEOUT). */
+ * kernels since the last call (DDGS_OK, or DDGS_ERR_CAPACITY when a no_sync
+ * render had more pairs than the reserved capacity: the tile lists that did
+ * not fit were left empty). */
 ddgs_status ddgs_sync_status(ddgs_workspace *ws, void *stream);
-
-/* Test hook of the radix sort's bounded waits (no counterpart in the paper).
- * The sort's passes take tiles of keys in order and each waits, with an
- * iteration limit, for the digit counts of the tiles before it. With tile >= 0,
- * the block holding that tile never publishes its counts. Later tiles then
- * wait until the limit, the sort latches DDGS_ERR_TIMEOUT (read with
- * ddgs_sync_status) and that render's binning is wrong, but its writes stay
- * in bounds. -1 (the default) turns the hook off. Host only. */
-ddgs_status ddgs_debug_withhold_tile(ddgs_workspace *ws, int32_t tile);
 
 /* Floats of a cloud: n * (3 + 4 + 3 + 1 + k) + k + k_L * k, i.e. 19 per
  * Gaussian and a 32-float shared basis at k = 8, L = 1 (Sec. 4.2). Host only. */

@@ -31,8 +31,7 @@ EXPORTS = ["ddgs_workspace_create", "ddgs_workspace_destroy", "ddgs_workspace_re
            "ddgs_status_string", "ddgs_last_cuda_error", "ddgs_device_supported",
            "ddgs_kernel_launches", "ddgs_profiler_enable", "ddgs_profiler_collect",
            "ddgs_profiler_kernel_name", "ddgs_render_static", "ddgs_render_batched",
-           "ddgs_render_batched_backward", "ddgs_request_times", "ddgs_rads",
-           "ddgs_debug_withhold_tile"]
+           "ddgs_render_batched_backward", "ddgs_request_times", "ddgs_rads"]
 
 
 class DDGSError(RuntimeError):
@@ -113,7 +112,6 @@ def load(path: Optional[str] = None):
     lib.ddgs_render_batched_backward.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
     lib.ddgs_request_times.argtypes = [vp, vp, vp, vp]
     lib.ddgs_rads.argtypes = [vp, i32, i32, C.c_uint64, vp, vp, vp, vp, vp, vp, vp]
-    lib.ddgs_debug_withhold_tile.argtypes = [vp, i32]
     lib.ddgs_kernel_launches.restype = i64
     lib.ddgs_profiler_enable.argtypes = [i32]
     lib.ddgs_profiler_collect.argtypes = [i32, vp, vp, vp]
@@ -591,8 +589,3 @@ def rads(hu: torch.Tensor, spacing, origin, n1: int = 15000, n2: int = 10000, se
         out["draw_voxels"] = draws[:m2]
     return out
 
-
-def debug_withhold_tile(ws: Workspace, tile: int):
-    """Test hook: the sort's block holding `tile` withholds its look-back counts
-    (-1 turns it off); later waits run out and the render reports a timeout."""
-    _check(load().ddgs_debug_withhold_tile(ws.handle, int(tile)), "ddgs_debug_withhold_tile")

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libddgs.so")
-SOURCES = ["api.cu", "preprocess.cu", "sort.cu", "raster.cu", "render_static.cu", "rads.cu"]
+SOURCES = ["api.cu", "preprocess.cu", "bin.cu", "raster.cu", "render_static.cu", "rads.cu"]
 HEADERS = ["ddgs_internal.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

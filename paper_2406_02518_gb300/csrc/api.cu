@@ -43,12 +43,6 @@ ddgs_status grow(Tp *&p, int64_t &cap_field, int64_t need, int64_t cur_cap, size
   return DDGS_OK;
 }
 
-int bits_for(uint64_t x) {  // bits needed to represent values 0..x
-  int b = 0;
-  while (x) { ++b; x >>= 1; }
-  return b;
-}
-
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 ddgs_status check_inputs(const ddgs_gaussians *g, const ddgs_views *v, const ddgs_config *c) {
@@ -138,7 +132,7 @@ ddgs_status make_layout(int32_t R, const int64_t *n, const int64_t *n_iso, const
   ddgs::RenderShape &s = L.shape;
   s.R = R; s.V = v; s.tile = tile;
   s.n_total = g; s.total_tiles = tiles; s.records = recs; s.pixels = pix; s.n_blocks = blk;
-  s.key_bits = 32 + bits_for(tiles > 0 ? (uint64_t)(tiles - 1) : 0);
+  ddgs::plan_binning(L.view.data(), v, L.req.data(), tiles, tile, s);
   L.hash = h ? h : 1;
   return DDGS_OK;
 }
@@ -196,6 +190,17 @@ ddgs_status upload_layout(ddgs_workspace *ws, Layout &L, bool no_sync, cudaStrea
   return DDGS_OK;
 }
 
+// Sort queues of the binning: sized by the tile and pair capacities.
+ddgs_status ensure_lists(ddgs_workspace *ws) {
+  const int64_t need = ddgs::list_capacity(ws->tile_cap, ws->pair_cap);
+  if (need <= ws->list_cap && ws->lists) return DDGS_OK;
+  const int64_t cap = need + need / 4;
+  ddgs_status st = grow(ws->lists, ws->list_cap, cap, 0, sizeof(uint64_t));
+  if (st) return st;
+  ws->list_cap = cap;
+  return DDGS_OK;
+}
+
 ddgs_status ensure_records(ddgs_workspace *ws, const ddgs::RenderShape &s) {
   const int64_t blk = s.n_blocks;
   if (s.records > ws->rec_cap || !ws->rec) {
@@ -216,7 +221,6 @@ ddgs_status ensure_records(ddgs_workspace *ws, const ddgs::RenderShape &s) {
     int64_t cap = blk + blk / 4 + 64;
     ddgs_status st;
     if ((st = grow(ws->blk_total, ws->blk_cap, cap, 0, sizeof(uint32_t)))) return st;
-    if ((st = grow(ws->blk_offset, ws->blk_cap, cap, 0, sizeof(uint64_t)))) return st;
     ws->blk_cap = cap;
   }
   if (s.total_tiles > ws->tile_cap || !ws->ranges) {
@@ -224,24 +228,29 @@ ddgs_status ensure_records(ddgs_workspace *ws, const ddgs::RenderShape &s) {
     ddgs_status st;
     if ((st = grow(ws->ranges, ws->tile_cap, cap, 0, sizeof(uint2)))) return st;
     if ((st = grow(ws->order, ws->tile_cap, cap, 0, sizeof(uint32_t)))) return st;
+    int64_t pc = 0;  // the part sums follow the tiles
+    if ((st = grow(ws->part, pc, ddgs::part_capacity(cap), 0, sizeof(uint64_t)))) return st;
     ws->tile_cap = cap;
   }
-  return DDGS_OK;
+  if (s.hist_slots > ws->hist_cap || !ws->hist) {
+    int64_t cap = std::max<int64_t>(s.hist_slots + s.hist_slots / 4, 1024);
+    ddgs_status st;
+    if ((st = grow(ws->hist, ws->hist_cap, cap, 0, sizeof(uint32_t)))) return st;
+    ws->hist_cap = cap;
+  }
+  return ensure_lists(ws);
 }
 
 ddgs_status ensure_pairs(ddgs_workspace *ws, int64_t pairs) {
+  if (pairs > ddgs::BIN_MAX_PAIRS) return DDGS_ERR_CAPACITY;
   if (pairs <= ws->pair_cap && ws->keys[0]) return DDGS_OK;
-  int64_t cap = pairs + pairs / 4 + 4096;
+  const int64_t cap = std::min<int64_t>(pairs + pairs / 4 + 4096, ddgs::BIN_MAX_PAIRS);
   ddgs_status st;
-  for (int b = 0; b < 2; ++b) {
+  for (int b = 0; b < 2; ++b)
     if ((st = grow(ws->keys[b], ws->pair_cap, cap, 0, sizeof(uint64_t)))) return st;
-    if ((st = grow(ws->vals[b], ws->pair_cap, cap, 0, sizeof(uint32_t)))) return st;
-  }
-  const int64_t sb = ddgs::sort_blocks((uint64_t)cap);
-  if ((st = grow(ws->lookback, ws->sblk_cap, sb * ddgs::RADIX, 0, sizeof(uint64_t)))) return st;
-  ws->sblk_cap = sb;
+  if ((st = grow(ws->vals, ws->pair_cap, cap, 0, sizeof(uint32_t)))) return st;
   ws->pair_cap = cap;
-  return DDGS_OK;
+  return ensure_lists(ws);
 }
 
 // ---- launch counter and event profiler ----
@@ -255,8 +264,8 @@ struct ProfRec {
 std::vector<ProfRec> g_pending;
 std::vector<cudaEvent_t> g_pool;
 const char *const KERNEL_NAMES[ddgs::KID_COUNT] = {
-    "preprocess_fwd", "scan_blocks", "emit_keys", "radix_hist", "radix_plan",
-    "radix_pass", "tile_ranges", "raster_fwd", "l1_loss", "raster_bwd",
+    "preprocess_fwd", "scan_blocks", "bin_count", "bin_offsets", "bin_scatter",
+    "bin_sort", "bin_merge", "raster_fwd", "l1_loss", "raster_bwd",
     "preprocess_bwd", "debug_copy", "tile_order", "rads_minmax", "rads_count", "rads_scan",
     "rads_emit", "rads_select", "rads_draw", "rads_knn"};
 
@@ -382,8 +391,7 @@ ddgs_status ddgs_workspace_create(ddgs_workspace **out) {
       (e = cudaMalloc(&ws->d_pairs, sizeof(uint64_t))) != cudaSuccess ||
       (e = cudaMalloc(&ws->d_status, sizeof(int32_t))) != cudaSuccess ||
       (e = cudaMalloc(&ws->queue, 2 * sizeof(uint32_t))) != cudaSuccess ||
-      (e = cudaMalloc(&ws->sort_state, sizeof(ddgs::SortState))) != cudaSuccess ||
-      (e = cudaMemset(ws->sort_state, 0, sizeof(ddgs::SortState))) != cudaSuccess ||
+      (e = cudaMalloc(&ws->list_count, ddgs::LIST_CLASSES * sizeof(uint32_t))) != cudaSuccess ||
       (e = cudaHostAlloc(&ws->h_pairs, sizeof(uint64_t), cudaHostAllocDefault)) != cudaSuccess ||
       (e = cudaMemset(ws->d_status, 0, sizeof(int32_t))) != cudaSuccess ||
       (e = cudaMemset(ws->d_pairs, 0, sizeof(uint64_t))) != cudaSuccess) {
@@ -396,8 +404,8 @@ ddgs_status ddgs_workspace_create(ddgs_workspace **out) {
     ddgs_workspace_destroy(ws);
     return DDGS_ERR_OUT_OF_MEMORY;
   }
-  if ((e = ddgs::prepare_sort_kernels()) != cudaSuccess) {
-    ddgs_status st = cuda_fail(e, "sort kernel set-up");
+  if ((e = ddgs::prepare_bin_kernels()) != cudaSuccess) {
+    ddgs_status st = cuda_fail(e, "binning kernel set-up");
     ddgs_workspace_destroy(ws);
     return st;
   }
@@ -408,9 +416,9 @@ ddgs_status ddgs_workspace_create(ddgs_workspace **out) {
 ddgs_status ddgs_workspace_destroy(ddgs_workspace *ws) {
   if (!ws) return DDGS_OK;
   void *dev[] = {ws->rec, ws->rect, ws->tiles_touched, ws->grad2d, ws->blk_total,
-                 ws->blk_offset, ws->keys[0], ws->keys[1], ws->vals[0], ws->vals[1], ws->lookback,
-                 ws->ranges, ws->d_pairs, ws->d_status, ws->d_req, ws->d_view,
-                 ws->order, ws->queue, ws->sort_state, ws->req_time, ws->rec2, ws->grad_h,
+                 ws->keys[0], ws->keys[1], ws->vals, ws->hist, ws->part, ws->lists,
+                 ws->list_count, ws->ranges, ws->d_pairs, ws->d_status, ws->d_req, ws->d_view,
+                 ws->order, ws->queue, ws->req_time, ws->rec2, ws->grad_h,
                  ws->rads_keys, ws->rads_buf};
   for (void *p : dev)
     if (p) cudaFree(p);
@@ -430,6 +438,7 @@ ddgs_status ddgs_workspace_reserve(ddgs_workspace *ws, int64_t records, int64_t 
   // preprocess blocks (one partial block per request, up to 4096 requests)
   s.n_blocks = records / ddgs::PRE_THREADS + 4096;
   s.total_tiles = tiles;
+  s.hist_slots = ddgs::hist_slot_bound(tiles);
   ddgs_status st = ensure_records(ws, s);
   if (st) return st;
   st = ensure_pairs(ws, pairs);
@@ -453,7 +462,8 @@ ddgs_status render_common(const ddgs_gaussians &g, const ddgs_views &v, const dd
   ddgs::RenderShape &s = L.shape;
   if (c->no_sync) {
     if (s.records > ws->rec_cap || s.n_blocks > ws->blk_cap || s.total_tiles > ws->tile_cap ||
-        !ws->keys[0])
+        s.hist_slots > ws->hist_cap || !ws->keys[0] ||
+        ddgs::list_capacity(s.total_tiles, ws->pair_cap) > ws->list_cap)
       return DDGS_ERR_CAPACITY;
     if (g.per_pixel && (!ws->rec2 || ws->pix_cap < s.records)) return DDGS_ERR_CAPACITY;
   } else {
@@ -481,23 +491,17 @@ ddgs_status render_common(const ddgs_gaussians &g, const ddgs_views &v, const dd
     if (!c->no_sync) {
       CK(cudaStreamSynchronize(s_));
       bound = *ws->h_pairs;
-      if (bound >= (uint64_t(1) << 32) - 1) return DDGS_ERR_CAPACITY;
+      if (bound > (uint64_t)ddgs::BIN_MAX_PAIRS) return DDGS_ERR_CAPACITY;
       if ((st = ensure_pairs(ws, (int64_t)bound))) return st;
     } else {
       bound = (uint64_t)ws->pair_cap;
-    }
-    if (bound > 0) {
-      ddgs::launch_emit_keys(s, *ws, s_);
-      CK(cudaGetLastError());
-      ddgs::launch_radix_sort(s, bound, *ws, s_);
-      CK(cudaGetLastError());
     }
   } else {
     *ws->h_pairs = 0;
     CK(cudaMemsetAsync(ws->d_pairs, 0, sizeof(uint64_t), s_));
   }
   if (s.total_tiles > 0) {
-    ddgs::launch_tile_ranges(s, bound, *ws, s_);
+    ddgs::launch_binning(s, bound, *ws, s_);
     CK(cudaGetLastError());
     ddgs::launch_tile_order(s, *ws, s_);
     CK(cudaGetLastError());
@@ -696,6 +700,18 @@ __global__ void tiles_touched_kernel(const uint4 *info, int64_t n, uint32_t *out
     out[j] = info[j].w;
 }
 
+// The sort key (global tile << 32 | depth bits) of every list entry, one
+// thread per tile writing its list's keys.
+__global__ void list_keys_kernel(ddgs::RenderShape s, const uint2 *ranges, const uint32_t *vals,
+                                 const uint4 *info, uint64_t *keys) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < s.total_tiles;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const uint2 r = ranges[t];
+    const ddgs::ViewTab vt = s.view[ddgs::find_view(s.view, s.V, t)];
+    for (uint32_t j = r.x; j < r.y; ++j) keys[j] = ((uint64_t)t << 32) | info[vt.rec_off + vals[j]].z;
+  }
+}
+
 __global__ void l1_loss_kernel(const float *image, const float *target, int per_view, int64_t hw,
                                float *loss, float *grad) {
   // one block row per view: blockIdx.y = view
@@ -752,15 +768,15 @@ ddgs_status ddgs_debug_binning(const ddgs_workspace *ws, uint32_t *tiles_touched
   }
   uint64_t m = *ws->h_pairs;
   if (m > (uint64_t)ws->pair_cap) m = (uint64_t)ws->pair_cap;  // after an overflow
-  int32_t sorted = 0;  // the sort's result buffer, decided on the device
-  if ((keys || vals) && m) {
-    CK(cudaMemcpyAsync(&sorted, ws->sort_state->cur + ws->sort_passes, sizeof(int32_t),
-                       cudaMemcpyDeviceToHost, s_));
-    CK(cudaStreamSynchronize(s_));
-    sorted = sorted ? 1 : 0;
+  if (keys && m && s.total_tiles > 0) {
+    int64_t b = (s.total_tiles + 255) / 256;
+    if (b > 4096) b = 4096;
+    ddgs::LaunchScope ls(ddgs::KID_DEBUG, s_);
+    list_keys_kernel<<<(unsigned)b, 256, 0, s_>>>(s, ws->ranges, ws->vals,
+                                                  reinterpret_cast<const uint4 *>(ws->rect), keys);
+    CK(cudaGetLastError());
   }
-  if (keys && m) CK(cudaMemcpyAsync(keys, ws->keys[sorted], m * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s_));
-  if (vals && m) CK(cudaMemcpyAsync(vals, ws->vals[sorted], m * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s_));
+  if (vals && m) CK(cudaMemcpyAsync(vals, ws->vals, m * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s_));
   if (ranges && s.total_tiles)
     CK(cudaMemcpyAsync(ranges, ws->ranges, (size_t)s.total_tiles * sizeof(uint2), cudaMemcpyDeviceToDevice, s_));
   return DDGS_OK;
@@ -775,12 +791,6 @@ ddgs_status ddgs_l1_loss(const float *image, const float *target, int32_t target
   CK(cudaMemsetAsync(loss, 0, (size_t)n_views * sizeof(float), s_));
   ddgs::launch_l1_loss(image, target, target_per_view, n_views, hw, loss, dL_dimage, s_);
   CK(cudaGetLastError());
-  return DDGS_OK;
-}
-
-ddgs_status ddgs_debug_withhold_tile(ddgs_workspace *ws, int32_t tile) {
-  if (!ws || tile < -1) return DDGS_ERR_INVALID_ARG;
-  ws->debug_withhold_tile = tile;
   return DDGS_OK;
 }
 

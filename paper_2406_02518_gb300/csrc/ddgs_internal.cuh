@@ -13,11 +13,15 @@ namespace ddgs {
 constexpr int K = DDGS_FEAT_DIM;          // features per Gaussian
 constexpr int PRE_THREADS = 256;          // Gaussians per preprocess block
 constexpr int VIEW_CHUNK = 64;            // views staged in shared memory at once
-constexpr int SORT_THREADS = 256;
-constexpr int SORT_ITEMS = 16;            // keys per thread per radix tile
-constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
-constexpr int RADIX_BITS = 8;
-constexpr int RADIX = 1 << RADIX_BITS;
+// Binning (bin.cu): blocks of Gaussians of one view count and place their
+// pairs with per-tile counters in shared memory, over bands of at most
+// BIN_HIST_MAX tiles; every tile list is then ordered in shared memory.
+constexpr int BIN_HIST_MAX = 8192;           // tiles of one band
+constexpr int64_t BIN_TARGET_ITEMS = 608;    // binning blocks aimed for (4 per SM)
+constexpr int64_t BIN_MIN_CHUNK = 1024;      // Gaussians per binning block, at least
+constexpr int64_t BIN_SLOT_BUDGET = int64_t(1) << 21;  // per-block tile counters of a render
+constexpr int BIN_LIST_LONG = 8192;          // longest list ordered by one block at once
+constexpr int64_t BIN_MAX_PAIRS = (int64_t(1) << 31) - 1;  // offsets leave bit 31 free
 constexpr float SH_C1 = 0.48860251190291992f;  // sqrt(3 / (4 pi))
 
 // Device status bits (latched in the workspace).
@@ -43,6 +47,11 @@ struct ViewTab {
   int64_t rec_off;    // first (view, Gaussian) record of the view
   int64_t img_off;    // first pixel of the view in the concatenated images
   int32_t req, H, W, tiles_x;
+  // binning: (band, chunk) blocks of the view, and their tile counters
+  int64_t item_base;  // first binning block of the view
+  int64_t hist_base;  // first tile counter of the view
+  int32_t chunks;     // Gaussian chunks (0 for an empty request)
+  int32_t band_w, band_h, bands_x;  // bands of band_w x band_h tiles, row-major
 };
 
 // Per-view constants staged in shared memory by the preprocess kernels
@@ -56,17 +65,13 @@ struct ViewConst {
   int64_t tile_base, rec_off;
 };
 
-// Device-side state of one radix sort. A pass whose digit is the same in
-// every key leaves the order unchanged and is skipped (found from the digit
-// histograms of the prepass), so the buffer holding the keys before each pass
-// is tracked on the device: consumers read cur[passes].
-constexpr int MAX_SORT_PASSES = 8;  // 64-bit keys, 8-bit digits
-struct SortState {
-  uint32_t hist[MAX_SORT_PASSES][RADIX];  // keys per digit value, per pass
-  uint32_t off[MAX_SORT_PASSES][RADIX];   // first output position of each digit value
-  uint32_t ticket[MAX_SORT_PASSES];       // next tile of each pass
-  uint32_t skip;                          // bit p: pass p is skipped
-  int32_t cur[MAX_SORT_PASSES + 1];       // buffer (0 / 1) holding the keys before pass p
+// Tile lists sorted by the binning, by length class: 2 to 32 entries (one
+// warp), up to 2048, up to BIN_LIST_LONG (one block each; longer lists are
+// cut into BIN_LIST_LONG-entry chunks here) and longer (chunks merged).
+enum : int { LIST_WARP = 0, LIST_SHORT, LIST_BLOCK, LIST_LONG, LIST_CLASSES };
+struct BinLists {
+  uint64_t *item[LIST_CLASSES];  // entries: global tile << 24 | chunk
+  uint32_t *count;               // device [LIST_CLASSES]
 };
 
 // Parameters shared by the rasterisers.
@@ -76,8 +81,9 @@ struct RasterParams {
 
 // Everything the kernels need about one render (passed by value).
 struct RenderShape {
-  int32_t R, V, tile, key_bits;
+  int32_t R, V, tile, hist_area;  // hist_area: largest band (tiles) of any view
   int64_t n_total, total_tiles, records, pixels, n_blocks;
+  int64_t n_items, hist_slots;    // binning blocks and their tile counters
   const ReqTab *req;    // device [R + 1]
   const ViewTab *view;  // device [V + 1]
 };
@@ -90,6 +96,67 @@ __device__ __forceinline__ int find_request(const ReqTab *tab, int R, int64_t b)
     if (tab[mid].blk_base <= b) lo = mid; else hi = mid;
   }
   return lo;
+}
+
+// Largest v with tab[v].item_base <= i: the view of binning block i (views
+// without blocks share their successor's item_base and are skipped).
+__device__ __forceinline__ int find_item_view(const ViewTab *tab, int V, int64_t i) {
+  int lo = 0, hi = V;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (tab[mid].item_base <= i) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Binning blocks of a layout (host): every view's Gaussians are cut into
+// chunks (about BIN_TARGET_ITEMS blocks in all, at least BIN_MIN_CHUNK
+// Gaussians each, and at most `budget` counters beyond one per tile) and its
+// tiles into bands of at most BIN_HIST_MAX tiles (whole rows where a row
+// fits). view[V] is the sentinel; req[r].n gives each request's size.
+inline void plan_binning(ViewTab *view, int32_t V, const ReqTab *req, int64_t total_tiles,
+                         int32_t tile, RenderShape &s, int64_t budget = BIN_SLOT_BUDGET) {
+  int64_t items = 0, slots = 0;
+  int32_t area = 0;
+  const int64_t per_view = V > 0 ? (BIN_TARGET_ITEMS + V - 1) / V : 1;
+  const int64_t by_slots = total_tiles > 0 ? budget / total_tiles : 1;
+  for (int32_t v = 0; v < V; ++v) {
+    ViewTab &t = view[v];
+    const int64_t n = req[t.req].n;
+    const int64_t tx = t.tiles_x, ty = (t.H + tile - 1) / tile;
+    int64_t chunks = (n + BIN_MIN_CHUNK - 1) / BIN_MIN_CHUNK;
+    if (chunks > per_view) chunks = per_view;
+    if (chunks > by_slots) chunks = by_slots;
+    if (chunks < 1) chunks = 1;
+    if (n == 0) chunks = 0;
+    int64_t bw = tx, bh = ty;
+    if (tx * ty > BIN_HIST_MAX) {
+      if (tx <= BIN_HIST_MAX) bh = BIN_HIST_MAX / tx;
+      else { bw = BIN_HIST_MAX; bh = 1; }
+    }
+    const int64_t bands = ((tx + bw - 1) / bw) * ((ty + bh - 1) / bh);
+    t.item_base = items;
+    t.hist_base = slots;
+    t.chunks = (int32_t)chunks;
+    t.band_w = (int32_t)bw;
+    t.band_h = (int32_t)bh;
+    t.bands_x = (int32_t)((tx + bw - 1) / bw);
+    items += chunks * bands;
+    slots += chunks * bands * bw * bh;
+    if (chunks > 0 && bw * bh > area) area = (int32_t)(bw * bh);
+  }
+  view[V].item_base = items;
+  view[V].hist_base = slots;
+  view[V].chunks = 0;
+  s.n_items = items;
+  s.hist_slots = slots;
+  s.hist_area = area;
+}
+
+// Tile counters any layout with this many tiles can need: bands cover less
+// than twice a view's tiles, and chunks x tiles stays within the budget.
+inline int64_t hist_slot_bound(int64_t tiles, int64_t budget = BIN_SLOT_BUDGET) {
+  return 2 * (tiles > budget ? tiles : budget);
 }
 
 // Largest v with tab[v].tile_base <= t.
@@ -158,7 +225,7 @@ __device__ __forceinline__ bool eval_pair(float u, float v, float ca, float cb, 
 // Workspace (device memory owned by the library).
 struct ddgs_workspace {
   int device = -1;
-  int64_t rec_cap = 0, pair_cap = 0, tile_cap = 0, blk_cap = 0, sblk_cap = 0;
+  int64_t rec_cap = 0, pair_cap = 0, tile_cap = 0, blk_cap = 0, hist_cap = 0, list_cap = 0;
   // per (view, Gaussian) records
   float4 *rec = nullptr;         // [records][2]: (u, v, conic a, conic b), (conic c, alpha,
                                  // colour, packed box half-extents): one 32-byte sector
@@ -174,14 +241,14 @@ struct ddgs_workspace {
   bool last_per_pixel = false;   // mode of the last forward render
   // scan
   uint32_t *blk_total = nullptr;
-  uint64_t *blk_offset = nullptr;
-  // pairs
-  uint64_t *keys[2] = {nullptr, nullptr};
-  uint32_t *vals[2] = {nullptr, nullptr};
-  ddgs::SortState *sort_state = nullptr;  // device: which buffer holds the sorted pairs
-  int sort_passes = 0;           // passes of the last sort: the result is cur[sort_passes]
-  int32_t debug_withhold_tile = -1;  // test hook of the sort's bounded look-back waits
-  uint64_t *lookback = nullptr;  // [sort tiles][RADIX] look-back words of the running pass
+  // pairs: (depth bits << 32 | Gaussian) placed by tile, then each tile's
+  // Gaussians in depth order
+  uint64_t *keys[2] = {nullptr, nullptr};  // [pairs]; keys[1] only for merging long lists
+  uint32_t *vals = nullptr;      // [pairs] the tile lists the rasterisers read
+  uint32_t *hist = nullptr;      // [hist_cap] per (binning block, tile) counts, then offsets
+  uint64_t *part = nullptr;      // [2 x tile blocks + 2] partial sums of the tile counts
+  uint64_t *lists = nullptr;     // [list_cap] tile lists to sort, by length class
+  uint32_t *list_count = nullptr;  // [LIST_CLASSES]
   uint2 *ranges = nullptr;       // [tiles]
   uint32_t *order = nullptr;     // [tiles] work order of the persistent rasterisers
   uint32_t *queue = nullptr;     // work-queue heads of the forward / backward rasterisers
@@ -212,8 +279,8 @@ namespace ddgs {
 
 // Kernel ids of the launch counter and profiler (api.cu).
 enum KernelId : int {
-  KID_PREPROCESS_FWD = 0, KID_SCAN_BLOCKS, KID_EMIT_KEYS, KID_RADIX_HIST, KID_RADIX_PLAN,
-  KID_RADIX_PASS, KID_TILE_RANGES, KID_RASTER_FWD, KID_L1_LOSS, KID_RASTER_BWD,
+  KID_PREPROCESS_FWD = 0, KID_SCAN_BLOCKS, KID_BIN_COUNT, KID_BIN_OFFSETS, KID_BIN_SCATTER,
+  KID_BIN_SORT, KID_BIN_MERGE, KID_RASTER_FWD, KID_L1_LOSS, KID_RASTER_BWD,
   KID_PREPROCESS_BWD, KID_DEBUG, KID_TILE_ORDER, KID_RADS_MINMAX, KID_RADS_COUNT, KID_RADS_SCAN,
   KID_RADS_EMIT, KID_RADS_SELECT, KID_RADS_DRAW, KID_RADS_KNN, KID_COUNT
 };
@@ -233,19 +300,19 @@ struct LaunchScope {
 // preprocess.cu
 void launch_preprocess_fwd(const ddgs_gaussians &g, const ddgs_views &v, const ddgs_config &c,
                            const RenderShape &s, ddgs_workspace &ws, cudaStream_t st);
-void launch_emit_keys(const RenderShape &s, ddgs_workspace &ws, cudaStream_t st);
 void launch_preprocess_bwd(const ddgs_gaussians &g, const ddgs_views &v, const ddgs_config &c,
                            const RenderShape &s, ddgs_workspace &ws, const ddgs_grads &out,
                            cudaStream_t st);
 
-// sort.cu
+// bin.cu
 void launch_scan_blocks(int64_t nblk, ddgs_workspace &ws, cudaStream_t st);
-void launch_radix_sort(const RenderShape &s, uint64_t pair_bound, ddgs_workspace &ws,
-                       cudaStream_t st);
-void launch_tile_ranges(const RenderShape &s, uint64_t pair_bound, ddgs_workspace &ws,
-                        cudaStream_t st);
-int64_t sort_blocks(uint64_t pair_bound);
-cudaError_t prepare_sort_kernels();  // once per device, before any capture
+// Tile lists of the render: ranges[tile] and vals, from the records' tile
+// rectangles and depths (ws.rect); pair_bound > 0 once pairs exist.
+void launch_binning(const RenderShape &s, uint64_t pair_bound, ddgs_workspace &ws,
+                    cudaStream_t st);
+int64_t list_capacity(int64_t tiles, int64_t pairs);  // entries of ws.lists
+int64_t part_capacity(int64_t tiles);                 // entries of ws.part
+cudaError_t prepare_bin_kernels();  // once per device, before any capture
 
 // raster.cu
 // Per-pixel ray angles (Eq. 3 variant): the views' poses and detectors, and

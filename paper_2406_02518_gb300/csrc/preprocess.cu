@@ -457,107 +457,6 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_fwd_kernel(PreArgs a) 
   if (tid == 0) a.blk_total[blockIdx.x] = bt;
 }
 
-// Block-wide exclusive scan of one uint32 per thread; returns the exclusive
-// prefix and writes the block total to *total.
-__device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t *s_warp, uint32_t *total) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  uint32_t inc = x;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += y;
-  }
-  if (lane == 31) s_warp[wid] = inc;
-  __syncthreads();
-  uint32_t before = 0, all = 0;
-  for (int w = 0; w < nw; ++w) {
-    uint32_t t = s_warp[w];
-    if (w < wid) before += t;
-    all += t;
-  }
-  __syncthreads();
-  *total = all;
-  return before + inc - x;
-}
-
-struct EmitArgs {
-  RenderShape s;
-  const uint4 *bin_info;
-  const uint64_t *blk_offset;
-  uint64_t *keys;
-  uint32_t *vals;
-  uint64_t cap;
-  int32_t *status;
-};
-
-// K3: pairs in (block, view, Gaussian, tile row, tile column) order, so that
-// pairs of one view with equal keys appear in ascending Gaussian index. The
-// value is the Gaussian's index within its request. A block's pairs of one
-// view are staged in shared memory and written out by consecutive threads
-// (direct writes when they exceed the staging area); the next view's
-// records are fetched before the block-wide scan of the current one.
-constexpr int EMIT_STAGE = 2048;  // pairs of one (block, view) staged at once
-
-__global__ void __launch_bounds__(PRE_THREADS) emit_keys_kernel(EmitArgs a) {
-  __shared__ uint32_t s_warp[PRE_THREADS / 32];
-  __shared__ uint64_t s_keys[EMIT_STAGE];
-  __shared__ uint32_t s_vals[EMIT_STAGE];
-  const RenderShape &s = a.s;
-  const BlockReq br(s);
-  const ReqTab &rq = br.rq;
-  uint64_t base = a.blk_offset[blockIdx.x];
-  bool overflow = false;
-  const int v_end = rq.v_off + rq.n_views;
-  uint4 next = (br.live && rq.n_views > 0) ? a.bin_info[s.view[rq.v_off].rec_off + br.l]
-                                            : make_uint4(0, 0, 0, 0);
-  for (int v = rq.v_off; v < v_end; ++v) {
-    const ViewTab vt = s.view[v];
-    const uint4 info = next;
-    if (br.live && v + 1 < v_end) next = a.bin_info[s.view[v + 1].rec_off + br.l];
-    uint32_t total;
-    const uint32_t excl = block_excl_scan(info.w, s_warp, &total);
-    const bool staged = total <= EMIT_STAGE;
-    if (info.w) {
-      const int tx0 = info.x & 0xffff, ty0 = info.x >> 16, tx1 = info.y & 0xffff, ty1 = info.y >> 16;
-      uint32_t o = excl;
-      if (staged) {
-        for (int ty = ty0; ty <= ty1; ++ty)
-          for (int tx = tx0; tx <= tx1; ++tx) {
-            const uint64_t gt = (uint64_t)vt.tile_base + (uint64_t)ty * vt.tiles_x + tx;
-            s_keys[o] = (gt << 32) | info.z;
-            s_vals[o] = (uint32_t)br.l;
-            ++o;
-          }
-      } else if (base + excl + info.w > a.cap) {
-        overflow = true;
-      } else {
-        uint64_t off = base + excl;
-        for (int ty = ty0; ty <= ty1; ++ty)
-          for (int tx = tx0; tx <= tx1; ++tx) {
-            const uint64_t gt = (uint64_t)vt.tile_base + (uint64_t)ty * vt.tiles_x + tx;
-            a.keys[off] = (gt << 32) | info.z;
-            a.vals[off] = (uint32_t)br.l;
-            ++off;
-          }
-      }
-    }
-    if (staged) {  // block-uniform
-      __syncthreads();
-      for (uint32_t e = threadIdx.x; e < total; e += PRE_THREADS) {
-        if (base + e < a.cap) {
-          a.keys[base + e] = s_keys[e];
-          a.vals[base + e] = s_vals[e];
-        } else {
-          overflow = true;
-        }
-      }
-      __syncthreads();  // the staging area is rewritten for the next view
-    }
-    base += total;
-  }
-  if (overflow) atomicOr(a.status, ST_CAPACITY);
-}
-
 // ---------------------------------------------------------------------------
 // Backward (K8)
 // ---------------------------------------------------------------------------
@@ -1011,21 +910,6 @@ void launch_preprocess_fwd(const ddgs_gaussians &g, const ddgs_views &v, const d
       preprocess_fwd_kernel<false><<<(unsigned)s.n_blocks, PRE_THREADS, 0, st>>>(a);
     else
       preprocess_fwd_kernel<true><<<(unsigned)s.n_blocks, PRE_THREADS, 0, st>>>(a);
-  }
-}
-
-void launch_emit_keys(const RenderShape &s, ddgs_workspace &ws, cudaStream_t st) {
-  EmitArgs a;
-  a.s = s;
-  a.bin_info = reinterpret_cast<const uint4 *>(ws.rect);
-  a.blk_offset = ws.blk_offset;
-  a.keys = ws.keys[0];
-  a.vals = ws.vals[0];
-  a.cap = (uint64_t)ws.pair_cap;
-  a.status = ws.d_status;
-  if (s.n_blocks > 0) {
-    LaunchScope ls(KID_EMIT_KEYS, st);
-    emit_keys_kernel<<<(unsigned)s.n_blocks, PRE_THREADS, 0, st>>>(a);
   }
 }
 

@@ -39,8 +39,7 @@ struct RasterArgs {
   RenderShape s;
   RasterParams P;
   const float4 *rec;  // two float4 per record
-  const uint32_t *vals0, *vals1;  // sort buffers: the sorted values are in vals1 if *sorted
-  const int32_t *sorted;
+  const uint32_t *vals;  // tile lists: Gaussian indices in depth order
   const uint2 *ranges;
   float4 *grad2d;
   float *image, *t_final;
@@ -165,7 +164,7 @@ __device__ __forceinline__ void fwd_tile(const RasterArgs &a, int64_t gt, float4
   const int tid = threadIdx.x;
   const TileGeom<T> tg(a.s, gt, threadIdx.x >> 5);
   const uint2 range = a.ranges[tg.gtile];
-  const uint32_t *vals = *a.sorted ? a.vals1 : a.vals0;
+  const uint32_t *vals = a.vals;
   const int64_t rec_base = tg.rec_base;
   const float px = tg.px + 0.5f, py = tg.py + 0.5f;
   PixRay ray;
@@ -340,7 +339,7 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs &a, int64_t gt, BwdSme
   const int tid = threadIdx.x;
   const TileGeom<T> tg(a.s, gt, threadIdx.x >> 5);
   const uint2 range = a.ranges[tg.gtile];
-  const uint32_t *vals = *a.sorted ? a.vals1 : a.vals0;
+  const uint32_t *vals = a.vals;
   const int64_t rec_base = tg.rec_base;
   const float px = tg.px + 0.5f, py = tg.py + 0.5f;
   PixRay ray;
@@ -557,7 +556,7 @@ __device__ __forceinline__ void fwd_warp_item(const RasterArgs &a, int64_t gt, i
   const int lane = threadIdx.x & 31;
   const TileGeom<T> tg(a.s, gt, region);
   const uint2 range = a.ranges[tg.gtile];
-  const uint32_t *vals = *a.sorted ? a.vals1 : a.vals0;
+  const uint32_t *vals = a.vals;
   const float px = tg.px + 0.5f, py = tg.py + 0.5f;
   PixRay ray;
   if (PIX) pixel_ray(a.world_to_cam + 12 * tg.v, a.detector + 5 * tg.v, tg.H, tg.W, px, py, ray);
@@ -638,7 +637,7 @@ __device__ __forceinline__ void bwd_warp_item(const RasterArgs &a, int64_t gt, i
   const int lane = threadIdx.x & 31;
   const TileGeom<T> tg(a.s, gt, region);
   const uint2 range = a.ranges[tg.gtile];
-  const uint32_t *vals = *a.sorted ? a.vals1 : a.vals0;
+  const uint32_t *vals = a.vals;
   const float px = tg.px + 0.5f, py = tg.py + 0.5f;
   PixRay ray;
   float gY[3] = {0.f, 0.f, 0.f};
@@ -980,9 +979,7 @@ void launch_raster_fwd(const RenderShape &s, const RasterParams &p, ddgs_workspa
   a.s = s;
   a.P = p;
   a.rec = ws.rec;
-  a.vals0 = ws.vals[0];
-  a.vals1 = ws.vals[1];
-  a.sorted = ws.sort_state->cur + ws.sort_passes;
+  a.vals = ws.vals;
   a.ranges = ws.ranges;
   a.image = image;
   a.t_final = t_final;
@@ -1015,9 +1012,7 @@ void launch_raster_bwd(const RenderShape &s, const RasterParams &p, ddgs_workspa
   a.s = s;
   a.P = p;
   a.rec = ws.rec;
-  a.vals0 = ws.vals[0];
-  a.vals1 = ws.vals[1];
-  a.sorted = ws.sort_state->cur + ws.sort_passes;
+  a.vals = ws.vals;
   a.ranges = ws.ranges;
   a.grad2d = ws.grad2d;
   a.dL_dimage = dL_dimage;

@@ -8,7 +8,7 @@
 // that the library cannot see. For those callers every cudaMalloc is either
 // forbidden or a source of stalls and fragmentation, so this entry point
 // allocates nothing: the caller passes inputs and outputs, and all scratch
-// (per-(view, Gaussian) records, sort buffers, tile ranges, counters) lives in
+// (per-(view, Gaussian) records, tile lists, tile counters and ranges) lives in
 // one static array that every GPU loading the library holds until exit.
 //
 // The array is shared by every call on a device and keeps the last call's
@@ -27,7 +27,10 @@ constexpr int64_t kMaxPairs = int64_t(1) << 20;    // (Gaussian, tile) pairs
 constexpr int64_t kMaxTiles = int64_t(1) << 16;    // views x tiles per view
 constexpr int64_t kMaxViews = 1024;                // views per call
 constexpr int64_t kMaxBlocks = kMaxRecords / ddgs::PRE_THREADS + 1;
-constexpr int64_t kMaxSortBlocks = (kMaxPairs + ddgs::SORT_TILE - 1) / ddgs::SORT_TILE;
+constexpr int64_t kSlotBudget = int64_t(1) << 18;  // tile counters of the binning blocks
+constexpr int64_t kMaxSlots = 2 * (kMaxTiles > kSlotBudget ? kMaxTiles : kSlotBudget);
+constexpr int64_t kMaxParts = 2 * ((kMaxTiles + 1023) / 1024) + 2;
+constexpr int64_t kMaxListItems = ddgs::LIST_CLASSES * kMaxTiles + kMaxPairs / ddgs::BIN_LIST_LONG + 64;
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // Byte offsets of each buffer inside the scratch array.
@@ -37,18 +40,18 @@ constexpr size_t kOffInfo = align256(kOffRec1 + kMaxRecords * sizeof(float4));
 static_assert(kOffRec1 == kOffRec0 + kMaxRecords * sizeof(float4),
               "the records are one interleaved array over both regions");
 constexpr size_t kOffBlkTotal = align256(kOffInfo + kMaxRecords * sizeof(uint4));
-constexpr size_t kOffBlkOffset = align256(kOffBlkTotal + kMaxBlocks * sizeof(uint32_t));
-constexpr size_t kOffKeys0 = align256(kOffBlkOffset + kMaxBlocks * sizeof(uint64_t));
+constexpr size_t kOffKeys0 = align256(kOffBlkTotal + kMaxBlocks * sizeof(uint32_t));
 constexpr size_t kOffKeys1 = align256(kOffKeys0 + kMaxPairs * sizeof(uint64_t));
-constexpr size_t kOffVals0 = align256(kOffKeys1 + kMaxPairs * sizeof(uint64_t));
-constexpr size_t kOffVals1 = align256(kOffVals0 + kMaxPairs * sizeof(uint32_t));
-constexpr size_t kOffLookback = align256(kOffVals1 + kMaxPairs * sizeof(uint32_t));
-constexpr size_t kOffRanges = align256(kOffLookback + kMaxSortBlocks * ddgs::RADIX * sizeof(uint64_t));
+constexpr size_t kOffVals = align256(kOffKeys1 + kMaxPairs * sizeof(uint64_t));
+constexpr size_t kOffHist = align256(kOffVals + kMaxPairs * sizeof(uint32_t));
+constexpr size_t kOffPart = align256(kOffHist + kMaxSlots * sizeof(uint32_t));
+constexpr size_t kOffLists = align256(kOffPart + kMaxParts * sizeof(uint64_t));
+constexpr size_t kOffListCount = align256(kOffLists + kMaxListItems * sizeof(uint64_t));
+constexpr size_t kOffRanges = align256(kOffListCount + ddgs::LIST_CLASSES * sizeof(uint32_t));
 constexpr size_t kOffPairs = align256(kOffRanges + kMaxTiles * sizeof(uint2));
 constexpr size_t kOffStatus = align256(kOffPairs + sizeof(uint64_t));
 constexpr size_t kOffOrder = align256(kOffStatus + sizeof(int32_t));
-constexpr size_t kOffSortState = align256(kOffOrder + kMaxTiles * sizeof(uint32_t));
-constexpr size_t kOffQueue = align256(kOffSortState + sizeof(ddgs::SortState));
+constexpr size_t kOffQueue = align256(kOffOrder + kMaxTiles * sizeof(uint32_t));
 constexpr size_t kOffReq = align256(kOffQueue + 2 * sizeof(uint32_t));
 constexpr size_t kOffView = align256(kOffReq + 2 * sizeof(ddgs::ReqTab));
 constexpr size_t kScratchBytes = align256(kOffView + (kMaxViews + 1) * sizeof(ddgs::ViewTab));
@@ -57,7 +60,7 @@ constexpr size_t kScratchBytes = align256(kOffView + (kMaxViews + 1) * sizeof(dd
 thread_local ddgs::ReqTab t_req[2];
 thread_local ddgs::ViewTab t_view[kMaxViews + 1];
 
-// The scratch itself (about 37 MiB per device).
+// The scratch itself (about 31 MiB per device).
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 // Device address of g_scratch per device, looked up once per device.
@@ -127,9 +130,6 @@ extern "C" ddgs_status ddgs_render_static(const ddgs_gaussians *g, const ddgs_vi
   s.records = (int64_t)v->n_views * g->n;
   s.pixels = (int64_t)v->n_views * v->height * v->width;
   s.n_blocks = (g->n + ddgs::PRE_THREADS - 1) / ddgs::PRE_THREADS;
-  int tb = 0;
-  for (uint64_t x = s.total_tiles > 0 ? (uint64_t)(s.total_tiles - 1) : 0; x; x >>= 1) ++tb;
-  s.key_bits = 32 + tb;
   // the sizes this fixed scratch can hold
   if (s.records > kMaxRecords || s.total_tiles > kMaxTiles) return DDGS_ERR_CAPACITY;
   t_req[0] = ddgs::ReqTab{0, g->n, g->n_iso, 0, 0, 0, 0, v->n_views};
@@ -144,6 +144,7 @@ extern "C" ddgs_status ddgs_render_static(const ddgs_gaussians *g, const ddgs_vi
     t.W = v->width;
     t.tiles_x = tx;
   }
+  ddgs::plan_binning(t_view, v->n_views, t_req, s.total_tiles, tile, s, kSlotBudget);
 
   unsigned char *base = nullptr;
   ddgs_status st = scratch_for_current_device(&base);
@@ -156,20 +157,21 @@ extern "C" ddgs_status ddgs_render_static(const ddgs_gaussians *g, const ddgs_vi
   ws.pair_cap = kMaxPairs;
   ws.tile_cap = kMaxTiles;
   ws.blk_cap = kMaxBlocks;
-  ws.sblk_cap = kMaxSortBlocks;
+  ws.hist_cap = kMaxSlots;
+  ws.list_cap = kMaxListItems;
   ws.rec = reinterpret_cast<float4 *>(base + kOffRec0);  // rec0 and rec1 regions, contiguous
   ws.rect = reinterpret_cast<uint2 *>(base + kOffInfo);
   ws.blk_total = reinterpret_cast<uint32_t *>(base + kOffBlkTotal);
-  ws.blk_offset = reinterpret_cast<uint64_t *>(base + kOffBlkOffset);
   ws.keys[0] = reinterpret_cast<uint64_t *>(base + kOffKeys0);
   ws.keys[1] = reinterpret_cast<uint64_t *>(base + kOffKeys1);
-  ws.vals[0] = reinterpret_cast<uint32_t *>(base + kOffVals0);
-  ws.vals[1] = reinterpret_cast<uint32_t *>(base + kOffVals1);
-  ws.lookback = reinterpret_cast<uint64_t *>(base + kOffLookback);
+  ws.vals = reinterpret_cast<uint32_t *>(base + kOffVals);
+  ws.hist = reinterpret_cast<uint32_t *>(base + kOffHist);
+  ws.part = reinterpret_cast<uint64_t *>(base + kOffPart);
+  ws.lists = reinterpret_cast<uint64_t *>(base + kOffLists);
+  ws.list_count = reinterpret_cast<uint32_t *>(base + kOffListCount);
   ws.ranges = reinterpret_cast<uint2 *>(base + kOffRanges);
   ws.d_pairs = reinterpret_cast<uint64_t *>(base + kOffPairs);
   ws.d_status = reinterpret_cast<int32_t *>(base + kOffStatus);
-  ws.sort_state = reinterpret_cast<ddgs::SortState *>(base + kOffSortState);
   ws.order = reinterpret_cast<uint32_t *>(base + kOffOrder);
   ws.queue = reinterpret_cast<uint32_t *>(base + kOffQueue);
   ws.req_time = nullptr;
@@ -200,13 +202,9 @@ extern "C" ddgs_status ddgs_render_static(const ddgs_gaussians *g, const ddgs_vi
         cudaStreamSynchronize(cs) != cudaSuccess)
       return DDGS_ERR_CUDA;
     if (pairs > (uint64_t)kMaxPairs) return DDGS_ERR_CAPACITY;
-    if (pairs > 0) {
-      ddgs::launch_emit_keys(s, ws, cs);
-      ddgs::launch_radix_sort(s, pairs, ws, cs);
-    }
   }
   if (s.total_tiles > 0) {
-    ddgs::launch_tile_ranges(s, pairs, ws, cs);
+    ddgs::launch_binning(s, pairs, ws, cs);
     ddgs::launch_tile_order(s, ws, cs);
     ddgs::RasterParams P{c->alpha_min, c->alpha_max, c->t_min, c->q_max};
     ddgs::launch_raster_fwd(s, P, ws, image, t_final, n_last, nullptr, cs);

@@ -63,8 +63,37 @@ def _bins(ws, scene, views, st):
     return B.debug_binning(ws, views.n_views, scene.n, tiles)
 
 
+def _crowded(n, extent, seed, z_levels=None):
+    """n Gaussians packed into a small cube at the isocentre (long tile lists);
+    with z_levels the means take only those depths (many exact depth ties)."""
+    sc = syn.uniform_cloud(n, seed=seed, extent=extent, log_scale_range=(-5.0, -4.0))
+    if z_levels is not None:
+        rng = np.random.default_rng(seed + 1)
+        means = sc.means.copy()
+        means[:, 2] = np.asarray(z_levels, np.float32)[rng.integers(0, len(z_levels), n)]
+        sc = dataclasses.replace(sc, means=means)
+    return sc
+
+
+def _plane(n, seed):
+    """Means on the plane z = 0 facing the first view: every depth of that view
+    is the same, so its lists are ordered by Gaussian index alone."""
+    sc = syn.uniform_cloud(n, seed=seed)
+    means = sc.means.copy()
+    means[:, 2] = 0.0
+    return dataclasses.replace(sc, means=means)
+
+
 CASES = {
     "plain_4096_128px": lambda: syn.plain_forward_workload(),
+    # one tile of each view holds 20k pairs: chunks sorted by blocks, then merged
+    "crowded_long_lists": lambda: (_crowded(20000, 0.05, 11, z_levels=(-0.01, 0.0, 0.01)),
+                                   _two_views(48, 48, 8.0 / 48), syn.Settings(near_plane=0.2, tile=16)),
+    # lists of a few hundred to a few thousand pairs around the centre
+    "crowded_block_lists": lambda: (_crowded(12000, 0.3, 12), _two_views(64, 64, 8.0 / 64),
+                                    syn.Settings(near_plane=0.2, tile=8)),
+    "equal_depths": lambda: (_plane(3000, 13), _two_views(64, 64, 8.0 / 64),
+                             syn.Settings(near_plane=0.2, tile=16)),
     "ragged_100x75_2views": lambda: (syn.uniform_cloud(2000, seed=5), _two_views(75, 100),
                                      syn.Settings(near_plane=0.2)),
     "tile8": lambda: (syn.uniform_cloud(1500, seed=6), _two_views(41, 57, 8.0 / 50),
