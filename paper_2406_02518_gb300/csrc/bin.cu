@@ -31,6 +31,7 @@ namespace {
 constexpr int BIN_THREADS = 256;
 constexpr int SORT_SHORT = 2048;  // lists of one 256-thread block (8 entries a thread)
 constexpr int MERGE_ITEMS = 8;    // outputs per thread per merge step
+constexpr int BIN_LOADS = 4;      // records a thread loads before using them
 
 // ---------------------------------------------------------------------------
 // Exclusive scan of block totals -> offsets (optional) and the total (one block)
@@ -132,15 +133,20 @@ __global__ void __launch_bounds__(BIN_THREADS) bin_count_kernel(RenderShape s, c
   const int area = it.bw * it.bh;
   for (int p = threadIdx.x; p < area; p += BIN_THREADS) s_cnt[p] = 0;
   __syncthreads();
-  int64_t l = it.l0 + threadIdx.x;
-  uint4 nb = l < it.l1 ? info[it.rec0 + l] : make_uint4(0, 0, 0, 0);
-  for (; l < it.l1; l += BIN_THREADS) {
-    const uint4 b = nb;
-    if (l + BIN_THREADS < it.l1) nb = info[it.rec0 + l + BIN_THREADS];
-    int x0, y0, x1, y1;
-    if (!band_rect(b, it, x0, y0, x1, y1)) continue;
-    for (int y = y0; y <= y1; ++y)
-      for (int x = x0; x <= x1; ++x) atomicAdd(&s_cnt[(y - it.ty0) * it.bw + (x - it.tx0)], 1u);
+  for (int64_t l0 = it.l0 + threadIdx.x; l0 < it.l1; l0 += BIN_LOADS * BIN_THREADS) {
+    uint4 b[BIN_LOADS];
+#pragma unroll
+    for (int k = 0; k < BIN_LOADS; ++k) {
+      const int64_t l = l0 + k * BIN_THREADS;
+      b[k] = l < it.l1 ? info[it.rec0 + l] : make_uint4(0, 0, 0, 0);
+    }
+#pragma unroll
+    for (int k = 0; k < BIN_LOADS; ++k) {
+      int x0, y0, x1, y1;
+      if (!band_rect(b[k], it, x0, y0, x1, y1)) continue;
+      for (int y = y0; y <= y1; ++y)
+        for (int x = x0; x <= x1; ++x) atomicAdd(&s_cnt[(y - it.ty0) * it.bw + (x - it.tx0)], 1u);
+    }
   }
   __syncthreads();
   for (int p = threadIdx.x; p < area; p += BIN_THREADS) hist[it.slot + p] = s_cnt[p];
@@ -276,24 +282,30 @@ __global__ void __launch_bounds__(BIN_THREADS) bin_scatter_kernel(RenderShape s,
     s_cur[p] = c;
   }
   __syncthreads();
-  int64_t l = it.l0 + threadIdx.x;
-  uint4 nb = l < it.l1 ? info[it.rec0 + l] : make_uint4(0, 0, 0, 0);
-  for (; l < it.l1; l += BIN_THREADS) {
-    const uint4 b = nb;
-    if (l + BIN_THREADS < it.l1) nb = info[it.rec0 + l + BIN_THREADS];
-    int x0, y0, x1, y1;
-    if (!band_rect(b, it, x0, y0, x1, y1)) continue;
-    const uint64_t key = ((uint64_t)b.z << 32) | (uint32_t)l;
-    for (int y = y0; y <= y1; ++y)
-      for (int x = x0; x <= x1; ++x) {
-        uint32_t *cur = &s_cur[(y - it.ty0) * it.bw + (x - it.tx0)];
-        if (*cur == CUR_DROP) continue;  // never advanced, so a plain read is exact
-        const uint32_t c = atomicAdd(cur, 1u);
-        const uint32_t pos = c & ~CUR_ONE;
-        if (pos >= cap) continue;
-        if (c & CUR_ONE) vals[pos] = (uint32_t)l;
-        else keys[pos] = key;
-      }
+  for (int64_t l0 = it.l0 + threadIdx.x; l0 < it.l1; l0 += BIN_LOADS * BIN_THREADS) {
+    uint4 b[BIN_LOADS];
+#pragma unroll
+    for (int k = 0; k < BIN_LOADS; ++k) {
+      const int64_t l = l0 + k * BIN_THREADS;
+      b[k] = l < it.l1 ? info[it.rec0 + l] : make_uint4(0, 0, 0, 0);
+    }
+#pragma unroll
+    for (int k = 0; k < BIN_LOADS; ++k) {
+      int x0, y0, x1, y1;
+      if (!band_rect(b[k], it, x0, y0, x1, y1)) continue;
+      const uint32_t l = (uint32_t)(l0 + k * BIN_THREADS);
+      const uint64_t key = ((uint64_t)b[k].z << 32) | l;
+      for (int y = y0; y <= y1; ++y)
+        for (int x = x0; x <= x1; ++x) {
+          uint32_t *cur = &s_cur[(y - it.ty0) * it.bw + (x - it.tx0)];
+          if (*cur == CUR_DROP) continue;  // never advanced, so a plain read is exact
+          const uint32_t c = atomicAdd(cur, 1u);
+          const uint32_t pos = c & ~CUR_ONE;
+          if (pos >= cap) continue;
+          if (c & CUR_ONE) vals[pos] = l;
+          else keys[pos] = key;
+        }
+    }
   }
 }
 
@@ -410,10 +422,15 @@ __device__ __forceinline__ void block_digit_pass(const uint64_t *src, uint64_t *
 }
 
 // Lists (or BIN_LIST_LONG-entry chunks of longer lists) of up to NT x E
-// entries: one block each, in shared memory. Passes run over the depth bits
-// that differ within the list; only if two depths are equal is the order
-// redone with the index digits first. Whole lists write their values; chunks
-// write their sorted keys back for the merge.
+// entries: one block each, in shared memory. First a bucket sort: the top
+// bits of (depth - smallest depth) spread the entries over about as many
+// buckets as entries (shared-memory counters), and each bucket is put in
+// order by insertion on the full (depth, index) key. Where a bucket would
+// hold more than BUCKET_MAX entries (clustered or equal depths), the list is
+// sorted instead by stable 8-bit passes over the depth bits that differ in
+// it, redone with the index digits first if two depths are equal. Whole
+// lists write their values; chunks write their sorted keys back for the merge.
+constexpr uint32_t BUCKET_MAX = 24;
 template <int NT, int E, int MINB>
 __global__ void __launch_bounds__(NT, MINB) bin_sort_block_kernel(const uint64_t *items,
                                                                     const uint32_t *count,
@@ -421,9 +438,10 @@ __global__ void __launch_bounds__(NT, MINB) bin_sort_block_kernel(const uint64_t
                                                                     uint64_t *keys, uint32_t *vals) {
   constexpr int NW = NT / 32, CAP = NT * E;
   extern __shared__ __align__(16) uint64_t s_buf[];  // [2][CAP]
-  __shared__ uint32_t cnt[NW][256];
-  __shared__ uint32_t s_wsum[8];
+  __shared__ uint32_t cnt[NW][256];  // digit counters, or NW x 256 bucket counters
+  __shared__ uint32_t s_wsum[NW];
   __shared__ uint32_t s_red[4][NW];
+  uint32_t *bc = &cnt[0][0];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const uint32_t n_items = *count;
   for (uint32_t i = blockIdx.x; i < n_items; i += gridDim.x) {
@@ -459,13 +477,93 @@ __global__ void __launch_bounds__(NT, MINB) bin_sort_block_kernel(const uint64_t
       dmin = min(dmin, s_red[0][x]); dmax = max(dmax, s_red[1][x]);
       lmin = min(lmin, s_red[2][x]); lmax = max(lmax, s_red[3][x]);
     }
+    bool sorted = false;
+    if (dmin != dmax && m > 1) {
+      // buckets: 2^lg >= m of them (at least 32, at most NW x 256)
+      int lg = 32 - __clz((uint32_t)m - 1u);
+      lg = max(5, min(lg, 31 - __clz((uint32_t)(NW * 256))));
+      const int nbk = 1 << lg;
+      const int sh = max(0, (32 - __clz(dmax - dmin)) - lg);
+      for (int b = tid; b < nbk; b += NT) bc[b] = 0;
+      __syncthreads();
+      uint32_t rk[E];
+#pragma unroll
+      for (int r = 0; r < E; ++r) {
+        const int j = tid + r * NT;
+        if (j < m) rk[r] = atomicAdd(&bc[((uint32_t)(cur[j] >> 32) - dmin) >> sh], 1u);
+      }
+      __syncthreads();
+      // exclusive scan of the bucket counts (contiguous runs per thread) and
+      // the largest bucket
+      const int q = (nbk + NT - 1) / NT;
+      uint32_t loc = 0, big = 0;
+      for (int k = 0; k < q; ++k) {
+        const int b = tid * q + k;
+        if (b < nbk) {
+          const uint32_t c = bc[b];
+          loc += c;
+          big = max(big, c);
+        }
+      }
+      uint32_t inc = loc;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+        big = max(big, __shfl_xor_sync(0xffffffffu, big, o));
+      }
+      if (lane == 31) s_wsum[w] = inc;
+      if (lane == 0) s_red[0][w] = big;
+      __syncthreads();
+      uint32_t ex = inc - loc;
+      big = 0;
+      for (int x = 0; x < NW; ++x) {
+        if (x < w) ex += s_wsum[x];
+        big = max(big, s_red[0][x]);
+      }
+      for (int k = 0; k < q; ++k) {
+        const int b = tid * q + k;
+        if (b < nbk) {
+          const uint32_t c = bc[b];
+          bc[b] = ex;
+          ex += c;
+        }
+      }
+      __syncthreads();
+      if (big <= BUCKET_MAX) {  // block-uniform
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+          const int j = tid + r * NT;
+          if (j < m) {
+            const uint64_t k = cur[j];
+            oth[bc[((uint32_t)(k >> 32) - dmin) >> sh] + rk[r]] = k;
+          }
+        }
+        __syncthreads();
+        for (int b = tid; b < nbk; b += NT) {
+          const uint32_t b0 = bc[b], b1 = b + 1 < nbk ? bc[b + 1] : (uint32_t)m;
+          for (uint32_t x = b0 + 1; x < b1; ++x) {
+            const uint64_t k = oth[x];
+            uint32_t y = x;
+            while (y > b0 && oth[y - 1] > k) {
+              oth[y] = oth[y - 1];
+              --y;
+            }
+            oth[y] = k;
+          }
+        }
+        __syncthreads();
+        uint64_t *t = cur; cur = oth; oth = t;
+        sorted = true;
+      }
+    }
     const int rows_all = (m + 31) / 32;
     const int rows = (rows_all + NW - 1) / NW, seg = rows * 32;
     // depth digits first; only if two depths tie, redo with the index digits
     // below them (least significant first)
-    const int nd = dmin == dmax ? 0 : (39 - __clz(dmin ^ dmax)) / 8;
+    const int nd = sorted || dmin == dmax ? 0 : (39 - __clz(dmin ^ dmax)) / 8;
     int nl = 0;
-    for (int round = 0; round < 2; ++round) {
+    for (int round = 0; round < 2 && !sorted; ++round) {
       for (int p = 0; p < nl + nd; ++p) {
         const int shift = p < nl ? 8 * p : 32 + 8 * (p - nl);
         block_digit_pass<NT, E>(cur, oth, m, seg, rows, shift, cnt, s_wsum);
