@@ -116,10 +116,10 @@ class Clocks:
 # shape and workload match; otherwise traffic is null.
 TRAFFIC = {
     "raster_bwd": {
-        "sources_sha256": {"raster.cu": "7f3925f559a8d20d1227736a48b433f3455802c4e693fc388bfaeaa8565859ca",
-                           "ddgs_internal.cuh": "b073281dd4262621b65c42bbee2253eee7c6efc36071e341d51a858465ac7332"},
+        "sources_sha256": {"raster.cu": "eda3ef966097be83a5325e72fb2a0f0a8c64817bd9db9190fef7f1d1142abb55",
+                           "ddgs_internal.cuh": "98fc52715cffcba44183e5cda5f7459843f89a876bc11cdd4dbbb923adb10a1e"},
         "tile": 8, "batch_depth": 32, "views": 64, "gaussians": 500_000,
-        "bytes_per_launch": 2460.0e6 + 579.5e6,
+        "bytes_per_launch": 2460.0e6 + 580.7e6,
         "how": "one-pass ncu capture of the 64-pose step; profiles/launches_registration_500k_64x256.md",
     },
 }

@@ -255,6 +255,29 @@ __global__ void __launch_bounds__(1024) bin_offsets_kernel(int64_t n_tiles, uint
   list_append(L, LIST_LONG, (uint64_t)gt, n > BIN_LIST_LONG ? 1u : 0u);
 }
 
+// L2 eviction priorities: the binning records stream through once (evict
+// first); the lists are written 8 bytes at a time into many open 32-byte
+// sectors, which should stay in L2 until they are complete (evict last).
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint4 ld_hint(const uint4 *a, uint64_t pol) {
+  uint4 v;
+  asm volatile("ld.global.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(a), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void st_hint(uint64_t *a, uint64_t v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.u64 [%0], %1, %2;" :: "l"(a), "l"(v), "l"(pol) : "memory");
+}
+
 // scatter: each pair of the block goes to the next free slot of its tile's
 // range (the block's slots start at the tile's offset plus the earlier
 // chunks' counts). Lists of one entry are final here (flag bit 31 of the
@@ -282,12 +305,13 @@ __global__ void __launch_bounds__(BIN_THREADS) bin_scatter_kernel(RenderShape s,
     s_cur[p] = c;
   }
   __syncthreads();
+  const uint64_t pol_in = l2_policy_evict_first(), pol_out = l2_policy_evict_last();
   for (int64_t l0 = it.l0 + threadIdx.x; l0 < it.l1; l0 += BIN_LOADS * BIN_THREADS) {
     uint4 b[BIN_LOADS];
 #pragma unroll
     for (int k = 0; k < BIN_LOADS; ++k) {
       const int64_t l = l0 + k * BIN_THREADS;
-      b[k] = l < it.l1 ? info[it.rec0 + l] : make_uint4(0, 0, 0, 0);
+      b[k] = l < it.l1 ? ld_hint(info + it.rec0 + l, pol_in) : make_uint4(0, 0, 0, 0);
     }
 #pragma unroll
     for (int k = 0; k < BIN_LOADS; ++k) {
@@ -303,7 +327,7 @@ __global__ void __launch_bounds__(BIN_THREADS) bin_scatter_kernel(RenderShape s,
           const uint32_t pos = c & ~CUR_ONE;
           if (pos >= cap) continue;
           if (c & CUR_ONE) vals[pos] = l;
-          else keys[pos] = key;
+          else st_hint(keys + pos, key, pol_out);
         }
     }
   }

@@ -94,6 +94,9 @@ CASES = {
                                     syn.Settings(near_plane=0.2, tile=8)),
     "equal_depths": lambda: (_plane(3000, 13), _two_views(64, 64, 8.0 / 64),
                              syn.Settings(near_plane=0.2, tile=16)),
+    # footprints of up to the whole view: binning rounds too large to stage
+    "large_footprints": lambda: (syn.uniform_cloud(4000, seed=14, log_scale_range=(-1.5, -0.5)),
+                                 _two_views(64, 64, 8.0 / 64), syn.Settings(near_plane=0.2, tile=8)),
     "ragged_100x75_2views": lambda: (syn.uniform_cloud(2000, seed=5), _two_views(75, 100),
                                      syn.Settings(near_plane=0.2)),
     "tile8": lambda: (syn.uniform_cloud(1500, seed=6), _two_views(41, 57, 8.0 / 50),
