@@ -60,7 +60,7 @@ constexpr size_t kScratchBytes = align256(kOffView + (kMaxViews + 1) * sizeof(dd
 thread_local ddgs::ReqTab t_req[2];
 thread_local ddgs::ViewTab t_view[kMaxViews + 1];
 
-// The scratch itself (about 31 MiB per device).
+// The scratch itself (about 37 MiB per device).
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 // Device address of g_scratch per device, looked up once per device.
