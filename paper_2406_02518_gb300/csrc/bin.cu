@@ -29,7 +29,8 @@ namespace ddgs {
 namespace {
 
 constexpr int BIN_THREADS = 256;
-constexpr int SORT_SHORT = 2048;  // lists of one 256-thread block (8 entries a thread)
+constexpr int SORT_SHORT = 1024;  // lists of one 128-thread block (8 entries a thread)
+constexpr int SORT_MID = 2048;    // lists of one 256-thread block (8 entries a thread)
 constexpr int MERGE_ITEMS = 8;    // outputs per thread per merge step
 constexpr int BIN_LOADS = 4;      // records a thread loads before using them
 
@@ -250,8 +251,9 @@ __global__ void __launch_bounds__(1024) bin_offsets_kernel(int64_t n_tiles, uint
   }
   list_append(L, LIST_WARP, (uint64_t)gt, n >= 2 && n <= 32 ? 1u : 0u);
   list_append(L, LIST_SHORT, (uint64_t)gt, n > 32 && n <= SORT_SHORT ? 1u : 0u);
+  list_append(L, LIST_MID, (uint64_t)gt, n > SORT_SHORT && n <= SORT_MID ? 1u : 0u);
   list_append(L, LIST_BLOCK, (uint64_t)gt,
-              n > SORT_SHORT ? (n + BIN_LIST_LONG - 1) / BIN_LIST_LONG : 0u);
+              n > SORT_MID ? (n + BIN_LIST_LONG - 1) / BIN_LIST_LONG : 0u);
   list_append(L, LIST_LONG, (uint64_t)gt, n > BIN_LIST_LONG ? 1u : 0u);
 }
 
@@ -408,15 +410,26 @@ __device__ __forceinline__ void block_digit_pass(const uint64_t *src, uint64_t *
     }
   }
   __syncthreads();
-  uint32_t run = 0, inc = 0;
-  if (tid < 256) {
+  // per digit: the warps' running bases, then an exclusive scan over digits
+  // (each thread takes DPT consecutive digits)
+  constexpr int DPT = NT < 256 ? 256 / NT : 1;
+  const bool dig = tid * DPT < 256;  // warp-uniform
+  uint32_t tot[DPT], loc = 0, inc = 0;
+  if (dig) {
 #pragma unroll
-    for (int x = 0; x < NW; ++x) {
-      const uint32_t c = cnt[x][tid];
-      cnt[x][tid] = run;
-      run += c;
+    for (int j = 0; j < DPT; ++j) {
+      const int d = tid * DPT + j;
+      uint32_t run = 0;
+#pragma unroll
+      for (int x = 0; x < NW; ++x) {
+        const uint32_t c = cnt[x][d];
+        cnt[x][d] = run;
+        run += c;
+      }
+      tot[j] = run;
+      loc += run;
     }
-    inc = run;
+    inc = loc;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
@@ -425,11 +438,16 @@ __device__ __forceinline__ void block_digit_pass(const uint64_t *src, uint64_t *
     if (lane == 31) s_wsum[w] = inc;
   }
   __syncthreads();
-  if (tid < 256) {
-    uint32_t ex = inc - run;
+  if (dig) {
+    uint32_t ex = inc - loc;
     for (int x = 0; x < w; ++x) ex += s_wsum[x];
 #pragma unroll
-    for (int x = 0; x < NW; ++x) cnt[x][tid] += ex;
+    for (int j = 0; j < DPT; ++j) {
+      const int d = tid * DPT + j;
+#pragma unroll
+      for (int x = 0; x < NW; ++x) cnt[x][d] += ex;
+      ex += tot[j];
+    }
   }
   __syncthreads();
 #pragma unroll
@@ -463,7 +481,7 @@ __global__ void __launch_bounds__(NT, MINB) bin_sort_block_kernel(const uint64_t
   constexpr int NW = NT / 32, CAP = NT * E;
   extern __shared__ __align__(16) uint64_t s_buf[];  // [2][CAP]
   __shared__ uint32_t cnt[NW][256];  // digit counters, or NW x 256 bucket counters
-  __shared__ uint32_t s_wsum[NW];
+  __shared__ uint32_t s_wsum[NW > 8 ? NW : 8];
   __shared__ uint32_t s_red[4][NW];
   uint32_t *bc = &cnt[0][0];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -651,6 +669,7 @@ __global__ void __launch_bounds__(256) bin_merge_kernel(const uint64_t *items, c
 
 constexpr int SORT_LONG_THREADS = 512, SORT_LONG_ITEMS = BIN_LIST_LONG / SORT_LONG_THREADS;
 constexpr size_t SHORT_SMEM = 2 * SORT_SHORT * sizeof(uint64_t);
+constexpr size_t MID_SMEM = 2 * SORT_MID * sizeof(uint64_t);
 constexpr size_t LONG_SMEM = 2 * (size_t)BIN_LIST_LONG * sizeof(uint64_t);
 
 }  // namespace
@@ -702,8 +721,9 @@ void launch_binning(const RenderShape &s, uint64_t pair_bound, ddgs_workspace &w
   BinLists L;  // at most T entries per class, except the chunks of long lists (last)
   L.item[LIST_WARP] = ws.lists;
   L.item[LIST_SHORT] = ws.lists + T;
-  L.item[LIST_LONG] = ws.lists + 2 * T;
-  L.item[LIST_BLOCK] = ws.lists + 3 * T;
+  L.item[LIST_MID] = ws.lists + 2 * T;
+  L.item[LIST_LONG] = ws.lists + 3 * T;
+  L.item[LIST_BLOCK] = ws.lists + 4 * T;
   L.count = ws.list_count;
   cudaMemsetAsync(ws.list_count, 0, LIST_CLASSES * sizeof(uint32_t), st);
   {
@@ -731,8 +751,13 @@ void launch_binning(const RenderShape &s, uint64_t pair_bound, ddgs_workspace &w
   }
   {
     LaunchScope ls(KID_BIN_SORT, st);
-    bin_sort_block_kernel<256, SORT_SHORT / 256, 4><<<152 * 4, 256, SHORT_SMEM, st>>>(
+    bin_sort_block_kernel<128, SORT_SHORT / 128, 8><<<152 * 8, 128, SHORT_SMEM, st>>>(
         L.item[LIST_SHORT], L.count + LIST_SHORT, ws.ranges, ws.keys[0], ws.vals);
+  }
+  {
+    LaunchScope ls(KID_BIN_SORT, st);
+    bin_sort_block_kernel<256, SORT_MID / 256, 4><<<152 * 4, 256, MID_SMEM, st>>>(
+        L.item[LIST_MID], L.count + LIST_MID, ws.ranges, ws.keys[0], ws.vals);
   }
   {
     LaunchScope ls(KID_BIN_SORT, st);

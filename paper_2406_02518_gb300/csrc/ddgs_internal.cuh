@@ -66,9 +66,10 @@ struct ViewConst {
 };
 
 // Tile lists sorted by the binning, by length class: 2 to 32 entries (one
-// warp), up to 2048, up to BIN_LIST_LONG (one block each; longer lists are
-// cut into BIN_LIST_LONG-entry chunks here) and longer (chunks merged).
-enum : int { LIST_WARP = 0, LIST_SHORT, LIST_BLOCK, LIST_LONG, LIST_CLASSES };
+// warp), up to 1024, up to 2048, up to BIN_LIST_LONG (one block each; longer
+// lists are cut into BIN_LIST_LONG-entry chunks here) and longer (chunks
+// merged).
+enum : int { LIST_WARP = 0, LIST_SHORT, LIST_MID, LIST_BLOCK, LIST_LONG, LIST_CLASSES };
 struct BinLists {
   uint64_t *item[LIST_CLASSES];  // entries: global tile << 24 | chunk
   uint32_t *count;               // device [LIST_CLASSES]
