@@ -563,6 +563,110 @@ def run_ours(args):
     return 0
 
 
+def run_fit(args, large):
+    """Fit step (configs C2 / C4): render, per-view L1 against the render of a
+    perturbed cloud (means + N(0, 1 mm), logits + N(0, 0.2)), backward to every
+    parameter. C2: 100k Gaussians, one 512^2 AP view; C4: 2M Gaussians with
+    bf16 direction features, 8 orbit views of 1024^2. Timed with CUDA events
+    over no-sync steps (workspace reserved beforehand)."""
+    import torch
+
+    from paper_2406_02518_gb300 import binding as B
+    from paper_2406_02518_gb300 import build as bld
+    from paper_2406_02518_gb300 import synthetic as syn
+
+    rank, world, local = _dist_env()
+    torch.cuda.set_device(local)
+    bld.build()
+    B.load()
+    dev = torch.device("cuda", local)
+    t0 = time.time()
+    scene, views, st = syn.large_fit_workload() if large else syn.fit_workload()
+    gen_s = time.time() - t0
+    if args.tile:
+        st = dataclasses.replace(st, tile=args.tile)
+    V, H, W = views.n_views, views.height, views.width
+    bf16 = bool(getattr(scene, "bf16_dir", False))
+    cloud = B.cloud_from_arrays(scene, feat_dir_bf16=bf16)
+    gv = B.views_from_arrays(views)
+    cfg = B.config_from_settings(st, batch_depth=args.depth or 256)
+    ws = B.Workspace()
+    target, _, _ = B.render(B.cloud_from_arrays(syn.perturb_scene(scene, seed=1), feat_dir_bf16=bf16),
+                            gv, cfg, ws)
+    target = target.clone()
+    img, tf, nl = B.render(cloud, gv, cfg, ws)
+    torch.cuda.synchronize()
+    pairs = ws.pairs()
+    tiles = V * (-(-H // st.tile)) * (-(-W // st.tile))
+    ws.reserve(V * scene.n, int(pairs * 1.10) + 4096, tiles)
+    cfg = B.config_from_settings(st, no_sync=True, batch_depth=args.depth or 256)
+    loss = torch.empty(V, dtype=torch.float32, device=dev)
+    dL = torch.empty_like(img)
+    grads = {}
+
+    def step():
+        B.render(cloud, gv, cfg, ws, out=(img, tf, nl))
+        B.l1_loss(img, target, loss=loss, grad=dL)
+        grads.update(B.render_backward(cloud, gv, cfg, ws, dL, tf, nl, out=grads or None))
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    launches0 = B.kernel_launches()
+    clocks = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
+                    if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/ddgs_clocks_{rank}.csv")
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+    clk = clocks.stop(local)
+    n_launch = B.kernel_launches() - launches0
+    assert ws.sync_status() == 0
+    B.profiler_enable(True)
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    prof = B.profiler_collect()
+    B.profiler_enable(False)
+    # end to end: the target from pinned host memory, the losses read back
+    target_h = target.cpu().pin_memory()
+    loss_h = torch.empty(V, dtype=torch.float32).pin_memory()
+    for it in range(args.steps + 1):
+        if it == 1:
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+        target.copy_(target_h, non_blocking=True)
+        step()
+        loss_h.copy_(loss, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    t_e2e = max_over_ranks((time.perf_counter() - t1) / args.steps, world, dev)
+    total = sum(v[0] for v in prof.values())
+    kernels = {k: {"ms_per_launch": round(v[0] / max(v[1], 1), 4), "launches_per_step": v[1] / 3,
+                   "share": round(v[0] / total, 4)} for k, v in prof.items()}
+    if rank != 0:
+        return 0
+    name = "large fit" if large else "fit"
+    line = {"metric": f"{name} step (render + L1 + backward to all parameters) steps/s",
+            "value": world * 1e3 / ms, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" + (" (bf16 direction features)" if bf16 else ""),
+            "data": "synthetic",
+            "config": {"workload": f"{name}: {scene.n} Gaussians, {V} view(s) of {H}x{W}, "
+                                   "target = render of a perturbed cloud",
+                       "tile": st.tile, "batch_depth": args.depth or 256, "pairs_per_step": pairs,
+                       "generation_s": round(gen_s, 1)},
+            "renders_per_s": world * V * 1e3 / ms,
+            "e2e": {"value": world / t_e2e, "unit": "steps/s", "h2d_bytes_per_step": target_h.numel() * 4,
+                    "d2h_bytes_per_step": V * 4},
+            "gpu_launches": n_launch, "clocks": clk, "kernels": kernels}
+    print(json.dumps(line))
+    return 0
+
+
 def run_uneven(args):
     """Uneven batch: 256 render + backward requests (own cloud of 10^4-10^6
     Gaussians, own detector 128^2-1024^2, one view each) in one batched call
@@ -866,7 +970,8 @@ def main():
                     help="run warm-up steps and one eager step in an NVTX range, then exit")
     ap.add_argument("--autotune", nargs="?", const="on", default="on", choices=["on", "off", "force"],
                     help="tune (tile, staging depth) before timing (cached per workload class)")
-    ap.add_argument("--workload", choices=["registration", "uneven", "registration-loop", "rads"],
+    ap.add_argument("--workload", choices=["registration", "uneven", "registration-loop", "rads",
+                                           "fit", "large-fit"],
                     default="registration")
     ap.add_argument("--volume", type=int, default=512, help="CT volume edge of --workload rads")
     ap.add_argument("--tile", type=int, choices=[8, 16, 32], default=None,
@@ -884,6 +989,8 @@ def main():
         args.autotune = None
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload in ("fit", "large-fit"):
+        return run_fit(args, args.workload == "large-fit")
     if args.workload == "uneven":
         return run_uneven(args)
     if args.workload == "registration-loop":
