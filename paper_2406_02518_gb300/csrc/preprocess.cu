@@ -461,6 +461,18 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_fwd_kernel(PreArgs a) 
 // Backward (K8)
 // ---------------------------------------------------------------------------
 
+// 16-byte asynchronous global -> shared copies (the thread that issues them
+// waits for them with cp_async_wait).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 struct PreBwdArgs {
   const float *means, *log_scales, *quats, *logits, *feat_iso;
   const void *feat_dir;
@@ -514,9 +526,15 @@ __device__ __forceinline__ int warp_reduce16(float v[16]) {
 template <bool GEN>
 __global__ void __launch_bounds__(PRE_THREADS) preprocess_bwd_kernel(PreBwdArgs a) {
   constexpr int KS = GEN ? KG : K, KLS = GEN ? KLG : 3;
+  // views whose gradient records are in flight ahead of the one being used
+  constexpr int AHEAD = GEN ? 2 : 4;
   const int Kr = GEN ? a.K : K, kL = GEN ? a.L * (a.L + 2) : 3;
   __shared__ ViewConst sv[VIEW_CHUNK];
   __shared__ float s_pose[VIEW_CHUNK][12];
+  // each thread's own 2D-gradient records (and dL/dh with per-pixel rays) for
+  // the next AHEAD views, copied asynchronously; only the copying thread reads
+  // its slots, so its own wait on the copies is enough
+  __shared__ float4 s_gr[AHEAD][GEN ? 3 : 2][PRE_THREADS];
   __shared__ float s_b[KS], s_B[KLS * KS], s_basis[(1 + KLS) * KS];
   __shared__ ShTable s_sh;
   const int tid = threadIdx.x, lane = tid & 31;
@@ -595,14 +613,28 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_bwd_kernel(PreBwdArgs 
     }
     for (int e = tid; e < nv * 12; e += blockDim.x) (&s_pose[0][0])[e] = 0.f;
     __syncthreads();
+    const bool with_h = GEN && a.per_pixel;
+    auto fetch = [&](int vv) {  // one commit group per view, empty past the chunk
+      if (live && vv < nv) {
+        const int64_t rec = sv[vv].rec_off + br.l;
+        float4 *slot = &s_gr[vv % AHEAD][0][tid];
+        cp_async16(slot, a.grad2d + 2 * rec);
+        cp_async16(slot + PRE_THREADS, a.grad2d + 2 * rec + 1);
+        if (GEN && with_h) cp_async16(slot + 2 * PRE_THREADS, a.grad_h + rec);
+      }
+      cp_async_commit();
+    };
+#pragma unroll
+    for (int vv = 0; vv < AHEAD; ++vv) fetch(vv);
     for (int vv = 0; vv < nv; ++vv) {
       const ViewConst &vc = sv[vv];
       float dW[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, dt[3] = {0, 0, 0};
       bool any = false;
+      cp_async_wait<AHEAD - 1>();  // this thread's copies of view vv have landed
+      const float4 g0 = s_gr[vv % AHEAD][0][tid], g1 = s_gr[vv % AHEAD][1][tid];
+      const float4 gh = with_h ? s_gr[vv % AHEAD][GEN ? 2 : 0][tid] : make_float4(0.f, 0.f, 0.f, 0.f);
+      fetch(vv + AHEAD);  // reuses the slot just read
       if (live) {
-        const int64_t rec = vc.rec_off + br.l;
-        const float4 g0 = a.grad2d[2 * rec], g1 = a.grad2d[2 * rec + 1];
-        const float4 gh = (GEN && a.per_pixel) ? a.grad_h[rec] : make_float4(0.f, 0.f, 0.f, 0.f);
         any = (g0.x != 0.f) | (g0.y != 0.f) | (g0.z != 0.f) | (g0.w != 0.f) | (g1.x != 0.f) |
               (g1.y != 0.f) | (g1.z != 0.f) | (gh.x != 0.f) | (gh.y != 0.f) | (gh.z != 0.f);
         ViewProj p;
