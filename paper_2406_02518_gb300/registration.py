@@ -5,7 +5,10 @@ rendering with the target X-ray (L1, the l1 term of Eq. 2), back-propagating
 to the pose and stepping Adam (learning rate 0.05), starting from the
 isocenter pose. Many candidates are registered at once: each is one view of a
 single batched render, so every iteration is one ddgs_render, one
-ddgs_l1_loss and one ddgs_render_backward for all candidates.
+ddgs_l1_loss and one ddgs_render_backward for all candidates. After a few
+eager iterations the whole iteration (pose map, render, loss, backward, Adam
+step) is captured once in a CUDA graph and replayed; the renders then run in
+no-sync mode on a workspace reserved for 1.5x the initial pair count.
 
 The pose is a 6-DoF correction (rotation vector w in units of `rot_unit`
 radians, translation d in units of `trans_unit` millimetres) applied about the
@@ -91,13 +94,19 @@ class RegistrationResult:
     loss: np.ndarray           # [iters, V]
 
 
+_EAGER_ITERS = 3  # iterations run before the capture (also the capture's warm-up)
+
+
 def register(cloud: B.Cloud, detector: torch.Tensor, height: int, width: int,
              targets: torch.Tensor, init_pose: torch.Tensor, cfg: B.Config,
              iters: int = 200, lr: float = 0.05, trans_unit: float = 10.0,
-             rot_unit: float = 0.1, true_poses: np.ndarray | None = None, ws: B.Workspace | None = None
-             ) -> RegistrationResult:
+             rot_unit: float = 0.1, true_poses: np.ndarray | None = None, ws: B.Workspace | None = None,
+             graph: bool = True) -> RegistrationResult:
     """Register V candidates at once. targets [V,H,W]; init_pose [V,3,4] or
-    [3,4]; detector [V,5]. Adam on (w, d) with learning rate `lr`."""
+    [3,4]; detector [V,5]. Adam on (w, d) with learning rate `lr`. With
+    graph=True the iterations after the first few replay one CUDA graph; if
+    the pair count ever outgrows the reserved workspace, the registration is
+    run again without the graph."""
     dev = cloud.means.device
     V = targets.shape[0]
     P0 = init_pose.to(dev, torch.float64).expand(V, 3, 4) if init_pose.dim() == 2 else \
@@ -105,22 +114,53 @@ def register(cloud: B.Cloud, detector: torch.Tensor, height: int, width: int,
     R0, t0 = P0[:, :, :3], P0[:, :, 3]
     w = torch.zeros((V, 3), dtype=torch.float64, device=dev, requires_grad=True)
     d = torch.zeros((V, 3), dtype=torch.float64, device=dev, requires_grad=True)
-    opt = torch.optim.Adam([w, d], lr=lr)
+    graph = graph and iters > _EAGER_ITERS
+    opt = torch.optim.Adam([w, d], lr=lr, capturable=graph)
     ws = ws or B.Workspace()
     det = detector.to(dev, torch.float32).expand(V, 5).contiguous()
-    losses = []
-    for _ in range(iters):
-        opt.zero_grad()
+    losses = torch.zeros((iters, V), dtype=torch.float32, device=dev)
+    run_cfg = cfg
+
+    def iteration():
+        opt.zero_grad(set_to_none=False)
         pose = compose(R0, t0, w, d, trans_unit, rot_unit).to(torch.float32).contiguous()
-        views = B.Views(pose, det, height, width)
         img, _, _ = B.RenderFunction.apply(cloud.means, cloud.log_scales, cloud.quats,
                                            cloud.opacity_logits, cloud.feat_iso, cloud.feat_dir,
-                                           cloud.b_iso, cloud.B_dir, views.world_to_cam,
-                                           views.detector, height, width, cfg, ws)
+                                           cloud.b_iso, cloud.B_dir, pose, det, height, width,
+                                           run_cfg, ws)
         loss = _L1.apply(img, targets)
         loss.sum().backward()
         opt.step()
-        losses.append(loss.detach().cpu().numpy())
+        return loss.detach()
+
+    if not graph:
+        for i in range(iters):
+            losses[i].copy_(iteration())
+    else:
+        # size the workspace for no-sync renders from the initial pose's pair count
+        with torch.no_grad():
+            pose = compose(R0, t0, w, d, trans_unit, rot_unit).to(torch.float32).contiguous()
+            B.render(cloud, B.Views(pose, det, height, width), cfg, ws)
+        torch.cuda.synchronize()
+        tiles = V * (-(-height // cfg.tile)) * (-(-width // cfg.tile))
+        ws.reserve(V * cloud.n, int(ws.pairs() * 1.5) + 4096, tiles)
+        run_cfg = dataclasses.replace(cfg, no_sync=True)
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for i in range(_EAGER_ITERS):
+                losses[i].copy_(iteration())
+        torch.cuda.current_stream().wait_stream(side)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            loss_static = iteration()
+        for i in range(_EAGER_ITERS, iters):
+            g.replay()
+            losses[i].copy_(loss_static)
+        torch.cuda.synchronize()
+        if ws.sync_status() != 0:  # a no-sync render ran out of room: redo without the graph
+            return register(cloud, detector, height, width, targets, init_pose, cfg, iters, lr,
+                            trans_unit, rot_unit, true_poses, ws, graph=False)
     with torch.no_grad():
         final = compose(R0, t0, w, d, trans_unit, rot_unit).cpu().numpy()
     if true_poses is not None:
@@ -128,7 +168,7 @@ def register(cloud: B.Cloud, detector: torch.Tensor, height: int, width: int,
         tr = translation_error_mm(final, true_poses)
     else:
         rot = tr = np.full(V, np.nan)
-    return RegistrationResult(final, rot, tr, np.array(losses))
+    return RegistrationResult(final, rot, tr, losses.cpu().numpy())
 
 
 def perturbed_poses(rng: np.random.Generator, base: np.ndarray, n: int, max_deg: float,
