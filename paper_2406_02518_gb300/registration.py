@@ -97,6 +97,34 @@ class RegistrationResult:
 _EAGER_ITERS = 3  # iterations run before the capture (also the capture's warm-up)
 
 
+class _Adam:
+    """Adam (Kingma & Ba) on a list of tensors with device-side state, so that a
+    step can be captured in a CUDA graph: m <- b1 m + (1 - b1) g,
+    v <- b2 v + (1 - b2) g^2, p <- p - lr m / (1 - b1^t) / (sqrt(v / (1 - b2^t)) + eps)."""
+
+    def __init__(self, params, lr, b1=0.9, b2=0.999, eps=1e-8):
+        self.params, self.lr, self.b1, self.b2, self.eps = list(params), lr, b1, b2, eps
+        self.m = [torch.zeros_like(p) for p in self.params]
+        self.v = [torch.zeros_like(p) for p in self.params]
+        self.t = torch.zeros((), dtype=torch.float64, device=self.params[0].device)
+
+    def zero_grad(self):
+        for p in self.params:
+            if p.grad is not None:
+                p.grad.zero_()
+
+    @torch.no_grad()
+    def step(self):
+        self.t += 1
+        c1 = 1 - torch.pow(self.b1, self.t)
+        c2 = 1 - torch.pow(self.b2, self.t)
+        for p, m, v in zip(self.params, self.m, self.v):
+            g = p.grad
+            m.mul_(self.b1).add_(g, alpha=1 - self.b1)
+            v.mul_(self.b2).addcmul_(g, g, value=1 - self.b2)
+            p.sub_(self.lr * (m / c1) / (torch.sqrt(v / c2) + self.eps))
+
+
 def register(cloud: B.Cloud, detector: torch.Tensor, height: int, width: int,
              targets: torch.Tensor, init_pose: torch.Tensor, cfg: B.Config,
              iters: int = 200, lr: float = 0.05, trans_unit: float = 10.0,
@@ -115,14 +143,14 @@ def register(cloud: B.Cloud, detector: torch.Tensor, height: int, width: int,
     w = torch.zeros((V, 3), dtype=torch.float64, device=dev, requires_grad=True)
     d = torch.zeros((V, 3), dtype=torch.float64, device=dev, requires_grad=True)
     graph = graph and iters > _EAGER_ITERS
-    opt = torch.optim.Adam([w, d], lr=lr, capturable=graph)
+    opt = _Adam([w, d], lr=lr)
     ws = ws or B.Workspace()
     det = detector.to(dev, torch.float32).expand(V, 5).contiguous()
     losses = torch.zeros((iters, V), dtype=torch.float32, device=dev)
     run_cfg = cfg
 
     def iteration():
-        opt.zero_grad(set_to_none=False)
+        opt.zero_grad()
         pose = compose(R0, t0, w, d, trans_unit, rot_unit).to(torch.float32).contiguous()
         img, _, _ = B.RenderFunction.apply(cloud.means, cloud.log_scales, cloud.quats,
                                            cloud.opacity_logits, cloud.feat_iso, cloud.feat_dir,
