@@ -30,7 +30,7 @@ namespace {
 
 constexpr int BIN_THREADS = 256;
 constexpr int SORT_SHORT = 1024;  // lists of one 128-thread block (8 entries a thread)
-constexpr int SORT_MID = 2048;    // lists of one 256-thread block (8 entries a thread)
+constexpr int SORT_MID = 2048;    // lists of one 128-thread block (16 entries a thread)
 constexpr int MERGE_ITEMS = 8;    // outputs per thread per merge step
 constexpr int BIN_LOADS = 4;      // records a thread loads before using them
 
@@ -756,7 +756,7 @@ void launch_binning(const RenderShape &s, uint64_t pair_bound, ddgs_workspace &w
   }
   {
     LaunchScope ls(KID_BIN_SORT, st);
-    bin_sort_block_kernel<256, SORT_MID / 256, 4><<<152 * 4, 256, MID_SMEM, st>>>(
+    bin_sort_block_kernel<128, SORT_MID / 128, 6><<<152 * 6, 128, MID_SMEM, st>>>(
         L.item[LIST_MID], L.count + LIST_MID, ws.ranges, ws.keys[0], ws.vals);
   }
   {
