@@ -56,7 +56,17 @@ struct RasterArgs {
   float *pose_grad;          // [V][12] or null
 };
 
-__device__ __forceinline__ float sigmoid_r(float x) { return 1.f / (1.f + __expf(-x)); }
+// 1 / x by the hardware's approximate reciprocal (about 1 ulp). Used where
+// the result feeds the image or the gradients only through tolerances far
+// above that error: the transmittance recovered in the backward as
+// T' / (1 - sigma) (1 - sigma >= 0.01) and the per-pixel radiosity sigmoid.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float sigmoid_r(float x) { return rcp_approx(1.f + __expf(-x)); }
 
 // The ray through pixel centre (px, py) of a view: rc = ((px - c_u) pitch_u,
 // (py - c_v) pitch_v, sdd) in camera coordinates, world direction d = W^T rc,
@@ -420,7 +430,7 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs &a, int64_t gt, BwdSme
           if (act) {
             // 1 / (1 - sigma) with sigma <= alpha_max < 1: the fast reciprocal's
             // relative error (~1 ulp) is far inside the gradient tolerance
-            const float inv_om = __frcp_rn(__fsub_rn(1.f, e.sigma));
+            const float inv_om = rcp_approx(__fsub_rn(1.f, e.sigma));
             Tr = Tr * inv_om;  // transmittance before this Gaussian
             float4 cz;
             if (PIX) cz = s_c[k];
@@ -704,7 +714,7 @@ __device__ __forceinline__ void bwd_warp_item(const RasterArgs &a, int64_t gt, i
         act = eval_pair(A.x, A.y, A.z, A.w, B.x, B.y, px, py, a.P, e);
         if (act) {
           // 1 / (1 - sigma) with sigma <= alpha_max < 1
-          const float inv_om = __frcp_rn(__fsub_rn(1.f, e.sigma));
+          const float inv_om = rcp_approx(__fsub_rn(1.f, e.sigma));
           Tr = Tr * inv_om;  // transmittance before this Gaussian
           float4 cz;
           if (PIX) cz = sC[k];

@@ -294,6 +294,17 @@ def test_capacity_overflow_is_reported_not_faulted(ws):
     B.render(cloud, gv, cfg, w2)
     assert w2.sync_status() == 2  # DDGS_ERR_CAPACITY
     assert w2.sync_status() == 0  # cleared
+    # whole lists only: the lists that fit are the first tiles' lists, exactly
+    # the oracle's; every list after the first one that did not fit is empty
+    ref = oracle.bin32(scene, views, st)
+    got = _bins(w2, scene, views, st)
+    rr, gr = ref["ranges"].reshape(-1, 2).astype(np.int64), got["ranges"].reshape(-1, 2).astype(np.int64)
+    kept, has = gr[:, 1] > gr[:, 0], rr[:, 1] > rr[:, 0]
+    assert kept.any() and not kept.all()
+    first_drop = int(np.argmax(has & ~kept))
+    assert not kept[first_drop:].any()
+    for t in np.nonzero(kept)[0]:
+        assert np.array_equal(got["vals"][gr[t, 0]:gr[t, 1]], ref["vals"][rr[t, 0]:rr[t, 1]])
     # the same workspace renders correctly once it is large enough
     w2.reserve(recs, m_needed, views.n_views * 42)
     img, tf, nl = B.render(cloud, gv, cfg, w2)
