@@ -181,6 +181,17 @@ __device__ __forceinline__ float dot3r(float a0, float a1, float a2, float b0, f
   return addr(addr(mulr(a0, b0), mulr(a1, b1)), mulr(a2, b2));
 }
 
+// 1 / x by the hardware's approximate reciprocal (about 1 ulp). Used only where
+// the result feeds the image or the gradients through tolerances far above
+// that error (never in the binning): the transmittance recovered in the
+// backward as T' / (1 - sigma) (1 - sigma >= 0.01), the per-pixel radiosity
+// sigmoid, and the backward preprocess's conic and perspective factors.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // Per-pair evaluation shared by the forward and backward rasterisers, written
 // with explicit rounding so both kernels take bit-identical decisions.
 struct PairEval {

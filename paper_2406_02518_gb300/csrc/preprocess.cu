@@ -654,7 +654,7 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_bwd_kernel(PreBwdArgs 
             } else {
               dir_grad = true;
               d[0] = mu[0] + vc.wt[0]; d[1] = mu[1] + vc.wt[1]; d[2] = mu[2] + vc.wt[2];
-              inv = 1.f / sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+              inv = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
               dh_[0] = d[0] * inv; dh_[1] = d[1] * inv; dh_[2] = d[2] * inv;
               float Y[3] = {-SH_C1 * dh_[1], SH_C1 * dh_[2], -SH_C1 * dh_[0]};
               float c = sigmoidf_(Y[0] * h[0] + Y[1] * h[1] + Y[2] * h[2]);
@@ -671,7 +671,7 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_bwd_kernel(PreBwdArgs 
             float zl = c_iso, Y[KLS], dYd[KLS][3];
             if (has_dir) {
               d[0] = mu[0] + vc.wt[0]; d[1] = mu[1] + vc.wt[1]; d[2] = mu[2] + vc.wt[2];
-              inv = 1.f / sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+              inv = rsqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
               dh_[0] = d[0] * inv; dh_[1] = d[1] * inv; dh_[2] = d[2] * inv;
               sh_eval(s_sh, kL, dh_[0], dh_[1], dh_[2], Y, dYd);
 #pragma unroll
@@ -709,7 +709,8 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_bwd_kernel(PreBwdArgs 
               dt[r] += vc.W[3 * r] * dd[0] + vc.W[3 * r + 1] * dd[1] + vc.W[3 * r + 2] * dd[2];
           }
           // conic = inverse 2D covariance: GS = -K GK K
-          const float k0 = divr(p.cov[2], p.det), k1 = divr(-p.cov[1], p.det), k2 = divr(p.cov[0], p.det);
+          const float idet = rcp_approx(p.det);
+          const float k0 = p.cov[2] * idet, k1 = -p.cov[1] * idet, k2 = p.cov[0] * idet;
           const float hb = 0.5f * gcb;
           const float m00 = k0 * gca + k1 * hb, m01 = k0 * hb + k1 * gcc;
           const float m10 = k1 * gca + k2 * hb, m11 = k1 * hb + k2 * gcc;
@@ -750,7 +751,7 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_bwd_kernel(PreBwdArgs 
             dW[6 + c3] += p.j02 * dA[c3] + p.j12 * dA[3 + c3];
           }
           // J(x_c) and the projected mean
-          const float iz = 1.f / p.xc[2];
+          const float iz = rcp_approx(p.xc[2]);
           float dxc[3];
           dxc[0] = -dJ02 * p.j00 * iz + gu * p.j00;
           dxc[1] = -dJ12 * p.j11 * iz + gv * p.j11;

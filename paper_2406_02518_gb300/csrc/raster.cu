@@ -56,16 +56,6 @@ struct RasterArgs {
   float *pose_grad;          // [V][12] or null
 };
 
-// 1 / x by the hardware's approximate reciprocal (about 1 ulp). Used where
-// the result feeds the image or the gradients only through tolerances far
-// above that error: the transmittance recovered in the backward as
-// T' / (1 - sigma) (1 - sigma >= 0.01) and the per-pixel radiosity sigmoid.
-__device__ __forceinline__ float rcp_approx(float x) {
-  float y;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
 __device__ __forceinline__ float sigmoid_r(float x) { return rcp_approx(1.f + __expf(-x)); }
 
 // The ray through pixel centre (px, py) of a view: rc = ((px - c_u) pitch_u,
