@@ -116,10 +116,10 @@ class Clocks:
 # shape and workload match; otherwise traffic is null.
 TRAFFIC = {
     "raster_bwd": {
-        "sources_sha256": {"raster.cu": "eda3ef966097be83a5325e72fb2a0f0a8c64817bd9db9190fef7f1d1142abb55",
-                           "ddgs_internal.cuh": "98fc52715cffcba44183e5cda5f7459843f89a876bc11cdd4dbbb923adb10a1e"},
+        "sources_sha256": {"raster.cu": "7549a43fa4defa813d0a4994caca017e67610cb3a6e9cf73d7b4689492056657",
+                           "ddgs_internal.cuh": "a975d19baf1ac2a29599a5d5770a68d6febc46b1c30bdcff0823f6c9037f94d5"},
         "tile": 8, "batch_depth": 32, "views": 64, "gaussians": 500_000,
-        "bytes_per_launch": 2460.0e6 + 580.7e6,
+        "bytes_per_launch": 2450.0e6 + 579.2e6,
         "how": "one-pass ncu capture of the 64-pose step; profiles/launches_registration_500k_64x256.md",
     },
 }
