@@ -511,3 +511,26 @@ def test_warp_streamed_rasterisers(case, per_pixel, ws):
     gpu["feat"] = np.concatenate([gpu.pop("feat_iso"), gpu.pop("feat_dir")])
     gpu["pose"] = gpu.pop("world_to_cam")
     compare_grads(gpu, gr, GRAD_NAMES)
+
+
+def _banded_case(shape):
+    """Views with more tiles than one binning band holds (8,192 at tile 8):
+    1024 x 1024 (128 x 128 tiles: two bands of 64 tile rows) and an 8-pixel
+    strip 66,000 pixels wide (one row of 8,250 tiles: two bands of columns)."""
+    H, W = shape
+    st = syn.Settings(near_plane=0.2, tile=8)
+    views = _views([syn.pose_matrix(np.eye(3), np.array([0.0, 0.0, 2.0]))], 4.0, 8.0 / W, H, W)
+    if H > 8:
+        return syn.uniform_cloud(3000, seed=21), views, st
+    sc = syn.uniform_cloud(3000, seed=22, log_scale_range=(-6.0, -5.0))
+    means = sc.means.copy()
+    means[:, 1] *= 2e-4  # the strip is 8 pixels = 0.001 units high
+    return dataclasses.replace(sc, means=means), views, st
+
+
+@pytest.mark.parametrize("shape", [(1024, 1024), (8, 66000)])
+def test_banded_views(shape, ws):
+    scene, views, st = _banded_case(shape)
+    _run(scene, views, st, ws)
+    compare_binning(_bins(ws, scene, views, st), oracle.bin32(scene, views, st))
+    _sampled_check(scene, views, st, ws, [0], 1024, 31, grads=("means", "opacity_logits", "pose"))
