@@ -802,7 +802,6 @@ ddgs_status ddgs_sync_status(ddgs_workspace *ws, void *stream) {
   CK(cudaMemcpy(&h, ws->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost));
   CK(cudaMemset(ws->d_status, 0, sizeof(int32_t)));
   if (h & ddgs::ST_CAPACITY) return DDGS_ERR_CAPACITY;
-  if (h & ddgs::ST_TIMEOUT) return DDGS_ERR_TIMEOUT;
   return DDGS_OK;
 }
 

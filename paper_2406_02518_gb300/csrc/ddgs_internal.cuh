@@ -25,7 +25,7 @@ constexpr int64_t BIN_MAX_PAIRS = (int64_t(1) << 31) - 1;  // offsets leave bit 
 constexpr float SH_C1 = 0.48860251190291992f;  // sqrt(3 / (4 pi))
 
 // Device status bits (latched in the workspace).
-enum : int32_t { ST_CAPACITY = 1, ST_TIMEOUT = 2 };
+enum : int32_t { ST_CAPACITY = 1 };
 
 // A batch is R requests; request r owns a contiguous range of Gaussians (its
 // own cloud and bases) and a contiguous range of views; every view has its
