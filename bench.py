@@ -151,7 +151,6 @@ def cpu_baseline(scene, views, st, target, n_pix=4096, n_small=16):
     """The oracle, as it stands, on a bounded sample: view 0, n_pix random
     pixels, forward + L1 backward; per-view setup separated from the per-pixel
     cost by a two-point fit, then scaled to a full 256^2 render."""
-    import dataclasses
 
     import oracle
     from paper_2406_02518_gb300 import synthetic as syn
@@ -212,7 +211,6 @@ def run_reference(args):
     scene = dataclasses.replace(scene, **VARIANTS[args.variant])
     # The L1 target (the AP view) is rendered by the oracle at each step's
     # sampled pixels, outside the timed part of the step.
-    import dataclasses
 
     import oracle
     from paper_2406_02518_gb300 import synthetic as syn
