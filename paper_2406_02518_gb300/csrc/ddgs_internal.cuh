@@ -192,6 +192,13 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return y;
 }
 
+// 2^x by the hardware's approximate base-2 exponential (ex2.approx).
+__device__ __forceinline__ float exp2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // Per-pair evaluation shared by the forward and backward rasterisers, written
 // with explicit rounding so both kernels take bit-identical decisions.
 struct PairEval {
@@ -226,7 +233,7 @@ __device__ __forceinline__ bool eval_pair(float u, float v, float ca, float cb, 
   e.ty = __fmaf_rn(cb, e.dx, __fmul_rn(cc, e.dy));
   const float q = __fmaf_rn(e.dx, e.tx, __fmul_rn(e.dy, e.ty));
   if (q > P.q_max || q < 0.f) return false;
-  e.G = __expf(__fmul_rn(-0.5f, q));
+  e.G = exp2_approx(__fmul_rn(q, -0.72134752044448170368f));  // exp(-q / 2) = 2^(-q log2(e) / 2)
   e.aG = __fmul_rn(alpha, e.G);
   e.sigma = fminf(P.alpha_max, e.aG);
   return e.sigma >= P.alpha_min;
