@@ -117,9 +117,9 @@ class Clocks:
 TRAFFIC = {
     "raster_bwd": {
         "sources_sha256": {"raster.cu": "7549a43fa4defa813d0a4994caca017e67610cb3a6e9cf73d7b4689492056657",
-                           "ddgs_internal.cuh": "882a42f135f5946cad3eb099c9117dcfc0272b998c394c1061a495c553f784fe"},
+                           "ddgs_internal.cuh": "79d2e305a0720d36ace629a48f5b6ba0468f3b5a724de309f9d563f4a41600b2"},
         "tile": 8, "batch_depth": 32, "views": 64, "gaussians": 500_000,
-        "bytes_per_launch": 2450.0e6 + 579.2e6,
+        "bytes_per_launch": 2450.0e6 + 579.0e6,
         "how": "one-pass ncu capture of the 64-pose step; profiles/launches_registration_500k_64x256.md",
     },
 }
