@@ -210,8 +210,12 @@ struct PairEval {
 // rounded up to binary16, packed into the record's fourth float (x in the low
 // half). The rasterisers cull with this box; rounding up keeps it conservative.
 __device__ __forceinline__ float box_halfwidths(const float cov[3], float q_max) {
-  const float ex = sqrtf(q_max * cov[0]) * 1.001f + 1e-3f;
-  const float ey = sqrtf(q_max * cov[2]) * 1.001f + 1e-3f;
+  // approximate square roots (a few ulp): far inside the 1e-3 widening
+  float ex, ey;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(ex) : "f"(q_max * cov[0]));
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(ey) : "f"(q_max * cov[2]));
+  ex = ex * 1.001f + 1e-3f;
+  ey = ey * 1.001f + 1e-3f;
   const uint32_t hx = __half_as_ushort(__float2half_ru(ex));
   const uint32_t hy = __half_as_ushort(__float2half_ru(ey));
   return __uint_as_float(hx | (hy << 16));

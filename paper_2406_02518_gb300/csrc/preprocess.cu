@@ -41,7 +41,9 @@ __device__ __forceinline__ float exp32(float x) {
   return mulr(p, __int_as_float((k + 127) << 23));
 }
 
-__device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + __expf(-x)); }
+// Opacity and radiosity sigmoids: they reach the image and the gradients only
+// (never the binning), so the approximate reciprocal serves.
+__device__ __forceinline__ float sigmoidf_(float x) { return rcp_approx(1.0f + __expf(-x)); }
 
 // View-independent geometry of one Gaussian (steps G1-G5).
 struct GaussGeom {
@@ -425,7 +427,9 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_fwd_kernel(PreArgs a) 
                                    (uint32_t)tx1 | ((uint32_t)ty1 << 16), __float_as_uint(depth), tt);
       if (tt == 0) continue;
       total += tt;
-      const float ca = divr(p.cov[2], p.det), cb = divr(-p.cov[1], p.det), cc = divr(p.cov[0], p.det);
+      // the record's conic feeds only the rasterisers: approximate reciprocal
+      const float idet = rcp_approx(p.det);
+      const float ca = p.cov[2] * idet, cb = -p.cov[1] * idet, cc = p.cov[0] * idet;
       float colour = c_iso;
       if (!GEN) {
         if (is_dir) {
