@@ -528,7 +528,7 @@ __device__ __forceinline__ int warp_reduce16(float v[16]) {
 }
 
 template <bool GEN>
-__global__ void __launch_bounds__(PRE_THREADS, GEN ? 1 : 3) preprocess_bwd_kernel(PreBwdArgs a) {
+__global__ void __launch_bounds__(PRE_THREADS, GEN ? 2 : 3) preprocess_bwd_kernel(PreBwdArgs a) {
   constexpr int KS = GEN ? KG : K, KLS = GEN ? KLG : 3;
   // views whose gradient records are in flight ahead of the one being used
   constexpr int AHEAD = GEN ? 2 : 4;
