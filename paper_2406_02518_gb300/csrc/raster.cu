@@ -285,33 +285,19 @@ __device__ __forceinline__ int quarter_reduce8(float v[8]) {
   return ((lane >> 2) & 1) * 4 + ((lane >> 1) & 1) * 2 + (lane & 1);
 }
 
-// Sum 16 per-lane values over each quarter (8 lanes) with 14 shuffles. Lane l
-// of the quarter ends with components c and c + 1 in v[0], v[1], where
-// c = ((l >> 2) & 1) * 8 + ((l >> 1) & 1) * 4 + (l & 1) * 2 is returned.
-__device__ __forceinline__ int quarter_reduce16(float v[16]) {
+// Sum 10 per-lane values over each quarter (8 lanes) with 10 shuffles: v[8]
+// and v[9] first (lanes with l % 4 == 0 end with component 8, if bit 2 of the
+// lane is clear, or 9 in v[8]), then v[0..7] as quarter_reduce8 (lane l ends
+// with the component it returns in v[0]).
+__device__ __forceinline__ int quarter_reduce10(float v[10]) {
   const int lane = threadIdx.x & 31;
-  bool hi = lane & 4;
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    float send = hi ? v[k] : v[k + 8];
-    float keep = hi ? v[k + 8] : v[k];
-    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-  }
-  hi = lane & 2;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    float send = hi ? v[k] : v[k + 4];
-    float keep = hi ? v[k + 4] : v[k];
-    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
-  }
-  hi = lane & 1;
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    float send = hi ? v[k] : v[k + 2];
-    float keep = hi ? v[k + 2] : v[k];
-    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
-  }
-  return ((lane >> 2) & 1) * 8 + ((lane >> 1) & 1) * 4 + (lane & 1) * 2;
+  const bool hi = lane & 4;
+  const float send = hi ? v[8] : v[9], keep = hi ? v[9] : v[8];
+  float w = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  w += __shfl_xor_sync(0xffffffffu, w, 2);
+  w += __shfl_xor_sync(0xffffffffu, w, 1);
+  v[8] = w;
+  return quarter_reduce8(v);
 }
 
 // Accumulated components per (tile, Gaussian): u, v, conic a, b, c, alpha and
@@ -409,9 +395,9 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs &a, int64_t gt, BwdSme
         const int k = has ? c0 + __ffs(mine) - 1 : c0;
         if (has) mine &= mine - 1;
         const uint32_t pos = (uint32_t)(hi - 1 - k);
-        float gv[PIX ? 16 : 8];
+        float gv[PIX ? 10 : 8];
 #pragma unroll
-        for (int c = 0; c < (PIX ? 16 : 8); ++c) gv[c] = 0.f;
+        for (int c = 0; c < (PIX ? 10 : 8); ++c) gv[c] = 0.f;
         bool act = has && pos < last;
         if (act) {
           const float4 A = s_a[k], B = s_b[k];
@@ -457,10 +443,10 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs &a, int64_t gt, BwdSme
         // sum the quarter's 8 lanes (each quarter has its own entry k)
         if (__any_sync(0xffffffffu, act)) {
           if (PIX) {
-            const int comp = quarter_reduce16(gv);
-            if (has && comp < 10) {
+            const int comp = quarter_reduce10(gv);
+            if (has) {
               if (gv[0] != 0.f) atomicAdd(&s_acc[k][comp], gv[0]);
-              if (gv[1] != 0.f) atomicAdd(&s_acc[k][comp + 1], gv[1]);
+              if ((lane & 3) == 0 && gv[8] != 0.f) atomicAdd(&s_acc[k][(lane & 4) ? 9 : 8], gv[8]);
             }
           } else {
             const int comp = quarter_reduce8(gv);
@@ -694,9 +680,9 @@ __device__ __forceinline__ void bwd_warp_item(const RasterArgs &a, int64_t gt, i
       const int k = has ? __ffs(mine) - 1 : 0;
       if (has) mine &= mine - 1;
       const uint32_t pos = (uint32_t)(hi - 1 - k);
-      float gv[PIX ? 16 : 8];
+      float gv[PIX ? 10 : 8];
 #pragma unroll
-      for (int c = 0; c < (PIX ? 16 : 8); ++c) gv[c] = 0.f;
+      for (int c = 0; c < (PIX ? 10 : 8); ++c) gv[c] = 0.f;
       bool act = has && pos < last;
       if (act) {
         const float4 A = sA[k], B = sB[k];
@@ -740,10 +726,10 @@ __device__ __forceinline__ void bwd_warp_item(const RasterArgs &a, int64_t gt, i
       }
       if (__any_sync(0xffffffffu, act)) {
         if (PIX) {
-          const int comp = quarter_reduce16(gv);
-          if (has && comp < 10) {
+          const int comp = quarter_reduce10(gv);
+          if (has) {
             if (gv[0] != 0.f) atomicAdd(&sAcc[k][comp], gv[0]);
-            if (gv[1] != 0.f) atomicAdd(&sAcc[k][comp + 1], gv[1]);
+            if ((lane & 3) == 0 && gv[8] != 0.f) atomicAdd(&sAcc[k][(lane & 4) ? 9 : 8], gv[8]);
           }
         } else {
           const int comp = quarter_reduce8(gv);
