@@ -13,10 +13,11 @@
 //            slots of each tile's list (shared-memory cursors);
 //   sort     every list is ordered by (depth bits, Gaussian) in shared
 //            memory: a warp for lists up to 32 entries (bitonic network), a
-//            block for longer ones (stable 8-bit counting passes over the
-//            depth bits that vary in the list, then over the Gaussian index
-//            where depths tie); lists longer than BIN_LIST_LONG are sorted in
-//            chunks that one block then merges (merge path).
+//            block for longer ones (buckets by the top bits of the depth, each
+//            ordered by insertion; where depths cluster, stable 8-bit counting
+//            passes over the depth bits that vary in the list, then over the
+//            Gaussian index where depths tie); lists longer than BIN_LIST_LONG
+//            are sorted in chunks that one block then merges (merge path).
 // Depth is positive, so its IEEE bits order like the number. The result is the
 // unique order of Gaussians by (depth, index), the order of a stable sort of
 // the pairs by depth in ascending Gaussian order. No block waits on another.
@@ -687,6 +688,7 @@ int64_t list_capacity(int64_t tiles, int64_t pairs) {
 
 int64_t part_capacity(int64_t tiles) { return 2 * ((tiles + 1023) / 1024) + 2; }
 
+
 cudaError_t prepare_bin_kernels() {
   // the block sorts keep two copies of a list in dynamic shared memory; the
   // attributes are set once per device, outside any stream capture
@@ -710,6 +712,7 @@ void launch_binning(const RenderShape &s, uint64_t pair_bound, ddgs_workspace &w
   if (prepare_bin_kernels() != cudaSuccess) return;  // surfaces via cudaGetLastError
   const uint64_t cap = (uint64_t)ws.pair_cap;
   const size_t hsm = (size_t)s.hist_area * sizeof(uint32_t);  // <= 32 KiB
+  const unsigned sms = (unsigned)device_sms();  // the sorts run persistent blocks per SM
   const bool pairs = pair_bound > 0 && s.n_items > 0;
   if (pairs) {
     LaunchScope ls(KID_BIN_COUNT, st);
@@ -746,28 +749,28 @@ void launch_binning(const RenderShape &s, uint64_t pair_bound, ddgs_workspace &w
   }
   {
     LaunchScope ls(KID_BIN_SORT, st);
-    bin_sort_warp_kernel<<<152 * 4, 256, 0, st>>>(L.item[LIST_WARP], L.count + LIST_WARP,
+    bin_sort_warp_kernel<<<sms * 4, 256, 0, st>>>(L.item[LIST_WARP], L.count + LIST_WARP,
                                                    ws.ranges, ws.keys[0], ws.vals);
   }
   {
     LaunchScope ls(KID_BIN_SORT, st);
-    bin_sort_block_kernel<128, SORT_SHORT / 128, 8><<<152 * 8, 128, SHORT_SMEM, st>>>(
+    bin_sort_block_kernel<128, SORT_SHORT / 128, 8><<<sms * 8, 128, SHORT_SMEM, st>>>(
         L.item[LIST_SHORT], L.count + LIST_SHORT, ws.ranges, ws.keys[0], ws.vals);
   }
   {
     LaunchScope ls(KID_BIN_SORT, st);
-    bin_sort_block_kernel<128, SORT_MID / 128, 6><<<152 * 6, 128, MID_SMEM, st>>>(
+    bin_sort_block_kernel<128, SORT_MID / 128, 6><<<sms * 6, 128, MID_SMEM, st>>>(
         L.item[LIST_MID], L.count + LIST_MID, ws.ranges, ws.keys[0], ws.vals);
   }
   {
     LaunchScope ls(KID_BIN_SORT, st);
     bin_sort_block_kernel<SORT_LONG_THREADS, SORT_LONG_ITEMS, 1>
-        <<<152, SORT_LONG_THREADS, LONG_SMEM, st>>>(L.item[LIST_BLOCK], L.count + LIST_BLOCK,
+        <<<sms, SORT_LONG_THREADS, LONG_SMEM, st>>>(L.item[LIST_BLOCK], L.count + LIST_BLOCK,
                                                    ws.ranges, ws.keys[0], ws.vals);
   }
   {
     LaunchScope ls(KID_BIN_MERGE, st);
-    bin_merge_kernel<<<152 * 2, 256, 0, st>>>(L.item[LIST_LONG], L.count + LIST_LONG, ws.ranges,
+    bin_merge_kernel<<<sms * 2, 256, 0, st>>>(L.item[LIST_LONG], L.count + LIST_LONG, ws.ranges,
                                               ws.keys[0], ws.keys[1], ws.vals);
   }
 }

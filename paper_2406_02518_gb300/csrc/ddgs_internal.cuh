@@ -353,6 +353,8 @@ void launch_raster_bwd(const RenderShape &s, const RasterParams &p, ddgs_workspa
                        const float *dL_dimage, const float *t_final, const uint32_t *n_last,
                        const PixelRays *pr, cudaStream_t st);
 
+int device_sms();  // streaming multiprocessors of the current device (raster.cu)
+
 // api.cu
 void launch_l1_loss(const float *image, const float *target, int per_view, int V, int64_t hw,
                     float *loss, float *grad, cudaStream_t st);

@@ -738,7 +738,7 @@ extern "C" ddgs_status ddgs_rads(const ddgs_volume *vol, int32_t n1, int32_t n2,
   const int64_t n_max = (int64_t)n1 + n2;
   // candidate slices of the neighbour search: enough blocks to fill the GPU
   const int64_t qblk = (n_max + KNN_T * KNN_Q - 1) / (KNN_T * KNN_Q);
-  const int slices = (int)std::max<int64_t>(1, std::min<int64_t>(32, qblk ? (8 * 152 + qblk - 1) / qblk : 1));
+  const int slices = (int)std::max<int64_t>(1, std::min<int64_t>(32, qblk ? (8 * device_sms() + qblk - 1) / qblk : 1));
 
   // scratch: state | cnt u32[nblk] | wsub u64[8 nblk] | wsum u64[nblk] | coff u64[nblk+1] |
   //          woff u64[nblk+1] | scan tops u64[2][1024] | knn partial f32x4[slices][n1+n2]
@@ -764,7 +764,7 @@ extern "C" ddgs_status ddgs_rads(const ddgs_volume *vol, int32_t n1, int32_t n2,
   {
     LaunchScope ls(KID_RADS_MINMAX, st);
     const int64_t want = (nvox / 8 + RT - 1) / RT;
-    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, 152 * 8));
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, 8 * device_sms()));
     rads_minmax_kernel<<<grid, RT, 0, st>>>(v, state);
   }
   {
@@ -803,7 +803,7 @@ extern "C" ddgs_status ddgs_rads(const ddgs_volume *vol, int32_t n1, int32_t n2,
         LaunchScope ls(KID_RADS_SELECT, st);
         rads_select_init_kernel<<<1, RT, 0, st>>>(state, (uint64_t)(n1 - 1));
       }
-      const unsigned hg = (unsigned)std::max<int64_t>(1, std::min<int64_t>((M + RT - 1) / RT, 152 * 2));
+      const unsigned hg = (unsigned)std::max<int64_t>(1, std::min<int64_t>((M + RT - 1) / RT, 2 * device_sms()));
       // digits of 11 bits from the top: shifts 53, 42, 31, 20, 9 and a last 9-bit digit
       for (int shift = 53; shift >= 0; shift -= 11) {
         LaunchScope ls(KID_RADS_SELECT, st);

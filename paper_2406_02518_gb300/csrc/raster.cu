@@ -837,18 +837,6 @@ __global__ void __launch_bounds__(256) tile_order_view_kernel(const ViewTab *vie
   }
 }
 
-int device_sms() {
-  static int sms[64] = {};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) return 152;
-  if (!sms[dev]) {
-    int n = 0;
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    sms[dev] = n > 0 ? n : 152;
-  }
-  return sms[dev];
-}
 
 // Resident blocks per SM of a kernel, cached per (device, kernel); the query
 // is not a stream operation, so it is also legal while a stream is captured.
@@ -1025,6 +1013,20 @@ void launch_raster_bwd(const RenderShape &s, const RasterParams &p, ddgs_workspa
   } else {
     bwd_dispatch<256, false>(a, s.tile, st);
   }
+}
+
+// Streaming multiprocessors of the current device (cached per device).
+int device_sms() {
+  static int sms[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return 152;
+  if (!sms[dev]) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    sms[dev] = n > 0 ? n : 152;
+  }
+  return sms[dev];
 }
 
 }  // namespace ddgs
