@@ -24,6 +24,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -399,8 +400,7 @@ def run_ours(args):
         graph.replay()
     torch.cuda.synchronize()
     launches0 = B.kernel_launches()
-    clocks = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
-                    if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/ddgs_clocks_{rank}.csv")
+    clocks = Clocks(os.path.join(tempfile.gettempdir(), f"ddgs_clocks_{os.getpid()}_{rank}.csv"))
     clocks.start()
     barrier()
     torch.cuda.synchronize()
@@ -611,8 +611,7 @@ def run_fit(args, large):
         step()
     torch.cuda.synchronize()
     launches0 = B.kernel_launches()
-    clocks = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
-                    if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/ddgs_clocks_{rank}.csv")
+    clocks = Clocks(os.path.join(tempfile.gettempdir(), f"ddgs_clocks_{os.getpid()}_{rank}.csv"))
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
