@@ -29,7 +29,8 @@
 namespace ddgs {
 namespace {
 
-constexpr int BIN_THREADS = 256;
+constexpr int BIN_THREADS = 256;   // count blocks
+constexpr int SCAT_THREADS = 512;  // scatter blocks: more records in flight per block
 constexpr int SORT_SHORT = 1024;  // lists of one 128-thread block (8 entries a thread)
 constexpr int SORT_MID = 2048;    // lists of one 128-thread block (16 entries a thread)
 constexpr int MERGE_ITEMS = 8;    // outputs per thread per merge step
@@ -288,7 +289,7 @@ __device__ __forceinline__ void st_hint(uint64_t *a, uint64_t v, uint64_t pol) {
 // empty by a capacity overflow are dropped.
 constexpr uint32_t CUR_ONE = 0x80000000u, CUR_DROP = 0xffffffffu;
 
-__global__ void __launch_bounds__(BIN_THREADS) bin_scatter_kernel(RenderShape s, const uint4 *info,
+__global__ void __launch_bounds__(SCAT_THREADS) bin_scatter_kernel(RenderShape s, const uint4 *info,
                                                                     const uint32_t *hist,
                                                                     const uint2 *ranges,
                                                                     uint64_t *keys, uint32_t *vals,
@@ -298,7 +299,7 @@ __global__ void __launch_bounds__(BIN_THREADS) bin_scatter_kernel(RenderShape s,
   const BinItem it = bin_item(s, vt, blockIdx.x);
   const int tiles_y = (vt.H + s.tile - 1) / s.tile;
   const int area = it.bw * it.bh;
-  for (int p = threadIdx.x; p < area; p += BIN_THREADS) {
+  for (int p = threadIdx.x; p < area; p += SCAT_THREADS) {
     const int x = it.tx0 + p % it.bw, y = it.ty0 + p / it.bw;
     uint32_t c = CUR_DROP;
     if (x < vt.tiles_x && y < tiles_y) {
@@ -309,18 +310,18 @@ __global__ void __launch_bounds__(BIN_THREADS) bin_scatter_kernel(RenderShape s,
   }
   __syncthreads();
   const uint64_t pol_in = l2_policy_evict_first(), pol_out = l2_policy_evict_last();
-  for (int64_t l0 = it.l0 + threadIdx.x; l0 < it.l1; l0 += BIN_LOADS * BIN_THREADS) {
+  for (int64_t l0 = it.l0 + threadIdx.x; l0 < it.l1; l0 += BIN_LOADS * SCAT_THREADS) {
     uint4 b[BIN_LOADS];
 #pragma unroll
     for (int k = 0; k < BIN_LOADS; ++k) {
-      const int64_t l = l0 + k * BIN_THREADS;
+      const int64_t l = l0 + k * SCAT_THREADS;
       b[k] = l < it.l1 ? ld_hint(info + it.rec0 + l, pol_in) : make_uint4(0, 0, 0, 0);
     }
 #pragma unroll
     for (int k = 0; k < BIN_LOADS; ++k) {
       int x0, y0, x1, y1;
       if (!band_rect(b[k], it, x0, y0, x1, y1)) continue;
-      const uint32_t l = (uint32_t)(l0 + k * BIN_THREADS);
+      const uint32_t l = (uint32_t)(l0 + k * SCAT_THREADS);
       const uint64_t key = ((uint64_t)b[k].z << 32) | l;
       for (int y = y0; y <= y1; ++y)
         for (int x = x0; x <= x1; ++x) {
@@ -744,7 +745,7 @@ void launch_binning(const RenderShape &s, uint64_t pair_bound, ddgs_workspace &w
   if (!pairs) return;
   {
     LaunchScope ls(KID_BIN_SCATTER, st);
-    bin_scatter_kernel<<<(unsigned)s.n_items, BIN_THREADS, hsm, st>>>(
+    bin_scatter_kernel<<<(unsigned)s.n_items, SCAT_THREADS, hsm, st>>>(
         s, reinterpret_cast<const uint4 *>(ws.rect), ws.hist, ws.ranges, ws.keys[0], ws.vals, cap);
   }
   {
