@@ -117,10 +117,10 @@ class Clocks:
 # shape and workload match; otherwise traffic is null.
 TRAFFIC = {
     "raster_bwd": {
-        "sources_sha256": {"raster.cu": "0920dbf1166fd74141728bd43342b2ec8d8617bd02238b817d1d45ef4a9a9af8",
+        "sources_sha256": {"raster.cu": "a3d7c702d57dcaaae01860adc6cf2d16834a1c0cf83ac9d34072c148134d2459",
                            "ddgs_internal.cuh": "fa72ca1a83418c995fe5d9ca47a902b9883fb2bb5b99268157df8a084bb8fb8d"},
         "tile": 8, "batch_depth": 32, "views": 64, "gaussians": 500_000,
-        "bytes_per_launch": 2450.0e6 + 579.5e6,
+        "bytes_per_launch": 2450.0e6 + 579.0e6,
         "how": "one-pass ncu capture of the 64-pose step; profiles/launches_registration_500k_64x256.md",
     },
 }

@@ -33,10 +33,13 @@ ddgs_status cuda_status(cudaError_t e, const char *what) { return cuda_fail(e, w
 
 namespace {
 
+// Reallocate p for `need` elements. The capacity field of p's group is zeroed
+// first and set by the caller once every buffer of the group has grown, so a
+// failed allocation leaves the group marked empty and the next call retries
+// it instead of running on a null or short buffer.
 template <class Tp>
-ddgs_status grow(Tp *&p, int64_t &cap_field, int64_t need, int64_t cur_cap, size_t elem) {
-  (void)cap_field;
-  if (need <= cur_cap && p) return DDGS_OK;
+ddgs_status grow(Tp *&p, int64_t &cap_field, int64_t need, size_t elem) {
+  cap_field = 0;
   if (p) CK(cudaFree(p));
   p = nullptr;
   CK(cudaMalloc(reinterpret_cast<void **>(&p), (size_t)(need > 0 ? need : 1) * elem));
@@ -195,7 +198,7 @@ ddgs_status ensure_lists(ddgs_workspace *ws) {
   const int64_t need = ddgs::list_capacity(ws->tile_cap, ws->pair_cap);
   if (need <= ws->list_cap && ws->lists) return DDGS_OK;
   const int64_t cap = need + need / 4;
-  ddgs_status st = grow(ws->lists, ws->list_cap, cap, 0, sizeof(uint64_t));
+  ddgs_status st = grow(ws->lists, ws->list_cap, cap, sizeof(uint64_t));
   if (st) return st;
   ws->list_cap = cap;
   return DDGS_OK;
@@ -206,36 +209,36 @@ ddgs_status ensure_records(ddgs_workspace *ws, const ddgs::RenderShape &s) {
   if (s.records > ws->rec_cap || !ws->rec) {
     int64_t cap = s.records + s.records / 4 + 1024;
     ddgs_status st;
-    if ((st = grow(ws->rec, ws->rec_cap, 2 * cap, 0, sizeof(float4)))) return st;
-    if ((st = grow(ws->rect, ws->rec_cap, cap, 0, sizeof(uint4)))) return st;
-    if ((st = grow(ws->grad2d, ws->rec_cap, 2 * cap, 0, sizeof(float4)))) return st;
+    if ((st = grow(ws->rec, ws->rec_cap, 2 * cap, sizeof(float4)))) return st;
+    if ((st = grow(ws->rect, ws->rec_cap, cap, sizeof(uint4)))) return st;
+    if ((st = grow(ws->grad2d, ws->rec_cap, 2 * cap, sizeof(float4)))) return st;
     ws->rec_cap = cap;
   }
   if (ws->rec2 && ws->pix_cap < ws->rec_cap) {  // per-pixel storage follows the records
     ddgs_status st;
-    if ((st = grow(ws->rec2, ws->pix_cap, ws->rec_cap, 0, sizeof(float4)))) return st;
-    if ((st = grow(ws->grad_h, ws->pix_cap, ws->rec_cap, 0, sizeof(float4)))) return st;
+    if ((st = grow(ws->rec2, ws->pix_cap, ws->rec_cap, sizeof(float4)))) return st;
+    if ((st = grow(ws->grad_h, ws->pix_cap, ws->rec_cap, sizeof(float4)))) return st;
     ws->pix_cap = ws->rec_cap;
   }
   if (blk > ws->blk_cap || !ws->blk_total) {
     int64_t cap = blk + blk / 4 + 64;
     ddgs_status st;
-    if ((st = grow(ws->blk_total, ws->blk_cap, cap, 0, sizeof(uint32_t)))) return st;
+    if ((st = grow(ws->blk_total, ws->blk_cap, cap, sizeof(uint32_t)))) return st;
     ws->blk_cap = cap;
   }
   if (s.total_tiles > ws->tile_cap || !ws->ranges) {
     int64_t cap = s.total_tiles + s.total_tiles / 4 + 64;
     ddgs_status st;
-    if ((st = grow(ws->ranges, ws->tile_cap, cap, 0, sizeof(uint2)))) return st;
-    if ((st = grow(ws->order, ws->tile_cap, cap, 0, sizeof(uint32_t)))) return st;
+    if ((st = grow(ws->ranges, ws->tile_cap, cap, sizeof(uint2)))) return st;
+    if ((st = grow(ws->order, ws->tile_cap, cap, sizeof(uint32_t)))) return st;
     int64_t pc = 0;  // the part sums follow the tiles
-    if ((st = grow(ws->part, pc, ddgs::part_capacity(cap), 0, sizeof(uint64_t)))) return st;
+    if ((st = grow(ws->part, pc, ddgs::part_capacity(cap), sizeof(uint64_t)))) return st;
     ws->tile_cap = cap;
   }
   if (s.hist_slots > ws->hist_cap || !ws->hist) {
     int64_t cap = std::max<int64_t>(s.hist_slots + s.hist_slots / 4, 1024);
     ddgs_status st;
-    if ((st = grow(ws->hist, ws->hist_cap, cap, 0, sizeof(uint32_t)))) return st;
+    if ((st = grow(ws->hist, ws->hist_cap, cap, sizeof(uint32_t)))) return st;
     ws->hist_cap = cap;
   }
   return ensure_lists(ws);
@@ -247,8 +250,8 @@ ddgs_status ensure_pairs(ddgs_workspace *ws, int64_t pairs) {
   const int64_t cap = std::min<int64_t>(pairs + pairs / 4 + 4096, ddgs::BIN_MAX_PAIRS);
   ddgs_status st;
   for (int b = 0; b < 2; ++b)
-    if ((st = grow(ws->keys[b], ws->pair_cap, cap, 0, sizeof(uint64_t)))) return st;
-  if ((st = grow(ws->vals, ws->pair_cap, cap, 0, sizeof(uint32_t)))) return st;
+    if ((st = grow(ws->keys[b], ws->pair_cap, cap, sizeof(uint64_t)))) return st;
+  if ((st = grow(ws->vals, ws->pair_cap, cap, sizeof(uint32_t)))) return st;
   ws->pair_cap = cap;
   return ensure_lists(ws);
 }
@@ -469,8 +472,8 @@ ddgs_status render_common(const ddgs_gaussians &g, const ddgs_views &v, const dd
   } else {
     if ((st = ensure_records(ws, s))) return st;
     if (g.per_pixel && !ws->rec2) {
-      if ((st = grow(ws->rec2, ws->pix_cap, ws->rec_cap, 0, sizeof(float4)))) return st;
-      if ((st = grow(ws->grad_h, ws->pix_cap, ws->rec_cap, 0, sizeof(float4)))) return st;
+      if ((st = grow(ws->rec2, ws->pix_cap, ws->rec_cap, sizeof(float4)))) return st;
+      if ((st = grow(ws->grad_h, ws->pix_cap, ws->rec_cap, sizeof(float4)))) return st;
       ws->pix_cap = ws->rec_cap;
     }
   }
@@ -583,6 +586,10 @@ ddgs_status check_batch(const ddgs_batch *b, const ddgs_config *c) {
     return DDGS_ERR_INVALID_ARG;
   int64_t n = 0, ni = 0, nv = 0;
   for (int32_t r = 0; r < b->n_requests; ++r) {
+    // per-request bounds first, so that the sums below cannot overflow
+    const int64_t nr = b->gaussian_counts[r], nir = b->iso_counts[r];
+    if (nr < 0 || nr >= (int64_t(1) << 31) || nir < 0 || nir > nr || b->view_counts[r] < 0)
+      return DDGS_ERR_INVALID_ARG;
     n += b->gaussian_counts[r];
     ni += b->iso_counts[r];
     nv += b->view_counts[r];
