@@ -145,6 +145,15 @@ def _stream():
     return C.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
+def _expect(t: torch.Tensor, name: str, shape, dtypes=(torch.float32,)):
+    """The library reads raw pointers with sizes taken from the counts, so a
+    tensor of another shape or dtype would be read out of bounds: refuse it."""
+    if t.dtype not in dtypes:
+        raise ValueError(f"{name}: dtype {t.dtype}, expected one of {tuple(dtypes)}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: shape {tuple(t.shape)}, expected {tuple(shape)}")
+
+
 @dataclasses.dataclass
 class Cloud:
     """Device tensors of a Gaussian cloud (layouts of ddgs_gaussians)."""
@@ -177,7 +186,21 @@ class Cloud:
     def sh_degree(self):
         return {3: 1, 8: 2, 15: 3}[int(self.B_dir.shape[-2])]
 
+    def validate(self):
+        n, ni, k = self.n, self.n_iso, self.feat_dim
+        _expect(self.means, "means", (n, 3))
+        _expect(self.log_scales, "log_scales", (n, 3))
+        _expect(self.quats, "quats", (n, 4))
+        _expect(self.opacity_logits, "opacity_logits", (n,))
+        _expect(self.feat_iso, "feat_iso", (ni, k))
+        _expect(self.feat_dir, "feat_dir", (n - ni, k), (torch.float32, torch.bfloat16))
+        _expect(self.b_iso, "b_iso", (k,))
+        if self.B_dir.dim() != 2 or int(self.B_dir.shape[0]) not in (3, 8, 15):
+            raise ValueError(f"B_dir: shape {tuple(self.B_dir.shape)}, expected (L(L+2), {k})")
+        _expect(self.B_dir, "B_dir", (self.B_dir.shape[0], k))
+
     def struct(self) -> _Gaussians:
+        self.validate()
         bf16 = self.feat_dir.dtype == torch.bfloat16
         return _Gaussians(self.n, self.n_iso, _ptr(self.means), _ptr(self.log_scales),
                           _ptr(self.quats), _ptr(self.opacity_logits),
@@ -198,7 +221,13 @@ class Views:
     def n_views(self):
         return self.world_to_cam.shape[0]
 
+    def validate(self):
+        V = self.n_views
+        _expect(self.world_to_cam, "world_to_cam", (V, 3, 4))
+        _expect(self.detector, "detector", (V, 5))
+
     def struct(self) -> _Views:
+        self.validate()
         return _Views(self.n_views, self.height, self.width, _ptr(self.world_to_cam),
                       _ptr(self.detector))
 
@@ -299,6 +328,9 @@ def render(cloud: Cloud, views: Views, cfg: Config, ws: Workspace, out=None):
                torch.empty((V, H, W), dtype=torch.float32, device=dev),
                torch.empty((V, H, W), dtype=torch.int32, device=dev))
     img, tf, nl = out
+    _expect(img, "image", (V, H, W))
+    _expect(tf, "t_final", (V, H, W))
+    _expect(nl, "n_last", (V, H, W), (torch.int32,))
     g, v, c = cloud.struct(), views.struct(), cfg.struct()
     _check(lib.ddgs_render(C.byref(g), C.byref(v), C.byref(c), ws.handle, _ptr(img), _ptr(tf),
                            _ptr(nl), _stream()), "ddgs_render")
@@ -323,6 +355,12 @@ def render_backward(cloud: Cloud, views: Views, cfg: Config, ws: Workspace, dL_d
     for k in want:
         if k not in grads:
             grads[k] = torch.empty(shapes[k], dtype=torch.float32, device=dev)
+    for k, t in grads.items():
+        _expect(t, f"gradient {k}", shapes[k])
+    img_shape = (views.n_views, views.height, views.width)
+    _expect(dL_dimage, "dL_dimage", img_shape)
+    _expect(t_final, "t_final", img_shape)
+    _expect(n_last, "n_last", img_shape, (torch.int32,))
     gs = _Grads(*[_ptr(grads[k]) if k in grads else None for k in GRAD_FIELDS])
     g, v, c = cloud.struct(), views.struct(), cfg.struct()
     _check(lib.ddgs_render_backward(C.byref(g), C.byref(v), C.byref(c), ws.handle,
@@ -339,6 +377,12 @@ def l1_loss(image: torch.Tensor, target: torch.Tensor, loss=None, grad=None):
     per_view = int(target.dim() == image.dim() and target.shape[0] == V and V > 1)
     loss = torch.empty(V, dtype=torch.float32, device=image.device) if loss is None else loss
     grad = torch.empty_like(image) if grad is None else grad
+    _expect(image, "image", image.shape)
+    if target.dtype != torch.float32 or target.numel() != (V * hw if per_view else hw):
+        raise ValueError(f"target: {tuple(target.shape)} {target.dtype}, expected float32 with "
+                         f"{V * hw if per_view else hw} elements")
+    _expect(loss, "loss", (V,))
+    _expect(grad, "grad", image.shape)
     _check(lib.ddgs_l1_loss(_ptr(image), _ptr(target.contiguous()), per_view, V, hw, _ptr(loss),
                             _ptr(grad), _stream()), "ddgs_l1_loss")
     return loss, grad
@@ -446,6 +490,11 @@ class ViewGroup:
     def n_views(self):
         return len(self.sizes)
 
+    def validate(self):
+        V = self.n_views
+        _expect(self.world_to_cam, "world_to_cam", (V, 3, 4))
+        _expect(self.detector, "detector", (V, 5))
+
     @staticmethod
     def of(views_list, device="cuda"):
         """From a list of single-size Views (device tensors)."""
@@ -466,7 +515,12 @@ class Batch:
     `views[r]` is a Views (one size) or a ViewGroup (per-view sizes)."""
 
     def __init__(self, clouds, views):
-        assert len(clouds) == len(views)
+        if len(clouds) != len(views):
+            raise ValueError(f"{len(clouds)} clouds but {len(views)} view sets")
+        for c in clouds:
+            c.validate()
+        for v in views:
+            v.validate()
         self.clouds, self.views = clouds, views
         self.means = torch.cat([c.means for c in clouds]).contiguous()
         self.log_scales = torch.cat([c.log_scales for c in clouds]).contiguous()
@@ -521,6 +575,9 @@ def render_batched(batch: Batch, cfg: Config, ws: Workspace, out=None):
                torch.empty(P, dtype=torch.float32, device=dev),
                torch.empty(P, dtype=torch.int32, device=dev))
     img, tf, nl = out
+    _expect(img, "image", (P,))
+    _expect(tf, "t_final", (P,))
+    _expect(nl, "n_last", (P,), (torch.int32,))
     b, c = batch.struct(), cfg.struct()
     _check(lib.ddgs_render_batched(C.byref(b), C.byref(c), ws.handle, _ptr(img), _ptr(tf),
                                    _ptr(nl), _stream()), "ddgs_render_batched")
@@ -540,6 +597,12 @@ def render_batched_backward(batch: Batch, cfg: Config, ws: Workspace, dL_dimage,
     for k in want:
         if k not in grads:
             grads[k] = torch.empty(shapes[k], dtype=torch.float32, device=dev)
+    for k, t in grads.items():
+        _expect(t, f"gradient {k}", shapes[k])
+    P = batch.pixels
+    _expect(dL_dimage, "dL_dimage", (P,))
+    _expect(t_final, "t_final", (P,))
+    _expect(n_last, "n_last", (P,), (torch.int32,))
     gs = _Grads(*[(_ptr(grads[k]) if grads[k].numel() else None) if k in grads else None
                   for k in GRAD_FIELDS])
     b, c = batch.struct(), cfg.struct()

@@ -59,3 +59,30 @@ def test_null_arguments_are_rejected_without_a_gpu(lib):
     assert lib.ddgs_render(None, None, None, None, None, None, None, None) == 1
     assert lib.ddgs_workspace_create(None) == 1
     assert lib.ddgs_l1_loss(None, None, 0, -1, 0, None, None, None) == 1
+
+
+def test_binding_refuses_mis_shaped_tensors_before_any_call(lib):
+    # the library takes raw pointers and sizes from the counts, so the binding
+    # checks every tensor's shape and dtype on the host first
+    import torch
+    n = 5
+    good = dict(means=torch.zeros(n, 3), log_scales=torch.zeros(n, 3), quats=torch.zeros(n, 4),
+                opacity_logits=torch.zeros(n), feat_iso=torch.zeros(3, 8),
+                feat_dir=torch.zeros(2, 8, dtype=torch.bfloat16), b_iso=torch.zeros(8),
+                B_dir=torch.zeros(3, 8))
+    B.Cloud(**good).validate()
+    bad = [("means", torch.zeros(n, 2)), ("log_scales", torch.zeros(n, 3, dtype=torch.float64)),
+           ("quats", torch.zeros(n, 3)), ("opacity_logits", torch.zeros(n, 1)),
+           ("feat_iso", torch.zeros(3, 4)), ("feat_dir", torch.zeros(3, 8)),
+           ("feat_dir", torch.zeros(2, 8, dtype=torch.float16)), ("b_iso", torch.zeros(1, 8)),
+           ("B_dir", torch.zeros(4, 8)), ("B_dir", torch.zeros(3, 7))]
+    for name, t in bad:
+        with pytest.raises(ValueError, match=name):
+            B.Cloud(**{**good, name: t}).validate()
+    B.Views(torch.zeros(2, 3, 4), torch.zeros(2, 5), 8, 8).validate()
+    with pytest.raises(ValueError, match="detector"):
+        B.Views(torch.zeros(2, 3, 4), torch.zeros(1, 5), 8, 8).validate()
+    with pytest.raises(ValueError, match="world_to_cam"):
+        B.Views(torch.zeros(2, 12), torch.zeros(2, 5), 8, 8).validate()
+    with pytest.raises(ValueError, match="target"):
+        B.l1_loss(torch.zeros(2, 4, 4), torch.zeros(3, 4))
