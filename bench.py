@@ -117,10 +117,10 @@ class Clocks:
 # shape and workload match; otherwise traffic is null.
 TRAFFIC = {
     "raster_bwd": {
-        "sources_sha256": {"raster.cu": "a3d7c702d57dcaaae01860adc6cf2d16834a1c0cf83ac9d34072c148134d2459",
+        "sources_sha256": {"raster.cu": "1f2c44896748d5dda5a10598448f083c6bbfc41f56104bf084018ab108622894",
                            "ddgs_internal.cuh": "fa72ca1a83418c995fe5d9ca47a902b9883fb2bb5b99268157df8a084bb8fb8d"},
         "tile": 8, "batch_depth": 32, "views": 64, "gaussians": 500_000,
-        "bytes_per_launch": 2450.0e6 + 579.0e6,
+        "bytes_per_launch": 2440.0e6 + 577.2e6,
         "how": "one-pass ncu capture of the 64-pose step; profiles/launches_registration_500k_64x256.md",
     },
 }

@@ -430,12 +430,14 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs &a, int64_t gt, BwdSme
               gv[5] = gs * e.G;
               gq = -0.5f * gs * B.y * e.G;
             }
-            const float gq2 = gq + gq;
-            gv[0] = gq2 * e.tx;
-            gv[1] = gq2 * e.ty;
-            gv[2] = gq * e.dx * e.dx;
-            gv[3] = gq2 * e.dx * e.dy;
-            gv[4] = gq * e.dy * e.dy;
+            // sums of gq dx, gq dy, gq dx^2, gq dx dy and gq dy^2; the mean and
+            // conic gradients are formed from them once per entry (below)
+            const float gdx = gq * e.dx, gdy = gq * e.dy;
+            gv[0] = gdx;
+            gv[1] = gdy;
+            gv[2] = gdx * e.dx;
+            gv[3] = gdx * e.dy;
+            gv[4] = gdy * e.dy;
             const float dcol = g * e.sigma * Tr;  // dL/dc
             if (PIX) {
               const float dz = dcol * c * (1.f - c);
@@ -474,7 +476,11 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs &a, int64_t gt, BwdSme
       if (PIX) nz |= (acc[7] != 0.f) | (acc[8] != 0.f) | (acc[9] != 0.f);
       if (nz) {
         float4 *dst = a.grad2d + 2 * (rec_base + s_id[e]);
-        atomicAdd(dst, make_float4(acc[0], acc[1], acc[2], acc[3]));
+        // dq/du = 2 (a dx + b dy), dq/dv = 2 (b dx + c dy), dq/db = 2 dx dy
+        const float ca = s_a[e].z, cb = s_a[e].w, cc = s_b[e].x;
+        const float du = 2.f * fmaf(ca, acc[0], cb * acc[1]);
+        const float dv = 2.f * fmaf(cb, acc[0], cc * acc[1]);
+        atomicAdd(dst, make_float4(du, dv, acc[2], 2.f * acc[3]));
         atomicAdd(dst + 1, make_float4(acc[4], acc[5], acc[6], 0.f));
         if (PIX) atomicAdd(a.grad_h + rec_base + s_id[e], make_float4(acc[7], acc[8], acc[9], 0.f));
       }
@@ -722,12 +728,14 @@ __device__ __forceinline__ void bwd_warp_item(const RasterArgs &a, int64_t gt, i
             gv[5] = gs * e.G;
             gq = -0.5f * gs * B.y * e.G;
           }
-          const float gq2 = gq + gq;
-          gv[0] = gq2 * e.tx;
-          gv[1] = gq2 * e.ty;
-          gv[2] = gq * e.dx * e.dx;
-          gv[3] = gq2 * e.dx * e.dy;
-          gv[4] = gq * e.dy * e.dy;
+          // sums of gq dx, gq dy, gq dx^2, gq dx dy and gq dy^2; the mean and
+          // conic gradients are formed from them once per entry (below)
+          const float gdx = gq * e.dx, gdy = gq * e.dy;
+          gv[0] = gdx;
+          gv[1] = gdy;
+          gv[2] = gdx * e.dx;
+          gv[3] = gdx * e.dy;
+          gv[4] = gdy * e.dy;
           const float dcol = g * e.sigma * Tr;  // dL/dc
           if (PIX) {
             const float dz = dcol * c * (1.f - c);
@@ -765,7 +773,11 @@ __device__ __forceinline__ void bwd_warp_item(const RasterArgs &a, int64_t gt, i
       if (nz) {
         const int64_t r = tg.rec_base + sId[lane];
         float4 *dst = a.grad2d + 2 * r;
-        atomicAdd(dst, make_float4(acc[0], acc[1], acc[2], acc[3]));
+        // dq/du = 2 (a dx + b dy), dq/dv = 2 (b dx + c dy), dq/db = 2 dx dy
+        const float ca = sA[lane].z, cb = sA[lane].w, cc = sB[lane].x;
+        const float du = 2.f * fmaf(ca, acc[0], cb * acc[1]);
+        const float dv = 2.f * fmaf(cb, acc[0], cc * acc[1]);
+        atomicAdd(dst, make_float4(du, dv, acc[2], 2.f * acc[3]));
         atomicAdd(dst + 1, make_float4(acc[4], acc[5], acc[6], 0.f));
         if (PIX) atomicAdd(a.grad_h + r, make_float4(acc[7], acc[8], acc[9], 0.f));
       }
