@@ -14,7 +14,6 @@
 // The array is shared by every call on a device and keeps the last call's
 // contents; whatever must start at zero is cleared by each call. Calls whose
 // work overlaps on the GPU (two streams, or two host threads) race on it.
-#include <cstdio>
 #include <mutex>
 
 #include "ddgs_internal.cuh"
@@ -67,7 +66,13 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 constexpr int kMaxDevices = 64;
 unsigned char *g_scratch_ptr[kMaxDevices] = {};
 std::mutex g_setup_mu;
-thread_local char g_static_err[160] = "";
+
+// A failed CUDA call: its message goes where ddgs_last_cuda_error reads it.
+#define CK_STATIC(call)                                             \
+  do {                                                              \
+    cudaError_t e_ = (call);                                        \
+    if (e_ != cudaSuccess) return ddgs::cuda_status(e_, #call);     \
+  } while (0)
 
 ddgs_status scratch_for_current_device(unsigned char **out) {
   int dev = -1;
@@ -75,12 +80,8 @@ ddgs_status scratch_for_current_device(unsigned char **out) {
   std::lock_guard<std::mutex> lk(g_setup_mu);
   if (!g_scratch_ptr[dev]) {
     void *p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess || !p) {
-      std::snprintf(g_static_err, sizeof g_static_err, "cudaGetSymbolAddress: %s",
-                    cudaGetErrorString(e));
-      return DDGS_ERR_CUDA;
-    }
+    CK_STATIC(cudaGetSymbolAddress(&p, g_scratch));
+    if (!p) return DDGS_ERR_CUDA;
     g_scratch_ptr[dev] = static_cast<unsigned char *>(p);
   }
   *out = g_scratch_ptr[dev];
@@ -145,10 +146,14 @@ extern "C" ddgs_status ddgs_render_static(const ddgs_gaussians *g, const ddgs_vi
     t.tiles_x = tx;
   }
   ddgs::plan_binning(t_view, v->n_views, t_req, s.total_tiles, tile, s, kSlotBudget);
+  if (s.hist_slots > kMaxSlots) return DDGS_ERR_CAPACITY;  // not reached: kMaxSlots bounds it
 
   unsigned char *base = nullptr;
   ddgs_status st = scratch_for_current_device(&base);
   if (st) return st;
+  // the long-list sort's shared-memory limit (set once per device; the binning
+  // would set it too, but here a failure is reported before any work is queued)
+  CK_STATIC(ddgs::prepare_bin_kernels());
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
 
   // A workspace view of the static array (host struct on the stack).
@@ -182,25 +187,21 @@ extern "C" ddgs_status ddgs_render_static(const ddgs_gaussians *g, const ddgs_vi
   s.req = d_req;
   s.view = d_view;
   // tables from pageable host memory: each copy returns once its source is staged
-  if (cudaMemcpyAsync(d_req, t_req, sizeof(t_req), cudaMemcpyHostToDevice, cs) != cudaSuccess ||
-      cudaMemcpyAsync(d_view, t_view, (size_t)(v->n_views + 1) * sizeof(ddgs::ViewTab),
-                      cudaMemcpyHostToDevice, cs) != cudaSuccess)
-    return DDGS_ERR_CUDA;
+  CK_STATIC(cudaMemcpyAsync(d_req, t_req, sizeof(t_req), cudaMemcpyHostToDevice, cs));
+  CK_STATIC(cudaMemcpyAsync(d_view, t_view, (size_t)(v->n_views + 1) * sizeof(ddgs::ViewTab),
+                            cudaMemcpyHostToDevice, cs));
 
   // counters left by the previous call start again from zero
-  if (cudaMemsetAsync(ws.d_status, 0, sizeof(int32_t), cs) != cudaSuccess ||
-      cudaMemsetAsync(ws.d_pairs, 0, sizeof(uint64_t), cs) != cudaSuccess)
-    return DDGS_ERR_CUDA;
+  CK_STATIC(cudaMemsetAsync(ws.d_status, 0, sizeof(int32_t), cs));
+  CK_STATIC(cudaMemsetAsync(ws.d_pairs, 0, sizeof(uint64_t), cs));
   uint64_t pairs = 0;
   if (s.records > 0) {
     ddgs::launch_preprocess_fwd(*g, *v, *c, s, ws, cs);
     ddgs::launch_scan_blocks(s.n_blocks, ws, cs);
-    if (cudaGetLastError() != cudaSuccess) return DDGS_ERR_CUDA;
+    CK_STATIC(cudaGetLastError());
     // the pair count decides the sort's size: read it (no allocation)
-    if (cudaMemcpyAsync(&pairs, ws.d_pairs, sizeof(uint64_t), cudaMemcpyDeviceToHost, cs) !=
-            cudaSuccess ||
-        cudaStreamSynchronize(cs) != cudaSuccess)
-      return DDGS_ERR_CUDA;
+    CK_STATIC(cudaMemcpyAsync(&pairs, ws.d_pairs, sizeof(uint64_t), cudaMemcpyDeviceToHost, cs));
+    CK_STATIC(cudaStreamSynchronize(cs));
     if (pairs > (uint64_t)kMaxPairs) return DDGS_ERR_CAPACITY;
   }
   if (s.total_tiles > 0) {
@@ -209,5 +210,6 @@ extern "C" ddgs_status ddgs_render_static(const ddgs_gaussians *g, const ddgs_vi
     ddgs::RasterParams P{c->alpha_min, c->alpha_max, c->t_min, c->q_max};
     ddgs::launch_raster_fwd(s, P, ws, image, t_final, n_last, nullptr, cs);
   }
-  return cudaGetLastError() == cudaSuccess ? DDGS_OK : DDGS_ERR_CUDA;
+  CK_STATIC(cudaGetLastError());
+  return DDGS_OK;
 }
