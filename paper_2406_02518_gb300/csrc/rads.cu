@@ -685,8 +685,13 @@ __global__ void rads_knn_merge_kernel(const float *part, int64_t n, int slices, 
 
 namespace {
 
-ddgs_status grow_bytes(unsigned char *&p, int64_t &cap, int64_t need) {
+// Reallocate the workspace buffer p (a field of the workspace) for `need`
+// bytes. Its capacity is zeroed first, so an allocation that fails leaves the
+// buffer marked empty and the next call retries it.
+template <class Tp>
+ddgs_status grow_bytes(Tp *&p, int64_t &cap, int64_t need) {
   if (need <= cap && p) return DDGS_OK;
+  cap = 0;
   if (p) RCK(cudaFree(p));
   p = nullptr;
   const int64_t c = need + need / 4 + 4096;
@@ -786,9 +791,8 @@ extern "C" ddgs_status ddgs_rads(const ddgs_volume *vol, int32_t n1, int32_t n2,
     const int64_t nkb = (M + RCH - 1) / RCH;
     const int64_t k_off = align256(8 * M), k_cnt = k_off + align256(8 * (nkb + 1)),
                   kbytes = k_cnt + align256(4 * nkb);
+    if ((s = grow_bytes(ws->rads_keys, ws->rads_key_cap, kbytes))) return s;
     unsigned char *kb = reinterpret_cast<unsigned char *>(ws->rads_keys);
-    if ((s = grow_bytes(kb, ws->rads_key_cap, kbytes))) return s;
-    ws->rads_keys = reinterpret_cast<uint64_t *>(kb);
     uint64_t *keys = ws->rads_keys;
     uint64_t *koff = reinterpret_cast<uint64_t *>(kb + k_off);
     uint32_t *kcnt = reinterpret_cast<uint32_t *>(kb + k_cnt);
