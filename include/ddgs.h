@@ -124,7 +124,9 @@ typedef struct ddgs_workspace ddgs_workspace;
 
 /* Workspace: per-(view, Gaussian) projections, tile lists and their counters,
  * request/view tables and the device status word, on the device that is
- * current at creation. Owned by the library between create and destroy. One
+ * current at creation; a call that uses the workspace while another device is
+ * current returns DDGS_ERR_INVALID_ARG. Owned by the library between create
+ * and destroy. One
  * workspace serves one render at a time; ddgs_render_backward reads what the
  * preceding ddgs_render left. A CUDA graph that captured calls on a workspace
  * stays valid while no call with another batch layout (counts, view sizes,

@@ -48,6 +48,13 @@ ddgs_status grow(Tp *&p, int64_t &cap_field, int64_t need, size_t elem) {
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// The workspace's buffers live on the device that was current at its
+// creation; kernels launched on another device must not receive them.
+bool on_workspace_device(const ddgs_workspace *ws) {
+  int dev = -1;
+  return cudaGetDevice(&dev) == cudaSuccess && dev == ws->device;
+}
+
 ddgs_status check_inputs(const ddgs_gaussians *g, const ddgs_views *v, const ddgs_config *c) {
   if (!g || !v || !c) return DDGS_ERR_INVALID_ARG;
   if (g->n < 0 || g->n_iso < 0 || g->n_iso > g->n || g->n >= (int64_t(1) << 31))
@@ -433,7 +440,8 @@ ddgs_status ddgs_workspace_destroy(ddgs_workspace *ws) {
 
 ddgs_status ddgs_workspace_reserve(ddgs_workspace *ws, int64_t records, int64_t pairs,
                                    int64_t tiles) {
-  if (!ws || records < 0 || pairs < 0 || tiles < 0) return DDGS_ERR_INVALID_ARG;
+  if (!ws || records < 0 || pairs < 0 || tiles < 0 || !on_workspace_device(ws))
+    return DDGS_ERR_INVALID_ARG;
   CK(cudaDeviceSynchronize());
   ddgs::RenderShape s{};
   s.records = records;
@@ -461,6 +469,7 @@ namespace {
 ddgs_status render_common(const ddgs_gaussians &g, const ddgs_views &v, const ddgs_config *c,
                           Layout &L, ddgs_workspace *ws, float *image, float *t_final,
                           uint32_t *n_last, cudaStream_t s_) {
+  if (!on_workspace_device(ws)) return DDGS_ERR_INVALID_ARG;
   ddgs_status st;
   ddgs::RenderShape &s = L.shape;
   if (c->no_sync) {
@@ -527,7 +536,7 @@ ddgs_status backward_common(const ddgs_gaussians &g, const ddgs_views &v, const 
                             const float *t_final, const uint32_t *n_last, const ddgs_grads *out,
                             cudaStream_t s_) {
   if (!ws || !out || !ws->have_render || L.hash != ws->last_hash ||
-      (g.per_pixel != 0) != ws->last_per_pixel)
+      (g.per_pixel != 0) != ws->last_per_pixel || !on_workspace_device(ws))
     return DDGS_ERR_INVALID_ARG;
   ddgs::RenderShape &s = L.shape;
   s.req = ws->d_req;
@@ -762,7 +771,7 @@ extern "C" {
 
 ddgs_status ddgs_debug_binning(const ddgs_workspace *ws, uint32_t *tiles_touched, uint64_t *keys,
                                uint32_t *vals, uint32_t *ranges, void *stream) {
-  if (!ws || !ws->have_render) return DDGS_ERR_INVALID_ARG;
+  if (!ws || !ws->have_render || !on_workspace_device(ws)) return DDGS_ERR_INVALID_ARG;
   cudaStream_t s_ = static_cast<cudaStream_t>(stream);
   const ddgs::RenderShape &s = ws->shape;
   if (tiles_touched && s.records > 0) {

@@ -730,6 +730,8 @@ extern "C" ddgs_status ddgs_rads(const ddgs_volume *vol, int32_t n1, int32_t n2,
                                  void *stream) {
   using namespace ddgs;
   if (!vol || !ws || !counts || !vol->hu || n1 < 0 || n2 < 0) return DDGS_ERR_INVALID_ARG;
+  int dev = -1;  // the workspace's buffers live on the device current at its creation
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != ws->device) return DDGS_ERR_INVALID_ARG;
   if (vol->nx < 1 || vol->ny < 1 || vol->nz < 1) return DDGS_ERR_INVALID_ARG;
   const int64_t nvox = (int64_t)vol->nx * vol->ny * vol->nz;
   if (nvox * 3 >= (int64_t(1) << 32)) return DDGS_ERR_INVALID_ARG;  // edge ids fill the key's low word
