@@ -18,3 +18,19 @@ def test_reference_arm_prints_its_line(monkeypatch, capsys):
     assert line["value"] > 0 and line["unit"] == bench.UNIT
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_traffic_is_reported_only_for_the_captured_sources_and_shape(monkeypatch):
+    import hashlib
+    import os
+    src = os.path.join(bench.ROOT, "paper_2406_02518_gb300", "csrc", "raster.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    entry = {"sources_sha256": {"raster.cu": sha}, "tile": 8, "batch_depth": 32, "views": 64,
+             "gaussians": 500_000, "bytes_per_launch": 123.0}
+    monkeypatch.setattr(bench, "TRAFFIC", {"raster_bwd": entry})
+    assert bench.captured_traffic("raster_bwd", 8, 32, 64, 500_000) == 123.0
+    assert bench.captured_traffic("raster_bwd", 16, 32, 64, 500_000) is None   # other shape
+    assert bench.captured_traffic("raster_bwd", 8, 32, 16, 500_000) is None    # other workload
+    assert bench.captured_traffic("raster_fwd", 8, 32, 64, 500_000) is None    # not captured
+    monkeypatch.setattr(bench, "TRAFFIC", {"raster_bwd": dict(entry, sources_sha256={"raster.cu": "0" * 64})})
+    assert bench.captured_traffic("raster_bwd", 8, 32, 64, 500_000) is None    # source changed
