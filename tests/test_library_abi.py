@@ -86,3 +86,20 @@ def test_binding_refuses_mis_shaped_tensors_before_any_call(lib):
         B.Views(torch.zeros(2, 12), torch.zeros(2, 5), 8, 8).validate()
     with pytest.raises(ValueError, match="target"):
         B.l1_loss(torch.zeros(2, 4, 4), torch.zeros(3, 4))
+
+
+def test_batch_refuses_mis_shaped_requests(lib):
+    import torch
+    n = 4
+    cloud = B.Cloud(torch.zeros(n, 3), torch.zeros(n, 3), torch.zeros(n, 4), torch.zeros(n),
+                    torch.zeros(n, 8), torch.zeros(0, 8), torch.zeros(8), torch.zeros(3, 8))
+    good = B.ViewGroup(torch.zeros(2, 3, 4), torch.zeros(2, 5), [(8, 8), (16, 4)])
+    good.validate()
+    with pytest.raises(ValueError, match="detector"):
+        B.ViewGroup(torch.zeros(2, 3, 4), torch.zeros(3, 5), [(8, 8), (16, 4)]).validate()
+    with pytest.raises(ValueError, match="clouds"):
+        B.Batch([cloud, cloud], [good])
+    bad_cloud = B.Cloud(torch.zeros(n, 3), torch.zeros(n, 3), torch.zeros(n, 4), torch.zeros(n + 1),
+                        torch.zeros(n, 8), torch.zeros(0, 8), torch.zeros(8), torch.zeros(3, 8))
+    with pytest.raises(ValueError, match="opacity_logits"):
+        B.Batch([bad_cloud], [good])
