@@ -126,3 +126,19 @@ def test_culling_near_far_and_offscreen():
     b = oracle.project32(sc, views, syn.Settings(near_plane=0.2))
     assert b["tiles_touched"][0, :3].tolist() == [0, 0, 0]
     assert b["tiles_touched"][0, 3:].min() > 0
+
+
+def test_non_finite_geometry_is_culled():
+    # a NaN depth, determinant, centre or extent fails the binning's comparisons
+    sc = syn.uniform_cloud(50, seed=1)
+    means, ls, qs = sc.means.copy(), sc.log_scales.copy(), sc.quats.copy()
+    means[0] = [np.nan, 0, 0]       # NaN centre (and depth through the rotation)
+    means[1, 0] = np.inf            # infinite centre
+    ls[2] = [np.nan, -3, -3]        # NaN covariance
+    qs[3] = [np.nan, 0, 0, 0]       # NaN rotation
+    sc.means, sc.log_scales, sc.quats = means, ls, qs
+    views = syn.Views(syn._f32(syn.pose_matrix(np.eye(3), np.array([0.0, 0.0, 2.0]))[None]),
+                      syn.detector(1, 4.0, 1 / 16), 128, 128)
+    b = oracle.project32(sc, views, syn.Settings(near_plane=0.2))
+    assert b["tiles_touched"][0, :4].tolist() == [0, 0, 0, 0]
+    assert b["tiles_touched"][0, 4:].min() > 0
