@@ -122,15 +122,18 @@ typedef struct {
 
 typedef struct ddgs_workspace ddgs_workspace;
 
-/* Workspace: per-(view, Gaussian) projections, tile lists and their counters,
+/* Workspace (infrastructure; no passage of the paper defines it): the
+ * per-(view, Gaussian) projections, the depth-ordered tile lists that Eq. 1's
+ * product over nearer Gaussians needs (Sec. 3.1), their counters, the
  * request/view tables and the device status word, on the device that is
  * current at creation; a call that uses the workspace while another device is
  * current returns DDGS_ERR_INVALID_ARG. Owned by the library between create
- * and destroy. One
- * workspace serves one render at a time; ddgs_render_backward reads what the
- * preceding ddgs_render left. A CUDA graph that captured calls on a workspace
- * stays valid while no call with another batch layout (counts, view sizes,
- * tile) or a larger size runs on that workspace. */
+ * and destroy (destroy accepts NULL). One workspace serves one render at a
+ * time; ddgs_render_backward reads what the preceding ddgs_render left. A
+ * CUDA graph that captured calls on a workspace stays valid while no call
+ * with another batch layout (counts, view sizes, tile) or a larger size runs
+ * on that workspace. Create returns DDGS_ERR_OUT_OF_MEMORY or DDGS_ERR_CUDA
+ * on failure, with *ws set to NULL. */
 ddgs_status ddgs_workspace_create(ddgs_workspace **ws);
 ddgs_status ddgs_workspace_destroy(ddgs_workspace *ws);
 
@@ -184,8 +187,8 @@ ddgs_status ddgs_render_backward(const ddgs_gaussians *g, const ddgs_views *v,
                                  const uint32_t *n_last, const ddgs_grads *out,
                                  void *stream);
 
-/* ddgs_render with no device allocation at all. (The paper has no
- * counterpart: this serves callers that may not allocate device memory while
+/* ddgs_render (Eq. 1 with Eq. 3) with no device allocation at all. (The
+ * paper has no counterpart for the allocation rule: this serves callers that may not allocate device memory while
  * they run -- a registration loop whose memory is fixed at start-up, code
  * running inside another runtime's allocator, a process whose device memory a
  * caching allocator owns.) Same inputs, outputs and results as ddgs_render;
@@ -242,7 +245,9 @@ ddgs_status ddgs_render_batched(const ddgs_batch *b, const ddgs_config *cfg,
                                 ddgs_workspace *ws, float *image, float *t_final,
                                 uint32_t *n_last, void *stream);
 
-/* ddgs_render_backward over a batch. Gradient layouts follow the batch's
+/* ddgs_render_backward over a batch: the gradients of Eq. 1 and Eq. 3
+ * (Sec. 3.1's differentiable rasteriser; Sec. 4.3's gradient to the pose) for
+ * every request. Gradient layouts follow the batch's
  * arrays: per-Gaussian fields [N][...], b_iso [R][k], B_dir [R][k_L][k],
  * world_to_cam [V][3][4]. Must follow the ddgs_render_batched that filled ws
  * with the same batch. */
@@ -301,7 +306,8 @@ ddgs_status ddgs_rads(const ddgs_volume *vol, int32_t n1, int32_t n2, uint64_t s
                       void *stream);
 
 /* Number of (Gaussian, tile) pairs of the last render, read from the host
- * mirror written by that render (valid after the stream has synchronised). */
+ * mirror written by that render (valid after the stream has synchronised;
+ * infrastructure, no counterpart in the paper). */
 ddgs_status ddgs_workspace_pairs(const ddgs_workspace *ws, int64_t *pairs);
 
 /* Per-request timing of the last batched render + backward on this workspace
@@ -313,7 +319,8 @@ ddgs_status ddgs_workspace_pairs(const ddgs_workspace *ws, int64_t *pairs);
 ddgs_status ddgs_request_times(const ddgs_workspace *ws, uint64_t *fwd_ns, uint64_t *bwd_ns,
                                void *stream);
 
-/* Copy the binning of the last render into caller buffers (device):
+/* Copy the binning of the last render (the per-tile depth order of Eq. 1's
+ * product, Sec. 3.1) into caller buffers (device):
  * tiles_touched [n_views][n], keys [pairs] ((global tile << 32) | depth bits,
  * global tile = view * tiles_per_view + row * tiles_x + col), vals [pairs]
  * (Gaussian index), ranges [n_views * tiles_per_view][2] ([start, end),
@@ -323,9 +330,9 @@ ddgs_status ddgs_debug_binning(const ddgs_workspace *ws, uint32_t *tiles_touched
                                void *stream);
 
 /* Synchronise the stream, then return and clear the status latched by
- * kernels since the last call (DDGS_OK, or DDGS_ERR_CAPACITY when a no_sync
- * render had more pairs than the reserved capacity: the tile lists that did
- * not fit were left empty). */
+ * kernels since the last call: DDGS_OK, or DDGS_ERR_CAPACITY when a no_sync
+ * render had more pairs than the reserved capacity (the tile lists that did
+ * not fit were left empty). Infrastructure, no counterpart in the paper. */
 ddgs_status ddgs_sync_status(ddgs_workspace *ws, void *stream);
 
 /* Floats of a cloud: n * (3 + 4 + 3 + 1 + k) + k + k_L * k, i.e. 19 per
