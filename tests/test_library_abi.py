@@ -103,3 +103,10 @@ def test_batch_refuses_mis_shaped_requests(lib):
                         torch.zeros(n, 8), torch.zeros(0, 8), torch.zeros(8), torch.zeros(3, 8))
     with pytest.raises(ValueError, match="opacity_logits"):
         B.Batch([bad_cloud], [good])
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    # no CPU fallback: without the built library the binding raises
+    monkeypatch.setattr(B, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        B.load(str(tmp_path / "libddgs.so"))
