@@ -76,7 +76,7 @@ def lib():
         _lib = C.CDLL(build())
         vp = C.c_void_p
         _lib.or_render.argtypes = [vp, vp, vp, vp, C.c_int64, vp, vp, vp, vp, vp, vp, vp, vp, C.c_int]
-        _lib.or_render_backward.argtypes = [vp, vp, vp, vp, C.c_int64, vp, vp] + [vp] * 9 + [C.c_int]
+        _lib.or_render_backward.argtypes = [vp, vp, vp, vp, C.c_int64, vp, vp, vp] + [vp] * 9 + [C.c_int]
         _lib.or_project.argtypes = [vp, vp, vp, vp]
         _lib.or32_project.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         _lib.or32_bin.argtypes = [vp, vp, C.c_int32, vp, vp, vp, C.c_int64, vp, vp, vp]
@@ -221,8 +221,11 @@ def render_alternatives(scene, views, settings, pix, n_flagged, max_flags=3,
 
 
 def render_backward(scene, views, settings, dL_dC, pix=None, depth32=None, threads=0,
-                    want_2d=False):
-    """FP64 gradient of sum_p dL_dC[p] C(p) with respect to every input."""
+                    want_2d=False, flip_masks=None):
+    """FP64 gradient of sum_p dL_dC[p] C(p) with respect to every input.
+
+    flip_masks (per requested pixel, optional) differentiates each pixel along
+    the forward walk with those flagged decisions inverted (see render)."""
     pk = _Pack(scene, views, settings)
     if depth32 is None:
         depth32 = project32(scene, views, settings)["depth"]
@@ -230,6 +233,9 @@ def render_backward(scene, views, settings, dL_dC, pix=None, depth32=None, threa
     pix, m = _pix(views, pix)
     g = np.ascontiguousarray(np.asarray(dL_dC, dtype=np.float64).reshape(-1))
     assert g.size == m
+    fm = None if flip_masks is None else np.ascontiguousarray(
+        np.asarray(flip_masks, dtype=np.uint32).reshape(-1))
+    assert fm is None or fm.size == m
     n, k, V = scene.n, scene.feat.shape[1], views.n_views
     out = dict(means=np.zeros((n, 3)), log_scales=np.zeros((n, 3)), quats=np.zeros((n, 4)),
                opacity_logits=np.zeros(n), feat=np.zeros((n, k)), b_iso=np.zeros(k),
@@ -237,7 +243,7 @@ def render_backward(scene, views, settings, dL_dC, pix=None, depth32=None, threa
     kl = int(np.asarray(scene.B_dir).shape[0])
     g2 = np.zeros((V, n, 7 + kl)) if want_2d else None
     rc = lib().or_render_backward(
-        C.byref(pk.scene), C.byref(pk.views), C.byref(pk.cfg), _p(depth32), m, _p(pix), _p(g),
+        C.byref(pk.scene), C.byref(pk.views), C.byref(pk.cfg), _p(depth32), m, _p(pix), _p(fm), _p(g),
         _p(out["means"]), _p(out["log_scales"]), _p(out["quats"]), _p(out["opacity_logits"]),
         _p(out["feat"]), _p(out["b_iso"]), _p(out["B_dir"]), _p(out["pose"]), _p(g2), threads)
     if rc:

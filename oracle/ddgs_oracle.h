@@ -99,10 +99,15 @@ int or_render(const or_scene *s, const or_views *vw, const or_config *cfg,
               int32_t *n_flagged, int n_threads);
 
 /* Backward of L = sum_p dL_dC[p] * C(p) over the requested pixels.
+ * flip_masks [n_pix] (nullable = all 0): the walk differentiated at each
+ * pixel is the forward's walk with the same mask (bit d inverts the d-th
+ * flagged decision), so a pixel can be differentiated along the outcome a
+ * binary32 renderer actually took near a cutoff.
  * Every output pointer may be NULL (skip). Outputs are overwritten. */
 int or_render_backward(const or_scene *s, const or_views *vw,
                        const or_config *cfg, const float *depth32,
-                       int64_t n_pix, const int32_t *pix, const double *dL_dC,
+                       int64_t n_pix, const int32_t *pix, const uint32_t *flip_masks,
+                       const double *dL_dC,
                        double *g_means, double *g_log_scales, double *g_quats,
                        double *g_opacity_logits, double *g_feat,
                        double *g_b_iso, double *g_B_dir,

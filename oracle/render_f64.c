@@ -636,7 +636,8 @@ int or_render(const or_scene *sc, const or_views *vw, const or_config *cfg,
 
 int or_render_backward(const or_scene *sc, const or_views *vw,
                        const or_config *cfg, const float *depth32,
-                       int64_t n_pix, const int32_t *pix, const double *dL_dC,
+                       int64_t n_pix, const int32_t *pix, const uint32_t *flip_masks,
+                       const double *dL_dC,
                        double *g_means, double *g_log_scales, double *g_quats,
                        double *g_opacity_logits, double *g_feat,
                        double *g_b_iso, double *g_B_dir, double *g_pose,
@@ -674,8 +675,10 @@ int or_render_backward(const or_scene *sc, const or_views *vw,
           pixel_ray(vw, v, col + 0.5, row + 0.5, rc, dhat, &dn);
           real_sh(sc->L, dhat, Yp, dYp);
         }
+        /* the same walk as the forward, with this pixel's flipped decisions */
+        const unsigned mask = flip_masks ? flip_masks[p] : 0u;
         int64_t cnt = walk_pixel(&vc, cfg, col + 0.5, row + 0.5, sc->per_pixel ? Yp : NULL, kL,
-                                 0u, NULL, NULL, NULL, NULL, NULL, rec);
+                                 mask, NULL, NULL, NULL, NULL, NULL, rec);
         double gC = dL_dC[p];
         /* S = sum over later Gaussians of c sigma T (suffix sum) */
         double S = 0.0;
