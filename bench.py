@@ -121,7 +121,8 @@ TRAFFIC = {
                            "ddgs_internal.cuh": "fa72ca1a83418c995fe5d9ca47a902b9883fb2bb5b99268157df8a084bb8fb8d"},
         "tile": 8, "batch_depth": 32, "views": 64, "gaussians": 500_000,
         "bytes_per_launch": 2440.0e6 + 577.2e6,
-        "how": "one-pass ncu capture of the 64-pose step; profiles/launches_registration_500k_64x256.md",
+        "how": "one-pass ncu launch list (dram__bytes_read.sum + dram__bytes_write.sum) of the "
+               "64-pose registration step",
     },
 }
 
@@ -273,7 +274,8 @@ def max_over_ranks(x: float, world: int, device=None) -> float:
 
 
 def algorithmic_bytes(kernel, s):
-    """Algorithmic DRAM bytes per launch of an HBM-bound kernel."""
+    """Algorithmic DRAM bytes of an HBM-bound kernel per STEP (all of its
+    launches in one step together)."""
     M, N, V = s["pairs"], s["n"], s["views"]
     return {
         "bin_count": 16 * N * V,            # read binning record
@@ -282,6 +284,28 @@ def algorithmic_bytes(kernel, s):
         "preprocess_fwd": 76 * N + 48 * N * V,  # read params once, write 48 B records
         "preprocess_bwd": 76 * N + 32 * N * V,  # read params once, read 2D gradients
     }.get(kernel)
+
+
+def kernel_table(prof, prof_steps, shape):
+    """Per-kernel figures from the event profiler: prof = {name: (total ms,
+    launches)} over prof_steps steps. A kernel's algorithmic GB/s divides its
+    bytes per step by its time per step (the sum of its launches), so a kernel
+    launched several times per step is not credited with one launch's time.
+    The list sort also gets the 24 B per pair of a read-write pass over
+    (key, value) pairs, the per-pass unit of a radix sort."""
+    total = sum(ms for ms, _ in prof.values()) or 1.0
+    out = {}
+    for k, (ms, n) in prof.items():
+        step_ms = ms / prof_steps
+        e = {"ms_per_launch": round(ms / max(n, 1), 4), "launches_per_step": n / prof_steps,
+             "ms_per_step": round(step_ms, 4), "share": round(ms / total, 4)}
+        b = algorithmic_bytes(k, shape)
+        if b is not None and step_ms > 0:
+            e["algorithmic_GBps"] = round(b / (step_ms / 1e3) / 1e9, 1)
+            if k == "bin_sort":
+                e["pass_24B_per_pair_GBps"] = round(24 * shape["pairs"] / (step_ms / 1e3) / 1e9, 1)
+        out[k] = e
+    return out
 
 
 def run_ours(args):
@@ -457,6 +481,55 @@ def run_ours(args):
     torch.cuda.synchronize()
     ms_plain = max_over_ranks(p0.elapsed_time(p1) / plain_steps, world, dev)
 
+    # ---- plain, graph-captured: each one-view call sequence captured once ----
+    # (separates what batching gains from what the host loop's launches and
+    # synchronisations cost)
+    ws_g = B.Workspace()
+    max_pairs = 0
+    for v1 in views1:
+        B.render(cloud, v1, cfg, ws_g, out=(img1, tf1, nl1))
+        max_pairs = max(max_pairs, ws_g.pairs())
+    torch.cuda.synchronize()
+    ws_g.reserve(scene.n, int(max_pairs * 1.10) + 4096, (-(-W // st.tile)) * (-(-H // st.tile)))
+    cfg1 = B.config_from_settings(st, no_sync=True, batch_depth=cfg.batch_depth)
+
+    def one_view(v1):
+        B.render(cloud, v1, cfg1, ws_g, out=(img1, tf1, nl1))
+        B.l1_loss(img1, target, loss=loss1, grad=dL1)
+        B.render_backward(cloud, v1, cfg1, ws_g, dL1, tf1, nl1, want=["world_to_cam"],
+                          out={"world_to_cam": gp1})
+
+    sg = torch.cuda.Stream()
+    sg.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(sg):
+        one_view(views1[0])
+    torch.cuda.current_stream().wait_stream(sg)
+    graphs1 = []
+    for v1 in views1:
+        g1 = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g1):
+            one_view(v1)
+        graphs1.append(g1)
+    torch.cuda.synchronize()
+
+    def plain_graph_step():
+        for g1 in graphs1:
+            g1.replay()
+
+    plain_graph_step()
+    torch.cuda.synchronize()
+    barrier()
+    q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    q0.record()
+    for _ in range(plain_steps):
+        plain_graph_step()
+    q1.record()
+    torch.cuda.synchronize()
+    ms_plain_graph = max_over_ranks(q0.elapsed_time(q1) / plain_steps, world, dev)
+    assert ws_g.sync_status() == 0, "one-view pair capacity exceeded"
+    del graphs1
+    ws_g.close()
+
     # ---- end to end through the API with host buffers ----
     poses_h = torch.empty((V, 3, 4), dtype=torch.float32).pin_memory()
     poses_h.copy_(torch.from_numpy(views.world_to_cam))
@@ -481,33 +554,29 @@ def run_ours(args):
     renders_step = V * world
     value = renders_step / (ms_batched / 1e3)
     plain_value = renders_step / (ms_plain / 1e3)
+    plain_graph_value = renders_step / (ms_plain_graph / 1e3)
     h2d = poses_h.numel() * 4 + target_h.numel() * 4
     d2h = gpose_h.numel() * 4 + loss_h.numel() * 4
 
     # ---- roofline of the dominant kernel ----
     peaks = measured_peaks()
-    per_launch = {k: (ms / max(n, 1), n / prof_steps) for k, (ms, n) in prof.items()}
-    total_ms = sum(ms for ms, _ in prof.values())
-    dom = max(prof.items(), key=lambda kv: kv[1][0])[0]
     shape = {"pairs": pairs, "n": scene.n, "views": V}
+    kernels = kernel_table(prof, prof_steps, shape)
+    dom = max(prof.items(), key=lambda kv: kv[1][0])[0]
     roof = None
-    algb = algorithmic_bytes(dom, shape)
-    ms_launch = per_launch[dom][0]
-    if algb is not None:
+    if "algorithmic_GBps" in kernels[dom]:
         peak = peaks.get("hbm_gbs", 6800.0)
-        ach = algb / (ms_launch / 1e3) / 1e9
+        ach = kernels[dom]["algorithmic_GBps"]
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                 "frac": ach / peak, "traffic": None,
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
     else:
         roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s",
                 "frac": None, "traffic": None, "note": "see rasteriser ALU roofline in kernels"}
-    kernels = {k: {"ms_per_launch": round(v[0], 4), "launches_per_step": v[1],
-                   "share": round(prof[k][0] / total_ms, 4)} for k, v in per_launch.items()}
-    for k in kernels:
-        b = algorithmic_bytes(k, shape)
-        if b is not None:
-            kernels[k]["algorithmic_GBps"] = round(b / (per_launch[k][0] / 1e3) / 1e9, 1)
+    if "hbm_gbs" in peaks:
+        for k in kernels:
+            if "algorithmic_GBps" in kernels[k]:
+                kernels[k]["hbm_frac"] = round(kernels[k]["algorithmic_GBps"] / peaks["hbm_gbs"], 3)
 
     if rank != 0:
         if world > 1:
@@ -524,8 +593,8 @@ def run_ours(args):
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
         fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
         for k, ops in (("raster_fwd", 15 + 1), ("raster_bwd", 45 + 1)):
-            if k in per_launch:
-                tf_s = blended * ops / (per_launch[k][0] / 1e3) / 1e12
+            if k in kernels:
+                tf_s = blended * ops / (kernels[k]["ms_per_step"] / 1e3) / 1e12
                 kernels[k]["algorithmic_TFLOPs"] = round(tf_s, 3)
                 kernels[k]["fp32_peak_TFLOPs"] = round(fp32_peak, 1)
                 kernels[k]["alu_frac"] = round(tf_s / fp32_peak, 4)
@@ -548,7 +617,11 @@ def run_ours(args):
                        "radiosity": args.variant, "autotune": tuned},
             "plain": {"value": plain_value, "ms_per_step": ms_plain,
                       "how": "64 x (ddgs_render + ddgs_l1_loss + ddgs_render_backward), 1 view each"},
+            "plain_graph": {"value": plain_graph_value, "ms_per_step": ms_plain_graph,
+                            "how": "64 CUDA graphs, each one view's ddgs_render + ddgs_l1_loss + "
+                                   "ddgs_render_backward (no-sync, reserved workspace), replayed in turn"},
             "batched_over_plain": value / plain_value,
+            "batched_over_plain_graph": value / plain_graph_value,
             "pairs_per_step": pairs,
             "e2e": {"value": renders_step / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
@@ -641,9 +714,7 @@ def run_fit(args, large):
         loss_h.copy_(loss, non_blocking=True)
         torch.cuda.current_stream().synchronize()
     t_e2e = max_over_ranks((time.perf_counter() - t1) / args.steps, world, dev)
-    total = sum(v[0] for v in prof.values())
-    kernels = {k: {"ms_per_launch": round(v[0] / max(v[1], 1), 4), "launches_per_step": v[1] / 3,
-                   "share": round(v[0] / total, 4)} for k, v in prof.items()}
+    kernels = kernel_table(prof, 3, {"pairs": pairs, "n": scene.n, "views": V})
     if rank != 0:
         return 0
     name = "large fit" if large else "fit"
@@ -660,6 +731,152 @@ def run_fit(args, large):
             "e2e": {"value": world / t_e2e, "unit": "steps/s", "h2d_bytes_per_step": target_h.numel() * 4,
                     "d2h_bytes_per_step": V * 4},
             "gpu_launches": n_launch, "clocks": clk, "kernels": kernels}
+    print(json.dumps(line))
+    return 0
+
+
+def run_plain_forward(args):
+    """Plain forward (4,096 Gaussians in [-1,1]^3, one 128^2 cone-beam view,
+    source-to-isocenter 2, source-to-detector 4): milliseconds per render.
+    Timed two ways, each render alone between L2 flushes (the whole input is
+    far smaller than L2): the synchronising ddgs_render a plain caller makes
+    (it reads the pair count once), and the same render captured in a CUDA
+    graph (no-sync, reserved workspace). The FP64 oracle renders the same
+    image on the host cores."""
+    import torch
+
+    import oracle
+    from paper_2406_02518_gb300 import binding as B
+    from paper_2406_02518_gb300 import build as bld
+    from paper_2406_02518_gb300 import synthetic as syn
+
+    rank, world, local = _dist_env()
+    torch.cuda.set_device(local)
+    bld.build()
+    B.load()
+    dev = torch.device("cuda", local)
+    scene, views, st = syn.plain_forward_workload()
+    if args.tile:
+        st = dataclasses.replace(st, tile=args.tile)
+    depth = args.depth or 256
+    V, H, W = views.n_views, views.height, views.width
+    cloud, gv = B.cloud_from_arrays(scene), B.views_from_arrays(views)
+    cfg = B.config_from_settings(st, batch_depth=depth)
+    ws = B.Workspace()
+    img, tf, nl = B.render(cloud, gv, cfg, ws)
+    torch.cuda.synchronize()
+    pairs = ws.pairs()
+    ws.reserve(V * scene.n, int(pairs * 1.10) + 4096, V * (-(-W // st.tile)) * (-(-H // st.tile)))
+    cfg_ns = B.config_from_settings(st, no_sync=True, batch_depth=depth)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # 512 MB > L2
+
+    def sync_call():
+        B.render(cloud, gv, cfg, ws, out=(img, tf, nl))
+
+    def graph_body():
+        B.render(cloud, gv, cfg_ns, ws, out=(img, tf, nl))
+
+    s_ = torch.cuda.Stream()
+    s_.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s_):
+        graph_body()
+    torch.cuda.current_stream().wait_stream(s_)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        graph_body()
+    torch.cuda.synchronize()
+
+    def timed(fn, k):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        for a, b in ev:
+            flush.fill_(1)
+            a.record()
+            fn()
+            b.record()
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / k
+
+    for _ in range(args.warmup):
+        sync_call()
+        graph.replay()
+    torch.cuda.synchronize()
+    launches0 = B.kernel_launches()
+    clocks = Clocks(os.path.join(tempfile.gettempdir(), f"ddgs_clocks_c1_{os.getpid()}.csv"))
+    clocks.start()
+    ms_graph = timed(graph.replay, args.steps)
+    ms_sync = timed(sync_call, args.steps)
+    clk = clocks.stop(local)
+    n_launch = B.kernel_launches() - launches0  # graph replays do not pass the counter
+    per_render = max(1, n_launch // max(args.steps, 1))
+    assert ws.sync_status() == 0
+    B.profiler_enable(True)
+    for _ in range(5):
+        sync_call()
+    torch.cuda.synchronize()
+    prof = B.profiler_collect()
+    B.profiler_enable(False)
+    kernels = kernel_table(prof, 5, {"pairs": pairs, "n": scene.n, "views": V})
+    # end to end: the cloud and pose from pinned host memory, the image read back
+    host = {k: getattr(cloud, k).detach().cpu().pin_memory() for k in
+            ("means", "log_scales", "quats", "opacity_logits", "feat_iso", "feat_dir", "b_iso", "B_dir")}
+    pose_h = gv.world_to_cam.cpu().pin_memory()
+    img_h = torch.empty((V, H, W), dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for k, t in host.items():
+            getattr(cloud, k).copy_(t, non_blocking=True)
+        gv.world_to_cam.copy_(pose_h, non_blocking=True)
+        sync_call()
+        img_h.copy_(img, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e2e_ms = 1e3 * (time.perf_counter() - t0) / args.steps
+    h2d = sum(t.numel() * t.element_size() for t in host.values()) + pose_h.numel() * 4
+    # parity of this very render against the oracle, and the oracle's time
+    t1 = time.perf_counter()
+    ref = oracle.render(scene, views, st)
+    cpu_s = time.perf_counter() - t1
+    rng = float(ref["image"].max() - ref["image"].min())
+    clean = ref["n_flagged"] == 0
+    err = float(np.abs(img.cpu().numpy() - ref["image"])[clean].max() / rng)
+    inside = float(oracle.count_inside(scene, views, st).sum())
+    peaks = measured_peaks()
+    sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
+    dom = max(prof.items(), key=lambda kv: kv[1][0])[0]
+    roof = {"kernel": dom, "bound": "latency", "achieved": None, "peak": None, "unit": None,
+            "frac": None, "traffic": None}
+    if "raster_fwd" in kernels:
+        tf_s = inside * 16 / (kernels["raster_fwd"]["ms_per_step"] / 1e3) / 1e12
+        kernels["raster_fwd"]["algorithmic_TFLOPs"] = round(tf_s, 4)
+        kernels["raster_fwd"]["alu_frac"] = round(tf_s / fp32_peak, 5)
+        if dom == "raster_fwd":
+            roof = {"kernel": dom, "bound": "alu", "achieved": tf_s, "peak": fp32_peak, "unit": "TFLOP/s",
+                    "frac": tf_s / fp32_peak, "traffic": None,
+                    "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz"}
+    if rank != 0:
+        return 0
+    line = {"metric": "plain forward ms/render (4,096 Gaussians, 128^2, one view)",
+            "value": ms_graph, "unit": "ms/render", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_graph, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "plain forward: 4,096 Gaussians (means U[-1,1]^3), one 128x128 view, "
+                                   "SID 2, SDD 4", "tile": st.tile, "batch_depth": depth,
+                       "pairs": pairs, "l2": "512 MB written between timed renders (L2 flush)",
+                       "graph": "value: the render replayed from a CUDA graph"},
+            "sync_call": {"ms_per_render": ms_sync,
+                          "how": "ddgs_render as a plain caller makes it (one stream sync for the pair count)"},
+            "e2e": {"value": e2e_ms, "unit": "ms/render", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": V * H * W * 4},
+            "parity": {"max_err_over_range": err, "tolerance": 1e-4,
+                       "flagged_frac": float(1 - clean.mean())},
+            "gpu_launches": n_launch, "kernels_per_render": per_render,
+            "clocks": clk, "roofline": roof, "kernels": kernels,
+            "cpu_baseline": {"value": 1e3 * cpu_s, "unit": "ms/render", "cores": os.cpu_count() or 1,
+                             "kind": "oracle",
+                             "sample": "the whole 128x128 render through the FP64 oracle (every "
+                                       "Gaussian at every pixel, OpenMP over pixels)"}}
     print(json.dumps(line))
     return 0
 
@@ -1001,8 +1218,8 @@ def main():
                     help="run warm-up steps and one eager step in an NVTX range, then exit")
     ap.add_argument("--autotune", nargs="?", const="on", default="on", choices=["on", "off", "force"],
                     help="tune (tile, staging depth) before timing (cached per workload class)")
-    ap.add_argument("--workload", choices=["registration", "uneven", "registration-loop", "rads",
-                                           "fit", "large-fit"],
+    ap.add_argument("--workload", choices=["registration", "plain-forward", "uneven",
+                                           "registration-loop", "rads", "fit", "large-fit"],
                     default="registration")
     ap.add_argument("--volume", type=int, default=512, help="CT volume edge of --workload rads")
     ap.add_argument("--tile", type=int, choices=[8, 16, 32], default=None,
@@ -1024,6 +1241,8 @@ def main():
         return run_fit(args, args.workload == "large-fit")
     if args.workload == "uneven":
         return run_uneven(args)
+    if args.workload == "plain-forward":
+        return run_plain_forward(args)
     if args.workload == "registration-loop":
         return run_registration_loop(args)
     if args.workload == "rads":

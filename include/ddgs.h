@@ -15,8 +15,10 @@
  *   - Every call is asynchronous on the given stream (a cudaStream_t passed as
  *     void*; NULL = legacy default stream) unless stated otherwise.
  *   - No call aborts, throws or prints. Each returns a ddgs_status. Errors
- *     found while kernels run (capacity overflow in the no-sync mode) are
- *     latched in the workspace and returned by ddgs_sync_status().
+ *     found while kernels run (capacity overflow in the no-sync mode, a
+ *     non-finite input) are latched in the workspace and returned by
+ *     ddgs_sync_status(); a synchronising render reports a non-finite input
+ *     itself.
  *   - Feature dimension k (1..32, default 8) and harmonic degree L (1..3,
  *     default 1; k_L = L(L+2)) per cloud: k = 8, L = 1 is the paper's
  *     evaluation setting (Sec. 4.1); Table 2 uses L = 3, Table 5 k = 1..32.
@@ -47,7 +49,8 @@ typedef enum {
   DDGS_OK = 0,
   DDGS_ERR_INVALID_ARG = 1,   /* a null pointer, negative size, bad tile ... */
   DDGS_ERR_CAPACITY = 2,      /* no-sync mode: pairs exceeded the reserved capacity */
-  DDGS_ERR_NONFINITE = 3,     /* reserved */
+  DDGS_ERR_NONFINITE = 3,     /* an input parameter (Gaussian, basis, pose or
+                                 detector entry) was NaN or infinite */
   DDGS_ERR_TIMEOUT = 4,       /* reserved: a bounded device wait gave up */
   DDGS_ERR_CUDA = 5,          /* a CUDA runtime call failed (see ddgs_last_cuda_error) */
   DDGS_ERR_UNSUPPORTED = 6,   /* e.g. no sm_103 device */
@@ -168,7 +171,12 @@ ddgs_status ddgs_workspace_reserve(ddgs_workspace *ws, int64_t records,
  *   n_last  1 + position, in the pixel's tile list, of the last Gaussian
  *           added (0 if none); needed by the backward pass.
  * Synchronises the stream once (to size the tile lists) unless cfg->no_sync.
- * Pairs are limited to 2^31 - 1 per render (DDGS_ERR_CAPACITY beyond). */
+ * Pairs are limited to 2^31 - 1 per render (DDGS_ERR_CAPACITY beyond).
+ * A NaN or infinite input (Gaussian parameter, basis entry, pose or detector
+ * entry) makes a synchronising call return DDGS_ERR_NONFINITE after writing
+ * its outputs as the kernels computed them (such a Gaussian is culled when its
+ * geometry is not finite, and otherwise reaches the image); with
+ * cfg->no_sync the status is latched for ddgs_sync_status(). */
 ddgs_status ddgs_render(const ddgs_gaussians *g, const ddgs_views *v,
                         const ddgs_config *cfg, ddgs_workspace *ws,
                         float *image, float *t_final, uint32_t *n_last,
@@ -330,9 +338,11 @@ ddgs_status ddgs_debug_binning(const ddgs_workspace *ws, uint32_t *tiles_touched
                                void *stream);
 
 /* Synchronise the stream, then return and clear the status latched by
- * kernels since the last call: DDGS_OK, or DDGS_ERR_CAPACITY when a no_sync
+ * kernels since the last call: DDGS_OK; DDGS_ERR_CAPACITY when a no_sync
  * render had more pairs than the reserved capacity (the tile lists that did
- * not fit were left empty). Infrastructure, no counterpart in the paper. */
+ * not fit were left empty); else DDGS_ERR_NONFINITE when a render's inputs
+ * held a NaN or infinite value not already reported by a synchronising
+ * render. Infrastructure, no counterpart in the paper. */
 ddgs_status ddgs_sync_status(ddgs_workspace *ws, void *stream);
 
 /* Floats of a cloud: n * (3 + 4 + 3 + 1 + k) + k + k_L * k, i.e. 19 per

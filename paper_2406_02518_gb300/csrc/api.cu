@@ -402,14 +402,14 @@ ddgs_status ddgs_workspace_create(ddgs_workspace **out) {
       (e = cudaMalloc(&ws->d_status, sizeof(int32_t))) != cudaSuccess ||
       (e = cudaMalloc(&ws->queue, 2 * sizeof(uint32_t))) != cudaSuccess ||
       (e = cudaMalloc(&ws->list_count, ddgs::LIST_CLASSES * sizeof(uint32_t))) != cudaSuccess ||
-      (e = cudaHostAlloc(&ws->h_pairs, sizeof(uint64_t), cudaHostAllocDefault)) != cudaSuccess ||
+      (e = cudaHostAlloc(&ws->h_pairs, 2 * sizeof(uint64_t), cudaHostAllocDefault)) != cudaSuccess ||
       (e = cudaMemset(ws->d_status, 0, sizeof(int32_t))) != cudaSuccess ||
       (e = cudaMemset(ws->d_pairs, 0, sizeof(uint64_t))) != cudaSuccess) {
     ddgs_status st = cuda_fail(e, "workspace create");
     ddgs_workspace_destroy(ws);
     return st;
   }
-  *ws->h_pairs = 0;
+  ws->h_pairs[0] = ws->h_pairs[1] = 0;
   if (ensure_tables(ws, 0, 0) != DDGS_OK) {
     ddgs_workspace_destroy(ws);
     return DDGS_ERR_OUT_OF_MEMORY;
@@ -494,6 +494,7 @@ ddgs_status render_common(const ddgs_gaussians &g, const ddgs_views &v, const dd
   CK(cudaMemsetAsync(ws->req_time, 0xff, sizeof(unsigned long long), s_));
   CK(cudaMemsetAsync(ws->req_time + 1, 0, 2 * (size_t)s.R * sizeof(unsigned long long), s_));
   uint64_t bound = 0;
+  bool nonfinite = false;
   if (s.records > 0) {
     ddgs::launch_preprocess_fwd(g, v, *c, s, *ws, s_);
     CK(cudaGetLastError());
@@ -501,7 +502,16 @@ ddgs_status render_common(const ddgs_gaussians &g, const ddgs_views &v, const dd
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(ws->h_pairs, ws->d_pairs, sizeof(uint64_t), cudaMemcpyDeviceToHost, s_));
     if (!c->no_sync) {
+      // the status word rides along with the pair count: a non-finite input
+      // is reported by this call (and cleared), other bits stay latched
+      int32_t *h_st = reinterpret_cast<int32_t *>(ws->h_pairs + 1);
+      CK(cudaMemcpyAsync(h_st, ws->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, s_));
       CK(cudaStreamSynchronize(s_));
+      if (h_st[0] & ddgs::ST_NONFINITE) {
+        nonfinite = true;
+        h_st[1] = h_st[0] & ~ddgs::ST_NONFINITE;
+        CK(cudaMemcpyAsync(ws->d_status, h_st + 1, sizeof(int32_t), cudaMemcpyHostToDevice, s_));
+      }
       bound = *ws->h_pairs;
       if (bound > (uint64_t)ddgs::BIN_MAX_PAIRS) return DDGS_ERR_CAPACITY;
       if ((st = ensure_pairs(ws, (int64_t)bound))) return st;
@@ -528,7 +538,7 @@ ddgs_status render_common(const ddgs_gaussians &g, const ddgs_views &v, const dd
   ws->shape = s;
   ws->pair_bound = bound;
   ws->have_render = true;
-  return DDGS_OK;
+  return nonfinite ? DDGS_ERR_NONFINITE : DDGS_OK;
 }
 
 ddgs_status backward_common(const ddgs_gaussians &g, const ddgs_views &v, const ddgs_config *c,
@@ -818,6 +828,7 @@ ddgs_status ddgs_sync_status(ddgs_workspace *ws, void *stream) {
   CK(cudaMemcpy(&h, ws->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost));
   CK(cudaMemset(ws->d_status, 0, sizeof(int32_t)));
   if (h & ddgs::ST_CAPACITY) return DDGS_ERR_CAPACITY;
+  if (h & ddgs::ST_NONFINITE) return DDGS_ERR_NONFINITE;
   return DDGS_OK;
 }
 

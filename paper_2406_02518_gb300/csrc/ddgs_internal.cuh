@@ -24,8 +24,9 @@ constexpr int BIN_LIST_LONG = 8192;          // longest list ordered by one bloc
 constexpr int64_t BIN_MAX_PAIRS = (int64_t(1) << 31) - 1;  // offsets leave bit 31 free
 constexpr float SH_C1 = 0.48860251190291992f;  // sqrt(3 / (4 pi))
 
-// Device status bits (latched in the workspace).
-enum : int32_t { ST_CAPACITY = 1 };
+// Device status bits (latched in the workspace): a tile list did not fit the
+// reserved pair capacity; an input parameter was NaN or infinite.
+enum : int32_t { ST_CAPACITY = 1, ST_NONFINITE = 2 };
 
 // A batch is R requests; request r owns a contiguous range of Gaussians (its
 // own cloud and bases) and a contiguous range of views; every view has its

@@ -12,8 +12,12 @@
 //
 // The steps that decide integers (culling, tile rectangle, depth key) use
 // one correctly rounded binary32 operation each, in the fixed order G1..G15
-// (see the design notes), so they can be compared bit for bit with a CPU
-// reference that follows the same definition.
+// (G1 scales; G2-G3 normalised quaternion and rotation; G4-G5 the 3D
+// covariance; then per view G6 the camera transform, G7 the depth test, G8 the
+// projection of the mean, G9-G12 the Jacobian and the 2D covariance, G13 its
+// determinant, G14 the ellipse extents, G15 the tile rectangle), so they can
+// be compared bit for bit with a CPU reference that follows the same
+// definition.
 #include "ddgs_internal.cuh"
 
 namespace ddgs {
@@ -298,7 +302,20 @@ struct PreArgs {
   uint4 *bin_info;  // (rect lo, rect hi, depth bits, tiles touched)
   uint32_t *blk_total;
   unsigned long long *t0;  // batch start (min over blocks of %globaltimer), or null
+  int32_t *status;         // device status word: ST_NONFINITE is or-ed in
 };
+
+// A parameter that is NaN or +-Inf (fitting by gradient descent, Sec. 3.1, is
+// where such values arise). The kernels keep going -- a NaN depth or
+// determinant is culled by the binning's comparisons, a NaN opacity or colour
+// reaches the image -- and the status word reports it.
+__device__ __forceinline__ bool nonfinite(float x) { return !(fabsf(x) <= 3.402823466e38f); }
+
+// One atomic per warp that saw a non-finite value.
+__device__ __forceinline__ void flag_nonfinite(bool bad, int32_t *status) {
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0 && status)
+    atomicOr(status, ST_NONFINITE);
+}
 
 __device__ __forceinline__ uint32_t block_sum_u32(uint32_t x, uint32_t *s_red) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -351,8 +368,15 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_fwd_kernel(PreArgs a) 
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     atomicMin(a.t0, t);
   }
-  for (int e = tid; e < Kr; e += PRE_THREADS) s_b[e] = a.b_iso[(int64_t)br.r * Kr + e];
-  for (int e = tid; e < kL * Kr; e += PRE_THREADS) s_B[e] = a.B_dir[(int64_t)br.r * kL * Kr + e];
+  bool bad = false;  // a non-finite input seen by this thread
+  for (int e = tid; e < Kr; e += PRE_THREADS) {
+    s_b[e] = a.b_iso[(int64_t)br.r * Kr + e];
+    bad |= nonfinite(s_b[e]);
+  }
+  for (int e = tid; e < kL * Kr; e += PRE_THREADS) {
+    s_B[e] = a.B_dir[(int64_t)br.r * kL * Kr + e];
+    bad |= nonfinite(s_B[e]);
+  }
   if (GEN && tid < kL) sh_table_row(tid, s_sh);
   __syncthreads();
 
@@ -367,11 +391,17 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_fwd_kernel(PreArgs a) 
     float4 q4 = reinterpret_cast<const float4 *>(a.quats)[i];
     float q[4] = {q4.x, q4.y, q4.z, q4.w};
     gauss_geom(ls, q, gg);
-    alpha = sigmoidf_(a.logits[i]);
+    const float logit = a.logits[i];
+    alpha = sigmoidf_(logit);
+    bad |= nonfinite(mu[0]) | nonfinite(mu[1]) | nonfinite(mu[2]) | nonfinite(ls[0]) |
+           nonfinite(ls[1]) | nonfinite(ls[2]) | nonfinite(q[0]) | nonfinite(q[1]) |
+           nonfinite(q[2]) | nonfinite(q[3]) | nonfinite(logit);
     is_dir = br.l >= rq.n_iso;
     if (!GEN) {
       float f[K];
       load_feat(a.feat_iso, a.feat_dir, a.feat_dir_bf16, rq, br.l, f);
+#pragma unroll
+      for (int k = 0; k < K; ++k) bad |= nonfinite(f[k]);
       if (!is_dir) {
         float zl = 0.f;
 #pragma unroll
@@ -393,6 +423,7 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_fwd_kernel(PreArgs a) 
       float zl = 0.f;
       for (int k = 0; k < Kr; ++k) {
         const float fk = load_feat1(a.feat_iso, a.feat_dir, a.feat_dir_bf16, rq, br.l, Kr, k);
+        bad |= nonfinite(fk);
         if (has_iso) zl = fmaf(s_b[k], fk, zl);
         if (has_dir) {
 #pragma unroll
@@ -411,6 +442,13 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_fwd_kernel(PreArgs a) 
     if (tid < nv) {
       const int v = rq.v_off + v0 + tid;
       load_view(a.world_to_cam + 12 * v, a.detector + 5 * v, s.view[v], sv[tid]);
+      // the pose and detector of the view: checked by the request's first block
+      if (blockIdx.x == rq.blk_base) {
+#pragma unroll
+        for (int e = 0; e < 12; ++e) bad |= nonfinite(a.world_to_cam[12 * v + e]);
+#pragma unroll
+        for (int e = 0; e < 5; ++e) bad |= nonfinite(a.detector[5 * v + e]);
+      }
     }
     __syncthreads();
     if (!live) continue;
@@ -457,6 +495,7 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_fwd_kernel(PreArgs a) 
       a.rec[2 * rec + 1] = make_float4(cc, alpha, colour, box_halfwidths(p.cov, a.q_max));
     }
   }
+  flag_nonfinite(bad, a.status);
   uint32_t bt = block_sum_u32(total, s_red);
   if (tid == 0) a.blk_total[blockIdx.x] = bt;
 }
@@ -941,6 +980,7 @@ void launch_preprocess_fwd(const ddgs_gaussians &g, const ddgs_views &v, const d
   a.bin_info = reinterpret_cast<uint4 *>(ws.rect);
   a.blk_total = ws.blk_total;
   a.t0 = ws.req_time;
+  a.status = ws.d_status;
   if (s.n_blocks > 0) {
     LaunchScope ls(KID_PREPROCESS_FWD, st);
     if (a.K == K && a.L == 1 && !a.entangled && !a.per_pixel)

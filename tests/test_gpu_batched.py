@@ -88,7 +88,8 @@ def test_batched_requests_match_single_renders():
             ref = dict(acc)
             ref["pose"] = torch.cat(poses)
             compare_grads({k: t.cpu().numpy() for k, t in got.items()},
-                          {k: ref[k].cpu().numpy() for k in got}, list(got), tol=1e-5)
+                          {k: ref[k].cpu().numpy() for k in got}, list(got), tol=1e-5,
+                          zero_ok=list(got))
         elif sc.n:
             a, b_ = g_off[r], g_off[r + 1]
             assert float(g["means"][a:b_].abs().max()) == 0.0

@@ -13,7 +13,7 @@ import torch
 import oracle
 from paper_2406_02518_gb300 import binding as B
 from paper_2406_02518_gb300 import synthetic as syn
-from _parity import check_image, compare_binning, compare_grads, last_ids
+from _parity import check_image, compare_binning, compare_grads, gradient_weights, last_ids
 
 pytestmark = pytest.mark.gpu
 
@@ -48,10 +48,10 @@ def _two_views(H, W, pitch=8.0 / 96):
                   4.0, pitch, H, W)
 
 
-def _run(scene, views, st, ws, bf16=None):
+def _run(scene, views, st, ws, bf16=None, depth=None):
     cloud = B.cloud_from_arrays(scene, feat_dir_bf16=bf16)
     gv = B.views_from_arrays(views)
-    cfg = B.config_from_settings(st)
+    cfg = B.config_from_settings(st) if depth is None else B.config_from_settings(st, batch_depth=depth)
     img, tf, nl = B.render(cloud, gv, cfg, ws)
     torch.cuda.synchronize()
     return cloud, gv, cfg, img, tf, nl
@@ -133,10 +133,15 @@ def bins_depth(scene, views, st):
     return oracle.project32(scene, views, st)["depth"]
 
 
-def _masked_weights(ref, seed=0):
-    rng = np.random.default_rng(seed)
-    w = rng.uniform(-1, 1, ref["image"].shape)
-    return np.where((ref["flags"] == 0), w, 0.0)
+def _resolved_weights(scene, views, st, ws, img, tf, nl, seed):
+    """Image check of the last render, then the loss weights of a gradient
+    check: every pixel resolved to the oracle outcome the GPU took (the oracle
+    differentiates it along that outcome), at most 1e-3 of a view left out."""
+    bins = _bins(ws, scene, views, st)
+    ids = last_ids(nl.cpu().numpy().view(np.uint32), bins, views, st.tile)
+    rep = check_image(scene, views, st, img.cpu().numpy(), tf.cpu().numpy(), ids)
+    w, fm = gradient_weights(rep, seed)
+    return rep, w, fm
 
 
 @pytest.mark.parametrize("case", ["plain_4096_128px", "ragged_100x75_2views", "strong_dir",
@@ -144,12 +149,11 @@ def _masked_weights(ref, seed=0):
 def test_gradients_match_oracle(case, ws):
     scene, views, st = CASES[case]()
     cloud, gv, cfg, img, tf, nl = _run(scene, views, st, ws)
-    ref = oracle.render(scene, views, st)
-    w = _masked_weights(ref)
+    _, w, fm = _resolved_weights(scene, views, st, ws, img, tf, nl, 0)
     dL = torch.as_tensor(w, dtype=torch.float32, device="cuda")
     g = B.render_backward(cloud, gv, cfg, ws, dL, tf, nl)
     torch.cuda.synchronize()
-    gr = oracle.render_backward(scene, views, st, w)
+    gr = oracle.render_backward(scene, views, st, w, flip_masks=fm)
     gpu = {k: v.cpu().numpy() for k, v in g.items()}
     gpu["feat"] = np.concatenate([gpu.pop("feat_iso"), gpu.pop("feat_dir")])
     gpu["pose"] = gpu.pop("world_to_cam")
@@ -166,12 +170,11 @@ def test_bf16_direction_features(ws):
     bins = _bins(ws, scene, views, st)
     compare_binning(bins, oracle.bin32(scene, views, st))
     ids = last_ids(nl.cpu().numpy().view(np.uint32), bins, views, st.tile)
-    check_image(scene, views, st, img.cpu().numpy(), tf.cpu().numpy(), ids)
-    ref = oracle.render(scene, views, st)
-    w = _masked_weights(ref, 1)
+    rep = check_image(scene, views, st, img.cpu().numpy(), tf.cpu().numpy(), ids)
+    w, fm = gradient_weights(rep, 1)
     g = B.render_backward(cloud, gv, cfg, ws, torch.as_tensor(w, dtype=torch.float32, device="cuda"),
                           tf, nl)
-    gr = oracle.render_backward(scene, views, st, w)
+    gr = oracle.render_backward(scene, views, st, w, flip_masks=fm)
     gpu = {k: v.float().cpu().numpy() for k, v in g.items()}
     gpu["feat"] = np.concatenate([gpu.pop("feat_iso"), gpu.pop("feat_dir")])
     gpu["pose"] = gpu.pop("world_to_cam")
@@ -315,14 +318,39 @@ def test_capacity_overflow_is_reported_not_faulted(ws):
     w2.close()
 
 
+def _compare_view_lists(gpu, ref, views_gpu, tiles_per_view):
+    """Tile lists of some views of a render (gpu: every view; ref: the FP32
+    binning reference of those views alone, in that order): per tile the same
+    range length, Gaussians and depth keys, entry for entry."""
+    gr = gpu["ranges"].reshape(-1, 2).astype(np.int64)
+    rr = ref["ranges"].reshape(-1, 2).astype(np.int64)
+    for j, v in enumerate(views_gpu):
+        g = gr[v * tiles_per_view:(v + 1) * tiles_per_view]
+        r = rr[j * tiles_per_view:(j + 1) * tiles_per_view]
+        assert np.array_equal(g[:, 1] - g[:, 0], r[:, 1] - r[:, 0]), f"list lengths of view {v}"
+        full = g[:, 1] > g[:, 0]  # empty lists are (0, 0) on both sides
+        assert np.array_equal(g[~full], r[~full]), f"empty ranges of view {v}"
+        if not full.any():
+            continue
+        g0, g1, r0, r1 = g[full, 0].min(), g[full, 1].max(), r[full, 0].min(), r[full, 1].max()
+        assert np.array_equal(g[full] - g0, r[full] - r0), f"ranges of view {v}"
+        assert np.array_equal(gpu["vals"][g0:g1], ref["vals"][r0:r1]), f"lists of view {v}"
+        gk, rk = gpu["keys"][g0:g1], ref["keys"][r0:r1]
+        assert np.array_equal(gk & 0xffffffff, rk & 0xffffffff), f"depth keys of view {v}"
+        shift = np.uint64((v - j) * tiles_per_view)
+        assert np.array_equal(gk >> np.uint64(32), (rk >> np.uint64(32)) + shift), f"tiles of view {v}"
+
+
 @pytest.mark.slow
 def test_registration_workload_sampled_pixels(ws):
-    """500k Gaussians, 64 poses, 256^2: the batched launch the benchmark times,
-    checked on sampled pixels of a few views (oracle one pixel at a time)."""
+    """500k Gaussians, 64 poses, 256^2, in the launch shape the benchmark
+    times (tile 8, warp-streamed rasterisers): bit-exact tile lists of two
+    views against the FP32 binning reference, image and pose gradients on
+    sampled pixels of those views (oracle one pixel at a time)."""
     scene, views, st = syn.registration_workload()
-    cloud, gv, cfg, img, tf, nl = _run(scene, views, st, ws)
+    st = dataclasses.replace(st, tile=8)
+    cloud, gv, cfg, img, tf, nl = _run(scene, views, st, ws, depth=32)
     bins = _bins(ws, scene, views, st)
-    # bit-exact binning on two views' worth of keys
     ref_proj = oracle.project32(scene, views, st)
     assert np.array_equal(bins["tiles_touched"].reshape(ref_proj["tiles_touched"].shape),
                           ref_proj["tiles_touched"])
@@ -332,6 +360,9 @@ def test_registration_workload_sampled_pixels(ws):
     check_views = [0, 37]
     sub = dataclasses.replace(views, world_to_cam=views.world_to_cam[check_views].copy(),
                               detector=views.detector[check_views].copy())
+    # bit-exact binning of two whole views: every tile's list, entry for entry
+    tpv = (views.width // 8) * (views.height // 8)
+    _compare_view_lists(bins, oracle.bin32(scene, sub, st), check_views, tpv)
     pix = syn.sample_pixels(sub, n_random=768, n_rows=1, seed=4)
     sel_v = np.array(check_views)[pix[:, 0]]
     ids_all = last_ids(nl.cpu().numpy().view(np.uint32), bins, views, st.tile)
@@ -340,15 +371,14 @@ def test_registration_workload_sampled_pixels(ws):
     gid = ids_all[sel_v, pix[:, 1], pix[:, 2]]
     rep = check_image(scene, sub, st, gi, gt, gid, depth32=ref_proj["depth"][check_views], pix=pix)
     assert rep["range"] > 0.1
-    # pose gradients of a loss on the sampled pixels only (same mask both sides)
+    # pose gradients of a loss on the sampled pixels only (same weights both sides)
     w = np.zeros(img.shape, np.float64)
-    flags = rep["ref"]["flags"]
-    rng = np.random.default_rng(9)
-    wv = np.where(flags == 0, rng.uniform(-1, 1, pix.shape[0]), 0.0)
+    wv, fm = gradient_weights(rep, 9)
     w[sel_v, pix[:, 1], pix[:, 2]] = wv
     g = B.render_backward(cloud, gv, cfg, ws, torch.as_tensor(w, dtype=torch.float32, device="cuda"),
                           tf, nl, want=["world_to_cam"])
-    gr = oracle.render_backward(scene, sub, st, wv, pix=pix, depth32=ref_proj["depth"][check_views])
+    gr = oracle.render_backward(scene, sub, st, wv, pix=pix, depth32=ref_proj["depth"][check_views],
+                                flip_masks=fm)
     gp = g["world_to_cam"].cpu().numpy()
     compare_grads({"pose": gp[check_views]}, {"pose": gr["pose"]}, ["pose"])
     others = np.setdiff1d(np.arange(views.n_views), check_views)
@@ -377,14 +407,13 @@ def _sampled_check(scene, views, st, ws, check_views, n_random, seed, grads=("po
     rep = check_image(scene, sub, st, gi, gt, gid, depth32=d32, pix=pix)
     assert rep["range"] > 0.05
     w = np.zeros(img.shape, np.float64)
-    rng = np.random.default_rng(seed + 1)
-    wv = np.where(rep["ref"]["flags"] == 0, rng.uniform(-1, 1, pix.shape[0]), 0.0)
+    wv, fm = gradient_weights(rep, seed + 1)
     w[sel_v, pix[:, 1], pix[:, 2]] = wv
     want = ["world_to_cam"] + [n for n in ("means", "log_scales", "quats", "opacity_logits",
                                            "feat_iso", "feat_dir", "b_iso", "B_dir") if n in grads]
     g = B.render_backward(cloud, gv, cfg, ws, torch.as_tensor(w, dtype=torch.float32, device="cuda"),
                           tf, nl, want=want)
-    gr = oracle.render_backward(scene, sub, st, wv, pix=pix, depth32=d32)
+    gr = oracle.render_backward(scene, sub, st, wv, pix=pix, depth32=d32, flip_masks=fm)
     gpu = {k: v.float().cpu().numpy() for k, v in g.items()}
     gpu["pose"] = gpu.pop("world_to_cam")[check_views]
     if "feat_iso" in gpu:
@@ -431,12 +460,11 @@ def test_feature_dimension_and_degree_variants(k, L, bf16, ws):
     bins = _bins(ws, scene, views, st)
     compare_binning(bins, oracle.bin32(scene, views, st))
     ids = last_ids(nl.cpu().numpy().view(np.uint32), bins, views, st.tile)
-    check_image(scene, views, st, img.cpu().numpy(), tf.cpu().numpy(), ids)
-    ref = oracle.render(scene, views, st)
-    w = _masked_weights(ref, 3)
+    rep = check_image(scene, views, st, img.cpu().numpy(), tf.cpu().numpy(), ids)
+    w, fm = gradient_weights(rep, 3)
     g = B.render_backward(cloud, gv, cfg, ws, torch.as_tensor(w, dtype=torch.float32, device="cuda"),
                           tf, nl)
-    gr = oracle.render_backward(scene, views, st, w)
+    gr = oracle.render_backward(scene, views, st, w, flip_masks=fm)
     gpu = {n: t.float().cpu().numpy() for n, t in g.items()}
     gpu["feat"] = np.concatenate([gpu.pop("feat_iso").reshape(-1, k), gpu.pop("feat_dir").reshape(-1, k)])
     gpu["pose"] = gpu.pop("world_to_cam")
@@ -460,12 +488,11 @@ def test_radiosity_variants(entangled, per_pixel, tile, bf16, ws):
     bins = _bins(ws, scene, views, st)
     compare_binning(bins, oracle.bin32(scene, views, st))
     ids = last_ids(nl.cpu().numpy().view(np.uint32), bins, views, st.tile)
-    check_image(scene, views, st, img.cpu().numpy(), tf.cpu().numpy(), ids)
-    ref = oracle.render(scene, views, st)
-    w = _masked_weights(ref, 3)
+    rep = check_image(scene, views, st, img.cpu().numpy(), tf.cpu().numpy(), ids)
+    w, fm = gradient_weights(rep, 3)
     g = B.render_backward(cloud, gv, cfg, ws, torch.as_tensor(w, dtype=torch.float32, device="cuda"),
                           tf, nl)
-    gr = oracle.render_backward(scene, views, st, w)
+    gr = oracle.render_backward(scene, views, st, w, flip_masks=fm)
     gpu = {n: t.float().cpu().numpy() for n, t in g.items()}
     gpu["feat"] = np.concatenate([gpu.pop("feat_iso").reshape(-1, 8), gpu.pop("feat_dir").reshape(-1, 8)])
     gpu["pose"] = gpu.pop("world_to_cam")
@@ -501,12 +528,11 @@ def test_warp_streamed_rasterisers(case, per_pixel, ws):
     torch.cuda.synchronize()
     bins = _bins(ws, scene, views, st)
     ids = last_ids(nl.cpu().numpy().view(np.uint32), bins, views, st.tile)
-    check_image(scene, views, st, img.cpu().numpy(), tf.cpu().numpy(), ids)
-    ref = oracle.render(scene, views, st)
-    w = _masked_weights(ref, 5)
+    rep = check_image(scene, views, st, img.cpu().numpy(), tf.cpu().numpy(), ids)
+    w, fm = gradient_weights(rep, 5)
     g = B.render_backward(cloud, gv, cfg, ws, torch.as_tensor(w, dtype=torch.float32, device="cuda"),
                           tf, nl)
-    gr = oracle.render_backward(scene, views, st, w)
+    gr = oracle.render_backward(scene, views, st, w, flip_masks=fm)
     gpu = {n: t.float().cpu().numpy() for n, t in g.items()}
     gpu["feat"] = np.concatenate([gpu.pop("feat_iso"), gpu.pop("feat_dir")])
     gpu["pose"] = gpu.pop("world_to_cam")
