@@ -414,7 +414,8 @@ ddgs_status ddgs_workspace_create(ddgs_workspace **out) {
     ddgs_workspace_destroy(ws);
     return DDGS_ERR_OUT_OF_MEMORY;
   }
-  if ((e = ddgs::prepare_bin_kernels()) != cudaSuccess) {
+  if ((e = ddgs::prepare_bin_kernels()) != cudaSuccess ||
+      (e = ddgs::prepare_raster_kernels()) != cudaSuccess) {
     ddgs_status st = cuda_fail(e, "binning kernel set-up");
     ddgs_workspace_destroy(ws);
     return st;

@@ -355,6 +355,7 @@ void launch_raster_bwd(const RenderShape &s, const RasterParams &p, ddgs_workspa
                        const PixelRays *pr, cudaStream_t st);
 
 int device_sms();  // streaming multiprocessors of the current device (raster.cu)
+cudaError_t prepare_raster_kernels();  // once per device, before any capture (raster.cu)
 
 // api.cu
 void launch_l1_loss(const float *image, const float *target, int per_view, int V, int64_t hw,

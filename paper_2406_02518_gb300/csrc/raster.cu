@@ -553,58 +553,110 @@ __device__ __forceinline__ uint32_t warp_next_item(uint32_t *counter) {
   return __shfl_sync(0xffffffffu, it, 0);
 }
 
+// ---- per-lane walks ----
+// Lane l owns pixel (l & 7, l >> 3) of the warp's 8 x 4 region. Every staged
+// entry turns its ellipse box into a 32-bit mask of the region's pixels whose
+// centres it covers; a bit-matrix transpose across the warp then gives each
+// lane the staged entries covering its own pixel, and each lane walks only
+// those (in list order). A lane evaluates far fewer entries than a group of
+// lanes sharing one walk would, and no lane waits for a group.
+
+// Warp-wide transpose of a 32 x 32 bit matrix: lane r holds row r on entry;
+// on return lane c holds column c (bit r = bit c of row r). Five rounds of
+// block swaps (16, 8, 4, 2, 1).
+__device__ __forceinline__ uint32_t transpose32(uint32_t x) {
+  const int lane = threadIdx.x & 31;
+  constexpr uint32_t LO[5] = {0x0000ffffu, 0x00ff00ffu, 0x0f0f0f0fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    const int d = 16 >> r;
+    const uint32_t y = __shfl_xor_sync(0xffffffffu, x, d);
+    x = (lane & d) ? ((x & ~LO[r]) | ((y >> d) & LO[r])) : ((x & LO[r]) | ((y << d) & ~LO[r]));
+  }
+  return x;
+}
+
+// Pixels of an 8 x 4 region whose centres lie in the box (x0, x1, y0, y1):
+// bit y * 8 + x for pixel centre (cx + x, cy + y).
+__device__ __forceinline__ uint32_t region_cover(float4 b, float cx, float cy) {
+  const int x0 = max(0, __float2int_ru(b.x - cx)), x1 = min(7, __float2int_rd(b.y - cx));
+  const int y0 = max(0, __float2int_ru(b.z - cy)), y1 = min(3, __float2int_rd(b.w - cy));
+  if (x0 > x1 || y0 > y1) return 0u;
+  const uint32_t row = (0xffu >> (7 - x1)) & (0xffu << x0);
+  const uint32_t rows = (0xffffffffu >> (8 * (3 - y1))) & (0xffffffffu << (8 * y0));
+  return (row * 0x01010101u) & rows;
+}
+
+// The 8 x 4 pixel region of a work item, lane l at pixel (l & 7, l >> 3).
+struct Region {
+  int v, H, W, wx0, wy0, px, py;
+  bool inside;
+  int64_t rec_base, img_off, n_req;
+  // tile edge T (8, 16 or 32): T / 8 regions per tile row
+  __device__ __forceinline__ Region(const RenderShape &s, int64_t gt, int region, int T) {
+    v = find_view(s.view, s.V, gt);
+    const ViewTab vt = s.view[v];
+    H = vt.H;
+    W = vt.W;
+    rec_base = vt.rec_off;
+    img_off = vt.img_off;
+    n_req = s.req[vt.req].n;
+    const int64_t local = gt - vt.tile_base;
+    const int tyi = (int)(local / vt.tiles_x), txi = (int)(local - (int64_t)tyi * vt.tiles_x);
+    const int WX = T / 8;
+    wx0 = txi * T + (region % WX) * 8;
+    wy0 = tyi * T + (region / WX) * 4;
+    const int lane = threadIdx.x & 31;
+    px = wx0 + (lane & 7);
+    py = wy0 + (lane >> 3);
+    inside = px < W && py < H;
+  }
+  __device__ __forceinline__ int64_t pixel() const { return img_off + (int64_t)py * W + px; }
+};
+
 template <int T, bool PIX>
-__device__ __forceinline__ void fwd_warp_item(const RasterArgs &a, int64_t gt, int region, float4 *sA,
+__device__ __forceinline__ void fwd_lane_item(const RasterArgs &a, int64_t gt, int region, float4 *sA,
                                               float4 *sB, float4 *sC) {
   const int lane = threadIdx.x & 31;
-  using Geom = TileGeom<T, 2>;  // eight 2 x 2 groups of 4 lanes
-  const Geom tg(a.s, gt, region);
-  const uint2 range = a.ranges[tg.gtile];
+  const Region rg(a.s, gt, region, T);
+  const uint2 range = a.ranges[gt];
   const uint32_t *vals = a.vals;
-  const float px = tg.px + 0.5f, py = tg.py + 0.5f;
-  const int qi = lane / Geom::LG;
-  constexpr uint32_t kGroup = (1u << Geom::LG) - 1u;
+  const float px = rg.px + 0.5f, py = rg.py + 0.5f;
+  const float cx = rg.wx0 + 0.5f, cy = rg.wy0 + 0.5f;
   PixRay ray;
-  if (PIX) pixel_ray(a.world_to_cam + 12 * tg.v, a.detector + 5 * tg.v, tg.H, tg.W, px, py, ray);
+  if (PIX) pixel_ray(a.world_to_cam + 12 * rg.v, a.detector + 5 * rg.v, rg.H, rg.W, px, py, ray);
   float Tr = 1.f, C = 0.f;
   uint32_t last = 0;
-  bool done = !tg.inside;
+  bool done = !rg.inside;
   for (uint32_t b0 = range.x; b0 < range.y; b0 += 32) {
-    const uint32_t dmask = __ballot_sync(0xffffffffu, done);
-    if (dmask == 0xffffffffu) break;
+    if (__all_sync(0xffffffffu, done)) break;
     const uint32_t j = b0 + lane;
-    const bool ok = j < range.y;
-    float4 box = empty_box();
-    if (ok) {
+    uint32_t cover = 0;
+    if (j < range.y) {
       const uint32_t id = vals[j];
-      if (id < tg.n_req) {  // else only after a capacity overflow
-        const int64_t r = tg.rec_base + id;
+      if (id < rg.n_req) {  // else only after a capacity overflow
+        const int64_t r = rg.rec_base + id;
         const float4 r0 = a.rec[2 * r], r1 = a.rec[2 * r + 1];
         sA[lane] = r0;
         sB[lane] = r1;
         if (PIX) sC[lane] = a.rec2[r];
-        box = ellipse_box(r0, r1, a.P.q_max);
+        cover = region_cover(ellipse_box(r0, r1, a.P.q_max), cx, cy);
       }
     }
     __syncwarp();
-    uint32_t mine = 0;  // entries this lane's group evaluates
-#pragma unroll
-    for (int q = 0; q < Geom::NG; ++q) {
-      const uint32_t m = __ballot_sync(0xffffffffu, ok && !tg.misses_q(box, q));
-      if (q == qi) mine = m;
-    }
-    if (((dmask >> (qi * Geom::LG)) & kGroup) == kGroup) mine = 0;  // group finished
+    uint32_t mine = transpose32(cover);  // staged entries covering this lane's pixel
+    if (done) mine = 0;
     while (__any_sync(0xffffffffu, mine != 0)) {
       if (mine == 0) continue;
       const int k = __ffs(mine) - 1;
       mine &= mine - 1;
-      if (done) continue;
       const float4 A = sA[k], B = sB[k];
       PairEval e;
       if (!eval_pair(A.x, A.y, A.z, A.w, B.x, B.y, px, py, a.P, e)) continue;
       const float Tn = __fmul_rn(Tr, __fsub_rn(1.f, e.sigma));
       if (Tn < a.P.t_min) {
         done = true;
+        mine = 0;
         continue;
       }
       const float col = PIX ? pixel_colour(ray, sC[k]) : B.z;
@@ -614,8 +666,8 @@ __device__ __forceinline__ void fwd_warp_item(const RasterArgs &a, int64_t gt, i
     }
     __syncwarp();  // the slice is rewritten by the next batch
   }
-  if (tg.inside) {
-    const int64_t pix = tg.pixel();
+  if (rg.inside) {
+    const int64_t pix = rg.pixel();
     a.image[pix] = C;
     a.t_final[pix] = Tr;
     a.n_last[pix] = last;
@@ -635,7 +687,7 @@ __global__ void __launch_bounds__(WARPS * 32, 5) raster_fwd_warp_kernel(RasterAr
     const uint32_t item = warp_next_item(a.counter);
     if (item >= n_items) break;
     const int64_t gt = a.order[item / NW];
-    fwd_warp_item<T, PIX>(a, gt, (int)(item % NW), s_a[w], s_b[w], s_c[w]);
+    fwd_lane_item<T, PIX>(a, gt, (int)(item % NW), s_a[w], s_b[w], s_c[w]);
     if (a.req_end && (threadIdx.x & 31) == 0)
       atomicMax(a.req_end + a.s.view[find_view(a.s.view, a.s.V, gt)].req, global_ns());
   }
@@ -830,6 +882,144 @@ __global__ void __launch_bounds__(WARPS * 32, 4) raster_bwd_warp_kernel(RasterAr
   }
 }
 
+// Backward of one (tile, region) item in two phases per staged batch of 32
+// entries (back to front):
+//  1. every lane walks the entries covering its pixel, from the last one the
+//     forward pass added, recovering T and the suffix sum S, and stores two
+//     numbers per (pixel, entry) it adds: A = dL/dsigma * G (0 where sigma
+//     was clamped) and Bc = dL/dc = g sigma T;
+//  2. after a transpose of the (pixel, entry) bits, lane e sums entry e's
+//     numbers over its pixels in registers: sum A, sum Bc and the moments
+//     sum A x, A y, A x^2, A x y, A y^2 of the pixel offsets (x, y) in the
+//     region. With u' = u - (region origin), dx = u' - x, dy = v' - y and
+//     dL/dq = -alpha A / 2, the sums of dL/dq dx, dL/dq dy, dL/dq dx^2, ...
+//     that the mean and conic gradients need follow from those moments.
+// No lane reduces another lane's values and no shared-memory atomic is used.
+constexpr int AB_STRIDE = 32;  // float2 per pixel row of the (pixel, entry) table
+
+struct LaneBwdSmem {
+  float4 a[32], b[32];
+  uint32_t id[32];
+  float2 ab[32 * AB_STRIDE];  // [pixel][entry ^ pixel]: (A, Bc)
+};
+
+template <int T>
+__device__ __forceinline__ void bwd_lane_item(const RasterArgs &a, int64_t gt, int region, LaneBwdSmem &sm) {
+  const int lane = threadIdx.x & 31;
+  const Region rg(a.s, gt, region, T);
+  const uint2 range = a.ranges[gt];
+  const uint32_t *vals = a.vals;
+  const float px = rg.px + 0.5f, py = rg.py + 0.5f;
+  const float cx = rg.wx0 + 0.5f, cy = rg.wy0 + 0.5f;
+  float Tr = 1.f, g = 0.f;
+  uint32_t last = 0;
+  if (rg.inside) {
+    const int64_t pix = rg.pixel();
+    Tr = a.t_final_in[pix];
+    last = a.n_last_in[pix];
+    g = a.dL_dimage[pix];
+  }
+  if (g == 0.f) last = 0;  // nothing to propagate from this pixel
+  if (last > range.y - range.x) last = range.y - range.x;  // never read past the list
+  uint32_t max_last = last;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) max_last = max(max_last, __shfl_xor_sync(0xffffffffu, max_last, o));
+  float S = 0.f;
+  for (int64_t hi = max_last; hi > 0; hi -= 32) {
+    const int cnt = (int)(hi > 32 ? 32 : hi);
+    // lane e stages list position hi - 1 - e (batches run back to front)
+    uint32_t cover = 0;
+    if (lane < cnt) {
+      const uint32_t id = vals[range.x + (uint32_t)(hi - 1 - lane)];
+      if (id < rg.n_req) {  // else only after a capacity overflow
+        const int64_t r = rg.rec_base + id;
+        const float4 r0 = a.rec[2 * r], r1 = a.rec[2 * r + 1];
+        sm.a[lane] = r0;
+        sm.b[lane] = r1;
+        cover = region_cover(ellipse_box(r0, r1, a.P.q_max), cx, cy);
+      }
+      sm.id[lane] = id;
+    }
+    __syncwarp();
+    uint32_t mine = transpose32(cover);
+    // staged entries e >= hi - last lie before this pixel's last added Gaussian
+    const int64_t skip = hi - (int64_t)last;
+    mine &= skip <= 0 ? 0xffffffffu : (skip >= 32 ? 0u : (0xffffffffu << skip));
+    uint32_t used = 0;
+    while (__any_sync(0xffffffffu, mine != 0)) {
+      if (mine == 0) continue;
+      const int k = __ffs(mine) - 1;
+      mine &= mine - 1;
+      const float4 A = sm.a[k], B = sm.b[k];
+      PairEval e;
+      if (!eval_pair(A.x, A.y, A.z, A.w, B.x, B.y, px, py, a.P, e)) continue;
+      // 1 / (1 - sigma) with sigma <= alpha_max < 1: the fast reciprocal's
+      // relative error (~1 ulp) is far inside the gradient tolerance
+      const float inv_om = rcp_approx(__fsub_rn(1.f, e.sigma));
+      Tr = Tr * inv_om;  // transmittance before this Gaussian
+      const float c = B.z;
+      const float dC_dsigma = fmaf(c, Tr, -S * inv_om);
+      S = fmaf(c * e.sigma, Tr, S);
+      const float gA = (e.aG > a.P.alpha_max) ? 0.f : g * dC_dsigma * e.G;
+      sm.ab[lane * AB_STRIDE + (k ^ lane)] = make_float2(gA, g * e.sigma * Tr);
+      used |= 1u << k;
+    }
+    __syncwarp();
+    uint32_t pm = transpose32(used);  // lane e: the pixels that added entry e
+    if (pm) {
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f, s5 = 0.f, s6 = 0.f;
+      do {
+        const int p = __ffs(pm) - 1;
+        pm &= pm - 1;
+        const float2 ab = sm.ab[p * AB_STRIDE + (lane ^ p)];
+        const float x = (float)(p & 7), y = (float)(p >> 3);
+        const float ax = ab.x * x, ay = ab.x * y;
+        s0 += ab.x;
+        s1 += ax;
+        s2 += ay;
+        s3 = fmaf(ax, x, s3);
+        s4 = fmaf(ax, y, s4);
+        s5 = fmaf(ay, y, s5);
+        s6 += ab.y;
+      } while (pm);
+      const float4 A = sm.a[lane], B = sm.b[lane];
+      const float u = A.x - cx, v = A.y - cy;  // mean relative to pixel (0, 0)
+      // sums over the entry's pixels of A dx, A dy, A dx^2, A dx dy, A dy^2
+      const float sdx = fmaf(u, s0, -s1), sdy = fmaf(v, s0, -s2);
+      const float sxx = fmaf(u, fmaf(u, s0, -2.f * s1), s3);
+      const float sxy = fmaf(u, fmaf(v, s0, -s2), fmaf(-v, s1, s4));
+      const float syy = fmaf(v, fmaf(v, s0, -2.f * s2), s5);
+      const float hq = -0.5f * B.y;  // dL/dq = -alpha A / 2
+      const float gx = hq * sdx, gy = hq * sdy;
+      // dq/du = 2 (a dx + b dy), dq/dv = 2 (b dx + c dy), dq/db = 2 dx dy
+      const float du = 2.f * fmaf(A.z, gx, A.w * gy);
+      const float dv = 2.f * fmaf(A.w, gx, B.x * gy);
+      float4 *dst = a.grad2d + 2 * (rg.rec_base + sm.id[lane]);
+      atomicAdd(dst, make_float4(du, dv, hq * sxx, 2.f * hq * sxy));
+      atomicAdd(dst + 1, make_float4(hq * syy, s0, s6, 0.f));
+    }
+    __syncwarp();  // the slice is rewritten by the next batch
+  }
+}
+
+template <int T>
+__global__ void __launch_bounds__(WARPS * 32, 3) raster_bwd_lane_kernel(RasterArgs a) {
+  constexpr int NW = T * T / 32;
+  extern __shared__ __align__(16) unsigned char lane_smem[];
+  LaneBwdSmem &sm = reinterpret_cast<LaneBwdSmem *>(lane_smem)[threadIdx.x >> 5];
+  const uint64_t n_items = (uint64_t)a.s.total_tiles * NW;
+  for (;;) {
+    const uint32_t item = warp_next_item(a.counter);
+    if (item >= n_items) break;
+    const int64_t gt = a.order[item / NW];
+    bwd_lane_item<T>(a, gt, (int)(item % NW), sm);
+    if (a.req_end && (threadIdx.x & 31) == 0)
+      atomicMax(a.req_end + a.s.view[find_view(a.s.view, a.s.V, gt)].req, global_ns());
+  }
+}
+
+constexpr size_t LANE_BWD_SMEM = WARPS * sizeof(LaneBwdSmem);
+
 // ---- work order: view by view, and within a view the tiles by descending
 // list length (bucketed by log2). At any time the persistent blocks then work
 // on a few views, whose records and gradient accumulators stay in L2 while
@@ -871,7 +1061,7 @@ __global__ void __launch_bounds__(256) tile_order_view_kernel(const ViewTab *vie
 
 // Resident blocks per SM of a kernel, cached per (device, kernel); the query
 // is not a stream operation, so it is also legal while a stream is captured.
-int blocks_per_sm(void (*k)(RasterArgs), int threads) {
+int blocks_per_sm(void (*k)(RasterArgs), int threads, size_t dyn_smem = 0) {
   static std::mutex mu;
   static std::map<std::pair<int, const void *>, int> cache;
   int dev = 0;
@@ -881,7 +1071,7 @@ int blocks_per_sm(void (*k)(RasterArgs), int threads) {
   auto it = cache.find(key);
   if (it != cache.end()) return it->second;
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, 0) != cudaSuccess || n < 1) n = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, dyn_smem) != cudaSuccess || n < 1) n = 1;
   cache[key] = n;
   return n;
 }
@@ -916,8 +1106,23 @@ void launch_fwd_warp_t(const RasterArgs &a, cudaStream_t st) {
   k<<<(unsigned)grid, WARPS * 32, 0, st>>>(a);
 }
 
+template <int T>
+void launch_bwd_lane_t(const RasterArgs &a, cudaStream_t st) {
+  if (prepare_raster_kernels() != cudaSuccess) return;  // surfaces via cudaGetLastError
+  auto k = raster_bwd_lane_kernel<T>;
+  const int64_t need = (a.s.total_tiles * (T * T / 32) + WARPS - 1) / WARPS;
+  int64_t grid = (int64_t)blocks_per_sm(k, WARPS * 32, LANE_BWD_SMEM) * device_sms();
+  if (grid > need) grid = need;
+  LaunchScope ls(KID_RASTER_BWD, st);
+  k<<<(unsigned)grid, WARPS * 32, LANE_BWD_SMEM, st>>>(a);
+}
+
 template <int T, bool PIX>
 void launch_bwd_warp_t(const RasterArgs &a, cudaStream_t st) {
+  if (!PIX) {
+    launch_bwd_lane_t<T>(a, st);
+    return;
+  }
   auto k = raster_bwd_warp_kernel<T, PIX>;
   const int64_t need = (a.s.total_tiles * (T * T / 32) + WARPS - 1) / WARPS;
   int64_t grid = (int64_t)blocks_per_sm(k, WARPS * 32) * device_sms();
@@ -1044,6 +1249,24 @@ void launch_raster_bwd(const RenderShape &s, const RasterParams &p, ddgs_workspa
   } else {
     bwd_dispatch<256, false>(a, s.tile, st);
   }
+}
+
+cudaError_t prepare_raster_kernels() {
+  // the per-lane backward keeps its (pixel, entry) tables in dynamic shared
+  // memory beyond the default 48 KiB; set once per device, outside any capture
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+  for (auto k : {raster_bwd_lane_kernel<8>, raster_bwd_lane_kernel<16>, raster_bwd_lane_kernel<32>}) {
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LANE_BWD_SMEM);
+    if (e != cudaSuccess) return e;
+  }
+  if (dev >= 0 && dev < 64) done[dev] = true;
+  return cudaSuccess;
 }
 
 // Streaming multiprocessors of the current device (cached per device).

@@ -154,6 +154,7 @@ extern "C" ddgs_status ddgs_render_static(const ddgs_gaussians *g, const ddgs_vi
   // the long-list sort's shared-memory limit (set once per device; the binning
   // would set it too, but here a failure is reported before any work is queued)
   CK_STATIC(ddgs::prepare_bin_kernels());
+  CK_STATIC(ddgs::prepare_raster_kernels());
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
 
   // A workspace view of the static array (host struct on the stack).
