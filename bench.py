@@ -1179,21 +1179,25 @@ def run_registration_loop(args):
     truth = views.world_to_cam.astype(np.float64)
     rot0 = reg.rotation_error_deg(np.repeat(base[None, :, :3], V, 0), truth[:, :, :3])
     tr0 = reg.translation_error_mm(np.repeat(base[None], V, 0), truth)
-    # untimed warm-up: a short registration (first-use costs of the process)
-    reg.register(cloud, det, H, W, targets, torch.as_tensor(base, device="cuda"), cfg,
-                 iters=2 * args.warmup + 2, ws=ws)
+    schedule = parse_stages(args.stages, args.iters, cfg.dilation)
+    # untimed warm-up: a short registration through the same stages
+    reg.register(cloud, det, H, W, targets, torch.as_tensor(base, device="cuda"), cfg, ws=ws,
+                 schedule=[(2 * args.warmup + 2, sc, dl) for _, sc, dl in schedule])
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     res = reg.register(cloud, det, H, W, targets, torch.as_tensor(base, device="cuda"), cfg,
-                       iters=args.iters, true_poses=truth, ws=ws)
+                       true_poses=truth, ws=ws, schedule=schedule)
     torch.cuda.synchronize()
     secs = time.perf_counter() - t0
+    iters = sum(n for n, _, _ in schedule)
     ok = (res.rot_err_deg < 1.0) & (res.trans_err_mm < 2.0)
     q = lambda a: {"p50": float(np.percentile(a, 50)), "p90": float(np.percentile(a, 90)),
                    "max": float(a.max())}
     line = {"metric": "pose registration: 64 candidates, 500k Gaussians, 256^2, Adam lr 0.05",
             "value": float(ok.mean()), "unit": "fraction registered (< 1 deg and < 2 mm)",
-            "n_gpus": 1, "iters": args.iters, "seconds": secs, "ms_per_iter": 1e3 * secs / args.iters,
+            "n_gpus": 1, "iters": iters, "seconds": secs, "ms_per_iter": 1e3 * secs / iters,
+            "schedule": [{"iters": n, "detector": f"{H // sc}x{W // sc}", "dilation_px2": dl}
+                         for n, sc, dl in schedule],
             "higher_is_better": True, "data": "synthetic",
             "initial_error": {"rot_deg": q(rot0), "trans_mm": q(tr0)},
             "final_error": {"rot_deg": q(res.rot_err_deg), "trans_mm": q(res.trans_err_mm)},
@@ -1202,6 +1206,20 @@ def run_registration_loop(args):
                        "graph": "iterations after the first 3 replay one CUDA graph"}}
     print(json.dumps(line))
     return 0
+
+
+def parse_stages(text, iters, dilation):
+    """'100x4@1.0,100x2@0.6,100x1@0.3' -> [(100, 4, 1.0), ...]: iterations x
+    detector downscale @ dilation (px^2). 'single' is one full-size stage of
+    `iters` iterations at the configured dilation."""
+    if not text or text == "single":
+        return [(iters, 1, dilation)]
+    out = []
+    for part in text.split(","):
+        n, rest = part.split("x")
+        sc, dl = rest.split("@")
+        out.append((int(n), int(sc), float(dl)))
+    return out
 
 
 def main():
@@ -1229,6 +1247,9 @@ def main():
                     help="Eq. 3 radiosity: the paper's disentangled sets, the direct-entangled "
                          "ablation (Table 3), or harmonics at each pixel's ray")
     ap.add_argument("--iters", type=int, default=300)
+    ap.add_argument("--stages", default="100x4@1.0,100x2@0.6,100x1@0.3",
+                    help="registration-loop stages, coarse to fine: iterations x detector "
+                         "downscale @ dilation px^2 ('single': --iters at full size)")
     ap.add_argument("--requests", type=int, default=256)
     args = ap.parse_args()
     if args.warmup < 3:

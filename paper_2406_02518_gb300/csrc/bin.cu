@@ -14,9 +14,10 @@
 //   sort     every list is ordered by (depth bits, Gaussian) in shared
 //            memory: a warp for lists up to 32 entries (bitonic network), a
 //            block for longer ones (buckets by the top bits of the depth, each
-//            ordered by insertion; where depths cluster, stable 8-bit counting
-//            passes over the depth bits that vary in the list, then over the
-//            Gaussian index where depths tie); lists longer than BIN_LIST_LONG
+//            entry placed by counting the smaller keys of its bucket; where
+//            depths cluster, stable 8-bit counting passes over the depth bits
+//            that vary in the list, then over the Gaussian index where depths
+//            tie); lists longer than BIN_LIST_LONG
 //            are sorted in chunks that one block then merges (merge path).
 // Depth is positive, so its IEEE bits order like the number. The result is the
 // unique order of Gaussians by (depth, index), the order of a stable sort of
@@ -30,7 +31,7 @@ namespace ddgs {
 namespace {
 
 constexpr int BIN_THREADS = 256;   // count blocks
-constexpr int SCAT_THREADS = 1024;  // scatter blocks (measured: 256: 0.96 ms, 1024: 0.71 ms)
+constexpr int SCAT_THREADS = 512;  // scatter blocks
 constexpr int SORT_SHORT = 1024;  // lists of one 128-thread block (8 entries a thread)
 constexpr int SORT_MID = 2048;    // lists of one 128-thread block (16 entries a thread)
 constexpr int MERGE_ITEMS = 8;    // outputs per thread per merge step
@@ -172,36 +173,49 @@ __device__ __forceinline__ bool tile_slot(const RenderShape &s, int64_t gt, int6
 }
 
 // offsets, part 1: per tile, the chunks' counts become running offsets within
-// the tile's list; the tile total goes to ranges[gt].y, the block's sum of
-// totals to part[block]. Without pairs (counted = 0) every list is empty.
-__global__ void __launch_bounds__(1024) bin_column_kernel(RenderShape s, int counted,
-                                                            uint32_t *hist, uint2 *ranges,
-                                                            uint64_t *part) {
-  __shared__ uint64_t s_w[32];
-  const int64_t gt = (int64_t)blockIdx.x * 1024 + threadIdx.x;
-  uint32_t cnt = 0;
-  if (gt < s.total_tiles) {
-    int64_t first, stride;
-    int chunks;
-    if (counted && tile_slot(s, gt, first, stride, chunks)) {
-      uint32_t *h = hist + first;
-      for (int c = 0; c < chunks; ++c) {
-        const uint32_t x = h[c * stride];
-        h[c * stride] = cnt;
-        cnt += x;
-      }
-    }
-    ranges[gt] = make_uint2(0u, cnt);
-  }
-  uint64_t x = cnt;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = x;
+// the tile's list; the tile total goes to ranges[gt].y, and each 1024-tile
+// group's sum of totals is added to part[group] (zeroed beforehand). A block
+// takes 32 tiles (one per lane) and splits their chunks over its 8 warps:
+// each warp sums its share of the chunks, the warps' sums are scanned in
+// shared memory, and each warp then rewrites its share as running offsets.
+// Without pairs (counted = 0) every list is empty.
+constexpr int COL_WARPS = 8;
+__global__ void __launch_bounds__(COL_WARPS * 32) bin_column_kernel(RenderShape s, int counted,
+                                                                     uint32_t *hist, uint2 *ranges,
+                                                                     uint64_t *part) {
+  __shared__ uint32_t s_sum[COL_WARPS][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t gt = (int64_t)blockIdx.x * 32 + lane;
+  int64_t first = 0, stride = 0;
+  int chunks = 0;
+  const bool has = gt < s.total_tiles && counted && tile_slot(s, gt, first, stride, chunks);
+  const int seg = (chunks + COL_WARPS - 1) / COL_WARPS;
+  const int c0 = min(chunks, w * seg), c1 = min(chunks, c0 + seg);
+  uint32_t *h = hist + first;
+  uint32_t sum = 0;
+  if (has)
+    for (int c = c0; c < c1; ++c) sum += h[c * stride];
+  s_sum[w][lane] = sum;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    uint64_t t = 0;
-    for (int w = 0; w < 32; ++w) t += s_w[w];
-    part[blockIdx.x] = t;
+  uint32_t run = 0, total = 0;
+#pragma unroll
+  for (int x = 0; x < COL_WARPS; ++x) {
+    const uint32_t v = s_sum[x][lane];
+    if (x < w) run += v;
+    total += v;
+  }
+  if (has)
+    for (int c = c0; c < c1; ++c) {
+      const uint32_t x = h[c * stride];
+      h[c * stride] = run;
+      run += x;
+    }
+  if (w == 0) {
+    if (gt < s.total_tiles) ranges[gt] = make_uint2(0u, total);
+    uint64_t t = total;  // the block's 32 tiles lie in one 1024-tile group
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0 && t) atomicAdd(reinterpret_cast<unsigned long long *>(part + (gt >> 10)), t);
   }
 }
 
@@ -259,17 +273,11 @@ __global__ void __launch_bounds__(1024) bin_offsets_kernel(int64_t n_tiles, uint
   list_append(L, LIST_LONG, (uint64_t)gt, n > BIN_LIST_LONG ? 1u : 0u);
 }
 
-// L2 eviction priorities: the binning records stream through once (evict
-// first); the lists are written 8 bytes at a time into many open 32-byte
-// sectors, which should stay in L2 until they are complete (evict last).
+// L2 eviction priority of the binning records: they stream through once
+// (evict first).
 __device__ __forceinline__ uint64_t l2_policy_evict_first() {
   uint64_t p;
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ uint64_t l2_policy_evict_last() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
   return p;
 }
 __device__ __forceinline__ uint4 ld_hint(const uint4 *a, uint64_t pol) {
@@ -278,62 +286,149 @@ __device__ __forceinline__ uint4 ld_hint(const uint4 *a, uint64_t pol) {
                : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(a), "l"(pol));
   return v;
 }
-__device__ __forceinline__ void st_hint(uint64_t *a, uint64_t v, uint64_t pol) {
-  asm volatile("st.global.L2::cache_hint.u64 [%0], %1, %2;" :: "l"(a), "l"(v), "l"(pol) : "memory");
+
+// scatter: every pair of the block goes to its tile's list, at the tile's
+// offset plus the earlier chunks' counts plus its rank within the block. The
+// block stages its pairs in shared memory, grouped by tile, and then writes
+// them out in that order, so that each tile's run of pairs leaves as one
+// stretch of consecutive 8-byte entries instead of single scattered stores.
+// A chunk whose pairs exceed the staging area is done in windows of
+// consecutive band tiles (its records are read again per window, from L2); a
+// single tile with more pairs than the area is written directly. Lists of one
+// entry are final here (flag bit 31 of the destination; offsets stay below
+// BIN_MAX_PAIRS < 2^31). Pairs of lists left empty by a capacity overflow are
+// dropped.
+constexpr uint32_t CUR_ONE = 0x80000000u, CUR_DROP = 0xffffffffu;
+constexpr int SCAT_STAGE = 6144;  // pairs staged per window (12 bytes each)
+
+__host__ __device__ constexpr size_t scatter_smem(int area) {
+  return (size_t)SCAT_STAGE * (sizeof(uint64_t) + sizeof(uint32_t)) + (size_t)area * 3 * sizeof(uint32_t);
 }
 
-// scatter: each pair of the block goes to the next free slot of its tile's
-// range (the block's slots start at the tile's offset plus the earlier
-// chunks' counts). Lists of one entry are final here (flag bit 31 of the
-// cursor; offsets stay below BIN_MAX_PAIRS < 2^31). Pairs of lists left
-// empty by a capacity overflow are dropped.
-constexpr uint32_t CUR_ONE = 0x80000000u, CUR_DROP = 0xffffffffu;
+// In-place exclusive scan of a[0, n) by the whole block; returns the total.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t *a, int n, uint32_t *s_wsum) {
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int per = (n + SCAT_THREADS - 1) / SCAT_THREADS, b = tid * per;
+  uint32_t loc = 0;
+  for (int k = 0; k < per; ++k)
+    if (b + k < n) loc += a[b + k];
+  uint32_t inc = loc;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) s_wsum[w] = inc;
+  __syncthreads();
+  uint32_t ex = inc - loc, total = 0;
+  for (int x = 0; x < SCAT_THREADS / 32; ++x) {
+    if (x < w) ex += s_wsum[x];
+    total += s_wsum[x];
+  }
+  for (int k = 0; k < per; ++k)
+    if (b + k < n) {
+      const uint32_t c = a[b + k];
+      a[b + k] = ex;
+      ex += c;
+    }
+  __syncthreads();
+  return total;
+}
 
 __global__ void __launch_bounds__(SCAT_THREADS) bin_scatter_kernel(RenderShape s, const uint4 *info,
                                                                     const uint32_t *hist,
                                                                     const uint2 *ranges,
                                                                     uint64_t *keys, uint32_t *vals,
                                                                     uint64_t cap) {
-  extern __shared__ uint32_t s_cur[];
+  extern __shared__ __align__(16) unsigned char scat_smem[];
+  __shared__ uint32_t s_wsum[SCAT_THREADS / 32];
   const ViewTab vt = s.view[find_item_view(s.view, s.V, blockIdx.x)];
   const BinItem it = bin_item(s, vt, blockIdx.x);
   const int tiles_y = (vt.H + s.tile - 1) / s.tile;
   const int area = it.bw * it.bh;
+  uint64_t *s_key = reinterpret_cast<uint64_t *>(scat_smem);  // [SCAT_STAGE] staged pairs
+  uint32_t *s_dst = reinterpret_cast<uint32_t *>(s_key + SCAT_STAGE);  // [SCAT_STAGE] their places
+  uint32_t *s_base = s_dst + SCAT_STAGE;  // [area] place of the tile's first pair of this block
+  uint32_t *s_beg = s_base + area;        // [area] counts, then their exclusive prefix
+  uint32_t *s_cur = s_beg + area;         // [area] staging cursors
+  const int64_t j = (int64_t)blockIdx.x - vt.item_base;
+  const bool last_chunk = j % vt.chunks == vt.chunks - 1;
   for (int p = threadIdx.x; p < area; p += SCAT_THREADS) {
     const int x = it.tx0 + p % it.bw, y = it.ty0 + p / it.bw;
-    uint32_t c = CUR_DROP;
+    uint32_t base = CUR_DROP, cnt = 0;
     if (x < vt.tiles_x && y < tiles_y) {
       const uint2 r = ranges[vt.tile_base + (int64_t)y * vt.tiles_x + x];
-      if (r.y > r.x) c = (r.x + hist[it.slot + p]) | (r.y - r.x == 1 ? CUR_ONE : 0u);
+      if (r.y > r.x) {
+        const uint32_t off = hist[it.slot + p];  // the chunk's offset within the list
+        const uint32_t next = last_chunk ? r.y - r.x : hist[it.slot + area + p];
+        base = (r.x + off) | (r.y - r.x == 1 ? CUR_ONE : 0u);
+        cnt = next - off;
+      }
     }
-    s_cur[p] = c;
+    s_base[p] = base;
+    s_beg[p] = cnt;
   }
   __syncthreads();
-  const uint64_t pol_in = l2_policy_evict_first(), pol_out = l2_policy_evict_last();
-  for (int64_t l0 = it.l0 + threadIdx.x; l0 < it.l1; l0 += BIN_LOADS * SCAT_THREADS) {
-    uint4 b[BIN_LOADS];
-#pragma unroll
-    for (int k = 0; k < BIN_LOADS; ++k) {
-      const int64_t l = l0 + k * SCAT_THREADS;
-      b[k] = l < it.l1 ? ld_hint(info + it.rec0 + l, pol_in) : make_uint4(0, 0, 0, 0);
+  const uint32_t all = block_exclusive_scan(s_beg, area, s_wsum);  // the block's pairs
+  for (int p = threadIdx.x; p < area; p += SCAT_THREADS) s_cur[p] = s_beg[p];
+  __syncthreads();
+  const uint64_t pol_in = l2_policy_evict_first();
+  int w0 = 0;
+  while (w0 < area) {  // block-uniform windows of tiles [w0, w1)
+    const uint32_t b0 = s_beg[w0];
+    // the largest w1 whose pairs fit the staging area (binary search on the
+    // prefix; prefix(area) = all)
+    int lo = w0, hi = area;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if ((mid < area ? s_beg[mid] : all) - b0 <= (uint32_t)SCAT_STAGE) lo = mid; else hi = mid - 1;
     }
+    const bool direct = lo == w0;  // tile w0 alone has more pairs than the area
+    const int w1 = direct ? w0 + 1 : lo;
+    const uint32_t n_win = direct ? 0u : (w1 < area ? s_beg[w1] : all) - b0;
+    for (int64_t l0 = it.l0 + threadIdx.x; (direct || n_win > 0) && l0 < it.l1;
+         l0 += BIN_LOADS * SCAT_THREADS) {
+      uint4 b[BIN_LOADS];
 #pragma unroll
-    for (int k = 0; k < BIN_LOADS; ++k) {
-      int x0, y0, x1, y1;
-      if (!band_rect(b[k], it, x0, y0, x1, y1)) continue;
-      const uint32_t l = (uint32_t)(l0 + k * SCAT_THREADS);
-      const uint64_t key = ((uint64_t)b[k].z << 32) | l;
-      for (int y = y0; y <= y1; ++y)
-        for (int x = x0; x <= x1; ++x) {
-          uint32_t *cur = &s_cur[(y - it.ty0) * it.bw + (x - it.tx0)];
-          if (*cur == CUR_DROP) continue;  // never advanced, so a plain read is exact
-          const uint32_t c = atomicAdd(cur, 1u);
-          const uint32_t pos = c & ~CUR_ONE;
-          if (pos >= cap) continue;
-          if (c & CUR_ONE) vals[pos] = l;
-          else st_hint(keys + pos, key, pol_out);
+      for (int k = 0; k < BIN_LOADS; ++k) {
+        const int64_t l = l0 + k * SCAT_THREADS;
+        b[k] = l < it.l1 ? ld_hint(info + it.rec0 + l, pol_in) : make_uint4(0, 0, 0, 0);
+      }
+#pragma unroll
+      for (int k = 0; k < BIN_LOADS; ++k) {
+        int x0, y0, x1, y1;
+        if (!band_rect(b[k], it, x0, y0, x1, y1)) continue;
+        const uint32_t l = (uint32_t)(l0 + k * SCAT_THREADS);
+        const uint64_t key = ((uint64_t)b[k].z << 32) | l;
+        for (int y = y0; y <= y1; ++y) {
+          const int row = (y - it.ty0) * it.bw;
+          for (int x = x0; x <= x1; ++x) {
+            const int p = row + (x - it.tx0);
+            if (p < w0 || p >= w1 || s_base[p] == CUR_DROP) continue;
+            const uint32_t c = atomicAdd(&s_cur[p], 1u);
+            const uint32_t dst = s_base[p] + (c - s_beg[p]);  // keeps the CUR_ONE flag
+            if (direct) {
+              const uint32_t pos = dst & ~CUR_ONE;
+              if (pos >= cap) continue;
+              if (dst & CUR_ONE) vals[pos] = l;
+              else keys[pos] = key;
+            } else {
+              s_key[c - b0] = key;
+              s_dst[c - b0] = dst;
+            }
+          }
         }
+      }
     }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < n_win; i += SCAT_THREADS) {
+      const uint32_t dst = s_dst[i], pos = dst & ~CUR_ONE;
+      if (pos >= cap) continue;
+      if (dst & CUR_ONE) vals[pos] = (uint32_t)s_key[i];
+      else keys[pos] = s_key[i];
+    }
+    __syncthreads();
+    w0 = w1;
   }
 }
 
@@ -468,12 +563,16 @@ __device__ __forceinline__ void block_digit_pass(const uint64_t *src, uint64_t *
 // Lists (or BIN_LIST_LONG-entry chunks of longer lists) of up to NT x E
 // entries: one block each, in shared memory. First a bucket sort: the top
 // bits of (depth - smallest depth) spread the entries over about as many
-// buckets as entries (shared-memory counters), and each bucket is put in
-// order by insertion on the full (depth, index) key. Where a bucket would
-// hold more than BUCKET_MAX entries (clustered or equal depths), the list is
-// sorted instead by stable 8-bit passes over the depth bits that differ in
-// it, redone with the index digits first if two depths are equal. Whole
-// lists write their values; chunks write their sorted keys back for the merge.
+// buckets as entries (shared-memory counters); then every entry finds its
+// place as its bucket's start plus the number of smaller (depth, index) keys
+// in its bucket (keys are unique), and goes straight to the output. (An
+// insertion sort per bucket, one thread a bucket, cost 25 % more at the
+// benchmark: views near an axis of the voxel grid put up to ~20 entries of
+// near-equal depth in one bucket.) Where a bucket would hold more than
+// BUCKET_MAX entries (clustered or equal depths), the list is sorted instead
+// by stable 8-bit passes over the depth bits that differ in it, redone with
+// the index digits first if two depths are equal. Whole lists write their
+// values; chunks write their sorted keys back for the merge.
 constexpr uint32_t BUCKET_MAX = 24;
 template <int NT, int E, int MINB>
 __global__ void __launch_bounds__(NT, MINB) bin_sort_block_kernel(const uint64_t *items,
@@ -584,21 +683,20 @@ __global__ void __launch_bounds__(NT, MINB) bin_sort_block_kernel(const uint64_t
           }
         }
         __syncthreads();
-        for (int b = tid; b < nbk; b += NT) {
-          const uint32_t b0 = bc[b], b1 = b + 1 < nbk ? bc[b + 1] : (uint32_t)m;
-          for (uint32_t x = b0 + 1; x < b1; ++x) {
-            const uint64_t k = oth[x];
-            uint32_t y = x;
-            while (y > b0 && oth[y - 1] > k) {
-              oth[y] = oth[y - 1];
-              --y;
-            }
-            oth[y] = k;
-          }
+        // every entry's place: its bucket's start plus the number of smaller
+        // keys in its bucket (keys are unique), written straight to the output
+        const bool whole = n_all <= (uint32_t)CAP;
+        for (int j = tid; j < m; j += NT) {
+          const uint64_t k = oth[j];
+          const uint32_t b = ((uint32_t)(k >> 32) - dmin) >> sh;
+          const uint32_t b0 = bc[b], b1 = b + 1 < (uint32_t)nbk ? bc[b + 1] : (uint32_t)m;
+          uint32_t pos = b0;
+          for (uint32_t x = b0; x < b1; ++x) pos += oth[x] < k;
+          if (whole) vals[base + pos] = (uint32_t)k;
+          else keys[base + pos] = k;
         }
         __syncthreads();
-        uint64_t *t = cur; cur = oth; oth = t;
-        sorted = true;
+        continue;
       }
     }
     const int rows_all = (m + 31) / 32;
@@ -702,6 +800,9 @@ cudaError_t prepare_bin_kernels() {
   if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
   e = cudaFuncSetAttribute(bin_sort_block_kernel<SORT_LONG_THREADS, SORT_LONG_ITEMS, 1>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LONG_SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(bin_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)scatter_smem(BIN_HIST_MAX));
   if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
   return e;
 }
@@ -730,9 +831,11 @@ void launch_binning(const RenderShape &s, uint64_t pair_bound, ddgs_workspace &w
   L.item[LIST_BLOCK] = ws.lists + 4 * T;
   L.count = ws.list_count;
   cudaMemsetAsync(ws.list_count, 0, LIST_CLASSES * sizeof(uint32_t), st);
+  cudaMemsetAsync(part, 0, (size_t)nb * sizeof(uint64_t), st);
   {
     LaunchScope ls(KID_BIN_OFFSETS, st);
-    bin_column_kernel<<<(unsigned)nb, 1024, 0, st>>>(s, pairs ? 1 : 0, ws.hist, ws.ranges, part);
+    bin_column_kernel<<<(unsigned)((T + 31) / 32), COL_WARPS * 32, 0, st>>>(s, pairs ? 1 : 0, ws.hist,
+                                                                          ws.ranges, part);
   }
   {
     LaunchScope ls(KID_BIN_OFFSETS, st);
@@ -745,7 +848,7 @@ void launch_binning(const RenderShape &s, uint64_t pair_bound, ddgs_workspace &w
   if (!pairs) return;
   {
     LaunchScope ls(KID_BIN_SCATTER, st);
-    bin_scatter_kernel<<<(unsigned)s.n_items, SCAT_THREADS, hsm, st>>>(
+    bin_scatter_kernel<<<(unsigned)s.n_items, SCAT_THREADS, scatter_smem(s.hist_area), st>>>(
         s, reinterpret_cast<const uint4 *>(ws.rect), ws.hist, ws.ranges, ws.keys[0], ws.vals, cap);
   }
   {

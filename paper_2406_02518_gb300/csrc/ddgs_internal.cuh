@@ -17,9 +17,9 @@ constexpr int VIEW_CHUNK = 64;            // views staged in shared memory at on
 // pairs with per-tile counters in shared memory, over bands of at most
 // BIN_HIST_MAX tiles; every tile list is then ordered in shared memory.
 constexpr int BIN_HIST_MAX = 8192;           // tiles of one band
-constexpr int64_t BIN_TARGET_ITEMS = 608;    // binning blocks aimed for (4 per SM)
-constexpr int64_t BIN_MIN_CHUNK = 1024;      // Gaussians per binning block, at least
-constexpr int64_t BIN_SLOT_BUDGET = int64_t(1) << 21;  // per-block tile counters of a render
+constexpr int64_t BIN_CHUNK = 2048;          // Gaussians per binning block (their pairs,
+                                             // about two per Gaussian, are staged at once)
+constexpr int64_t BIN_SLOT_BUDGET = int64_t(1) << 24;  // per-block tile counters of a render
 constexpr int BIN_LIST_LONG = 8192;          // longest list ordered by one block at once
 constexpr int64_t BIN_MAX_PAIRS = (int64_t(1) << 31) - 1;  // offsets leave bit 31 free
 constexpr float SH_C1 = 0.48860251190291992f;  // sqrt(3 / (4 pi))
@@ -112,22 +112,20 @@ __device__ __forceinline__ int find_item_view(const ViewTab *tab, int V, int64_t
 }
 
 // Binning blocks of a layout (host): every view's Gaussians are cut into
-// chunks (about BIN_TARGET_ITEMS blocks in all, at least BIN_MIN_CHUNK
-// Gaussians each, and at most `budget` counters beyond one per tile) and its
-// tiles into bands of at most BIN_HIST_MAX tiles (whole rows where a row
-// fits). view[V] is the sentinel; req[r].n gives each request's size.
+// chunks of about BIN_CHUNK (fewer and larger where the tile counters would
+// exceed `budget` beyond one per tile) and its tiles into bands of at most
+// BIN_HIST_MAX tiles (whole rows where a row fits). view[V] is the sentinel;
+// req[r].n gives each request's size.
 inline void plan_binning(ViewTab *view, int32_t V, const ReqTab *req, int64_t total_tiles,
                          int32_t tile, RenderShape &s, int64_t budget = BIN_SLOT_BUDGET) {
   int64_t items = 0, slots = 0;
   int32_t area = 0;
-  const int64_t per_view = V > 0 ? (BIN_TARGET_ITEMS + V - 1) / V : 1;
   const int64_t by_slots = total_tiles > 0 ? budget / total_tiles : 1;
   for (int32_t v = 0; v < V; ++v) {
     ViewTab &t = view[v];
     const int64_t n = req[t.req].n;
     const int64_t tx = t.tiles_x, ty = (t.H + tile - 1) / tile;
-    int64_t chunks = (n + BIN_MIN_CHUNK - 1) / BIN_MIN_CHUNK;
-    if (chunks > per_view) chunks = per_view;
+    int64_t chunks = (n + BIN_CHUNK - 1) / BIN_CHUNK;
     if (chunks > by_slots) chunks = by_slots;
     if (chunks < 1) chunks = 1;
     if (n == 0) chunks = 0;

@@ -566,7 +566,9 @@ __device__ __forceinline__ int warp_reduce16(float v[16]) {
   return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
 }
 
-template <bool GEN>
+// POSE = true: only the pose gradient is wanted (a registration step,
+// Sec. 4.3); the per-Gaussian accumulators are left out.
+template <bool GEN, bool POSE = false>
 __global__ void __launch_bounds__(PRE_THREADS, GEN ? 2 : 3) preprocess_bwd_kernel(PreBwdArgs a) {
   constexpr int KS = GEN ? KG : K, KLS = GEN ? KLG : 3;
   // views whose gradient records are in flight ahead of the one being used
@@ -687,13 +689,13 @@ __global__ void __launch_bounds__(PRE_THREADS, GEN ? 2 : 3) preprocess_bwd_kerne
         }
         if (any) {
           const float gu = g0.x, gv = g0.y, gca = g0.z, gcb = g0.w, gcc = g1.x;
-          galpha += g1.y;
+          if (!POSE) galpha += g1.y;
           // radiosity (Eq. 3); dir_grad: the colour depends on the mean's direction
           bool dir_grad = false;
           float d[3], inv = 0.f, dh_[3], ddh[3] = {0.f, 0.f, 0.f};
           if (!GEN) {
             if (!is_dir) {
-              dz_iso += g1.z * c_iso * (1.f - c_iso);
+              if (!POSE) dz_iso += g1.z * c_iso * (1.f - c_iso);
             } else {
               dir_grad = true;
               d[0] = mu[0] + vc.wt[0]; d[1] = mu[1] + vc.wt[1]; d[2] = mu[2] + vc.wt[2];
@@ -702,7 +704,7 @@ __global__ void __launch_bounds__(PRE_THREADS, GEN ? 2 : 3) preprocess_bwd_kerne
               float Y[3] = {-SH_C1 * dh_[1], SH_C1 * dh_[2], -SH_C1 * dh_[0]};
               float c = sigmoidf_(Y[0] * h[0] + Y[1] * h[1] + Y[2] * h[2]);
               float dz = g1.z * c * (1.f - c);
-              dh[0] += dz * Y[0]; dh[1] += dz * Y[1]; dh[2] += dz * Y[2];
+              if (!POSE) { dh[0] += dz * Y[0]; dh[1] += dz * Y[1]; dh[2] += dz * Y[2]; }
               float dY[3] = {dz * h[0], dz * h[1], dz * h[2]};
               ddh[0] = -SH_C1 * dY[2]; ddh[1] = -SH_C1 * dY[0]; ddh[2] = SH_C1 * dY[1];
             }
@@ -743,7 +745,7 @@ __global__ void __launch_bounds__(PRE_THREADS, GEN ? 2 : 3) preprocess_bwd_kerne
                            (ddh[2] - dh_[2] * dot) * inv};
 #pragma unroll
             for (int c3 = 0; c3 < 3; ++c3) {
-              dmu[c3] += dd[c3];
+              if (!POSE) dmu[c3] += dd[c3];
 #pragma unroll
               for (int r = 0; r < 3; ++r) dW[3 * r + c3] += vc.t[r] * dd[c3];
             }
@@ -776,12 +778,14 @@ __global__ void __launch_bounds__(PRE_THREADS, GEN ? 2 : 3) preprocess_bwd_kerne
             Q[k] = GS00 * p.A[k] + GS01 * p.A[3 + k];
             Q[3 + k] = GS01 * p.A[k] + GS11 * p.A[3 + k];
           }
-          dSig[0] += p.A[0] * Q[0] + p.A[3] * Q[3];
-          dSig[1] += p.A[0] * Q[1] + p.A[3] * Q[4];
-          dSig[2] += p.A[0] * Q[2] + p.A[3] * Q[5];
-          dSig[3] += p.A[1] * Q[1] + p.A[4] * Q[4];
-          dSig[4] += p.A[1] * Q[2] + p.A[4] * Q[5];
-          dSig[5] += p.A[2] * Q[2] + p.A[5] * Q[5];
+          if (!POSE) {
+            dSig[0] += p.A[0] * Q[0] + p.A[3] * Q[3];
+            dSig[1] += p.A[0] * Q[1] + p.A[3] * Q[4];
+            dSig[2] += p.A[0] * Q[2] + p.A[3] * Q[5];
+            dSig[3] += p.A[1] * Q[1] + p.A[4] * Q[4];
+            dSig[4] += p.A[1] * Q[2] + p.A[4] * Q[5];
+            dSig[5] += p.A[2] * Q[2] + p.A[5] * Q[5];
+          }
           // A = J W: dJ = dA W^T (entries 00, 02, 11, 12), dW += J^T dA
           const float dJ00 = dA[0] * vc.W[0] + dA[1] * vc.W[1] + dA[2] * vc.W[2];
           const float dJ02 = dA[0] * vc.W[6] + dA[1] * vc.W[7] + dA[2] * vc.W[8];
@@ -801,9 +805,11 @@ __global__ void __launch_bounds__(PRE_THREADS, GEN ? 2 : 3) preprocess_bwd_kerne
           dxc[2] = -(dJ00 * p.j00 + dJ11 * p.j11) * iz - 2.f * (dJ02 * p.j02 + dJ12 * p.j12) * iz +
                    gu * p.j02 + gv * p.j12;
           // x_c = W mu + t
+          if (!POSE) {
 #pragma unroll
-          for (int c3 = 0; c3 < 3; ++c3)
-            dmu[c3] += vc.W[c3] * dxc[0] + vc.W[3 + c3] * dxc[1] + vc.W[6 + c3] * dxc[2];
+            for (int c3 = 0; c3 < 3; ++c3)
+              dmu[c3] += vc.W[c3] * dxc[0] + vc.W[3 + c3] * dxc[1] + vc.W[6 + c3] * dxc[2];
+          }
 #pragma unroll
           for (int r = 0; r < 3; ++r) {
 #pragma unroll
@@ -832,7 +838,7 @@ __global__ void __launch_bounds__(PRE_THREADS, GEN ? 2 : 3) preprocess_bwd_kerne
   }
 
   // per-Gaussian outputs
-  if (live && a.want_param) {
+  if (!POSE && live && a.want_param) {
     if (a.out.opacity_logits) a.out.opacity_logits[i] = galpha * alpha * (1.f - alpha);
     if (a.out.means) {
       a.out.means[3 * i] = dmu[0]; a.out.means[3 * i + 1] = dmu[1]; a.out.means[3 * i + 2] = dmu[2];
@@ -913,7 +919,7 @@ __global__ void __launch_bounds__(PRE_THREADS, GEN ? 2 : 3) preprocess_bwd_kerne
       }
     }
   }
-  if (a.want_basis && GEN) {
+  if (!POSE && a.want_basis && GEN) {
     // b_iso gradient: dz_iso f (isotropic); B_dir gradient: dh f^T (directional)
     if (live) {
       for (int k = 0; k < Kr; ++k) {
@@ -937,7 +943,7 @@ __global__ void __launch_bounds__(PRE_THREADS, GEN ? 2 : 3) preprocess_bwd_kerne
       }
     }
   }
-  if (a.want_basis && !GEN) {
+  if (!POSE && a.want_basis && !GEN) {
     // b_iso gradient: dz_iso f (isotropic); B_dir gradient: dh f^T (directional)
     float v32[4 * K];
 #pragma unroll
@@ -1012,7 +1018,10 @@ void launch_preprocess_bwd(const ddgs_gaussians &g, const ddgs_views &v, const d
   a.want_pose = out.world_to_cam ? 1 : 0;
   if (s.n_blocks > 0) {
     LaunchScope ls(KID_PREPROCESS_BWD, st);
-    if (a.K == K && a.L == 1 && !a.entangled && !a.per_pixel)
+    const bool fast = a.K == K && a.L == 1 && !a.entangled && !a.per_pixel;
+    if (fast && !a.want_param && !a.want_basis)
+      preprocess_bwd_kernel<false, true><<<(unsigned)s.n_blocks, PRE_THREADS, 0, st>>>(a);
+    else if (fast)
       preprocess_bwd_kernel<false><<<(unsigned)s.n_blocks, PRE_THREADS, 0, st>>>(a);
     else
       preprocess_bwd_kernel<true><<<(unsigned)s.n_blocks, PRE_THREADS, 0, st>>>(a);

@@ -628,15 +628,26 @@ __device__ __forceinline__ void fwd_lane_item(const RasterArgs &a, int64_t gt, i
   float Tr = 1.f, C = 0.f;
   uint32_t last = 0;
   bool done = !rg.inside;
+  // software pipeline: the list ids two batches ahead and the records one
+  // batch ahead are in flight while a batch is walked
+  uint32_t id1 = 0xffffffffu, id2 = 0xffffffffu;
+  float4 n0 = make_float4(0.f, 0.f, 0.f, 0.f), n1 = n0;
+  if (range.x + lane < range.y) id1 = vals[range.x + lane];
+  if (range.x + 32 + lane < range.y) id2 = vals[range.x + 32 + lane];
+  if (id1 < rg.n_req) { const int64_t r = rg.rec_base + id1; n0 = a.rec[2 * r]; n1 = a.rec[2 * r + 1]; }
   for (uint32_t b0 = range.x; b0 < range.y; b0 += 32) {
     if (__all_sync(0xffffffffu, done)) break;
     const uint32_t j = b0 + lane;
     uint32_t cover = 0;
+    const uint32_t id = id1;
+    const float4 r0 = n0, r1 = n1;
+    id1 = id2;
+    id2 = 0xffffffffu;
+    if (b0 + 64 + lane < range.y) id2 = vals[b0 + 64 + lane];
+    if (id1 < rg.n_req) { const int64_t r = rg.rec_base + id1; n0 = a.rec[2 * r]; n1 = a.rec[2 * r + 1]; }
     if (j < range.y) {
-      const uint32_t id = vals[j];
-      if (id < rg.n_req) {  // else only after a capacity overflow
+      if (id < rg.n_req) {
         const int64_t r = rg.rec_base + id;
-        const float4 r0 = a.rec[2 * r], r1 = a.rec[2 * r + 1];
         sA[lane] = r0;
         sB[lane] = r1;
         if (PIX) sC[lane] = a.rec2[r];
@@ -674,10 +685,9 @@ __device__ __forceinline__ void fwd_lane_item(const RasterArgs &a, int64_t gt, i
   }
 }
 
+// Resident blocks per SM asked of the register allocator: 5 for the forward
+// (6 makes the pipelined walk spill: 1.55 -> 1.83 ms at 64 poses).
 template <int T, bool PIX>
-// Resident blocks per SM asked of the register allocator: 5 (48 registers) for
-// the forward and 4 (64) for the backward; without block barriers fewer
-// resident warps keep the SM busy.
 __global__ void __launch_bounds__(WARPS * 32, 5) raster_fwd_warp_kernel(RasterArgs a) {
   constexpr int NW = T * T / 32;
   __shared__ float4 s_a[WARPS][32], s_b[WARPS][32], s_c[WARPS][PIX ? 32 : 1];
@@ -896,6 +906,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) raster_bwd_warp_kernel(RasterAr
 //     that the mean and conic gradients need follow from those moments.
 // No lane reduces another lane's values and no shared-memory atomic is used.
 constexpr int AB_STRIDE = 32;  // float2 per pixel row of the (pixel, entry) table
+constexpr int LANE_WARPS = 8;  // warps per block of the per-lane backward (3 blocks per SM)
 
 struct LaneBwdSmem {
   float4 a[32], b[32];
@@ -925,15 +936,25 @@ __device__ __forceinline__ void bwd_lane_item(const RasterArgs &a, int64_t gt, i
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) max_last = max(max_last, __shfl_xor_sync(0xffffffffu, max_last, o));
   float S = 0.f;
+  // software pipeline: the list ids two batches ahead and the records one
+  // batch ahead are in flight while a batch is walked
+  uint32_t id1 = 0xffffffffu, id2 = 0xffffffffu;
+  float4 n0 = make_float4(0.f, 0.f, 0.f, 0.f), n1 = n0;
+  if ((int64_t)lane < (int64_t)max_last) id1 = vals[range.x + (uint32_t)(max_last - 1 - lane)];
+  if ((int64_t)max_last > 32 && (int64_t)lane < (int64_t)max_last - 32)
+    id2 = vals[range.x + (uint32_t)(max_last - 33 - lane)];
+  if (id1 < rg.n_req) { const int64_t r = rg.rec_base + id1; n0 = a.rec[2 * r]; n1 = a.rec[2 * r + 1]; }
   for (int64_t hi = max_last; hi > 0; hi -= 32) {
     const int cnt = (int)(hi > 32 ? 32 : hi);
-    // lane e stages list position hi - 1 - e (batches run back to front)
     uint32_t cover = 0;
+    const uint32_t id = id1;
+    const float4 r0 = n0, r1 = n1;
+    id1 = id2;
+    id2 = 0xffffffffu;
+    if (hi - 64 > 0 && (int64_t)lane < hi - 64) id2 = vals[range.x + (uint32_t)(hi - 65 - lane)];
+    if (id1 < rg.n_req) { const int64_t r = rg.rec_base + id1; n0 = a.rec[2 * r]; n1 = a.rec[2 * r + 1]; }
     if (lane < cnt) {
-      const uint32_t id = vals[range.x + (uint32_t)(hi - 1 - lane)];
-      if (id < rg.n_req) {  // else only after a capacity overflow
-        const int64_t r = rg.rec_base + id;
-        const float4 r0 = a.rec[2 * r], r1 = a.rec[2 * r + 1];
+      if (id < rg.n_req) {
         sm.a[lane] = r0;
         sm.b[lane] = r1;
         cover = region_cover(ellipse_box(r0, r1, a.P.q_max), cx, cy);
@@ -968,19 +989,25 @@ __device__ __forceinline__ void bwd_lane_item(const RasterArgs &a, int64_t gt, i
     uint32_t pm = transpose32(used);  // lane e: the pixels that added entry e
     if (pm) {
       float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f, s5 = 0.f, s6 = 0.f;
-      do {
+      do {  // two pixels per trip: half the loop overhead, two loads in flight
         const int p = __ffs(pm) - 1;
         pm &= pm - 1;
+        const bool two = pm != 0;
+        const int q = two ? __ffs(pm) - 1 : p;
+        pm &= pm - 1;
         const float2 ab = sm.ab[p * AB_STRIDE + (lane ^ p)];
+        float2 cd = sm.ab[q * AB_STRIDE + (lane ^ q)];
+        if (!two) cd = make_float2(0.f, 0.f);
         const float x = (float)(p & 7), y = (float)(p >> 3);
-        const float ax = ab.x * x, ay = ab.x * y;
-        s0 += ab.x;
-        s1 += ax;
-        s2 += ay;
-        s3 = fmaf(ax, x, s3);
-        s4 = fmaf(ax, y, s4);
-        s5 = fmaf(ay, y, s5);
-        s6 += ab.y;
+        const float x2 = (float)(q & 7), y2 = (float)(q >> 3);
+        const float ax = ab.x * x, ay = ab.x * y, cx2 = cd.x * x2, cy2 = cd.x * y2;
+        s0 += ab.x + cd.x;
+        s1 += ax + cx2;
+        s2 += ay + cy2;
+        s3 = fmaf(ax, x, fmaf(cx2, x2, s3));
+        s4 = fmaf(ax, y, fmaf(cx2, y2, s4));
+        s5 = fmaf(ay, y, fmaf(cy2, y2, s5));
+        s6 += ab.y + cd.y;
       } while (pm);
       const float4 A = sm.a[lane], B = sm.b[lane];
       const float u = A.x - cx, v = A.y - cy;  // mean relative to pixel (0, 0)
@@ -1003,7 +1030,7 @@ __device__ __forceinline__ void bwd_lane_item(const RasterArgs &a, int64_t gt, i
 }
 
 template <int T>
-__global__ void __launch_bounds__(WARPS * 32, 3) raster_bwd_lane_kernel(RasterArgs a) {
+__global__ void __launch_bounds__(LANE_WARPS * 32, 3) raster_bwd_lane_kernel(RasterArgs a) {
   constexpr int NW = T * T / 32;
   extern __shared__ __align__(16) unsigned char lane_smem[];
   LaneBwdSmem &sm = reinterpret_cast<LaneBwdSmem *>(lane_smem)[threadIdx.x >> 5];
@@ -1018,7 +1045,7 @@ __global__ void __launch_bounds__(WARPS * 32, 3) raster_bwd_lane_kernel(RasterAr
   }
 }
 
-constexpr size_t LANE_BWD_SMEM = WARPS * sizeof(LaneBwdSmem);
+constexpr size_t LANE_BWD_SMEM = LANE_WARPS * sizeof(LaneBwdSmem);
 
 // ---- work order: view by view, and within a view the tiles by descending
 // list length (bucketed by log2). At any time the persistent blocks then work
@@ -1110,11 +1137,11 @@ template <int T>
 void launch_bwd_lane_t(const RasterArgs &a, cudaStream_t st) {
   if (prepare_raster_kernels() != cudaSuccess) return;  // surfaces via cudaGetLastError
   auto k = raster_bwd_lane_kernel<T>;
-  const int64_t need = (a.s.total_tiles * (T * T / 32) + WARPS - 1) / WARPS;
-  int64_t grid = (int64_t)blocks_per_sm(k, WARPS * 32, LANE_BWD_SMEM) * device_sms();
+  const int64_t need = (a.s.total_tiles * (T * T / 32) + LANE_WARPS - 1) / LANE_WARPS;
+  int64_t grid = (int64_t)blocks_per_sm(k, LANE_WARPS * 32, LANE_BWD_SMEM) * device_sms();
   if (grid > need) grid = need;
   LaunchScope ls(KID_RASTER_BWD, st);
-  k<<<(unsigned)grid, WARPS * 32, LANE_BWD_SMEM, st>>>(a);
+  k<<<(unsigned)grid, LANE_WARPS * 32, LANE_BWD_SMEM, st>>>(a);
 }
 
 template <int T, bool PIX>

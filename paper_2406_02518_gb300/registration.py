@@ -125,16 +125,43 @@ class _Adam:
             p.sub_(self.lr * (m / c1) / (torch.sqrt(v / c2) + self.eps))
 
 
+def coarse_targets(targets: torch.Tensor, scale: int, blur_px2: float) -> torch.Tensor:
+    """Targets [V,H,W] for a coarse stage: means over scale x scale pixel
+    blocks, then a Gaussian blur of variance blur_px2 (coarse pixels^2) with
+    replicated edges. A preprocessing of the fixed target images, once per
+    stage; the renders of every iteration run in the library's kernels."""
+    t = targets.unsqueeze(1)
+    if scale > 1:
+        t = torch.nn.functional.avg_pool2d(t, scale)
+    if blur_px2 > 0:
+        r = int(math.ceil(3 * math.sqrt(blur_px2)))
+        x = torch.arange(-r, r + 1, dtype=t.dtype, device=t.device)
+        k = torch.exp(-0.5 * x * x / blur_px2)
+        k = k / k.sum()
+        pad = torch.nn.functional.pad
+        t = torch.nn.functional.conv2d(pad(t, (r, r, 0, 0), mode="replicate"), k.view(1, 1, 1, -1))
+        t = torch.nn.functional.conv2d(pad(t, (0, 0, r, r), mode="replicate"), k.view(1, 1, -1, 1))
+    return t.squeeze(1).contiguous()
+
+
 def register(cloud: B.Cloud, detector: torch.Tensor, height: int, width: int,
              targets: torch.Tensor, init_pose: torch.Tensor, cfg: B.Config,
              iters: int = 200, lr: float = 0.05, trans_unit: float = 10.0,
              rot_unit: float = 0.1, true_poses: np.ndarray | None = None, ws: B.Workspace | None = None,
-             graph: bool = True) -> RegistrationResult:
+             graph: bool = True, schedule=None) -> RegistrationResult:
     """Register V candidates at once. targets [V,H,W]; init_pose [V,3,4] or
     [3,4]; detector [V,5]. Adam on (w, d) with learning rate `lr`. With
-    graph=True the iterations after the first few replay one CUDA graph; if
-    the pair count ever outgrows the reserved workspace, the registration is
-    run again without the graph."""
+    graph=True the iterations of a stage after its first few replay one CUDA
+    graph; if the pair count ever outgrows the reserved workspace, the stage
+    is run again without the graph.
+
+    schedule: stages (iterations, scale, dilation px^2) run in order with one
+    Adam state, coarse to fine. A stage renders a detector of
+    (height / scale) x (width / scale) pixels of scale times the pitch, with
+    the given dilation, against coarse_targets(targets, scale, blur) where the
+    blur makes up the difference between that dilation and the full-size
+    render's (cfg.dilation / scale^2) and the block mean (1/12 px^2 per axis).
+    The default is one stage: (iters, 1, cfg.dilation)."""
     dev = cloud.means.device
     V = targets.shape[0]
     P0 = init_pose.to(dev, torch.float64).expand(V, 3, 4) if init_pose.dim() == 2 else \
@@ -142,12 +169,46 @@ def register(cloud: B.Cloud, detector: torch.Tensor, height: int, width: int,
     R0, t0 = P0[:, :, :3], P0[:, :, 3]
     w = torch.zeros((V, 3), dtype=torch.float64, device=dev, requires_grad=True)
     d = torch.zeros((V, 3), dtype=torch.float64, device=dev, requires_grad=True)
-    graph = graph and iters > _EAGER_ITERS
     opt = _Adam([w, d], lr=lr)
     ws = ws or B.Workspace()
     det = detector.to(dev, torch.float32).expand(V, 5).contiguous()
-    losses = torch.zeros((iters, V), dtype=torch.float32, device=dev)
+    schedule = list(schedule) if schedule else [(iters, 1, cfg.dilation)]
+    total = sum(int(n) for n, _, _ in schedule)
+    losses = torch.zeros((total, V), dtype=torch.float32, device=dev)
+    done = 0
+    for n_it, scale, dil in schedule:
+        n_it, scale = int(n_it), int(scale)
+        if n_it <= 0:
+            continue
+        if height % scale or width % scale:
+            raise ValueError("a stage's scale must divide the detector size")
+        H_s, W_s = height // scale, width // scale
+        det_s = det.clone()
+        det_s[:, 1:3] *= scale   # pitch
+        det_s[:, 3:5] /= scale   # principal point offsets, pixels
+        cfg_s = dataclasses.replace(cfg, dilation=float(dil))
+        blur = max(0.0, float(dil) - cfg.dilation / scale ** 2 - (1.0 / 12.0 if scale > 1 else 0.0))
+        tgt = coarse_targets(targets, scale, blur) if (scale > 1 or blur > 0) else targets
+        _run_stage(cloud, det_s, H_s, W_s, tgt, R0, t0, w, d, opt, cfg_s, n_it, trans_unit,
+                   rot_unit, ws, graph, losses[done:done + n_it])
+        done += n_it
+    with torch.no_grad():
+        final = compose(R0, t0, w, d, trans_unit, rot_unit).cpu().numpy()
+    if true_poses is not None:
+        rot = rotation_error_deg(final[:, :, :3], true_poses[:, :, :3])
+        tr = translation_error_mm(final, true_poses)
+    else:
+        rot = tr = np.full(V, np.nan)
+    return RegistrationResult(final, rot, tr, losses.cpu().numpy())
+
+
+def _run_stage(cloud, det, height, width, targets, R0, t0, w, d, opt, cfg, iters, trans_unit,
+               rot_unit, ws, graph, losses):
+    """iters Adam iterations of one stage; per-iteration losses into losses."""
+    graph = graph and iters > _EAGER_ITERS
     run_cfg = cfg
+    state = ([p.detach().clone() for p in (w, d)], [m.clone() for m in opt.m],
+             [v.clone() for v in opt.v], opt.t.clone())
 
     def iteration():
         opt.zero_grad()
@@ -164,39 +225,41 @@ def register(cloud: B.Cloud, detector: torch.Tensor, height: int, width: int,
     if not graph:
         for i in range(iters):
             losses[i].copy_(iteration())
-    else:
-        # size the workspace for no-sync renders from the initial pose's pair count
-        with torch.no_grad():
-            pose = compose(R0, t0, w, d, trans_unit, rot_unit).to(torch.float32).contiguous()
-            B.render(cloud, B.Views(pose, det, height, width), cfg, ws)
-        torch.cuda.synchronize()
-        tiles = V * (-(-height // cfg.tile)) * (-(-width // cfg.tile))
-        ws.reserve(V * cloud.n, int(ws.pairs() * 1.5) + 4096, tiles)
-        run_cfg = dataclasses.replace(cfg, no_sync=True)
-        side = torch.cuda.Stream()
-        side.wait_stream(torch.cuda.current_stream())
-        with torch.cuda.stream(side):
-            for i in range(_EAGER_ITERS):
-                losses[i].copy_(iteration())
-        torch.cuda.current_stream().wait_stream(side)
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g):
-            loss_static = iteration()
-        for i in range(_EAGER_ITERS, iters):
-            g.replay()
-            losses[i].copy_(loss_static)
-        torch.cuda.synchronize()
-        if ws.sync_status() != 0:  # a no-sync render ran out of room: redo without the graph
-            return register(cloud, detector, height, width, targets, init_pose, cfg, iters, lr,
-                            trans_unit, rot_unit, true_poses, ws, graph=False)
+        return
+    V = targets.shape[0]
+    # size the workspace for no-sync renders from the stage's starting pair count
     with torch.no_grad():
-        final = compose(R0, t0, w, d, trans_unit, rot_unit).cpu().numpy()
-    if true_poses is not None:
-        rot = rotation_error_deg(final[:, :, :3], true_poses[:, :, :3])
-        tr = translation_error_mm(final, true_poses)
-    else:
-        rot = tr = np.full(V, np.nan)
-    return RegistrationResult(final, rot, tr, losses.cpu().numpy())
+        pose = compose(R0, t0, w, d, trans_unit, rot_unit).to(torch.float32).contiguous()
+        B.render(cloud, B.Views(pose, det, height, width), cfg, ws)
+    torch.cuda.synchronize()
+    tiles = V * (-(-height // cfg.tile)) * (-(-width // cfg.tile))
+    ws.reserve(V * cloud.n, int(ws.pairs() * 1.5) + 4096, tiles)
+    run_cfg = dataclasses.replace(cfg, no_sync=True)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for i in range(_EAGER_ITERS):
+            losses[i].copy_(iteration())
+    torch.cuda.current_stream().wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        loss_static = iteration()
+    for i in range(_EAGER_ITERS, iters):
+        g.replay()
+        losses[i].copy_(loss_static)
+    torch.cuda.synchronize()
+    del g
+    if ws.sync_status() != 0:  # a no-sync render ran out of room: redo the stage without the graph
+        with torch.no_grad():
+            for p, q in zip((w, d), state[0]):
+                p.copy_(q)
+            for m, q in zip(opt.m, state[1]):
+                m.copy_(q)
+            for v, q in zip(opt.v, state[2]):
+                v.copy_(q)
+            opt.t.copy_(state[3])
+        _run_stage(cloud, det, height, width, targets, R0, t0, w, d, opt, cfg, iters, trans_unit,
+                   rot_unit, ws, False, losses)
 
 
 def perturbed_poses(rng: np.random.Generator, base: np.ndarray, n: int, max_deg: float,

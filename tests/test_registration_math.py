@@ -59,3 +59,22 @@ def test_device_adam_matches_torch_adam():
             loss.backward()
             opt.step()
     assert torch.allclose(p_ref, p_our, rtol=0, atol=1e-12)
+
+
+def test_coarse_targets_pool_and_blur():
+    rng = np.random.default_rng(0)
+    t = torch.as_tensor(rng.uniform(0, 1, (2, 16, 24)), dtype=torch.float32)
+    # block means only
+    c = reg.coarse_targets(t, 4, 0.0)
+    assert c.shape == (2, 4, 6)
+    assert torch.allclose(c[1, 2, 3], t[1, 8:12, 12:16].mean())
+    # a blur keeps a constant image and spreads a centred spike with the given variance
+    const = torch.full((1, 20, 20), 0.7)
+    assert torch.allclose(reg.coarse_targets(const, 1, 2.0), const, atol=1e-6)
+    spike = torch.zeros((1, 41, 41))
+    spike[0, 20, 20] = 1.0
+    b = reg.coarse_targets(spike, 1, 2.0)[0].double()
+    assert abs(float(b.sum()) - 1.0) < 1e-5
+    x = torch.arange(41, dtype=torch.float64) - 20
+    var_x = float((b.sum(0) * x * x).sum())
+    assert abs(var_x - 2.0) < 0.05
