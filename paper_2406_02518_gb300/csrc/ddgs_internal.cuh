@@ -201,7 +201,7 @@ __device__ __forceinline__ float exp2_approx(float x) {
 // Per-pair evaluation shared by the forward and backward rasterisers, written
 // with explicit rounding so both kernels take bit-identical decisions.
 struct PairEval {
-  float dx, dy, tx, ty, G, aG, sigma;
+  float dx, dy, G, aG, sigma;
 };
 
 // Half-extents of the q <= q_max ellipse of a 2D covariance, sqrt(q_max
@@ -226,15 +226,15 @@ __device__ __forceinline__ float2 unpack_halfwidths(float w) {
                      __half2float(__ushort_as_half((unsigned short)(b >> 16))));
 }
 
-// q = d^T K d computed as d . t with t = K d (t is reused by the gradients).
-__device__ __forceinline__ bool eval_pair(float u, float v, float ca, float cb, float cc,
+// q = d^T K d for the conic K = [[a, b], [b, c]], evaluated as
+// dx (a dx + 2b dy) + c dy^2 from the record's (a, 2b, c).
+__device__ __forceinline__ bool eval_pair(float u, float v, float ca, float cb2, float cc,
                                           float alpha, float px, float py,
                                           const RasterParams &P, PairEval &e) {
   e.dx = __fsub_rn(u, px);
   e.dy = __fsub_rn(v, py);
-  e.tx = __fmaf_rn(ca, e.dx, __fmul_rn(cb, e.dy));
-  e.ty = __fmaf_rn(cb, e.dx, __fmul_rn(cc, e.dy));
-  const float q = __fmaf_rn(e.dx, e.tx, __fmul_rn(e.dy, e.ty));
+  const float t = __fmaf_rn(cb2, e.dy, __fmul_rn(ca, e.dx));
+  const float q = __fmaf_rn(__fmul_rn(cc, e.dy), e.dy, __fmul_rn(e.dx, t));
   if (q > P.q_max || q < 0.f) return false;
   e.G = exp2_approx(__fmul_rn(q, -0.72134752044448170368f));  // exp(-q / 2) = 2^(-q log2(e) / 2)
   e.aG = __fmul_rn(alpha, e.G);
@@ -249,9 +249,9 @@ struct ddgs_workspace {
   int device = -1;
   int64_t rec_cap = 0, pair_cap = 0, tile_cap = 0, blk_cap = 0, hist_cap = 0, list_cap = 0;
   // per (view, Gaussian) records
-  float4 *rec = nullptr;         // [records][2]: (u, v, conic a, conic b), (conic c, alpha,
-                                 // colour, packed box half-extents): one 32-byte sector
-                                 // per gather
+  float4 *rec = nullptr;         // [records][2]: (u, v, conic a, 2 x conic b), (conic c,
+                                 // alpha, colour, packed box half-extents): one 32-byte
+                                 // sector per gather
   uint2 *rect = nullptr;         // (tx0 | ty0 << 16, tx1 | ty1 << 16)
   uint32_t *tiles_touched = nullptr;
   float4 *grad2d = nullptr;      // [records][2]: (u, v, ca, cb), (cc, alpha, colour, 0);

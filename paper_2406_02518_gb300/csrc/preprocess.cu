@@ -491,7 +491,7 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_fwd_kernel(PreArgs a) 
         }
         colour = sigmoidf_(zl);
       }
-      a.rec[2 * rec] = make_float4(p.u, p.v, ca, cb);
+      a.rec[2 * rec] = make_float4(p.u, p.v, ca, 2.f * cb);  // 2b: see eval_pair
       a.rec[2 * rec + 1] = make_float4(cc, alpha, colour, box_halfwidths(p.cov, a.q_max));
     }
   }

@@ -477,7 +477,7 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs &a, int64_t gt, BwdSme
       if (nz) {
         float4 *dst = a.grad2d + 2 * (rec_base + s_id[e]);
         // dq/du = 2 (a dx + b dy), dq/dv = 2 (b dx + c dy), dq/db = 2 dx dy
-        const float ca = s_a[e].z, cb = s_a[e].w, cc = s_b[e].x;
+        const float ca = s_a[e].z, cb = 0.5f * s_a[e].w, cc = s_b[e].x;  // the record holds 2b
         const float du = 2.f * fmaf(ca, acc[0], cb * acc[1]);
         const float dv = 2.f * fmaf(cb, acc[0], cc * acc[1]);
         atomicAdd(dst, make_float4(du, dv, acc[2], 2.f * acc[3]));
@@ -657,7 +657,9 @@ __device__ __forceinline__ void fwd_lane_item(const RasterArgs &a, int64_t gt, i
     __syncwarp();
     uint32_t mine = transpose32(cover);  // staged entries covering this lane's pixel
     if (done) mine = 0;
-    while (__any_sync(0xffffffffu, mine != 0)) {
+    const uint32_t pos1 = b0 - range.x + 1u;  // 1 + list position of staged entry 0
+    const int trips = (int)__reduce_max_sync(0xffffffffu, (uint32_t)__popc(mine));
+    for (int t = 0; t < trips; ++t) {
       if (mine == 0) continue;
       const int k = __ffs(mine) - 1;
       mine &= mine - 1;
@@ -673,7 +675,7 @@ __device__ __forceinline__ void fwd_lane_item(const RasterArgs &a, int64_t gt, i
       const float col = PIX ? pixel_colour(ray, sC[k]) : B.z;
       C = fmaf(col * e.sigma, Tr, C);
       Tr = Tn;
-      last = b0 + (uint32_t)k - range.x + 1u;
+      last = pos1 + (uint32_t)k;
     }
     __syncwarp();  // the slice is rewritten by the next batch
   }
@@ -836,7 +838,7 @@ __device__ __forceinline__ void bwd_warp_item(const RasterArgs &a, int64_t gt, i
         const int64_t r = tg.rec_base + sId[lane];
         float4 *dst = a.grad2d + 2 * r;
         // dq/du = 2 (a dx + b dy), dq/dv = 2 (b dx + c dy), dq/db = 2 dx dy
-        const float ca = sA[lane].z, cb = sA[lane].w, cc = sB[lane].x;
+        const float ca = sA[lane].z, cb = 0.5f * sA[lane].w, cc = sB[lane].x;  // the record holds 2b
         const float du = 2.f * fmaf(ca, acc[0], cb * acc[1]);
         const float dv = 2.f * fmaf(cb, acc[0], cc * acc[1]);
         atomicAdd(dst, make_float4(du, dv, acc[2], 2.f * acc[3]));
@@ -967,7 +969,8 @@ __device__ __forceinline__ void bwd_lane_item(const RasterArgs &a, int64_t gt, i
     const int64_t skip = hi - (int64_t)last;
     mine &= skip <= 0 ? 0xffffffffu : (skip >= 32 ? 0u : (0xffffffffu << skip));
     uint32_t used = 0;
-    while (__any_sync(0xffffffffu, mine != 0)) {
+    const int trips = (int)__reduce_max_sync(0xffffffffu, (uint32_t)__popc(mine));
+    for (int t = 0; t < trips; ++t) {
       if (mine == 0) continue;
       const int k = __ffs(mine) - 1;
       mine &= mine - 1;
@@ -1019,8 +1022,9 @@ __device__ __forceinline__ void bwd_lane_item(const RasterArgs &a, int64_t gt, i
       const float hq = -0.5f * B.y;  // dL/dq = -alpha A / 2
       const float gx = hq * sdx, gy = hq * sdy;
       // dq/du = 2 (a dx + b dy), dq/dv = 2 (b dx + c dy), dq/db = 2 dx dy
-      const float du = 2.f * fmaf(A.z, gx, A.w * gy);
-      const float dv = 2.f * fmaf(A.w, gx, B.x * gy);
+      // (the record holds a in A.z, 2b in A.w, c in B.x)
+      const float du = fmaf(2.f * A.z, gx, A.w * gy);
+      const float dv = fmaf(A.w, gx, 2.f * B.x * gy);
       float4 *dst = a.grad2d + 2 * (rg.rec_base + sm.id[lane]);
       atomicAdd(dst, make_float4(du, dv, hq * sxx, 2.f * hq * sxy));
       atomicAdd(dst + 1, make_float4(hq * syy, s0, s6, 0.f));
