@@ -150,6 +150,41 @@ __device__ __forceinline__ void view_proj(const float mu[3], const float S[6], c
   p.valid = p.det > 0.0f;
 }
 
+// The same projection for the backward chain, in plain FP32 with contracted
+// multiply-adds and one approximate reciprocal of z: no integer decision
+// depends on it, and a record reaches the backward only if the forward's
+// exact chain kept it (its 2D gradient is non-zero), so it is not culled here.
+__device__ __forceinline__ void view_proj_grad(const float mu[3], const float S[6], const ViewConst &vc,
+                                               float dilation, ViewProj &p) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+    p.xc[r] = fmaf(vc.W[3 * r + 2], mu[2], fmaf(vc.W[3 * r + 1], mu[1], fmaf(vc.W[3 * r], mu[0], vc.t[r])));
+  const float iz = rcp_approx(p.xc[2]);
+  p.xz = p.xc[0] * iz;
+  p.yz = p.xc[1] * iz;
+  p.j00 = vc.fu * iz;
+  p.j11 = vc.fv * iz;
+  p.j02 = -p.j00 * p.xz;
+  p.j12 = -p.j11 * p.yz;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    p.A[k] = fmaf(p.j02, vc.W[6 + k], p.j00 * vc.W[k]);
+    p.A[3 + k] = fmaf(p.j12, vc.W[6 + k], p.j11 * vc.W[3 + k]);
+  }
+  float B[6];
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      B[3 * r + k] = fmaf(p.A[3 * r + 2], sym(S, 2, k),
+                          fmaf(p.A[3 * r + 1], sym(S, 1, k), p.A[3 * r] * sym(S, 0, k)));
+  p.cov[0] = fmaf(B[2], p.A[2], fmaf(B[1], p.A[1], fmaf(B[0], p.A[0], dilation)));
+  p.cov[1] = fmaf(B[2], p.A[5], fmaf(B[1], p.A[4], B[0] * p.A[3]));
+  p.cov[2] = fmaf(B[5], p.A[5], fmaf(B[4], p.A[4], fmaf(B[3], p.A[3], dilation)));
+  p.det = fmaf(p.cov[0], p.cov[2], -p.cov[1] * p.cov[1]);
+  p.valid = true;
+}
+
 // G14-G15: inclusive tile rectangle; returns tiles touched (0 = none).
 __device__ __forceinline__ uint32_t tile_rect(const ViewProj &p, float q_max, int H, int W, int tile,
                                               int &tx0, int &ty0, int &tx1, int &ty1) {
@@ -683,10 +718,7 @@ __global__ void __launch_bounds__(PRE_THREADS, GEN ? 2 : 3) preprocess_bwd_kerne
         any = (g0.x != 0.f) | (g0.y != 0.f) | (g0.z != 0.f) | (g0.w != 0.f) | (g1.x != 0.f) |
               (g1.y != 0.f) | (g1.z != 0.f) | (gh.x != 0.f) | (gh.y != 0.f) | (gh.z != 0.f);
         ViewProj p;
-        if (any) {
-          view_proj(mu, gg.S, vc, a.dilation, a.near_plane, p);
-          any = p.valid;
-        }
+        if (any) view_proj_grad(mu, gg.S, vc, a.dilation, p);
         if (any) {
           const float gu = g0.x, gv = g0.y, gca = g0.z, gcb = g0.w, gcc = g1.x;
           if (!POSE) galpha += g1.y;

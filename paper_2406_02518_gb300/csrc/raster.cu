@@ -969,24 +969,40 @@ __device__ __forceinline__ void bwd_lane_item(const RasterArgs &a, int64_t gt, i
     const int64_t skip = hi - (int64_t)last;
     mine &= skip <= 0 ? 0xffffffffu : (skip >= 32 ? 0u : (0xffffffffu << skip));
     uint32_t used = 0;
-    const int trips = (int)__reduce_max_sync(0xffffffffu, (uint32_t)__popc(mine));
-    for (int t = 0; t < trips; ++t) {
+    const int trips = (int)__reduce_max_sync(0xffffffffu, (uint32_t)(__popc(mine) + 1) >> 1);
+    for (int t = 0; t < trips; ++t) {  // two entries per trip: their evaluations overlap
       if (mine == 0) continue;
       const int k = __ffs(mine) - 1;
       mine &= mine - 1;
-      const float4 A = sm.a[k], B = sm.b[k];
-      PairEval e;
-      if (!eval_pair(A.x, A.y, A.z, A.w, B.x, B.y, px, py, a.P, e)) continue;
-      // 1 / (1 - sigma) with sigma <= alpha_max < 1: the fast reciprocal's
-      // relative error (~1 ulp) is far inside the gradient tolerance
-      const float inv_om = rcp_approx(__fsub_rn(1.f, e.sigma));
-      Tr = Tr * inv_om;  // transmittance before this Gaussian
-      const float c = B.z;
-      const float dC_dsigma = fmaf(c, Tr, -S * inv_om);
-      S = fmaf(c * e.sigma, Tr, S);
-      const float gA = (e.aG > a.P.alpha_max) ? 0.f : g * dC_dsigma * e.G;
-      sm.ab[lane * AB_STRIDE + (k ^ lane)] = make_float2(gA, g * e.sigma * Tr);
-      used |= 1u << k;
+      const bool two = mine != 0;
+      const int k2 = two ? __ffs(mine) - 1 : k;
+      mine &= mine - 1;
+      const float4 A = sm.a[k], B = sm.b[k], A2 = sm.a[k2], B2 = sm.b[k2];
+      PairEval e, e2;
+      const bool ok = eval_pair(A.x, A.y, A.z, A.w, B.x, B.y, px, py, a.P, e);
+      const bool ok2 = two && eval_pair(A2.x, A2.y, A2.z, A2.w, B2.x, B2.y, px, py, a.P, e2);
+      if (ok) {
+        // 1 / (1 - sigma) with sigma <= alpha_max < 1: the fast reciprocal's
+        // relative error (~1 ulp) is far inside the gradient tolerance
+        const float inv_om = rcp_approx(__fsub_rn(1.f, e.sigma));
+        Tr = Tr * inv_om;
+        const float c = B.z;
+        const float dC_dsigma = fmaf(c, Tr, -S * inv_om);
+        S = fmaf(c * e.sigma, Tr, S);
+        const float gA = (e.aG > a.P.alpha_max) ? 0.f : g * dC_dsigma * e.G;
+        sm.ab[lane * AB_STRIDE + (k ^ lane)] = make_float2(gA, g * e.sigma * Tr);
+        used |= 1u << k;
+      }
+      if (ok2) {
+        const float inv_om = rcp_approx(__fsub_rn(1.f, e2.sigma));
+        Tr = Tr * inv_om;
+        const float c = B2.z;
+        const float dC_dsigma = fmaf(c, Tr, -S * inv_om);
+        S = fmaf(c * e2.sigma, Tr, S);
+        const float gA = (e2.aG > a.P.alpha_max) ? 0.f : g * dC_dsigma * e2.G;
+        sm.ab[lane * AB_STRIDE + (k2 ^ lane)] = make_float2(gA, g * e2.sigma * Tr);
+        used |= 1u << k2;
+      }
     }
     __syncwarp();
     uint32_t pm = transpose32(used);  // lane e: the pixels that added entry e
