@@ -222,7 +222,7 @@ __device__ __forceinline__ void fwd_tile(const RasterArgs &a, int64_t gt, float4
         const float4 A = s_a[k], B = s_b[k];
         PairEval e;
         if (!eval_pair(A.x, A.y, A.z, A.w, B.x, B.y, px, py, a.P, e)) continue;
-        const float Tn = __fmul_rn(Tr, __fsub_rn(1.f, e.sigma));
+        const float Tn = __fmaf_rn(-Tr, e.sigma, Tr);  // T (1 - sigma)
         if (Tn < a.P.t_min) {
           done = true;
           continue;
@@ -666,7 +666,7 @@ __device__ __forceinline__ void fwd_lane_item(const RasterArgs &a, int64_t gt, i
       const float4 A = sA[k], B = sB[k];
       PairEval e;
       if (!eval_pair(A.x, A.y, A.z, A.w, B.x, B.y, px, py, a.P, e)) continue;
-      const float Tn = __fmul_rn(Tr, __fsub_rn(1.f, e.sigma));
+      const float Tn = __fmaf_rn(-Tr, e.sigma, Tr);  // T (1 - sigma)
       if (Tn < a.P.t_min) {
         done = true;
         mine = 0;
