@@ -218,11 +218,13 @@ ddgs_status ensure_records(ddgs_workspace *ws, const ddgs::RenderShape &s) {
     ddgs_status st;
     if ((st = grow(ws->rec, ws->rec_cap, 2 * cap, sizeof(float4)))) return st;
     if ((st = grow(ws->rect, ws->rec_cap, cap, sizeof(uint4)))) return st;
+    ws->grad_zero = false;
     if ((st = grow(ws->grad2d, ws->rec_cap, 2 * cap, sizeof(float4)))) return st;
     ws->rec_cap = cap;
   }
   if (ws->rec2 && ws->pix_cap < ws->rec_cap) {  // per-pixel storage follows the records
     ddgs_status st;
+    ws->grad_zero = false;
     if ((st = grow(ws->rec2, ws->pix_cap, ws->rec_cap, sizeof(float4)))) return st;
     if ((st = grow(ws->grad_h, ws->pix_cap, ws->rec_cap, sizeof(float4)))) return st;
     ws->pix_cap = ws->rec_cap;
@@ -482,6 +484,7 @@ ddgs_status render_common(const ddgs_gaussians &g, const ddgs_views &v, const dd
   } else {
     if ((st = ensure_records(ws, s))) return st;
     if (g.per_pixel && !ws->rec2) {
+      ws->grad_zero = false;
       if ((st = grow(ws->rec2, ws->pix_cap, ws->rec_cap, sizeof(float4)))) return st;
       if ((st = grow(ws->grad_h, ws->pix_cap, ws->rec_cap, sizeof(float4)))) return st;
       ws->pix_cap = ws->rec_cap;
@@ -563,10 +566,15 @@ ddgs_status backward_common(const ddgs_gaussians &g, const ddgs_views &v, const 
   if (out->world_to_cam)
     CK(cudaMemsetAsync(out->world_to_cam, 0, (size_t)s.V * 12 * sizeof(float), s_));
   if (s.n_total == 0) return DDGS_OK;  // parameter gradients empty, pose/basis zero
-  // with no views the backward preprocess still writes the (zero) gradients
-  if (s.records > 0) CK(cudaMemsetAsync(ws->grad2d, 0, (size_t)s.records * 2 * sizeof(float4), s_));
-  if (s.records > 0 && g.per_pixel)
-    CK(cudaMemsetAsync(ws->grad_h, 0, (size_t)s.records * sizeof(float4), s_));
+  // The rasteriser accumulates 2D gradients into zeros, and the backward
+  // preprocess clears every record it consumes, so the buffers are cleared
+  // here only after an allocation or a failed call.
+  if (!ws->grad_zero) {
+    if (ws->rec_cap > 0) CK(cudaMemsetAsync(ws->grad2d, 0, (size_t)ws->rec_cap * 2 * sizeof(float4), s_));
+    if (ws->grad_h && ws->pix_cap > 0)
+      CK(cudaMemsetAsync(ws->grad_h, 0, (size_t)ws->pix_cap * sizeof(float4), s_));
+  }
+  ws->grad_zero = false;  // until both kernels are queued
   ddgs::RasterParams P{c->alpha_min, c->alpha_max, c->t_min, c->q_max};
   if (s.records > 0 && s.total_tiles > 0 && ws->pair_bound > 0) {
     ddgs::PixelRays pr;
@@ -578,6 +586,7 @@ ddgs_status backward_common(const ddgs_gaussians &g, const ddgs_views &v, const 
   }
   ddgs::launch_preprocess_bwd(g, v, *c, s, *ws, *out, s_);
   CK(cudaGetLastError());
+  ws->grad_zero = true;
   return DDGS_OK;
 }
 

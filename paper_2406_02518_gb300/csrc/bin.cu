@@ -587,6 +587,23 @@ __global__ void __launch_bounds__(NT, MINB) bin_sort_block_kernel(const uint64_t
   uint32_t *bc = &cnt[0][0];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const uint32_t n_items = *count;
+  // the next item's keys are copied to s_buf asynchronously while the
+  // current one is placed (once its keys have left s_buf)
+  auto prefetch = [&](uint32_t in) {
+    if (in >= n_items) return false;
+    const uint64_t it2 = items[in];
+    const uint2 r2 = ranges[it2 >> 24];
+    const uint32_t c2 = (uint32_t)(it2 & 0xffffffu);
+    const uint32_t b2 = r2.x + c2 * (uint32_t)CAP;
+    const int m2 = (int)min((uint32_t)CAP, (r2.y - r2.x) - c2 * (uint32_t)CAP);
+    for (int j = tid; j < m2; j += NT) {
+      const unsigned sa = (unsigned)__cvta_generic_to_shared(s_buf + j);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(keys + b2 + j) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    return true;
+  };
+  bool have = false;
   for (uint32_t i = blockIdx.x; i < n_items; i += gridDim.x) {
     const uint64_t item = items[i];
     const uint2 r = ranges[item >> 24];
@@ -596,13 +613,23 @@ __global__ void __launch_bounds__(NT, MINB) bin_sort_block_kernel(const uint64_t
     const int m = (int)min((uint32_t)CAP, n_all - chunk * (uint32_t)CAP);
     uint64_t *cur = s_buf, *oth = s_buf + CAP;
     uint32_t dmin = ~0u, dmax = 0u, lmin = ~0u, lmax = 0u;
+    if (have) {
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      __syncthreads();
+    }
     for (int j = tid; j < m; j += NT) {
-      const uint64_t k = keys[base + j];
-      cur[j] = k;
+      uint64_t k;
+      if (have) {
+        k = cur[j];
+      } else {
+        k = keys[base + j];
+        cur[j] = k;
+      }
       const uint32_t d = (uint32_t)(k >> 32), l = (uint32_t)k;
       dmin = min(dmin, d); dmax = max(dmax, d);
       lmin = min(lmin, l); lmax = max(lmax, l);
     }
+    have = false;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       dmin = min(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
@@ -683,6 +710,7 @@ __global__ void __launch_bounds__(NT, MINB) bin_sort_block_kernel(const uint64_t
           }
         }
         __syncthreads();
+        have = prefetch(i + gridDim.x);  // s_buf (cur) is free from here
         // every entry's place: its bucket's start plus the number of smaller
         // keys in its bucket (keys are unique), written straight to the output
         const bool whole = n_all <= (uint32_t)CAP;
@@ -723,6 +751,7 @@ __global__ void __launch_bounds__(NT, MINB) bin_sort_block_kernel(const uint64_t
       for (int j = tid; j < m; j += NT) keys[base + j] = cur[j];
     }
     __syncthreads();
+    have = prefetch(i + gridDim.x);
   }
 }
 

@@ -256,6 +256,8 @@ struct ddgs_workspace {
   uint32_t *tiles_touched = nullptr;
   float4 *grad2d = nullptr;      // [records][2]: (u, v, ca, cb), (cc, alpha, colour, 0);
                                  // with per-pixel directions the colour slot holds dL/dz
+  bool grad_zero = false;        // grad2d (and grad_h) hold zeros over their whole capacity:
+                                 // the backward preprocess clears what it consumed
   // per-pixel directions only (allocated by the first such render)
   float4 *rec2 = nullptr;        // (a, h_0, h_1, h_2): colour logit z = a + Y(ray) . h
   float4 *grad_h = nullptr;      // (dL/dh_0, dL/dh_1, dL/dh_2, 0)

@@ -560,8 +560,8 @@ struct PreBwdArgs {
   RenderShape s;
   int K, L;
   int entangled, per_pixel;
-  const float4 *grad2d;
-  const float4 *grad_h;  // per_pixel: dL/dh summed over pixels
+  float4 *grad2d;        // consumed records are cleared (left all-zero for the next backward)
+  float4 *grad_h;        // per_pixel: dL/dh summed over pixels (cleared the same way)
   ddgs_grads out;
   int want_param, want_basis, want_pose;
 };
@@ -717,6 +717,12 @@ __global__ void __launch_bounds__(PRE_THREADS, GEN ? 2 : 3) preprocess_bwd_kerne
       if (live) {
         any = (g0.x != 0.f) | (g0.y != 0.f) | (g0.z != 0.f) | (g0.w != 0.f) | (g1.x != 0.f) |
               (g1.y != 0.f) | (g1.z != 0.f) | (gh.x != 0.f) | (gh.y != 0.f) | (gh.z != 0.f);
+        if (any) {  // leave the record zero for the next backward
+          const int64_t rec = vc.rec_off + br.l;
+          a.grad2d[2 * rec] = make_float4(0.f, 0.f, 0.f, 0.f);
+          a.grad2d[2 * rec + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (with_h) a.grad_h[rec] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         ViewProj p;
         if (any) view_proj_grad(mu, gg.S, vc, a.dilation, p);
         if (any) {

@@ -560,3 +560,29 @@ def test_banded_views(shape, ws):
     _run(scene, views, st, ws)
     compare_binning(_bins(ws, scene, views, st), oracle.bin32(scene, views, st))
     _sampled_check(scene, views, st, ws, [0], 1024, 31, grads=("means", "opacity_logits", "pose"))
+
+
+def test_backward_leaves_its_accumulators_clear(ws):
+    """The backward preprocess clears every 2D-gradient record it consumes, so
+    a second backward of the same render (and one after a render of another
+    layout) gives the same gradients as the first."""
+    scene, views, st = CASES["ragged_100x75_2views"]()
+    cloud, gv, cfg, img, tf, nl = _run(scene, views, st, ws)
+    w = torch.as_tensor(np.random.default_rng(17).uniform(-1, 1, img.shape), dtype=torch.float32,
+                        device="cuda")
+    g1 = {k: v.clone() for k, v in B.render_backward(cloud, gv, cfg, ws, w, tf, nl).items()}
+    g2 = B.render_backward(cloud, gv, cfg, ws, w, tf, nl)
+    torch.cuda.synchronize()
+    # equal up to the order of the float atomics (a record added twice would
+    # be off by its whole value)
+    ref = {k: v.cpu().numpy() for k, v in g1.items()}
+    compare_grads({k: v.cpu().numpy() for k, v in g2.items()}, ref, list(g1), tol=1e-5,
+                  zero_ok=list(g1))
+    other, oviews, ost = CASES["tile8"]()
+    c2, gv2, cfg2, img2, tf2, nl2 = _run(other, oviews, ost, ws)
+    B.render_backward(c2, gv2, cfg2, ws, torch.ones_like(img2), tf2, nl2)
+    cloud, gv, cfg, img, tf, nl = _run(scene, views, st, ws)
+    g3 = B.render_backward(cloud, gv, cfg, ws, w, tf, nl)
+    torch.cuda.synchronize()
+    compare_grads({k: v.cpu().numpy() for k, v in g3.items()}, ref, list(g1), tol=1e-5,
+                  zero_ok=list(g1))
