@@ -117,10 +117,10 @@ class Clocks:
 # shape and workload match; otherwise traffic is null.
 TRAFFIC = {
     "raster_bwd": {
-        "sources_sha256": {"raster.cu": "1f2c44896748d5dda5a10598448f083c6bbfc41f56104bf084018ab108622894",
-                           "ddgs_internal.cuh": "fa72ca1a83418c995fe5d9ca47a902b9883fb2bb5b99268157df8a084bb8fb8d"},
+        "sources_sha256": {"raster.cu": "6186f174c8b0f7d3bf9e7c8c0059fa2c466ceaf6f42048a15582dd368016045e",
+                           "ddgs_internal.cuh": "00bb7b2c0b28ca453ddc2474eacb92ba5983593b3fe2d70197c3ab661219fb85"},
         "tile": 8, "batch_depth": 32, "views": 64, "gaussians": 500_000,
-        "bytes_per_launch": 2440.0e6 + 577.2e6,
+        "bytes_per_launch": 2185.7e6 + 571.4e6,
         "how": "one-pass ncu launch list (dram__bytes_read.sum + dram__bytes_write.sum) of the "
                "64-pose registration step",
     },
