@@ -531,7 +531,8 @@ ddgs_status render_common(const ddgs_gaussians &g, const ddgs_views &v, const dd
     CK(cudaGetLastError());
     ddgs::launch_tile_order(s, *ws, s_);
     CK(cudaGetLastError());
-    ddgs::RasterParams P{c->alpha_min, c->alpha_max, c->t_min, c->q_max};
+    ddgs::RasterParams P{c->alpha_min, c->alpha_max, c->t_min, c->q_max,
+                          c->q_max * ddgs::CONIC_SCALE};
     ddgs::PixelRays pr;
     pr.world_to_cam = v.world_to_cam;
     pr.detector = v.detector;
@@ -575,7 +576,8 @@ ddgs_status backward_common(const ddgs_gaussians &g, const ddgs_views &v, const 
       CK(cudaMemsetAsync(ws->grad_h, 0, (size_t)ws->pix_cap * sizeof(float4), s_));
   }
   ws->grad_zero = false;  // until both kernels are queued
-  ddgs::RasterParams P{c->alpha_min, c->alpha_max, c->t_min, c->q_max};
+  ddgs::RasterParams P{c->alpha_min, c->alpha_max, c->t_min, c->q_max,
+                          c->q_max * ddgs::CONIC_SCALE};
   if (s.records > 0 && s.total_tiles > 0 && ws->pair_bound > 0) {
     ddgs::PixelRays pr;
     pr.world_to_cam = v.world_to_cam;

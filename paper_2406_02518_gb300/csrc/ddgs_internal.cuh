@@ -76,10 +76,17 @@ struct BinLists {
   uint32_t *count;               // device [LIST_CLASSES]
 };
 
-// Parameters shared by the rasterisers.
+// Parameters shared by the rasterisers. q_lim = CONIC_SCALE q_max: the q cutoff
+// in the units of the records' scaled conic (see eval_pair).
 struct RasterParams {
-  float alpha_min, alpha_max, t_min, q_max;
+  float alpha_min, alpha_max, t_min, q_max, q_lim;
 };
+
+// The records hold the conic multiplied by -log2(e) / 2, so that the
+// rasterisers' q' = CONIC_SCALE q is already the exponent of
+// G = exp(-q / 2) = 2^q'. INV_CONIC_SCALE = 1 / CONIC_SCALE = -2 ln 2.
+constexpr float CONIC_SCALE = -0.72134752044448170368f;
+constexpr float INV_CONIC_SCALE = -1.38629436111989061883f;
 
 // Everything the kernels need about one render (passed by value).
 struct RenderShape {
@@ -226,8 +233,10 @@ __device__ __forceinline__ float2 unpack_halfwidths(float w) {
                      __half2float(__ushort_as_half((unsigned short)(b >> 16))));
 }
 
-// q = d^T K d for the conic K = [[a, b], [b, c]], evaluated as
-// dx (a dx + 2b dy) + c dy^2 from the record's (a, 2b, c).
+// q = d^T K d for the conic K = [[a, b], [b, c]], evaluated in the records'
+// scaled units as q' = dx (a' dx + 2b' dy) + c' dy^2 from the record's
+// (a', 2b', c') = CONIC_SCALE (a, 2b, c); q <= q_max is q' >= q_lim (both
+// sides negative), and G = exp(-q / 2) = 2^q'.
 __device__ __forceinline__ bool eval_pair(float u, float v, float ca, float cb2, float cc,
                                           float alpha, float px, float py,
                                           const RasterParams &P, PairEval &e) {
@@ -235,8 +244,8 @@ __device__ __forceinline__ bool eval_pair(float u, float v, float ca, float cb2,
   e.dy = __fsub_rn(v, py);
   const float t = __fmaf_rn(cb2, e.dy, __fmul_rn(ca, e.dx));
   const float q = __fmaf_rn(__fmul_rn(cc, e.dy), e.dy, __fmul_rn(e.dx, t));
-  if (q > P.q_max || q < 0.f) return false;
-  e.G = exp2_approx(__fmul_rn(q, -0.72134752044448170368f));  // exp(-q / 2) = 2^(-q log2(e) / 2)
+  if (q < P.q_lim || q > 0.f) return false;
+  e.G = exp2_approx(q);
   e.aG = __fmul_rn(alpha, e.G);
   e.sigma = fminf(P.alpha_max, e.aG);
   return e.sigma >= P.alpha_min;
@@ -249,9 +258,9 @@ struct ddgs_workspace {
   int device = -1;
   int64_t rec_cap = 0, pair_cap = 0, tile_cap = 0, blk_cap = 0, hist_cap = 0, list_cap = 0;
   // per (view, Gaussian) records
-  float4 *rec = nullptr;         // [records][2]: (u, v, conic a, 2 x conic b), (conic c,
-                                 // alpha, colour, packed box half-extents): one 32-byte
-                                 // sector per gather
+  float4 *rec = nullptr;         // [records][2]: (u, v, a', 2b'), (c', alpha, colour, packed
+                                 // box half-extents), (a', b', c') = CONIC_SCALE x conic:
+                                 // one 32-byte sector per gather
   uint2 *rect = nullptr;         // (tx0 | ty0 << 16, tx1 | ty1 << 16)
   uint32_t *tiles_touched = nullptr;
   float4 *grad2d = nullptr;      // [records][2]: (u, v, ca, cb), (cc, alpha, colour, 0);

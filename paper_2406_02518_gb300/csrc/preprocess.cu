@@ -526,8 +526,9 @@ __global__ void __launch_bounds__(PRE_THREADS) preprocess_fwd_kernel(PreArgs a) 
         }
         colour = sigmoidf_(zl);
       }
-      a.rec[2 * rec] = make_float4(p.u, p.v, ca, 2.f * cb);  // 2b: see eval_pair
-      a.rec[2 * rec + 1] = make_float4(cc, alpha, colour, box_halfwidths(p.cov, a.q_max));
+      // the conic in the rasterisers' units, (a', 2b', c') (see eval_pair)
+      a.rec[2 * rec] = make_float4(p.u, p.v, ca * CONIC_SCALE, (2.f * CONIC_SCALE) * cb);
+      a.rec[2 * rec + 1] = make_float4(cc * CONIC_SCALE, alpha, colour, box_halfwidths(p.cov, a.q_max));
     }
   }
   flag_nonfinite(bad, a.status);

@@ -477,7 +477,9 @@ __device__ __forceinline__ void bwd_tile(const RasterArgs &a, int64_t gt, BwdSme
       if (nz) {
         float4 *dst = a.grad2d + 2 * (rec_base + s_id[e]);
         // dq/du = 2 (a dx + b dy), dq/dv = 2 (b dx + c dy), dq/db = 2 dx dy
-        const float ca = s_a[e].z, cb = 0.5f * s_a[e].w, cc = s_b[e].x;  // the record holds 2b
+        // the record holds CONIC_SCALE (a, 2b, c)
+        const float ca = s_a[e].z * INV_CONIC_SCALE, cb = (0.5f * INV_CONIC_SCALE) * s_a[e].w,
+                    cc = s_b[e].x * INV_CONIC_SCALE;
         const float du = 2.f * fmaf(ca, acc[0], cb * acc[1]);
         const float dv = 2.f * fmaf(cb, acc[0], cc * acc[1]);
         atomicAdd(dst, make_float4(du, dv, acc[2], 2.f * acc[3]));
@@ -838,7 +840,9 @@ __device__ __forceinline__ void bwd_warp_item(const RasterArgs &a, int64_t gt, i
         const int64_t r = tg.rec_base + sId[lane];
         float4 *dst = a.grad2d + 2 * r;
         // dq/du = 2 (a dx + b dy), dq/dv = 2 (b dx + c dy), dq/db = 2 dx dy
-        const float ca = sA[lane].z, cb = 0.5f * sA[lane].w, cc = sB[lane].x;  // the record holds 2b
+        // the record holds CONIC_SCALE (a, 2b, c)
+        const float ca = sA[lane].z * INV_CONIC_SCALE, cb = (0.5f * INV_CONIC_SCALE) * sA[lane].w,
+                    cc = sB[lane].x * INV_CONIC_SCALE;
         const float du = 2.f * fmaf(ca, acc[0], cb * acc[1]);
         const float dv = 2.f * fmaf(cb, acc[0], cc * acc[1]);
         atomicAdd(dst, make_float4(du, dv, acc[2], 2.f * acc[3]));
@@ -1036,9 +1040,10 @@ __device__ __forceinline__ void bwd_lane_item(const RasterArgs &a, int64_t gt, i
       const float sxy = fmaf(u, fmaf(v, s0, -s2), fmaf(-v, s1, s4));
       const float syy = fmaf(v, fmaf(v, s0, -2.f * s2), s5);
       const float hq = -0.5f * B.y;  // dL/dq = -alpha A / 2
-      const float gx = hq * sdx, gy = hq * sdy;
-      // dq/du = 2 (a dx + b dy), dq/dv = 2 (b dx + c dy), dq/db = 2 dx dy
-      // (the record holds a in A.z, 2b in A.w, c in B.x)
+      // dq/du = 2 (a dx + b dy), dq/dv = 2 (b dx + c dy), dq/db = 2 dx dy;
+      // the record holds (a', 2b', c') = CONIC_SCALE (a, 2b, c) in A.z, A.w, B.x
+      const float hk = hq * INV_CONIC_SCALE;
+      const float gx = hk * sdx, gy = hk * sdy;
       const float du = fmaf(2.f * A.z, gx, A.w * gy);
       const float dv = fmaf(A.w, gx, 2.f * B.x * gy);
       float4 *dst = a.grad2d + 2 * (rg.rec_base + sm.id[lane]);

@@ -208,7 +208,8 @@ extern "C" ddgs_status ddgs_render_static(const ddgs_gaussians *g, const ddgs_vi
   if (s.total_tiles > 0) {
     ddgs::launch_binning(s, pairs, ws, cs);
     ddgs::launch_tile_order(s, ws, cs);
-    ddgs::RasterParams P{c->alpha_min, c->alpha_max, c->t_min, c->q_max};
+    ddgs::RasterParams P{c->alpha_min, c->alpha_max, c->t_min, c->q_max,
+                          c->q_max * ddgs::CONIC_SCALE};
     ddgs::launch_raster_fwd(s, P, ws, image, t_final, n_last, nullptr, cs);
   }
   CK_STATIC(cudaGetLastError());
