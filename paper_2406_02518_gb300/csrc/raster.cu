@@ -915,6 +915,7 @@ constexpr int AB_STRIDE = 32;  // float2 per pixel row of the (pixel, entry) tab
 constexpr int LANE_WARPS = 8;  // warps per block of the per-lane backward (3 blocks per SM)
 
 struct LaneBwdSmem {
+  float2 xy[32];  // (x, y) of pixel l of the region
   float4 a[32], b[32];
   uint32_t id[32];
   float2 ab[32 * AB_STRIDE];  // [pixel][entry ^ pixel]: (A, Bc)
@@ -930,6 +931,7 @@ __device__ __forceinline__ void bwd_lane_item(const RasterArgs &a, int64_t gt, i
   const float cx = rg.wx0 + 0.5f, cy = rg.wy0 + 0.5f;
   float Tr = 1.f, g = 0.f;
   uint32_t last = 0;
+  sm.xy[lane] = make_float2((float)(lane & 7), (float)(lane >> 3));  // pixel coordinates
   if (rg.inside) {
     const int64_t pix = rg.pixel();
     Tr = a.t_final_in[pix];
@@ -938,6 +940,9 @@ __device__ __forceinline__ void bwd_lane_item(const RasterArgs &a, int64_t gt, i
   }
   if (g == 0.f) last = 0;  // nothing to propagate from this pixel
   if (last > range.y - range.x) last = range.y - range.x;  // never read past the list
+  // the walk carries g T and g S (Tr, S), so that g drops out of the per-pair
+  // products: g dC/dsigma = c gT - gS / (1 - sigma), g dC/dc = sigma gT
+  Tr *= g;
   uint32_t max_last = last;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) max_last = max(max_last, __shfl_xor_sync(0xffffffffu, max_last, o));
@@ -974,38 +979,56 @@ __device__ __forceinline__ void bwd_lane_item(const RasterArgs &a, int64_t gt, i
     mine &= skip <= 0 ? 0xffffffffu : (skip >= 32 ? 0u : (0xffffffffu << skip));
     uint32_t used = 0;
     const int trips = (int)__reduce_max_sync(0xffffffffu, (uint32_t)(__popc(mine) + 1) >> 1);
-    for (int t = 0; t < trips; ++t) {  // two entries per trip: their evaluations overlap
-      if (mine == 0) continue;
-      const int k = __ffs(mine) - 1;
+    // two entries per trip, their evaluations overlapping; written without
+    // branches (a lane past its last entry evaluates entry 31 and discards
+    // it): eval_pair's decisions, in the same arithmetic
+    for (int t = 0; t < trips; ++t) {
+      const bool l1 = mine != 0;
+      const int k = (__ffs(mine) - 1) & 31;
       mine &= mine - 1;
-      const bool two = mine != 0;
-      const int k2 = two ? __ffs(mine) - 1 : k;
+      const bool l2 = mine != 0;
+      const int k2 = (__ffs(mine) - 1) & 31;
       mine &= mine - 1;
       const float4 A = sm.a[k], B = sm.b[k], A2 = sm.a[k2], B2 = sm.b[k2];
-      PairEval e, e2;
-      const bool ok = eval_pair(A.x, A.y, A.z, A.w, B.x, B.y, px, py, a.P, e);
-      const bool ok2 = two && eval_pair(A2.x, A2.y, A2.z, A2.w, B2.x, B2.y, px, py, a.P, e2);
-      if (ok) {
+      float G1, aG1, s1, G2, aG2, s2;
+      bool ok, ok2;
+      {
+        const float dx = __fsub_rn(A.x, px), dy = __fsub_rn(A.y, py);
+        const float tq = __fmaf_rn(A.w, dy, __fmul_rn(A.z, dx));
+        const float q = __fmaf_rn(__fmul_rn(B.x, dy), dy, __fmul_rn(dx, tq));
+        G1 = exp2_approx(q); aG1 = __fmul_rn(B.y, G1); s1 = fminf(a.P.alpha_max, aG1);
+        ok = l1 && !(q < a.P.q_lim || q > 0.f) && s1 >= a.P.alpha_min;
+      }
+      {
+        const float dx = __fsub_rn(A2.x, px), dy = __fsub_rn(A2.y, py);
+        const float tq = __fmaf_rn(A2.w, dy, __fmul_rn(A2.z, dx));
+        const float q = __fmaf_rn(__fmul_rn(B2.x, dy), dy, __fmul_rn(dx, tq));
+        G2 = exp2_approx(q); aG2 = __fmul_rn(B2.y, G2); s2 = fminf(a.P.alpha_max, aG2);
+        ok2 = l2 && !(q < a.P.q_lim || q > 0.f) && s2 >= a.P.alpha_min;
+      }
+      {
         // 1 / (1 - sigma) with sigma <= alpha_max < 1: the fast reciprocal's
         // relative error (~1 ulp) is far inside the gradient tolerance
-        const float inv_om = rcp_approx(__fsub_rn(1.f, e.sigma));
-        Tr = Tr * inv_om;
-        const float c = B.z;
-        const float dC_dsigma = fmaf(c, Tr, -S * inv_om);
-        S = fmaf(c * e.sigma, Tr, S);
-        const float gA = (e.aG > a.P.alpha_max) ? 0.f : g * dC_dsigma * e.G;
-        sm.ab[lane * AB_STRIDE + (k ^ lane)] = make_float2(gA, g * e.sigma * Tr);
-        used |= 1u << k;
+        const float inv_om = rcp_approx(__fsub_rn(1.f, s1));
+        const float Tn = Tr * inv_om;
+        const float g_dC = fmaf(B.z, Tn, -S * inv_om);  // g dC/dsigma
+        const float Sn = fmaf(B.z * s1, Tn, S);
+        const float gA = (aG1 > a.P.alpha_max) ? 0.f : g_dC * G1;
+        if (ok) sm.ab[lane * AB_STRIDE + (k ^ lane)] = make_float2(gA, s1 * Tn);
+        Tr = ok ? Tn : Tr;
+        S = ok ? Sn : S;
+        used |= ok ? 1u << k : 0u;
       }
-      if (ok2) {
-        const float inv_om = rcp_approx(__fsub_rn(1.f, e2.sigma));
-        Tr = Tr * inv_om;
-        const float c = B2.z;
-        const float dC_dsigma = fmaf(c, Tr, -S * inv_om);
-        S = fmaf(c * e2.sigma, Tr, S);
-        const float gA = (e2.aG > a.P.alpha_max) ? 0.f : g * dC_dsigma * e2.G;
-        sm.ab[lane * AB_STRIDE + (k2 ^ lane)] = make_float2(gA, g * e2.sigma * Tr);
-        used |= 1u << k2;
+      {
+        const float inv_om = rcp_approx(__fsub_rn(1.f, s2));
+        const float Tn = Tr * inv_om;
+        const float g_dC = fmaf(B2.z, Tn, -S * inv_om);  // g dC/dsigma
+        const float Sn = fmaf(B2.z * s2, Tn, S);
+        const float gA = (aG2 > a.P.alpha_max) ? 0.f : g_dC * G2;
+        if (ok2) sm.ab[lane * AB_STRIDE + (k2 ^ lane)] = make_float2(gA, s2 * Tn);
+        Tr = ok2 ? Tn : Tr;
+        S = ok2 ? Sn : S;
+        used |= ok2 ? 1u << k2 : 0u;
       }
     }
     __syncwarp();
@@ -1021,8 +1044,9 @@ __device__ __forceinline__ void bwd_lane_item(const RasterArgs &a, int64_t gt, i
         const float2 ab = sm.ab[p * AB_STRIDE + (lane ^ p)];
         float2 cd = sm.ab[q * AB_STRIDE + (lane ^ q)];
         if (!two) cd = make_float2(0.f, 0.f);
-        const float x = (float)(p & 7), y = (float)(p >> 3);
-        const float x2 = (float)(q & 7), y2 = (float)(q >> 3);
+        const float2 pxy = sm.xy[p], qxy = sm.xy[q];
+        const float x = pxy.x, y = pxy.y;
+        const float x2 = qxy.x, y2 = qxy.y;
         const float ax = ab.x * x, ay = ab.x * y, cx2 = cd.x * x2, cy2 = cd.x * y2;
         s0 += ab.x + cd.x;
         s1 += ax + cx2;
