@@ -299,7 +299,10 @@ __device__ __forceinline__ uint4 ld_hint(const uint4 *a, uint64_t pol) {
 // BIN_MAX_PAIRS < 2^31). Pairs of lists left empty by a capacity overflow are
 // dropped.
 constexpr uint32_t CUR_ONE = 0x80000000u, CUR_DROP = 0xffffffffu;
-constexpr int SCAT_STAGE = 6144;  // pairs staged per window (12 bytes each)
+// pairs staged per window (12 bytes each): with a band of 1,024 tiles a block
+// then takes 74 KB and three fit an SM (0.59 -> 0.58 ms at 64 poses; 4,096
+// makes more chunks need a second window, 0.76 ms)
+constexpr int SCAT_STAGE = 5120;
 
 __host__ __device__ constexpr size_t scatter_smem(int area) {
   return (size_t)SCAT_STAGE * (sizeof(uint64_t) + sizeof(uint32_t)) + (size_t)area * 3 * sizeof(uint32_t);

@@ -384,8 +384,11 @@ struct BlockReq {
 // the isotropic term (every one of the isotropic range; all when entangled),
 // h = B_dir f for one with the directional term. With per-pixel directions
 // the record carries (a, h) and the rasteriser evaluates Y per pixel.
+// Four resident blocks per SM for the k = 8, L = 1 instance (64 registers, a
+// few bytes spilled: 0.38 -> 0.37 ms at 64 poses); the generic one keeps its
+// registers.
 template <bool GEN>
-__global__ void __launch_bounds__(PRE_THREADS) preprocess_fwd_kernel(PreArgs a) {
+__global__ void __launch_bounds__(PRE_THREADS, GEN ? 1 : 4) preprocess_fwd_kernel(PreArgs a) {
   constexpr int KS = GEN ? KG : K, KLS = GEN ? KLG : 3;
   const int Kr = GEN ? a.K : K, kL = GEN ? a.L * (a.L + 2) : 3;
   __shared__ ViewConst sv[VIEW_CHUNK];
