@@ -756,11 +756,44 @@ def run_plain_forward(args):
     B.load()
     dev = torch.device("cuda", local)
     scene, views, st = syn.plain_forward_workload()
-    if args.tile:
-        st = dataclasses.replace(st, tile=args.tile)
-    depth = args.depth or 256
     V, H, W = views.n_views, views.height, views.width
     cloud, gv = B.cloud_from_arrays(scene), B.views_from_arrays(views)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # 512 MB > L2
+
+    # the launch shape (tile edge, staging depth): pinned, autotuned on this
+    # render (each candidate timed alone after an L2 flush), or the defaults
+    def tune_step(tile, depth):
+        c = B.config_from_settings(dataclasses.replace(st, tile=tile), batch_depth=depth)
+        w = B.Workspace()
+        try:
+            for _ in range(3):
+                B.render(cloud, gv, c, w)
+            ts = []
+            for _ in range(9):
+                flush.fill_(1)
+                a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a0.record()
+                B.render(cloud, gv, c, w)
+                a1.record()
+                torch.cuda.synchronize()
+                ts.append(a0.elapsed_time(a1))
+            return sorted(ts)[len(ts) // 2]
+        finally:
+            w.close()
+
+    tuned = None
+    if args.tile and args.depth:
+        tuned = {"tile": args.tile, "batch_depth": args.depth, "pinned": True}
+    elif args.autotune:
+        from paper_2406_02518_gb300 import autotune as at
+        props = torch.cuda.get_device_properties(dev)
+        key = at.workload_key(props.name, props.multi_processor_count, H * W, scene.n, V) + "|plain-forward"
+        tuned = at.tune(tune_step, key, force=args.autotune == "force")
+    if tuned:
+        st = dataclasses.replace(st, tile=tuned["tile"])
+    elif args.tile:
+        st = dataclasses.replace(st, tile=args.tile)
+    depth = tuned["batch_depth"] if tuned else (args.depth or 256)
     cfg = B.config_from_settings(st, batch_depth=depth)
     ws = B.Workspace()
     img, tf, nl = B.render(cloud, gv, cfg, ws)
@@ -768,7 +801,6 @@ def run_plain_forward(args):
     pairs = ws.pairs()
     ws.reserve(V * scene.n, int(pairs * 1.10) + 4096, V * (-(-W // st.tile)) * (-(-H // st.tile)))
     cfg_ns = B.config_from_settings(st, no_sync=True, batch_depth=depth)
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # 512 MB > L2
 
     def sync_call():
         B.render(cloud, gv, cfg, ws, out=(img, tf, nl))
@@ -863,6 +895,7 @@ def run_plain_forward(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "plain forward: 4,096 Gaussians (means U[-1,1]^3), one 128x128 view, "
                                    "SID 2, SDD 4", "tile": st.tile, "batch_depth": depth,
+                       "autotune": tuned,
                        "pairs": pairs, "l2": "512 MB written between timed renders (L2 flush)",
                        "graph": "value: the render replayed from a CUDA graph"},
             "sync_call": {"ms_per_render": ms_sync,

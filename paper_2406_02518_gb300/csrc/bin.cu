@@ -888,28 +888,32 @@ void launch_binning(const RenderShape &s, uint64_t pair_bound, ddgs_workspace &w
     bin_scatter_kernel<<<(unsigned)s.n_items, SCAT_THREADS, scatter_smem(s.hist_area), st>>>(
         s, reinterpret_cast<const uint4 *>(ws.rect), ws.hist, ws.ranges, ws.keys[0], ws.vals, cap);
   }
-  {
+  // A list holds at most one entry per Gaussian of its request, so a render of
+  // n_total Gaussians in all cannot fill the classes of longer lists: those
+  // sorts (and the merge) are not launched.
+  const int64_t nmax = s.n_total;
+  if (nmax >= 2) {
     LaunchScope ls(KID_BIN_SORT, st);
     bin_sort_warp_kernel<<<sms * 4, 256, 0, st>>>(L.item[LIST_WARP], L.count + LIST_WARP,
                                                    ws.ranges, ws.keys[0], ws.vals);
   }
-  {
+  if (nmax > 32) {
     LaunchScope ls(KID_BIN_SORT, st);
     bin_sort_block_kernel<128, SORT_SHORT / 128, 8><<<sms * 8, 128, SHORT_SMEM, st>>>(
         L.item[LIST_SHORT], L.count + LIST_SHORT, ws.ranges, ws.keys[0], ws.vals);
   }
-  {
+  if (nmax > SORT_SHORT) {
     LaunchScope ls(KID_BIN_SORT, st);
     bin_sort_block_kernel<128, SORT_MID / 128, 6><<<sms * 6, 128, MID_SMEM, st>>>(
         L.item[LIST_MID], L.count + LIST_MID, ws.ranges, ws.keys[0], ws.vals);
   }
-  {
+  if (nmax > SORT_MID) {
     LaunchScope ls(KID_BIN_SORT, st);
     bin_sort_block_kernel<SORT_LONG_THREADS, SORT_LONG_ITEMS, 1>
         <<<sms, SORT_LONG_THREADS, LONG_SMEM, st>>>(L.item[LIST_BLOCK], L.count + LIST_BLOCK,
                                                    ws.ranges, ws.keys[0], ws.vals);
   }
-  {
+  if (nmax > BIN_LIST_LONG) {
     LaunchScope ls(KID_BIN_MERGE, st);
     bin_merge_kernel<<<sms * 2, 256, 0, st>>>(L.item[LIST_LONG], L.count + LIST_LONG, ws.ranges,
                                               ws.keys[0], ws.keys[1], ws.vals);
