@@ -583,12 +583,23 @@ def run_ours(args):
             dist.destroy_process_group()
         return 0
     cpu = None
+    pair_counts = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(scene, views, st, target.cpu().numpy())
-        cpu.pop("contrib_per_pixel")
+        contrib = cpu.pop("contrib_per_pixel")
         inside = cpu.pop("inside_per_pixel")
         # ALU roofline of the rasterisers: pairs inside the q <= q_max ellipse
         blended = inside * H * W * V
+        # (pixel, Gaussian) pairs a tile list puts in front of the rasterisers,
+        # against those inside the ellipse and those Eq. 1 adds before the
+        # walk stops (oracle counts on the sampled pixels, scaled)
+        visited = pairs * st.tile * st.tile
+        pair_counts = {"tile_pairs": int(pairs), "visited_pixel_pairs": int(visited),
+                       "in_ellipse_pixel_pairs": int(round(blended)),
+                       "added_pixel_pairs": int(round(contrib * H * W * V)),
+                       "in_ellipse_over_visited": round(blended / max(visited, 1), 4),
+                       "how": "visited = tile pairs x tile^2 pixels; the other two from the oracle's "
+                              "per-pixel counts on the CPU baseline's sampled pixels"}
         sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1447.0)
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
         fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -623,6 +634,7 @@ def run_ours(args):
             "batched_over_plain": value / plain_value,
             "batched_over_plain_graph": value / plain_graph_value,
             "pairs_per_step": pairs,
+            "pair_counts": pair_counts,
             "e2e": {"value": renders_step / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": kernels_per_step * args.steps,
