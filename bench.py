@@ -666,23 +666,58 @@ def run_fit(args, large):
     t0 = time.time()
     scene, views, st = syn.large_fit_workload() if large else syn.fit_workload()
     gen_s = time.time() - t0
-    if args.tile:
-        st = dataclasses.replace(st, tile=args.tile)
     V, H, W = views.n_views, views.height, views.width
     bf16 = bool(getattr(scene, "bf16_dir", False))
     cloud = B.cloud_from_arrays(scene, feat_dir_bf16=bf16)
     gv = B.views_from_arrays(views)
-    cfg = B.config_from_settings(st, batch_depth=args.depth or 256)
     ws = B.Workspace()
     target, _, _ = B.render(B.cloud_from_arrays(syn.perturb_scene(scene, seed=1), feat_dir_bf16=bf16),
-                            gv, cfg, ws)
+                            gv, B.config_from_settings(st), ws)
     target = target.clone()
+
+    # the launch shape (tile edge, staging depth): pinned, autotuned on this
+    # step, or the defaults
+    def tune_step(tile, depth):
+        c = B.config_from_settings(dataclasses.replace(st, tile=tile), batch_depth=depth)
+        w = B.Workspace()
+        try:
+            def one():
+                im, t_, n_ = B.render(cloud, gv, c, w)
+                _, d_ = B.l1_loss(im, target)
+                B.render_backward(cloud, gv, c, w, d_, t_, n_)
+            for _ in range(2):
+                one()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record()
+            for _ in range(3):
+                one()
+            a1.record()
+            torch.cuda.synchronize()
+            return a0.elapsed_time(a1) / 3
+        finally:
+            w.close()
+
+    tuned = None
+    if args.tile and args.depth:
+        tuned = {"tile": args.tile, "batch_depth": args.depth, "pinned": True}
+    elif args.autotune:
+        from paper_2406_02518_gb300 import autotune as at
+        props = torch.cuda.get_device_properties(dev)
+        key = at.workload_key(props.name, props.multi_processor_count, H * W, scene.n, V) + \
+            ("|large-fit" if large else "|fit")
+        tuned = at.tune(tune_step, key, force=args.autotune == "force")
+    if tuned:
+        st = dataclasses.replace(st, tile=tuned["tile"])
+    elif args.tile:
+        st = dataclasses.replace(st, tile=args.tile)
+    depth = tuned["batch_depth"] if tuned else (args.depth or 256)
+    cfg = B.config_from_settings(st, batch_depth=depth)
     img, tf, nl = B.render(cloud, gv, cfg, ws)
     torch.cuda.synchronize()
     pairs = ws.pairs()
     tiles = V * (-(-H // st.tile)) * (-(-W // st.tile))
     ws.reserve(V * scene.n, int(pairs * 1.10) + 4096, tiles)
-    cfg = B.config_from_settings(st, no_sync=True, batch_depth=args.depth or 256)
+    cfg = B.config_from_settings(st, no_sync=True, batch_depth=depth)
     loss = torch.empty(V, dtype=torch.float32, device=dev)
     dL = torch.empty_like(img)
     grads = {}
@@ -737,7 +772,7 @@ def run_fit(args, large):
             "data": "synthetic",
             "config": {"workload": f"{name}: {scene.n} Gaussians, {V} view(s) of {H}x{W}, "
                                    "target = render of a perturbed cloud",
-                       "tile": st.tile, "batch_depth": args.depth or 256, "pairs_per_step": pairs,
+                       "tile": st.tile, "batch_depth": depth, "autotune": tuned, "pairs_per_step": pairs,
                        "generation_s": round(gen_s, 1)},
             "renders_per_s": world * V * 1e3 / ms,
             "e2e": {"value": world / t_e2e, "unit": "steps/s", "h2d_bytes_per_step": target_h.numel() * 4,

@@ -385,10 +385,11 @@ def test_registration_workload_sampled_pixels(ws):
     assert np.abs(gp[others]).max() == 0.0
 
 
-def _sampled_check(scene, views, st, ws, check_views, n_random, seed, grads=("pose",), bf16=None):
+def _sampled_check(scene, views, st, ws, check_views, n_random, seed, grads=("pose",), bf16=None,
+                   depth=None):
     """Full-size render and backward on the GPU; the oracle evaluates sampled
     pixels of a few views one by one; gradients of a loss on those pixels only."""
-    cloud, gv, cfg, img, tf, nl = _run(scene, views, st, ws, bf16=bf16)
+    cloud, gv, cfg, img, tf, nl = _run(scene, views, st, ws, bf16=bf16, depth=depth)
     bins = _bins(ws, scene, views, st)
     ref_proj = oracle.project32(scene, views, st)
     assert np.array_equal(bins["tiles_touched"].reshape(ref_proj["tiles_touched"].shape),
@@ -425,22 +426,29 @@ def _sampled_check(scene, views, st, ws, check_views, n_random, seed, grads=("po
 
 
 @pytest.mark.slow
-def test_fit_workload_sampled_pixels(ws):
+@pytest.mark.parametrize("tile,depth", [(16, 256), (8, 32)])
+def test_fit_workload_sampled_pixels(tile, depth, ws):
     """100k Gaussians from a 128^3 phantom, 512^2 at 0.5 mm: forward + backward
-    with respect to every Gaussian parameter, the bases and the pose."""
+    with respect to every Gaussian parameter, the bases and the pose, in the
+    block-staged launch shape and the warp-streamed one the fit benchmark
+    autotunes to."""
     scene, views, st = syn.fit_workload()
-    _sampled_check(scene, views, st, ws, [0], 2048, 5,
+    st = dataclasses.replace(st, tile=tile)
+    _sampled_check(scene, views, st, ws, [0], 2048, 5, depth=depth,
                    grads=("means", "log_scales", "quats", "opacity_logits", "feat_iso", "feat_dir",
                           "b_iso", "B_dir", "pose"))
 
 
 @pytest.mark.slow
-def test_large_fit_workload_sampled_pixels(ws):
+@pytest.mark.parametrize("tile,depth", [(16, 256), (8, 32)])
+def test_large_fit_workload_sampled_pixels(tile, depth, ws):
     """2M Gaussians from a 512^3 phantom with lesions, 8 orbit views at 1024^2,
-    bf16 direction features: sampled pixels of two views, all gradients."""
+    bf16 direction features: sampled pixels of two views, all gradients, in
+    both launch shapes."""
     scene, views, st = syn.large_fit_workload()
     assert scene.feat_dir_bf16
-    _sampled_check(scene, views, st, ws, [0, 5], 640, 6, bf16=True,
+    st = dataclasses.replace(st, tile=tile)
+    _sampled_check(scene, views, st, ws, [0, 5], 640, 6, bf16=True, depth=depth,
                    grads=("means", "log_scales", "quats", "opacity_logits", "feat_iso", "feat_dir",
                           "b_iso", "B_dir", "pose"))
 
