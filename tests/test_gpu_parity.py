@@ -282,15 +282,24 @@ def test_l1_loss_kernel(ws):
     assert np.array_equal(grad.cpu().numpy(), (np.sign(d) / (17 * 23)).astype(np.float32))
 
 
-def test_capacity_overflow_is_reported_not_faulted(ws):
-    scene = syn.uniform_cloud(20000, seed=5)
+@pytest.mark.parametrize("direct", [False, True])
+def test_capacity_overflow_is_reported_not_faulted(direct, ws):
+    """A no-sync render with too small a pair capacity drops whole lists and
+    reports it. direct: large footprints and a capacity of about 60 % of the
+    pairs, so that the scatter takes its unstaged instance (its blocks average
+    more pairs than two staging windows) and still overflows."""
+    scene = syn.uniform_cloud(20000, seed=5, **({"log_scale_range": (-1.5, -0.5)} if direct else {}))
     views = _two_views(75, 100)
     st = syn.Settings(near_plane=0.2)
     m_needed = oracle.bin32(scene, views, st)["m"]
     w2 = B.Workspace()
     recs = views.n_views * scene.n
-    w2.reserve(recs, 64, views.n_views * 42)  # far fewer pairs than needed
-    assert m_needed > 64 + 64 // 4 + 4096
+    cap = m_needed // 2 if direct else 64
+    w2.reserve(recs, cap, views.n_views * 42)  # fewer pairs than needed
+    granted = cap + cap // 4 + 4096  # what the workspace reserves for cap
+    assert m_needed > granted
+    if direct:  # 10 chunks per view, 2 views: the unstaged scatter from 204,800 pairs
+        assert granted > 2 * 5120 * 20
     cloud = B.cloud_from_arrays(scene)
     gv = B.views_from_arrays(views)
     cfg = B.config_from_settings(st, no_sync=True)
