@@ -1327,7 +1327,7 @@ def main():
                     help="Eq. 3 radiosity: the paper's disentangled sets, the direct-entangled "
                          "ablation (Table 3), or harmonics at each pixel's ray")
     ap.add_argument("--iters", type=int, default=300)
-    ap.add_argument("--stages", default="100x4@1.0,100x2@0.6,100x1@0.3",
+    ap.add_argument("--stages", default="100x4@1.5,100x2@0.8,100x1@0.3",
                     help="registration-loop stages, coarse to fine: iterations x detector "
                          "downscale @ dilation px^2 ('single': --iters at full size)")
     ap.add_argument("--requests", type=int, default=256)
