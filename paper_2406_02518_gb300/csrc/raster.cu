@@ -689,10 +689,12 @@ __device__ __forceinline__ void fwd_lane_item(const RasterArgs &a, int64_t gt, i
   }
 }
 
-// Resident blocks per SM asked of the register allocator: 5 for the forward
-// (6 makes the pipelined walk spill: 1.55 -> 1.83 ms at 64 poses).
+// Resident blocks per SM asked of the register allocator: eight for the
+// forward (32 registers, a few bytes spilled; 64 warps per SM: 1.48 -> 1.42 ms
+// at 64 poses, where six blocks at 40 registers measured 1.69 and five at 48
+// 1.48); five with per-pixel directions, whose walk would spill far more.
 template <int T, bool PIX>
-__global__ void __launch_bounds__(WARPS * 32, 5) raster_fwd_warp_kernel(RasterArgs a) {
+__global__ void __launch_bounds__(WARPS * 32, PIX ? 5 : 8) raster_fwd_warp_kernel(RasterArgs a) {
   constexpr int NW = T * T / 32;
   __shared__ float4 s_a[WARPS][32], s_b[WARPS][32], s_c[WARPS][PIX ? 32 : 1];
   const int w = threadIdx.x >> 5;
