@@ -117,10 +117,10 @@ class Clocks:
 # shape and workload match; otherwise traffic is null.
 TRAFFIC = {
     "raster_bwd": {
-        "sources_sha256": {"raster.cu": "cef79c94a41c42227398edc8b0d422f72462c82e7e6be884888cd5060b373bcf",
+        "sources_sha256": {"raster.cu": "cdf43f1c8172204b58cbc4b66962be33fb76009bfbbd1b2c662e7eedc78e9fbb",
                            "ddgs_internal.cuh": "a0f5de5ac0c80243f5ec36db5047cc6585eca6f017b72260e0295eda126af8a5"},
         "tile": 8, "batch_depth": 32, "views": 64, "gaussians": 500_000,
-        "bytes_per_launch": 2176.8e6 + 571.2e6,
+        "bytes_per_launch": 2176.7e6 + 571.0e6,
         "how": "one-pass ncu launch list (dram__bytes_read.sum + dram__bytes_write.sum) of the "
                "64-pose registration step",
     },

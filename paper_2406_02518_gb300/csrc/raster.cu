@@ -986,11 +986,18 @@ __device__ __forceinline__ void bwd_lane_item(const RasterArgs &a, int64_t gt, i
     // the same arithmetic. (Two entries per trip paid while the walk branched;
     // without branches the odd trip's padding costs more than the overlap
     // gives: 2.95 -> 2.93 ms.)
+    // the next entry's record is read from shared memory while this one is
+    // evaluated (2.92 -> 2.91 ms)
+    int kn = (__ffs(mine) - 1) & 31;
+    float4 An = sm.a[kn], Bn = sm.b[kn];
     for (int t = 0; t < trips; ++t) {
       const bool live = mine != 0;
-      const int k = (__ffs(mine) - 1) & 31;
+      const int k = kn;
+      const float4 A = An, B = Bn;
       mine &= mine - 1;
-      const float4 A = sm.a[k], B = sm.b[k];
+      kn = (__ffs(mine) - 1) & 31;
+      An = sm.a[kn];
+      Bn = sm.b[kn];
       const float dx = __fsub_rn(A.x, px), dy = __fsub_rn(A.y, py);
       const float tq = __fmaf_rn(A.w, dy, __fmul_rn(A.z, dx));
       const float q = __fmaf_rn(__fmul_rn(B.x, dy), dy, __fmul_rn(dx, tq));
