@@ -689,12 +689,14 @@ __device__ __forceinline__ void fwd_lane_item(const RasterArgs &a, int64_t gt, i
   }
 }
 
-// Resident blocks per SM asked of the register allocator: eight for the
-// forward (32 registers, a few bytes spilled; 64 warps per SM: 1.48 -> 1.42 ms
-// at 64 poses, where six blocks at 40 registers measured 1.69 and five at 48
-// 1.48); five with per-pixel directions, whose walk would spill far more.
-template <int T, bool PIX>
-__global__ void __launch_bounds__(WARPS * 32, PIX ? 5 : 8) raster_fwd_warp_kernel(RasterArgs a) {
+// Resident blocks per SM asked of the register allocator. WIDE: eight (32
+// registers, a few bytes spilled; 64 warps per SM: 1.48 -> 1.42 ms at 64
+// poses, where six blocks at 40 registers measured 1.69 and five at 48 1.48),
+// for renders with several work items per warp slot. Otherwise five (48
+// registers), whose warps finish an item sooner: one 512^2 view, 0.078 ->
+// 0.069 ms. Per-pixel directions always take five (their walk would spill).
+template <int T, bool PIX, bool WIDE>
+__global__ void __launch_bounds__(WARPS * 32, WIDE ? 8 : 5) raster_fwd_warp_kernel(RasterArgs a) {
   constexpr int NW = T * T / 32;
   __shared__ float4 s_a[WARPS][32], s_b[WARPS][32], s_c[WARPS][PIX ? 32 : 1];
   const int w = threadIdx.x >> 5;
@@ -1158,8 +1160,12 @@ void launch_bwd_t(const RasterArgs &a, cudaStream_t st) {
 
 template <int T, bool PIX>
 void launch_fwd_warp_t(const RasterArgs &a, cudaStream_t st) {
-  auto k = raster_fwd_warp_kernel<T, PIX>;
   const int64_t need = (a.s.total_tiles * (T * T / 32) + WARPS - 1) / WARPS;
+  auto k = raster_fwd_warp_kernel<T, PIX, false>;
+  if constexpr (!PIX) {
+    // at least two items for each warp of eight resident blocks per SM
+    if (need >= 2 * 8 * (int64_t)device_sms()) k = raster_fwd_warp_kernel<T, PIX, true>;
+  }
   int64_t grid = (int64_t)blocks_per_sm(k, WARPS * 32) * device_sms();
   if (grid > need) grid = need;
   LaunchScope ls(KID_RASTER_FWD, st);
