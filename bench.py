@@ -117,7 +117,7 @@ class Clocks:
 # shape and workload match; otherwise traffic is null.
 TRAFFIC = {
     "raster_bwd": {
-        "sources_sha256": {"raster.cu": "cdf43f1c8172204b58cbc4b66962be33fb76009bfbbd1b2c662e7eedc78e9fbb",
+        "sources_sha256": {"raster.cu": "2dc40b2ef6f647756e4c2ab97b85545c860aeb474dfc28ecb51c54c7ae448bc0",
                            "ddgs_internal.cuh": "a0f5de5ac0c80243f5ec36db5047cc6585eca6f017b72260e0295eda126af8a5"},
         "tile": 8, "batch_depth": 32, "views": 64, "gaussians": 500_000,
         "bytes_per_launch": 2176.7e6 + 571.0e6,

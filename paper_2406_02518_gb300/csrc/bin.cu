@@ -619,10 +619,16 @@ __global__ void __launch_bounds__(NT, MINB) bin_sort_block_kernel(const uint64_t
                                                                     uint64_t *keys, uint32_t *vals) {
   constexpr int NW = NT / 32, CAP = NT * E;
   extern __shared__ __align__(16) uint64_t s_buf[];  // [2][CAP]
-  __shared__ uint32_t cnt[NW][256];  // digit counters, or NW x 256 bucket counters
+  // digit counters, or up to NW x 256 bucket counters stored with one pad word
+  // after every eight (bkp), so that the bucket scan's per-thread runs of
+  // eight counters fall in distinct banks (0.70 -> 0.64 ms for the sorts at 64
+  // poses; unpadded, the runs of a warp's lanes met 8-way bank conflicts)
+  __shared__ __align__(16) uint32_t s_bk[NW * 256 + NW * 32];
+  uint32_t(*cnt)[256] = reinterpret_cast<uint32_t(*)[256]>(s_bk);
+  auto bkp = [](uint32_t b) { return b + (b >> 3); };
   __shared__ uint32_t s_wsum[NW > 8 ? NW : 8];
   __shared__ uint32_t s_red[4][NW];
-  uint32_t *bc = &cnt[0][0];
+  uint32_t *bc = s_bk;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const uint32_t n_items = *count;
   // the next item's keys are copied to s_buf asynchronously while the
@@ -692,13 +698,13 @@ __global__ void __launch_bounds__(NT, MINB) bin_sort_block_kernel(const uint64_t
       lg = max(5, min(lg, 31 - __clz((uint32_t)(NW * 256))));
       const int nbk = 1 << lg;
       const int sh = max(0, (32 - __clz(dmax - dmin)) - lg);
-      for (int b = tid; b < nbk; b += NT) bc[b] = 0;
+      for (int b = tid; b < nbk; b += NT) bc[bkp(b)] = 0;
       __syncthreads();
       uint32_t rk[E];
 #pragma unroll
       for (int r = 0; r < E; ++r) {
         const int j = tid + r * NT;
-        if (j < m) rk[r] = atomicAdd(&bc[((uint32_t)(cur[j] >> 32) - dmin) >> sh], 1u);
+        if (j < m) rk[r] = atomicAdd(&bc[bkp(((uint32_t)(cur[j] >> 32) - dmin) >> sh)], 1u);
       }
       __syncthreads();
       // exclusive scan of the bucket counts (contiguous runs per thread) and
@@ -708,7 +714,7 @@ __global__ void __launch_bounds__(NT, MINB) bin_sort_block_kernel(const uint64_t
       for (int k = 0; k < q; ++k) {
         const int b = tid * q + k;
         if (b < nbk) {
-          const uint32_t c = bc[b];
+          const uint32_t c = bc[bkp(b)];
           loc += c;
           big = max(big, c);
         }
@@ -732,8 +738,8 @@ __global__ void __launch_bounds__(NT, MINB) bin_sort_block_kernel(const uint64_t
       for (int k = 0; k < q; ++k) {
         const int b = tid * q + k;
         if (b < nbk) {
-          const uint32_t c = bc[b];
-          bc[b] = ex;
+          const uint32_t c = bc[bkp(b)];
+          bc[bkp(b)] = ex;
           ex += c;
         }
       }
@@ -744,7 +750,7 @@ __global__ void __launch_bounds__(NT, MINB) bin_sort_block_kernel(const uint64_t
           const int j = tid + r * NT;
           if (j < m) {
             const uint64_t k = cur[j];
-            oth[bc[((uint32_t)(k >> 32) - dmin) >> sh] + rk[r]] = k;
+            oth[bc[bkp(((uint32_t)(k >> 32) - dmin) >> sh)] + rk[r]] = k;
           }
         }
         __syncthreads();
@@ -755,7 +761,7 @@ __global__ void __launch_bounds__(NT, MINB) bin_sort_block_kernel(const uint64_t
         for (int j = tid; j < m; j += NT) {
           const uint64_t k = oth[j];
           const uint32_t b = ((uint32_t)(k >> 32) - dmin) >> sh;
-          const uint32_t b0 = bc[b], b1 = b + 1 < (uint32_t)nbk ? bc[b + 1] : (uint32_t)m;
+          const uint32_t b0 = bc[bkp(b)], b1 = b + 1 < (uint32_t)nbk ? bc[bkp(b + 1)] : (uint32_t)m;
           uint32_t pos = b0;
           for (uint32_t x = b0; x < b1; ++x) pos += oth[x] < k;
           if (whole) vals[base + pos] = (uint32_t)k;
