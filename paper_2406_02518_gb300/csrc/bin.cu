@@ -195,8 +195,18 @@ __global__ void __launch_bounds__(COL_WARPS * 32) bin_column_kernel(RenderShape 
   const int c0 = min(chunks, w * seg), c1 = min(chunks, c0 + seg);
   uint32_t *h = hist + first;
   uint32_t sum = 0;
-  if (has)
-    for (int c = c0; c < c1; ++c) sum += h[c * stride];
+  if (has) {  // eight loads in flight per lane (the kernel waits on DRAM latency:
+              // 0.081 -> 0.060 ms for the three offset launches at 64 poses)
+    int c = c0;
+    for (; c + 8 <= c1; c += 8) {
+      uint32_t v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = h[(int64_t)(c + j) * stride];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) sum += v[j];
+    }
+    for (; c < c1; ++c) sum += h[(int64_t)c * stride];
+  }
   s_sum[w][lane] = sum;
   __syncthreads();
   uint32_t run = 0, total = 0;
@@ -206,12 +216,24 @@ __global__ void __launch_bounds__(COL_WARPS * 32) bin_column_kernel(RenderShape 
     if (x < w) run += v;
     total += v;
   }
-  if (has)
-    for (int c = c0; c < c1; ++c) {
-      const uint32_t x = h[c * stride];
-      h[c * stride] = run;
+  if (has) {
+    int c = c0;
+    for (; c + 8 <= c1; c += 8) {
+      uint32_t v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = h[(int64_t)(c + j) * stride];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        h[(int64_t)(c + j) * stride] = run;
+        run += v[j];
+      }
+    }
+    for (; c < c1; ++c) {
+      const uint32_t x = h[(int64_t)c * stride];
+      h[(int64_t)c * stride] = run;
       run += x;
     }
+  }
   if (w == 0) {
     if (gt < s.total_tiles) ranges[gt] = make_uint2(0u, total);
     uint64_t t = total;  // the block's 32 tiles lie in one 1024-tile group
