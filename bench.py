@@ -117,10 +117,10 @@ class Clocks:
 # shape and workload match; otherwise traffic is null.
 TRAFFIC = {
     "raster_bwd": {
-        "sources_sha256": {"raster.cu": "0a512431a4ab852934c4b0a3fee98a0e3b0f296b73c69455427d10291659a591",
+        "sources_sha256": {"raster.cu": "eb7b3b4ab2593018599b8e8d0e6a7259807d3ca18c568b6b55f05caf4ef97020",
                            "ddgs_internal.cuh": "a0f5de5ac0c80243f5ec36db5047cc6585eca6f017b72260e0295eda126af8a5"},
         "tile": 8, "batch_depth": 32, "views": 64, "gaussians": 500_000,
-        "bytes_per_launch": 2195.0e6 + 573.8e6,
+        "bytes_per_launch": 2198.0e6 + 574.5e6,
         "how": "one-pass ncu launch list (dram__bytes_read.sum + dram__bytes_write.sum) of the "
                "64-pose registration step",
     },
