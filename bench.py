@@ -117,10 +117,10 @@ class Clocks:
 # shape and workload match; otherwise traffic is null.
 TRAFFIC = {
     "raster_bwd": {
-        "sources_sha256": {"raster.cu": "eb7b3b4ab2593018599b8e8d0e6a7259807d3ca18c568b6b55f05caf4ef97020",
+        "sources_sha256": {"raster.cu": "157cedcbf58b9646916a142b74a710b9346906413136ca4bbe50f67cdaf3ba18",
                            "ddgs_internal.cuh": "a0f5de5ac0c80243f5ec36db5047cc6585eca6f017b72260e0295eda126af8a5"},
         "tile": 8, "batch_depth": 32, "views": 64, "gaussians": 500_000,
-        "bytes_per_launch": 2198.0e6 + 574.5e6,
+        "bytes_per_launch": 2186.7e6 + 573.1e6,
         "how": "one-pass ncu launch list (dram__bytes_read.sum + dram__bytes_write.sum) of the "
                "64-pose registration step",
     },
