@@ -971,9 +971,11 @@ void launch_binning(const RenderShape &s, uint64_t pair_bound, ddgs_workspace &w
   }
   if (nmax > SORT_SHORT) {
     LaunchScope ls(KID_BIN_SORT, st);
-    // five blocks per SM (96 registers, a few bytes spilled): 0.72 -> 0.69 ms
-    // for the sorts at 64 poses, against six at 80 registers or four at 128
-    bin_sort_block_kernel<128, SORT_MID / 128, 5><<<sms * 5, 128, MID_SMEM, st>>>(
+    // six blocks per SM (80 registers, a few bytes spilled): with the padded
+    // bucket counters 0.636 -> 0.629 ms for the sorts at 64 poses against five
+    // at 96 registers (which led before the padding, 0.69 against 0.72; four
+    // at 128 registers measured 0.75)
+    bin_sort_block_kernel<128, SORT_MID / 128, 6><<<sms * 6, 128, MID_SMEM, st>>>(
         L.item[LIST_MID], L.count + LIST_MID, ws.ranges, ws.keys[0], ws.vals);
   }
   if (nmax > SORT_MID) {
